@@ -1,0 +1,476 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: the closed forms
+printed in Sec. 2.1 (eqs. D..Dijkl, quad_mom, octo_mom, hexa_mom), finite
+differences, harmonicity, exact polynomial identities, the O(N^2) direct sum
+(eq. jia), the conservation statements of Sec. 2 (eq. netforce) and Sec. 3, and
+closed-form Plummer/Hernquist energies."""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2107_07166_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def alpha_of(idx):
+    a = [0, 0, 0]
+    for i in idx:
+        a[i] += 1
+    return tuple(a)
+
+
+def index_map(orc, p):
+    mi = orc.multi_indices(p)
+    return {tuple(int(v) for v in a): k for k, a in enumerate(mi)}
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# ---------------------------------------------------------------- tensors
+
+def test_dtensor_golden_R122(orc):
+    """D..D_ijkl at R=(1,2,2) equal the paper's closed forms (exact rationals)."""
+    im = index_map(orc, 4)
+    D = orc.dtensor(4, [1.0, 2.0, 2.0])
+    n = 0
+    with open(os.path.join(GOLD, "dtensor_R122.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            idx, num, den = line.split()
+            a = (0, 0, 0) if idx == "-" else alpha_of(int(c) for c in idx.split(","))
+            want = float(Fraction(int(num), int(den)))
+            assert D[im[a]] == pytest.approx(want, rel=1e-14, abs=1e-16), (idx, D[im[a]], want)
+            n += 1
+    assert n == 1 + 3 + 9 + 27 + 81
+
+
+def _paper_D(R, idx):
+    """Closed forms of Sec. 2.1 for orders <= 4 in floating point."""
+    R = np.asarray(R, float)
+    R2 = R @ R
+    r = math.sqrt(R2)
+    dl = lambda i, j: 1.0 if i == j else 0.0
+    n = len(idx)
+    if n == 0:
+        return -1 / r
+    if n == 1:
+        return R[idx[0]] / r ** 3
+    if n == 2:
+        i, j = idx
+        return (-3 * R[i] * R[j] + dl(i, j) * R2) / r ** 5
+    if n == 3:
+        i, j, k = idx
+        return (15 * R[i] * R[j] * R[k] - 3 * R2 * (dl(i, j) * R[k] + dl(j, k) * R[i] + dl(i, k) * R[j])) / r ** 7
+    i, j, k, l = idx
+    t = -105 * R[i] * R[j] * R[k] * R[l]
+    t += 15 * R2 * (dl(i, j) * R[k] * R[l] + dl(i, l) * R[j] * R[k] + dl(i, k) * R[j] * R[l]
+                    + dl(j, l) * R[i] * R[k] + dl(j, k) * R[i] * R[l] + dl(l, k) * R[i] * R[j])
+    t -= 3 * R2 * R2 * (dl(i, j) * dl(k, l) + dl(i, k) * dl(j, l) + dl(i, l) * dl(j, k))
+    return t / r ** 9
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_dtensor_closed_forms_random(orc, seed):
+    rng = np.random.default_rng(seed)
+    R = rng.normal(size=3) * (0.3 + 3 * rng.random())
+    im = index_map(orc, 4)
+    D = orc.dtensor(4, R)
+    for n in range(5):
+        for idx in itertools.product(range(3), repeat=n):
+            want = _paper_D(R, idx)
+            got = D[im[alpha_of(idx)]]
+            scale = np.linalg.norm(R) ** -(n + 1)
+            assert abs(got - want) <= 1e-13 * scale, (idx, got, want)
+
+
+@pytest.mark.parametrize("which", ["d", "h"])
+def test_tensor_finite_differences(orc, which):
+    """Order n+1 components equal central differences of order n components (n <= 7)."""
+    rng = np.random.default_rng(11)
+    R = np.array([0.7, -1.1, 0.4])
+    f = orc.dtensor if which == "d" else orc.htensor
+    im = index_map(orc, 8)
+    T = f(8, R)
+    h = 1e-5
+    for a, k in im.items():
+        if sum(a) >= 8:
+            continue
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = h
+            fd = (f(8, R + e)[k] - f(8, R - e)[k]) / (2 * h)
+            b = list(a)
+            b[i] += 1
+            exact = T[im[tuple(b)]]
+            assert abs(fd - exact) <= 1e-6 * max(1.0, abs(exact)), (a, i, fd, exact)
+
+
+def test_dtensor_traceless(orc):
+    """1/r is harmonic: sum_i D_{alpha + 2 e_i} = 0 for every alpha."""
+    R = np.array([0.3, 1.7, -0.9])
+    im = index_map(orc, 8)
+    D = orc.dtensor(8, R)
+    for a, k in im.items():
+        if sum(a) > 6:
+            continue
+        s = 0.0
+        mag = 0.0
+        for i in range(3):
+            b = list(a)
+            b[i] += 2
+            s += D[im[tuple(b)]]
+            mag += abs(D[im[tuple(b)]])
+        assert abs(s) <= 1e-13 * mag
+
+
+def test_htensor_low_orders(orc):
+    """h = -r^-3: h_i = 3 R_i r^-5, h_ij = 3 d_ij r^-5 - 15 R_i R_j r^-7."""
+    R = np.array([1.3, -0.2, 0.8])
+    r = np.linalg.norm(R)
+    im = index_map(orc, 2)
+    H = orc.htensor(2, R)
+    assert H[im[(0, 0, 0)]] == pytest.approx(-r ** -3, rel=1e-15)
+    for i in range(3):
+        a = [0, 0, 0]
+        a[i] = 1
+        assert H[im[tuple(a)]] == pytest.approx(3 * R[i] * r ** -5, rel=1e-14)
+        for j in range(3):
+            b = list(a)
+            b[j] += 1
+            want = 3 * (i == j) * r ** -5 - 15 * R[i] * R[j] * r ** -7
+            assert H[im[tuple(b)]] == pytest.approx(want, rel=1e-13, abs=1e-15)
+
+
+# ---------------------------------------------------------------- moments and shifts
+
+def test_moments_match_paper_QHX(orc):
+    """Raw moments reproduce the paper's traceless Q, H, X (eqs. quad_mom, octo_mom, hexa_mom)."""
+    rng = np.random.default_rng(3)
+    Y = rng.normal(size=(17, 3))
+    m = rng.random(17)
+    Z = (m[:, None] * Y).sum(0) / m.sum()
+    im = index_map(orc, 4)
+    Mr = orc.p2m(4, Z, Y, m)
+
+    def raw(idx):     # sum_b m_b y^i y^j ... from M_alpha = sum m (-y)^alpha / alpha!
+        a = alpha_of(idx)
+        fac = math.factorial(a[0]) * math.factorial(a[1]) * math.factorial(a[2])
+        return Mr[im[a]] * fac * (-1) ** len(idx)
+
+    y = Y - Z
+    q2 = (y * y).sum(1)
+    dl = np.eye(3)
+    assert Mr[im[(0, 0, 0)]] == pytest.approx(m.sum(), rel=1e-15)
+    for i in range(3):            # dipole vanishes about the COM
+        a = [0, 0, 0]
+        a[i] = 1
+        assert abs(Mr[im[tuple(a)]]) < 1e-14
+    tr2 = sum(raw((l, l)) for l in range(3))
+    for i, j in itertools.product(range(3), repeat=2):
+        Q = (m * (3 * y[:, i] * y[:, j] - dl[i, j] * q2)).sum()
+        assert 3 * raw((i, j)) - dl[i, j] * tr2 == pytest.approx(Q, rel=1e-12, abs=1e-13)
+    for i, j, k in itertools.product(range(3), repeat=3):
+        H = (m * (15 * y[:, i] * y[:, j] * y[:, k]
+                  - 3 * q2 * (dl[i, j] * y[:, k] + dl[j, k] * y[:, i] + dl[i, k] * y[:, j]))).sum()
+        tr = lambda u: sum(raw((l, l, u)) for l in range(3))
+        got = 15 * raw((i, j, k)) - 3 * (dl[i, j] * tr(k) + dl[j, k] * tr(i) + dl[i, k] * tr(j))
+        assert got == pytest.approx(H, rel=1e-12, abs=1e-12)
+    for i, j, k, l in itertools.product(range(3), repeat=4):
+        X = (m * (105 * y[:, i] * y[:, j] * y[:, k] * y[:, l]
+                  - 15 * q2 * (dl[i, j] * y[:, k] * y[:, l] + dl[i, l] * y[:, j] * y[:, k]
+                               + dl[i, k] * y[:, j] * y[:, l] + dl[j, l] * y[:, i] * y[:, k]
+                               + dl[j, k] * y[:, i] * y[:, l] + dl[l, k] * y[:, i] * y[:, j])
+                  + 3 * q2 * q2 * (dl[i, j] * dl[k, l] + dl[i, k] * dl[j, l] + dl[i, l] * dl[j, k]))).sum()
+        t2 = lambda u, v: sum(raw((s, s, u, v)) for s in range(3))
+        t4 = sum(raw((s, s, u, u)) for s in range(3) for u in range(3))
+        got = (105 * raw((i, j, k, l))
+               - 15 * (dl[i, j] * t2(k, l) + dl[i, l] * t2(j, k) + dl[i, k] * t2(j, l)
+                       + dl[j, l] * t2(i, k) + dl[j, k] * t2(i, l) + dl[l, k] * t2(i, j))
+               + 3 * t4 * (dl[i, j] * dl[k, l] + dl[i, k] * dl[j, l] + dl[i, l] * dl[j, k]))
+        assert got == pytest.approx(X, rel=1e-11, abs=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6, 8])
+def test_m2m_equals_direct_p2m(orc, p):
+    """Shifting child moments to the parent centre equals P2M about the parent centre."""
+    rng = np.random.default_rng(p)
+    Y = rng.normal(size=(23, 3)) * 0.3
+    m = rng.random(23)
+    Zc = (m[:, None] * Y).sum(0) / m.sum()
+    Zp = Zc + rng.normal(size=3) * 0.4
+    shifted = orc.m2m(p, Zc, Zp, orc.p2m(p, Zc, Y, m))
+    direct = orc.p2m(p, Zp, Y, m)
+    assert np.allclose(shifted, direct, rtol=1e-12, atol=1e-13 * np.abs(direct).max())
+
+
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_l2l_is_polynomial_shift(orc, p):
+    """The shifted local polynomial evaluated at x equals the original at x + s."""
+    rng = np.random.default_rng(100 + p)
+    n = orc.nmi(p)
+    mi = orc.multi_indices(p)
+    Lp = rng.normal(size=n)
+    s = rng.normal(size=3) * 0.5
+    Lc = orc.l2l(p, s, Lp)
+    fact = np.array([math.factorial(a) * math.factorial(b) * math.factorial(c) for a, b, c in mi])
+    ev = lambda L, x: (L * np.prod(x[None, :] ** mi, axis=1) / fact).sum()
+    for _ in range(5):
+        x = rng.normal(size=3) * 0.3
+        assert ev(Lc, x) == pytest.approx(ev(Lp, x + s), rel=1e-12, abs=1e-12)
+    back = orc.l2l(p, -s, Lc)
+    assert np.allclose(back, Lp, rtol=1e-11, atol=1e-11)
+
+
+# ---------------------------------------------------------------- M2L / L2P algebra
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+def test_multipole_route_equals_pair_taylor(orc, p, variant):
+    """P2M -> M2L -> L2P equals the per-pair truncated Taylor sum of eq. taylor
+    (standard) or of the realigned pair force (conserving), to rounding."""
+    rng = np.random.default_rng(7 * p + variant)
+    XA = rng.normal(size=(9, 3)) * 0.25
+    YB = rng.normal(size=(13, 3)) * 0.3 + np.array([2.5, -1.0, 0.7])
+    mB = rng.random(13)
+    ZA = XA.mean(0) + 0.05
+    ZB = (mB[:, None] * YB).sum(0) / mB.sum()
+    a1, p1 = orc.cell_pair(p, variant, ZA, XA, ZB, YB, mB)
+    a2, p2 = orc.pair_taylor(p, variant, ZA, XA, ZB, YB, mB)
+    assert rel(a1, a2) < 1e-13
+    assert rel(p1, p2) < 1e-13
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_pair_taylor_converges_to_newton(orc, variant):
+    """The truncated pair series converges to the exact force as p grows (|d|/R < 1)."""
+    rng = np.random.default_rng(5)
+    XA = rng.normal(size=(6, 3)) * 0.2
+    YB = rng.normal(size=(6, 3)) * 0.2 + np.array([2.0, 0.0, 0.0])
+    mB = rng.random(6)
+    ZA, ZB = XA.mean(0), YB.mean(0)
+    x = np.concatenate([XA, YB])
+    mm = np.concatenate([np.zeros(6), mB])
+    exact, _ = orc.direct(x, mm)
+    errs = []
+    for p in range(1, 9):
+        a, _ = orc.pair_taylor(p, variant, ZA, XA, ZB, YB, mB)
+        errs.append(rel(a, exact[:6]))
+    # odd and even orders can tie (offsets nearly normal to R cancel odd terms), so
+    # require a decrease over every two orders
+    assert all(errs[i + 2] < errs[i] for i in range(len(errs) - 2)), errs
+    assert errs[-1] < 1e-3 * errs[0]
+
+
+def test_conserving_pair_force_is_central(orc):
+    """Each realigned pair force is parallel to X_a - Y_b (eq. realign): single-particle B."""
+    rng = np.random.default_rng(9)
+    XA = rng.normal(size=(5, 3)) * 0.2
+    YB = np.array([[2.1, 0.3, -0.4]])
+    for p in (1, 2, 4, 8):
+        a, _ = orc.pair_taylor(p, 1, XA.mean(0), XA, YB[0] + 0.05, YB, np.array([1.0]))
+        d = XA - YB
+        cr = np.cross(a, d)
+        assert np.abs(cr).max() <= 1e-15 * np.abs(a).max() * np.abs(d).max() * 10
+
+
+# ---------------------------------------------------------------- keys, sort, tree, walk
+
+def test_keys_quantise_positions(orc):
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(300, 3))
+    lo, side = orc.bbox(x)
+    assert np.allclose(lo, x.min(0), rtol=0, atol=0)
+    assert side == (x.max(0) - x.min(0)).max()
+    k = orc.keys(x, lo, side)
+    q = np.zeros((300, 3), dtype=np.int64)
+    for b in range(21):                 # de-interleave
+        for d in range(3):
+            q[:, d] |= ((k.astype(np.int64) >> (3 * b + 2 - d)) & 1) << b
+    cell = side / 2 ** 21
+    t = (x - lo) / cell
+    assert np.all(q >= 0) and np.all(q <= 2 ** 21 - 1)
+    assert np.all(np.abs(q - np.minimum(np.floor(t), 2 ** 21 - 1)) <= 1)
+    assert np.all(k < 2 ** 63)
+
+
+def test_sort_is_stable(orc):
+    rng = np.random.default_rng(2)
+    k = rng.integers(0, 50, 500).astype(np.uint64)
+    sk, perm = orc.sort(k)
+    ref = np.argsort(k, kind="stable")
+    assert np.array_equal(perm, ref)
+    assert np.array_equal(sk, k[ref])
+
+
+def check_tree(r, N, leaf):
+    t = r.tree
+    nn = r.n_nodes
+    assert t["parent"][0] == -1 and t["first"][0] == 0 and t["count"][0] == N
+    assert np.all(np.diff(t["level"]) >= 0)                        # breadth-first
+    for n in range(nn):
+        nc, c0 = t["nchild"][n], t["child_first"][n]
+        if nc == 0:
+            assert c0 == -1
+            assert t["count"][n] <= leaf or t["level"][n] == 21
+        else:
+            assert t["count"][n] > leaf
+            ch = np.arange(c0, c0 + nc)
+            assert np.all(t["parent"][ch] == n)
+            assert t["first"][ch[0]] == t["first"][n]
+            assert np.all(t["first"][ch[1:]] == t["first"][ch[:-1]] + t["count"][ch[:-1]])
+            assert t["count"][ch].sum() == t["count"][n]
+            assert np.all(t["level"][ch] == t["level"][n] + 1)
+    leaves = t["nchild"] == 0
+    assert t["count"][leaves].sum() == N
+    assert np.all(np.diff(r.keys.astype(np.float64)) >= 0)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_walk_covers_every_pair_once(orc, variant):
+    x, m = synth.plummer(3000, 4)
+    r = orc.run(x, m, 8, 3, 0.5, variant)
+    check_tree(r, 3000, 8)
+    c = r.tree["count"]
+    m2l, p2p = r.m2l, r.p2p
+    assert np.all(m2l[:, 0] < m2l[:, 1])
+    assert np.all(p2p[:, 0] <= p2p[:, 1])
+    for L in (m2l, p2p):
+        key = L[:, 0].astype(np.int64) * 2 ** 32 + L[:, 1]
+        assert np.all(np.diff(key) > 0)                               # canonical, unique
+    leaf = r.tree["nchild"] == 0
+    assert np.all(leaf[p2p[:, 0]]) and np.all(leaf[p2p[:, 1]])
+    selfp = p2p[:, 0] == p2p[:, 1]
+    total = (c[m2l[:, 0]].astype(np.int64) * c[m2l[:, 1]]).sum()
+    total += np.where(selfp, c[p2p[:, 0]].astype(np.int64) * (c[p2p[:, 0]] - 1) // 2,
+                      c[p2p[:, 0]].astype(np.int64) * c[p2p[:, 1]]).sum()
+    assert total == 3000 * 2999 // 2
+    # every particle pair is covered exactly once: mark (particle, particle) coverage
+    leaf_of = np.empty(3000, dtype=np.int64)
+    anc = {}
+    for n in range(r.n_nodes):
+        anc[n] = (r.tree["first"][n], r.tree["first"][n] + c[n])
+    cover = np.zeros((3000, 3000), dtype=np.int8)
+    for A, B in np.concatenate([m2l, p2p]):
+        a0, a1 = anc[A]
+        b0, b1 = anc[B]
+        cover[a0:a1, b0:b1] += 1
+        if A != B:
+            cover[b0:b1, a0:a1] += 1
+    np.fill_diagonal(cover, 1)
+    assert np.all(cover == 1)
+    # MAC holds for every accepted pair (eq. mac_criterion)
+    Z, rm = r.Z, r.rmax
+    d = Z[m2l[:, 0]] - Z[m2l[:, 1]]
+    R = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
+    assert np.all(rm[m2l[:, 0]] + rm[m2l[:, 1]] <= 0.5 * R)
+
+
+def test_geometry_matches_definition(orc):
+    x, m = synth.hernquist(2000, 6)
+    r = orc.run(x, m, 12, 2, 0.5, 0)
+    xs, ms = x[r.perm], m[r.perm]
+    for n in range(r.n_nodes):
+        f, c = r.tree["first"][n], r.tree["count"][n]
+        M = ms[f:f + c].sum()
+        Z = (ms[f:f + c, None] * xs[f:f + c]).sum(0) / M
+        assert r.M[n] == pytest.approx(M, rel=1e-13)
+        assert np.allclose(r.Z[n], Z, rtol=1e-12, atol=1e-14)
+        rmax = np.sqrt(((xs[f:f + c] - r.Z[n]) ** 2).sum(1).max())
+        assert r.rmax[n] == pytest.approx(rmax, rel=1e-13, abs=1e-15)
+
+
+# ---------------------------------------------------------------- whole method
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_theta_zero_is_direct_sum(orc, variant):
+    """At theta = 0 only zero-size cells pass the MAC, where the expansion is exact."""
+    x, m = synth.plummer(1500, 8)
+    r = orc.run(x, m, 6, 3, 0.0, variant)
+    a, ph = orc.direct(x, m)
+    assert rel(r.acc, a) < 1e-13
+    assert rel(r.pot, ph) < 1e-13
+
+
+def test_direct_two_body(orc):
+    x = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [2.0, 0.0, 0.0]])
+    m = np.array([3.0, 1.0, 0.5])
+    a, ph = orc.direct(x, m)
+    assert np.allclose(a[0], [1.5 / 4, 0, 0])
+    assert np.allclose(a[1], [-3.0 / 4, 0, 0])      # coincident partner ignored
+    assert ph[0] == pytest.approx(-1.5 / 2)
+
+
+def _net(x, m, a):
+    F = (m[:, None] * a).sum(0)
+    T = (m[:, None] * np.cross(x, a)).sum(0)
+    fs = (m * np.linalg.norm(a, axis=1)).sum()
+    ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+    return np.linalg.norm(F) / fs, np.linalg.norm(T) / ts
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
+def test_conservation(orc, p):
+    """Net force vanishes for both forms (eq. netforce); net torque vanishes for the
+    realigned form at every p and for the standard form at p = 1 (Sec. 3.1), and is
+    far from zero for the standard form at p >= 2 (eq. total_torque)."""
+    x, m = synth.plummer(4096, 1)
+    for variant in (0, 1):
+        r = orc.run(x, m, 16, p, 0.5, variant, want_pot=False, want_internals=False)
+        f, t = _net(x, m, r.acc)
+        assert f < 1e-14
+        if variant == 1 or p == 1:
+            assert t < 1e-14, (variant, p, t)
+        else:
+            assert t > 1e-8, (variant, p, t)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_convergence_in_p_and_theta(orc, variant):
+    x, m = synth.plummer(4096, 1)
+    a, _ = orc.direct(x, m, want_pot=False)
+    e = {}
+    for p in (1, 2, 4, 6):
+        for th in (0.3, 0.5, 0.7):
+            r = orc.run(x, m, 16, p, th, variant, want_pot=False, want_internals=False)
+            e[p, th] = rel(r.acc, a)
+    for th in (0.3, 0.5, 0.7):
+        assert e[1, th] > e[2, th] > e[4, th] > e[6, th]
+    for p in (1, 2, 4, 6):
+        assert e[p, 0.3] < e[p, 0.5] < e[p, 0.7]
+    assert e[6, 0.3] < 1e-4
+
+
+def test_plummer_energy(orc):
+    """Potential energy W = 1/2 sum m phi of a unit Plummer sphere is -3 pi / 32."""
+    x, m = synth.plummer(16384, 21)
+    r = orc.run(x, m, 16, 4, 0.5, 0, want_pot=True, want_internals=False)
+    W = 0.5 * (m * r.pot).sum()
+    assert W == pytest.approx(-3 * math.pi / 32, rel=0.03)
+
+
+def test_hernquist_energy(orc):
+    """W = -1/(6a) for a unit-mass Hernquist sphere (a = 1); the u <= 0.999 cut lowers |W| slightly."""
+    x, m = synth.hernquist(16384, 22)
+    r = orc.run(x, m, 16, 4, 0.5, 0, want_pot=True, want_internals=False)
+    W = 0.5 * (m * r.pot).sum()
+    assert W == pytest.approx(-1.0 / 6.0, rel=0.05)
+
+
+def test_plummer_potential_profile(orc):
+    """The FMM potential follows Phi(r) = -1/sqrt(r^2 + 1) (shell averages)."""
+    x, m = synth.plummer(16384, 23)
+    r = orc.run(x, m, 16, 4, 0.5, 0, want_pot=True, want_internals=False)
+    rad = np.linalg.norm(x, axis=1)
+    for lo, hi in ((0.2, 0.4), (0.5, 0.8), (1.0, 1.5), (2.0, 3.0)):
+        s = (rad > lo) & (rad < hi)
+        want = (-1 / np.sqrt(rad[s] ** 2 + 1)).mean()
+        assert r.pot[s].mean() == pytest.approx(want, rel=0.02)
