@@ -1,0 +1,331 @@
+"""Benchmark: one force evaluation of the angular-momentum-conserving FMM (tree build +
+forces) on a Plummer sphere of N = 2^20 particles, p = 4, theta = 0.6, leaf size 32,
+binary64 -- particles per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbfmm|reference]
+
+One step = fmm_build + fmm_forces on device-resident inputs.  Each timed step is
+bracketed by CUDA events on the library's stream; between steps a 512 MiB buffer is
+rewritten to flush the 129 MB L2.  Under torchrun every rank runs the same workload on
+its own GPU (independent replicas, weak scaling, no collective on the data path); rank 0
+prints one JSON line with the whole-job throughput.  `--impl reference` times the CPU
+oracle (the FP64 C reference this library is checked against) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="plummer-1m-conserving", N=1 << 20, seed=2, p=4, theta=0.6, leaf=32,
+                variant="conserving", precision="fp64")
+METRIC = "particles/s, AM-conserving FMM force eval, N=1M p=4 θ=0.6; force err; |Σx×F|"
+CPU_SAMPLE_N = 1 << 17          # oracle sample: same generator, p, theta, leaf; ~10-20 s of CPU
+STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def algorithmic_flops(counts, tree_counts, p, variant):
+    """Algorithmic FLOPs of the dominant stages (FMA = 2):
+    P2P: 26 per unordered particle pair (difference 3, r^2 5, rsqrt 1, r^-3 2, the two
+    mass factors 2, two accumulations 12, one comparison counted 1).
+    M2L per mutual cell pair: contraction terms of both partners x 2 flops plus one
+    derivative-tensor evaluation of ~6 C(p+3,3) flops."""
+    c = tree_counts
+    m2l, p2p = counts
+    selfp = p2p[:, 0] == p2p[:, 1]
+    n_pp = int(np.where(selfp, c[p2p[:, 0]] * (c[p2p[:, 0]] - 1) // 2, c[p2p[:, 0]] * c[p2p[:, 1]]).sum())
+    comb = math.comb
+    if variant == 1:
+        per_m2l = 2 * 2 * 4 * comb(p - 1 + 6, 6) + 6 * comb(p + 2, 3)
+    else:
+        per_m2l = 2 * 2 * comb(p + 6, 6) + 6 * comb(p + 3, 3)
+    return {"p2p": 26.0 * n_pp, "m2l": float(per_m2l) * len(m2l), "n_pp": n_pp, "n_m2l": len(m2l),
+            "per_m2l_pair": per_m2l}
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    """binary64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_gbfmm(args):
+    import torch
+    from paper_2107_07166_gb300 import fmm, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    W = WORKLOAD
+    N = W["N"]
+    x, m = synth.plummer(N, W["seed"])
+    xd = torch.from_numpy(x).to(dev)
+    md = torch.from_numpy(m).to(dev)
+    acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    f = fmm.FMM(local, fmm.FP64, stream)
+    variant = fmm.CONSERVING
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        f.build(xd, md, W["leaf"])
+        f.forces(W["p"], W["theta"], variant, acc, None)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # structure counts for the algorithmic work model (not timed)
+    tree = f.get_tree()
+    lists = f.get_lists()
+    work = algorithmic_flops(lists, tree["count"].astype(np.int64), W["p"], 1)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    step_ms, stage_ms = [], {s: [] for s in STAGES}
+    l0 = fmm.kernel_launches()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = f.stage_times()
+        for s in STAGES:
+            stage_ms[s].append(st[s])
+    launches = (fmm.kernel_launches() - l0) // max(args.steps, 1) * args.steps
+    barrier()
+    clocks = sampler.stop()
+    t_step = sum(step_ms) / len(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * N / t_step
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    xh = torch.from_numpy(x).pin_memory()
+    mh = torch.from_numpy(m).pin_memory()
+    acch = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        f.build(xh, mh, W["leaf"])
+        f.forces(W["p"], W["theta"], variant, acch, None)
+        torch.cuda.synchronize(dev)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_step = statistics.median(e2e_t)
+
+    # accuracy and conservation of the timed configuration
+    Fsum, Tsum = f.diagnostics()
+    a = acc.cpu().numpy()
+    ts = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum())
+    fsum = float((m * np.linalg.norm(a, axis=1)).sum())
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return None
+
+    stage_avg = {s: (statistics.mean(v) if v and v[0] >= 0 else None) for s, v in stage_ms.items()}
+    dom = "m2l" if (stage_avg["m2l"] or 0) >= (stage_avg["p2p"] or 0) else "p2p"
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = fp64_peak_tflops(2070.0)
+    achieved = work[dom] / (stage_avg[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": f"{dom}_con_k" if dom == "m2l" else "p2p_k",
+                "peak_basis": "binary64 FMA rate derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz",
+                "sm_mhz_median": sm_mhz}
+    cpu = cpu_baseline() if (args.cpu_baseline and world == 1) else None
+    rng = np.random.default_rng(0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer sphere)",
+        "config": {"workload": W["workload"], "N": N, "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
+                   "variant": W["variant"], "precision": W["precision"], "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
+        "work": {"n_m2l_pairs": work["n_m2l"], "n_p2p_particle_pairs": work["n_pp"],
+                 "m2l_flops": work["m2l"], "p2p_flops": work["p2p"]},
+        "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
+        "roofline": roofline,
+        "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
+                "d2h_bytes_per_step": int(24 * N)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line
+
+
+def oracle_sample_rate():
+    """The CPU oracle on a bounded sample of the workload (same generator, p, theta,
+    leaf, variant; N = 2^17): particles/s."""
+    import oracle
+    from paper_2107_07166_gb300 import synth
+    W = WORKLOAD
+    x, m = synth.plummer(CPU_SAMPLE_N, W["seed"])
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run(x, m, W["leaf"], W["p"], W["theta"], 1, want_pot=False, want_internals=False)
+    dt = time.perf_counter() - t0
+    return CPU_SAMPLE_N / dt, dt
+
+
+def cpu_baseline():
+    rate, dt = oracle_sample_rate()
+    return {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+            "sample": f"Plummer N={CPU_SAMPLE_N} (seed 2), p=4, theta=0.6, leaf 32, conserving, "
+                      f"one build+forces, {dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        oracle_sample_rate()
+    times = []
+    for _ in range(max(1, args.steps)):
+        rate, dt = oracle_sample_rate()
+        times.append(dt)
+    t = statistics.mean(times)
+    rate = CPU_SAMPLE_N / t
+    line = {
+        "metric": METRIC, "value": rate, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer sphere)", "impl": "reference",
+        "config": {"workload": WORKLOAD["workload"], "N": WORKLOAD["N"], "p": WORKLOAD["p"],
+                   "theta": WORKLOAD["theta"], "leaf_size": WORKLOAD["leaf"], "variant": WORKLOAD["variant"],
+                   "precision": WORKLOAD["precision"], "parallelism": "cpu-oracle"},
+        "cpu_baseline": {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                         "sample": f"Plummer N={CPU_SAMPLE_N} per step (bounded sample of the N=2^20 workload), "
+                                   "single-threaded FP64 C oracle"},
+        "e2e": {"value": rate, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    run_gbfmm(args)
+
+
+if __name__ == "__main__":
+    main()

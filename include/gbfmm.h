@@ -1,0 +1,139 @@
+/*
+ * gbfmm.h -- C ABI of the GB300 (sm_103a) symmetric Cartesian fast multipole method
+ * for Newtonian gravity, standard and angular-momentum-conserving, after
+ * Korobkin et al., "Conservation of Angular Momentum in the Fast Multipole Method"
+ * (arXiv:2107.07166).
+ *
+ * Problem (Sec. 2, eq. jia): N particles at X_a with masses m_a; compute for every a
+ *   acceleration a_a = -sum_{b != a} m_b (X_a - X_b) / |X_a - X_b|^3   (G = 1, no softening)
+ *   potential   phi_a = -sum_{b != a} m_b / |X_a - X_b|
+ * with the FMM of Sec. 2: an octree of nodes with centre of mass Z and radius r_max,
+ * multipoles up to order p about Z, mutual cell-cell interactions for pairs passing the
+ * acceptance test (r_A,max + r_B,max) / R <= theta (eq. mac_criterion, theta = tan of the
+ * MAC angle), and exact particle-particle sums for the rest.  Coincident particles
+ * (r = 0) exert nothing on each other.
+ *
+ * Order p is the multipole/potential order of Sec. 2.1 ("expansion up to 4-th order" is
+ * p = 4); the paper's "zeroth order FMM" of Sec. 3.1 is p = 1.
+ *
+ * Conventions for every call:
+ *   - return 0 (FMM_OK) or a negative FMM_ERR_* code; fmm_strerror() names it and
+ *     fmm_last_error() gives the detail of the last failure on this thread;
+ *   - on error no output buffer is written;
+ *   - every array argument may be host memory or device memory of the context's
+ *     device (detected with cudaPointerGetAttributes); the caller owns all arrays;
+ *     inputs are copied, outputs are written in the caller's particle order;
+ *   - work is queued on the context's stream; calls that return results on the host
+ *     synchronise that stream first;
+ *   - a context is not thread-safe.
+ */
+#ifndef GBFMM_H
+#define GBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx fmm_ctx;
+
+#if defined(__GNUC__)
+#define GBFMM_API __attribute__((visibility("default")))
+#else
+#define GBFMM_API
+#endif
+
+/* highest multipole order compiled into the library */
+#define FMM_P_MAX 6
+
+/* variants */
+enum {
+    FMM_STANDARD = 0,  /* Sec. 2: symmetric Taylor expansion (eq. taylor), forces a = -grad phi */
+    FMM_CONSERVING = 1 /* Sec. 3.2: every approximated pair force realigned onto the line X_a - Y_b */
+};
+
+/* arithmetic of the expansion and particle-particle kernels */
+enum {
+    FMM_FP64 = 0, /* all FMM arithmetic in IEEE binary64 */
+    FMM_MIXED = 1 /* reserved: binary32 M2L/P2P with binary64 translations and accumulators */
+};
+
+/* status codes */
+enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID = -1,  /* bad argument: N < 1, leaf_size < 1, p not in [1,FMM_P_MAX], theta not in [0,1),
+                              unknown variant, non-finite x or m, m < 0, NULL required pointer */
+    FMM_ERR_STATE = -2,    /* call out of order (forces before build, diagnostics before forces) */
+    FMM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    FMM_ERR_OOM = -4,      /* device allocation failed */
+    FMM_ERR_CAPACITY = -5, /* an internal size limit was exceeded (N >= 2^31, > 2^31 list entries) */
+    FMM_ERR_TIMEOUT = -6   /* reserved for bounded device waits */
+};
+
+/* Create a context on CUDA device `device` with arithmetic `precision` (FMM_FP64).
+ * `cuda_stream` is a cudaStream_t to queue work on, or NULL for a private stream. */
+GBFMM_API int fmm_create(fmm_ctx **out, int device, int precision, void *cuda_stream);
+
+/* Release the context and all device memory it holds.  NULL is accepted. */
+GBFMM_API int fmm_destroy(fmm_ctx *c);
+
+/* Re-target the context's work to another stream of the same device (NULL: private). */
+GBFMM_API int fmm_set_stream(fmm_ctx *c, void *cuda_stream);
+
+/* Build the tree (Sec. 2: nodes with COM Z and r_max, eq. mac_criterion).
+ *   x: N x 3 row-major positions (float64); m: N masses (float64, >= 0, finite).
+ *   leaf_size: a node with more than leaf_size particles is split into its non-empty
+ *   octants, down to level 21 at most.
+ * Steps: bounding cube, 63-bit Morton keys, stable radix sort, breadth-first octree,
+ * centres of mass and exact r_max.  Invalidates previous moments, lists and forces. */
+GBFMM_API int fmm_build(fmm_ctx *c, const double *x, const double *m, int64_t N, int leaf_size);
+
+/* One force evaluation on the last built tree.
+ *   p in [1,FMM_P_MAX]: multipole order (Sec. 2.1); theta in [0,1): acceptance parameter
+ *   (eq. mac_criterion); variant: FMM_STANDARD or FMM_CONSERVING.
+ *   acc: N x 3 row-major output accelerations (required).
+ *   pot: N output potentials, or NULL to skip them.  For FMM_CONSERVING the potential
+ *   is the standard order-p potential (a realigned force field has no potential).
+ * Steps: P2M/M2M (cached per p), dual-tree walk (cached per theta), M2L, L2L, L2P,
+ * mutual P2P, deterministic reductions (no floating-point atomics). */
+GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
+
+/* Diagnostics of the last fmm_forces (eqs. netforce, total_torque), float64,
+ * summed in a fixed order:  sum_ma = sum_a m_a acc_a,  sum_mxa = sum_a m_a X_a x acc_a. */
+GBFMM_API int fmm_diagnostics(fmm_ctx *c, double sum_ma[3], double sum_mxa[3]);
+
+/* Sizes of the last build/walk: nodes, mutual M2L pairs, P2P pairs (self pairs included),
+ * number of tree levels.  Any pointer may be NULL. */
+GBFMM_API int fmm_counts(fmm_ctx *c, int64_t *n_nodes, int64_t *n_m2l, int64_t *n_p2p, int32_t *n_levels);
+
+/* Parity exports (copies into caller buffers of the sizes given by fmm_counts). */
+/* keys_sorted[N]: Morton keys in sorted order; perm[N]: input index of each sorted particle;
+ * lo[3], side[1]: the bounding cube (either may be NULL). */
+GBFMM_API int fmm_get_keys(fmm_ctx *c, uint64_t *keys_sorted, int64_t *perm, double *lo, double *side);
+/* breadth-first node arrays, n_nodes each: first sorted particle, particle count, level,
+ * parent (-1 for the root), first child (-1 for leaves), number of children */
+GBFMM_API int fmm_get_tree(fmm_ctx *c, int32_t *first, int32_t *count, int32_t *level, int32_t *parent,
+                 int32_t *child_first, int32_t *nchild);
+/* node mass M[n], centre of mass Z[n x 3], radius rmax[n] */
+GBFMM_API int fmm_get_geometry(fmm_ctx *c, double *M, double *Z, double *rmax);
+/* canonical lists of the last walk: pairs (min id, max id) in lexicographic order,
+ * m2l[n_m2l x 2], p2p[n_p2p x 2] (self pairs (A, A) included) */
+GBFMM_API int fmm_get_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p);
+
+/* Device time in milliseconds of each stage of the last build/forces call, measured
+ * with CUDA events on the context's stream: [build, moments, walk, m2l, l2l, p2p, l2p].
+ * A stage that did not run in that call reports -1. */
+GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
+
+/* Number of CUDA kernels this library has launched in this process so far (all contexts). */
+GBFMM_API int64_t fmm_kernel_launches(void);
+
+GBFMM_API const char *fmm_strerror(int status);
+GBFMM_API const char *fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFMM_H */

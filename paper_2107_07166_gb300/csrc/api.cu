@@ -1,0 +1,388 @@
+// The C ABI of gbfmm (include/gbfmm.h): argument checks, host/device staging of inputs
+// and outputs, the order of the stages, and the conversion of errors to status codes.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fmm_device.cuh"
+#include "fmm_internal.h"
+
+namespace gbfmm {
+long long launches();
+void run_moments_dispatch(fmm_ctx* c, int p);
+void run_far_field_dispatch(fmm_ctx* c, int p, int variant, bool want_pot);
+void run_finish_dispatch(fmm_ctx* c, int p, int variant, bool want_pot, double* acc, double* pot);
+}  // namespace gbfmm
+
+using namespace gbfmm;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+// true when ptr is device (or managed) memory
+static bool is_device_ptr(const void* ptr) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class F>
+static int guarded(fmm_ctx* c, F&& f) {
+    try {
+        DeviceGuard g(c->device);
+        return f();
+    } catch (const FmmError& e) {
+        return fail(e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        return fail(FMM_ERR_OOM, "host allocation failed");
+    }
+}
+
+extern "C" {
+
+const char* fmm_strerror(int status) {
+    switch (status) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_INVALID: return "invalid argument";
+        case FMM_ERR_STATE: return "call out of order";
+        case FMM_ERR_CUDA: return "CUDA runtime error";
+        case FMM_ERR_OOM: return "out of device memory";
+        case FMM_ERR_CAPACITY: return "internal size limit exceeded";
+        case FMM_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* fmm_last_error(void) { return g_last_error.c_str(); }
+
+int64_t fmm_kernel_launches(void) { return (int64_t)launches(); }
+
+int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
+    if (!out) return fail(FMM_ERR_INVALID, "fmm_create: out is NULL");
+    if (precision != FMM_FP64) return fail(FMM_ERR_INVALID, "fmm_create: only FMM_FP64 is available");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(FMM_ERR_CUDA, "fmm_create: no such CUDA device");
+    }
+    fmm_ctx* c = new (std::nothrow) fmm_ctx();
+    if (!c) return fail(FMM_ERR_OOM, "fmm_create: host allocation failed");
+    c->device = device;
+    c->precision = precision;
+    int rc = guarded(c, [&]() -> int {
+        if (cuda_stream) {
+            c->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            GB_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        return FMM_OK;
+    });
+    if (rc != FMM_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return FMM_OK;
+}
+
+int fmm_destroy(fmm_ctx* c) {
+    if (!c) return FMM_OK;
+    {
+        DeviceGuard g(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        DevBuf* bufs[] = {&c->x_stage, &c->m_stage, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->xs, &c->ys,
+                          &c->zs, &c->ms, &c->perm, &c->flags, &c->scan_out, &c->scan_tmp, &c->geom, &c->errflag,
+                          &c->rs_hist, &c->rs_offs, &c->cur, &c->nal, &c->leaf_of, &c->nfirst, &c->ncount,
+                          &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
+                          &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nrmax, &c->mom, &c->loc, &c->locp, &c->fr0,
+                          &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
+                          &c->p2p_dir, &c->p2p_dval, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
+                          &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp};
+        for (DevBuf* b : bufs) release(*b);
+        for (cudaEvent_t& e : c->ev)
+            if (e) cudaEventDestroy(e);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+    return FMM_OK;
+}
+
+int fmm_set_stream(fmm_ctx* c, void* cuda_stream) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_stream: NULL context");
+    return guarded(c, [&]() -> int {
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        if (c->own_stream) GB_CUDA(cudaStreamDestroy(c->stream));
+        c->own_stream = false;
+        if (cuda_stream) {
+            c->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            GB_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        return FMM_OK;
+    });
+}
+
+int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_size) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_build: NULL context");
+    if (!x || !m) return fail(FMM_ERR_INVALID, "fmm_build: x and m are required");
+    if (N < 1) return fail(FMM_ERR_INVALID, "fmm_build: N must be >= 1");
+    if (N >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_CAPACITY, "fmm_build: N must be < 2^31 - 1");
+    if (leaf_size < 1) return fail(FMM_ERR_INVALID, "fmm_build: leaf_size must be >= 1");
+    return guarded(c, [&]() -> int {
+        for (int s = 0; s < ST_COUNT; s++) c->stage_valid[s] = false;
+        c->built = false;
+        c->have_forces = false;
+        c->mom_p = -1;
+        c->list_theta = -1.0;
+        c->N = N;
+        c->leaf = leaf_size;
+        const double* xd = x;
+        const double* md = m;
+        if (!is_device_ptr(x)) {
+            ensure(c->x_stage, sizeof(double) * 3 * (size_t)N);
+            GB_CUDA(cudaMemcpyAsync(c->x_stage.p, x, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice,
+                                    c->stream));
+            xd = c->x_stage.as<double>();
+        }
+        if (!is_device_ptr(m)) {
+            ensure(c->m_stage, sizeof(double) * (size_t)N);
+            GB_CUDA(cudaMemcpyAsync(c->m_stage.p, m, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, c->stream));
+            md = c->m_stage.as<double>();
+        }
+        stage_begin(c, ST_BUILD);
+        int rc = build_tree(c, xd, md);
+        if (rc != FMM_OK) return fail(rc, "fmm_build: non-finite position or mass, or negative mass");
+        stage_end(c, ST_BUILD);
+        c->built = true;
+        return FMM_OK;
+    });
+}
+
+int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double* pot) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_forces: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_forces: call fmm_build first");
+    if (p < 1 || p > FMM_P_MAX) return fail(FMM_ERR_INVALID, "fmm_forces: p must be in [1, FMM_P_MAX]");
+    if (!(theta >= 0.0 && theta < 1.0)) return fail(FMM_ERR_INVALID, "fmm_forces: theta must be in [0, 1)");
+    if (variant != FMM_STANDARD && variant != FMM_CONSERVING)
+        return fail(FMM_ERR_INVALID, "fmm_forces: unknown variant");
+    if (!acc) return fail(FMM_ERR_INVALID, "fmm_forces: acc is required");
+    return guarded(c, [&]() -> int {
+        for (int s = ST_MOMENTS; s < ST_COUNT; s++) c->stage_valid[s] = false;
+        bool want_pot = pot != nullptr;
+        size_t n = (size_t)c->N;
+        if (c->mom_p != p) {
+            stage_begin(c, ST_MOMENTS);
+            run_moments_dispatch(c, p);
+            stage_end(c, ST_MOMENTS);
+            c->mom_p = p;
+        }
+        if (c->list_theta != theta) {
+            stage_begin(c, ST_WALK);
+            run_walk(c, theta);
+            stage_end(c, ST_WALK);
+        }
+        run_far_field_dispatch(c, p, variant, want_pot);
+        run_p2p(c, want_pot);
+        ensure(c->acc_s, sizeof(double) * 3 * n);
+        ensure(c->pot_s, sizeof(double) * n);
+        bool acc_dev = is_device_ptr(acc);
+        bool pot_dev = want_pot && is_device_ptr(pot);
+        ensure(c->out_stage, sizeof(double) * 4 * n);
+        double* acc_d = acc_dev ? acc : c->out_stage.as<double>();
+        double* pot_d = want_pot ? (pot_dev ? pot : c->out_stage.as<double>() + 3 * n) : nullptr;
+        stage_begin(c, ST_L2P);
+        run_finish_dispatch(c, p, variant, want_pot, acc_d, pot_d);
+        stage_end(c, ST_L2P);
+        if (!acc_dev)
+            GB_CUDA(cudaMemcpyAsync(acc, acc_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+        if (want_pot && !pot_dev)
+            GB_CUDA(cudaMemcpyAsync(pot, pot_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        if (!acc_dev || (want_pot && !pot_dev)) GB_CUDA(cudaStreamSynchronize(c->stream));
+        c->have_forces = true;
+        return FMM_OK;
+    });
+}
+
+int fmm_diagnostics(fmm_ctx* c, double sum_ma[3], double sum_mxa[3]) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_diagnostics: NULL context");
+    if (!c->have_forces) return fail(FMM_ERR_STATE, "fmm_diagnostics: call fmm_forces first");
+    return guarded(c, [&]() -> int {
+        double out[6];
+        run_diagnostics(c, out);
+        if (sum_ma)
+            for (int d = 0; d < 3; d++) sum_ma[d] = out[d];
+        if (sum_mxa)
+            for (int d = 0; d < 3; d++) sum_mxa[d] = out[3 + d];
+        return FMM_OK;
+    });
+}
+
+int fmm_counts(fmm_ctx* c, int64_t* n_nodes, int64_t* n_m2l, int64_t* n_p2p, int32_t* n_levels) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_counts: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_counts: call fmm_build first");
+    if (n_nodes) *n_nodes = c->n_nodes;
+    if (n_m2l) *n_m2l = c->list_theta >= 0 ? c->n_m2l : 0;
+    if (n_p2p) *n_p2p = c->list_theta >= 0 ? c->n_p2p : 0;
+    if (n_levels) *n_levels = c->n_levels;
+    return FMM_OK;
+}
+
+// copy n elements of device array src to dst (host or device)
+static void copy_out(fmm_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (!dst || bytes == 0) return;
+    GB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+}
+
+int fmm_get_keys(fmm_ctx* c, uint64_t* keys_sorted, int64_t* perm, double* lo, double* side) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_get_keys: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_get_keys: call fmm_build first");
+    return guarded(c, [&]() -> int {
+        size_t n = (size_t)c->N;
+        copy_out(c, keys_sorted, c->keys0.p, sizeof(uint64_t) * n);
+        std::vector<uint32_t> p32(perm ? n : 0);
+        if (perm) copy_out(c, p32.data(), c->perm.p, sizeof(uint32_t) * n);
+        double g[5];
+        copy_out(c, g, c->geom.p, sizeof(double) * 5);
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        if (perm) {
+            if (is_device_ptr(perm)) {
+                std::vector<int64_t> p64(p32.begin(), p32.end());
+                GB_CUDA(cudaMemcpy(perm, p64.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+            } else {
+                for (size_t i = 0; i < n; i++) perm[i] = p32[i];
+            }
+        }
+        if (lo) copy_out(c, lo, c->geom.p, sizeof(double) * 3);
+        if (side) copy_out(c, side, c->geom.as<double>() + 3, sizeof(double));
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        return FMM_OK;
+    });
+}
+
+int fmm_get_tree(fmm_ctx* c, int32_t* first, int32_t* count, int32_t* level, int32_t* parent, int32_t* child_first,
+                 int32_t* nchild) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_get_tree: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_get_tree: call fmm_build first");
+    return guarded(c, [&]() -> int {
+        size_t b = sizeof(int32_t) * (size_t)c->n_nodes;
+        copy_out(c, first, c->nfirst.p, b);
+        copy_out(c, count, c->ncount.p, b);
+        copy_out(c, level, c->nlevel.p, b);
+        copy_out(c, parent, c->nparent.p, b);
+        copy_out(c, child_first, c->nchildf.p, b);
+        copy_out(c, nchild, c->nnchild.p, b);
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        return FMM_OK;
+    });
+}
+
+int fmm_get_geometry(fmm_ctx* c, double* M, double* Z, double* rmax) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_get_geometry: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_get_geometry: call fmm_build first");
+    return guarded(c, [&]() -> int {
+        size_t nn = (size_t)c->n_nodes;
+        copy_out(c, M, c->nM.p, sizeof(double) * nn);
+        copy_out(c, rmax, c->nrmax.p, sizeof(double) * nn);
+        if (Z) {
+            std::vector<double> zx(nn), zy(nn), zz(nn), zall(3 * nn);
+            copy_out(c, zx.data(), c->nZx.p, sizeof(double) * nn);
+            copy_out(c, zy.data(), c->nZy.p, sizeof(double) * nn);
+            copy_out(c, zz.data(), c->nZz.p, sizeof(double) * nn);
+            GB_CUDA(cudaStreamSynchronize(c->stream));
+            for (size_t i = 0; i < nn; i++) {
+                zall[3 * i] = zx[i];
+                zall[3 * i + 1] = zy[i];
+                zall[3 * i + 2] = zz[i];
+            }
+            GB_CUDA(cudaMemcpy(Z, zall.data(), sizeof(double) * 3 * nn, cudaMemcpyDefault));
+        }
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        return FMM_OK;
+    });
+}
+
+int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_get_lists: NULL context");
+    if (c->list_theta < 0) return fail(FMM_ERR_STATE, "fmm_get_lists: call fmm_forces first");
+    return guarded(c, [&]() -> int {
+        int b = c->id_bits;
+        uint64_t mask = (1ull << b) - 1ull;
+        // the directed entries with target < source, in sorted order, are the canonical list
+        if (m2l && c->n_m2l > 0) {
+            std::vector<uint64_t> k(2 * (size_t)c->n_m2l);
+            copy_out(c, k.data(), c->m2l_dir.p, sizeof(uint64_t) * k.size());
+            GB_CUDA(cudaStreamSynchronize(c->stream));
+            std::vector<int32_t> out;
+            out.reserve(2 * (size_t)c->n_m2l);
+            for (uint64_t e : k) {
+                int32_t t = (int32_t)(e >> b), s = (int32_t)(e & mask);
+                if (t < s) {
+                    out.push_back(t);
+                    out.push_back(s);
+                }
+            }
+            GB_CUDA(cudaMemcpy(m2l, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
+        }
+        if (p2p && c->n_p2p > 0) {
+            std::vector<uint64_t> k(2 * (size_t)c->n_p2p);
+            copy_out(c, k.data(), c->p2p_dir.p, sizeof(uint64_t) * k.size());
+            GB_CUDA(cudaStreamSynchronize(c->stream));
+            std::vector<int32_t> out;
+            out.reserve(2 * (size_t)c->n_p2p);
+            uint64_t invalid = (1ull << (2 * b)) - 1ull;
+            for (uint64_t e : k) {
+                if (e == invalid) continue;
+                int32_t t = (int32_t)(e >> b), s = (int32_t)(e & mask);
+                if (t <= s) {
+                    out.push_back(t);
+                    out.push_back(s);
+                }
+            }
+            GB_CUDA(cudaMemcpy(p2p, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
+        }
+        return FMM_OK;
+    });
+}
+
+int fmm_stage_times(fmm_ctx* c, double* ms, int n) {
+    if (!c || !ms) return fail(FMM_ERR_INVALID, "fmm_stage_times: NULL argument");
+    return guarded(c, [&]() -> int {
+        GB_CUDA(cudaStreamSynchronize(c->stream));
+        for (int s = 0; s < n && s < ST_COUNT; s++) {
+            ms[s] = -1.0;
+            if (c->stage_valid[s]) {
+                float t = 0.f;
+                GB_CUDA(cudaEventElapsedTime(&t, c->ev[2 * s], c->ev[2 * s + 1]));
+                ms[s] = t;
+            }
+        }
+        return FMM_OK;
+    });
+}
+
+}  // extern "C"

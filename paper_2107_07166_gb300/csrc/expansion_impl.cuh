@@ -1,0 +1,314 @@
+// Expansion kernels of order P (included once per P by the generated expansion_p*.cu):
+// P2M, M2M (upward pass), target-major M2L, L2L (downward pass) and the final
+// per-particle kernel (L2P + P2P partial reduction + return to input order).
+//
+// Layouts (device, node ids breadth-first):
+//   mom[n * NM + k]     raw moments M_alpha about Z_n, alpha in generated order
+//   loc[n * NM + k]     standard locals L_gamma                       (variant 0)
+//   loc[n * NSU + k]    conserving locals [S | Ux | Uy | Uz]          (variant 1)
+//   m2l_dir[e]          directed entry tgt << bits | src, sorted; m2l_seg[n] = first entry of n
+#pragma once
+#include "fmm_device.cuh"
+#include "fmm_internal.h"
+#include "fmm_math.cuh"
+
+namespace gbfmm {
+
+constexpr int EB = 128;
+
+// a5 P2M: moments of every leaf from its particles (y = X - Z)
+template <int P>
+__global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                                            const int* __restrict__ nnchild, const double* __restrict__ xs,
+                                            const double* __restrict__ ys, const double* __restrict__ zs,
+                                            const double* __restrict__ ms, const double* __restrict__ Zx,
+                                            const double* __restrict__ Zy, const double* __restrict__ Zz,
+                                            double* __restrict__ mom) {
+    using E = Exp<P>;
+    int nd = blockIdx.x * EB + threadIdx.x;
+    if (nd >= nn || nnchild[nd] != 0) return;
+    double M[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) M[k] = 0.0;
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    int f = nfirst[nd], e = f + ncount[nd];
+    for (int i = f; i < e; i++) E::p2m(ms[i], xs[i] - zx, ys[i] - zy, zs[i] - zz, M);
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
+}
+
+// a6 M2M: inner nodes of one level from their children (c = Z_child - Z_parent)
+template <int P>
+__global__ void __launch_bounds__(EB) m2m_k(int lo, int hi, const int* __restrict__ nchildf,
+                                            const int* __restrict__ nnchild, const double* __restrict__ Zx,
+                                            const double* __restrict__ Zy, const double* __restrict__ Zz,
+                                            double* __restrict__ mom) {
+    using E = Exp<P>;
+    int nd = lo + blockIdx.x * EB + threadIdx.x;
+    if (nd >= hi || nnchild[nd] == 0) return;
+    double M[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) M[k] = 0.0;
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    int c0 = nchildf[nd], c1 = c0 + nnchild[nd];
+    for (int ch = c0; ch < c1; ch++)
+        E::m2m(mom + (int64_t)ch * E::NM, Zx[ch] - zx, Zy[ch] - zy, Zz[ch] - zz, M);
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
+}
+
+// a8 M2L, standard: every cell accumulates D(Z_tgt - Z_src) contracted with the source
+// moments over its directed entries, in increasing source id (deterministic order).
+template <int P>
+__global__ void __launch_bounds__(EB) m2l_std_k(int nn, const uint64_t* __restrict__ dir,
+                                                const long long* __restrict__ seg, int bits,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, const double* __restrict__ mom,
+                                                double* __restrict__ loc) {
+    using E = Exp<P>;
+    int nd = blockIdx.x * EB + threadIdx.x;
+    if (nd >= nn) return;
+    double L[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) L[k] = 0.0;
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    uint64_t mask = (1ull << bits) - 1ull;
+    long long e0 = seg[nd], e1 = seg[nd + 1];
+    for (long long e = e0; e < e1; e++) {
+        int src = (int)(dir[e] & mask);
+        double D[E::NM];
+        E::dtensor(zx - Zx[src], zy - Zy[src], zz - Zz[src], D);
+        E::m2l_std(mom + (int64_t)src * E::NM, D, L);
+    }
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) loc[(int64_t)nd * E::NM + k] = L[k];
+}
+
+// a8' M2L, conserving: S and U of the realigned pair forces
+template <int P>
+__global__ void __launch_bounds__(EB) m2l_con_k(int nn, const uint64_t* __restrict__ dir,
+                                                const long long* __restrict__ seg, int bits,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, const double* __restrict__ mom,
+                                                double* __restrict__ loc) {
+    using E = Exp<P>;
+    int nd = blockIdx.x * EB + threadIdx.x;
+    if (nd >= nn) return;
+    double SU[E::NSU];
+#pragma unroll
+    for (int k = 0; k < E::NSU; k++) SU[k] = 0.0;
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    uint64_t mask = (1ull << bits) - 1ull;
+    long long e0 = seg[nd], e1 = seg[nd + 1];
+    for (long long e = e0; e < e1; e++) {
+        int src = (int)(dir[e] & mask);
+        double rx = zx - Zx[src], ry = zy - Zy[src], rz = zz - Zz[src];
+        double H[E::NQ];
+        E::htensor(rx, ry, rz, H);
+        E::m2l_con(mom + (int64_t)src * E::NM, H, rx, ry, rz, SU);
+    }
+#pragma unroll
+    for (int k = 0; k < E::NSU; k++) loc[(int64_t)nd * E::NSU + k] = SU[k];
+}
+
+// a10 L2L, one level: child += shift(parent) by s = Z_child - Z_parent
+template <int P>
+__global__ void __launch_bounds__(EB) l2l_std_k(int lo, int hi, const int* __restrict__ nparent,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, double* __restrict__ loc) {
+    using E = Exp<P>;
+    int nd = lo + blockIdx.x * EB + threadIdx.x;
+    if (nd >= hi) return;
+    int par = nparent[nd];
+    double L[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) L[k] = loc[(int64_t)nd * E::NM + k];
+    E::l2l(loc + (int64_t)par * E::NM, Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par], L);
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) loc[(int64_t)nd * E::NM + k] = L[k];
+}
+
+template <int P>
+__global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __restrict__ nparent,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, double* __restrict__ loc) {
+    using E = Exp<P>;
+    constexpr int NQ = E::NQ;
+    int nd = lo + blockIdx.x * EB + threadIdx.x;
+    if (nd >= hi) return;
+    int par = nparent[nd];
+    double sx = Zx[nd] - Zx[par], sy = Zy[nd] - Zy[par], sz = Zz[nd] - Zz[par];
+    const double* Lp = loc + (int64_t)par * E::NSU;
+    double* Lc = loc + (int64_t)nd * E::NSU;
+    double sh[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; k++) sh[k] = 0.0;
+    E::l2l_q(Lp, sx, sy, sz, sh);  // shifted parent S
+    double t[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; k++) t[k] = Lc[k] + sh[k];
+#pragma unroll
+    for (int k = 0; k < NQ; k++) Lc[k] = t[k];
+    const double s3[3] = {sx, sy, sz};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) t[k] = Lc[(d + 1) * NQ + k];
+        E::l2l_q(Lp + (d + 1) * NQ, sx, sy, sz, t);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) Lc[(d + 1) * NQ + k] = fma(s3[d], sh[k], t[k]);
+    }
+}
+
+// a11 + a13: far field at every particle from its leaf's locals, plus the P2P partials
+// of every directed entry of the leaf (increasing partner id), written in input order.
+//   part[] holds double4 (ax, ay, az, phi) per (pair, side, slot); pair k's block starts
+//   at off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+template <int P, int V>
+__global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ leaf_of, const int* __restrict__ nfirst,
+                                               const int* __restrict__ ncount, const double* __restrict__ xs,
+                                               const double* __restrict__ ys, const double* __restrict__ zs,
+                                               const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                               const double* __restrict__ Zz, const double* __restrict__ loc,
+                                               const double* __restrict__ locp, const uint32_t* __restrict__ pdval,
+                                               const long long* __restrict__ pseg, const int2* __restrict__ pairs,
+                                               const long long* __restrict__ poff, const double4* __restrict__ part,
+                                               const uint32_t* __restrict__ perm, double* __restrict__ acc_s,
+                                               double* __restrict__ pot_s, double* __restrict__ acc_out,
+                                               double* __restrict__ pot_out) {
+    using E = Exp<P>;
+    int i = blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    int lf = leaf_of[i];
+    int slot = i - nfirst[lf];
+    double x = xs[i] - Zx[lf], y = ys[i] - Zy[lf], z = zs[i] - Zz[lf];
+    double ax, ay, az, ph = 0.0;
+    if (V == 0) {
+        E::l2p_std(loc + (int64_t)lf * E::NM, x, y, z, ax, ay, az, ph);
+    } else {
+        E::l2p_con(loc + (int64_t)lf * E::NSU, x, y, z, ax, ay, az);
+        if (locp) {
+            double bx, by, bz;
+            E::l2p_std(locp + (int64_t)lf * E::NM, x, y, z, bx, by, bz, ph);
+        }
+    }
+    double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
+    for (long long e = pseg[lf]; e < pseg[lf + 1]; e++) {
+        uint32_t v = pdval[e];
+        uint32_t k = v >> 1;
+        long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
+        double4 q = part[o];
+        px += q.x;
+        py += q.y;
+        pz += q.z;
+        pp += q.w;
+    }
+    ax += px;
+    ay += py;
+    az += pz;
+    ph += pp;
+    acc_s[i] = ax;
+    acc_s[n + i] = ay;
+    acc_s[2 * (int64_t)n + i] = az;
+    int64_t j = perm[i];
+    acc_out[3 * j] = ax;
+    acc_out[3 * j + 1] = ay;
+    acc_out[3 * j + 2] = az;
+    if (pot_out) {
+        pot_s[i] = ph;
+        pot_out[j] = ph;
+    }
+}
+
+// host side, one order P
+template <int P>
+void run_moments_p(fmm_ctx* c) {
+    using E = Exp<P>;
+    cudaStream_t s = c->stream;
+    int nn = (int)c->n_nodes;
+    ensure(c->mom, sizeof(double) * (size_t)nn * E::NM);
+    p2m_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nfirst.as<int>(), c->ncount.as<int>(), c->nnchild.as<int>(),
+                                             c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
+                                             c->ms.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
+                                             c->nZz.as<double>(), c->mom.as<double>());
+    GB_LAUNCH("p2m_k");
+    for (int l = c->n_levels - 2; l >= 0; l--) {
+        int lo = c->level_start[l], hi = c->level_start[l + 1];
+        m2m_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nchildf.as<int>(), c->nnchild.as<int>(),
+                                                      c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                                                      c->mom.as<double>());
+        GB_LAUNCH("m2m_k");
+    }
+}
+
+template <int P>
+void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
+    using E = Exp<P>;
+    cudaStream_t s = c->stream;
+    int nn = (int)c->n_nodes;
+    const uint64_t* dir = c->m2l_dir.as<uint64_t>();
+    const long long* seg = c->m2l_seg.as<long long>();
+    bool std_locals = (variant == 0) || want_pot;
+    stage_begin(c, ST_M2L);
+    if (variant == 1) {
+        ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
+        m2l_con_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, dir, seg, c->id_bits, c->nZx.as<double>(),
+                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
+                                                     c->loc.as<double>());
+        GB_LAUNCH("m2l_con_k");
+    }
+    if (std_locals) {
+        DevBuf& L = variant == 0 ? c->loc : c->locp;
+        ensure(L, sizeof(double) * (size_t)nn * E::NM);
+        m2l_std_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, dir, seg, c->id_bits, c->nZx.as<double>(),
+                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
+                                                     L.as<double>());
+        GB_LAUNCH("m2l_std_k");
+    }
+    stage_end(c, ST_M2L);
+    stage_begin(c, ST_L2L);
+    for (int l = 1; l < c->n_levels; l++) {
+        int lo = c->level_start[l], hi = c->level_start[l + 1];
+        if (variant == 1) {
+            l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
+                                                              c->nZy.as<double>(), c->nZz.as<double>(),
+                                                              c->loc.as<double>());
+            GB_LAUNCH("l2l_con_k");
+        }
+        if (std_locals) {
+            DevBuf& L = variant == 0 ? c->loc : c->locp;
+            l2l_std_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
+                                                              c->nZy.as<double>(), c->nZz.as<double>(),
+                                                              L.as<double>());
+            GB_LAUNCH("l2l_std_k");
+        }
+    }
+    stage_end(c, ST_L2L);
+}
+
+template <int P>
+void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
+    cudaStream_t s = c->stream;
+    int n = (int)c->N;
+    const double* locp = (variant == 1 && want_pot) ? c->locp.as<double>() : nullptr;
+    auto args = [&](auto kern) {
+        kern<<<grid_for(n, EB), EB, 0, s>>>(
+            n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+            c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->loc.as<double>(),
+            locp, c->p2p_dval.as<uint32_t>(), c->p2p_seg.as<long long>(), c->p2p_pairs.as<int2>(),
+            c->p2p_off.as<long long>(), c->p2p_part.as<double4>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(),
+            c->pot_s.as<double>(), acc_out, want_pot ? pot_out : nullptr);
+    };
+    if (variant == 0)
+        args(finish_k<P, 0>);
+    else
+        args(finish_k<P, 1>);
+    GB_LAUNCH("finish_k");
+}
+
+#define GBFMM_INSTANTIATE(P)                                                                             \
+    template void run_moments_p<P>(fmm_ctx*);                                                           \
+    template void run_far_field_p<P>(fmm_ctx*, int, bool);                                              \
+    template void run_finish_p<P>(fmm_ctx*, int, bool, double*, double*);
+
+}  // namespace gbfmm

@@ -1,0 +1,150 @@
+// Internal state of a gbfmm context and the host-side launchers shared by the
+// translation units of the CUDA library.  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbfmm.h"
+#include "fmm_device.cuh"
+
+namespace gbfmm {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+// Error carried out of the launchers as a C++ exception and turned into a status
+// code at the C boundary.
+struct FmmError {
+    int code;
+    std::string msg;
+};
+
+void cuda_check(cudaError_t e, const char* what);
+void count_launch();
+#define GB_CUDA(call) ::gbfmm::cuda_check((call), #call)
+#define GB_LAUNCH(what) (::gbfmm::count_launch(), ::gbfmm::cuda_check(cudaGetLastError(), what))
+
+// Node arrays (breadth-first order); all device pointers.
+struct NodeView {
+    const int* first;
+    const int* count;
+    const int* parent;
+    const int* child_first;
+    const int* nchild;
+    const double* Zx;
+    const double* Zy;
+    const double* Zz;
+    const double* rmax;
+};
+
+enum Stage {
+    ST_BUILD = 0,   // bounding cube .. r_max
+    ST_MOMENTS,     // P2M + M2M
+    ST_WALK,        // dual-tree walk + list canonicalisation
+    ST_M2L,         // M2L (target-major, both partners of every mutual pair)
+    ST_L2L,         // L2L
+    ST_P2P,         // mutual P2P tiles
+    ST_L2P,         // L2P + particle reduction + unpermute
+    ST_COUNT
+};
+
+}  // namespace gbfmm
+
+struct fmm_ctx {
+    int device = 0;
+    int precision = FMM_FP64;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // particles
+    int64_t N = 0;
+    int leaf = 0;
+    bool built = false;
+    // device buffers (see the kernels for layouts)
+    gbfmm::DevBuf x_stage, m_stage;           // host inputs staged on the device
+    gbfmm::DevBuf keys0, keys1, vals0, vals1;  // sort ping-pong
+    gbfmm::DevBuf xs, ys, zs, ms;              // sorted SoA positions and masses
+    gbfmm::DevBuf perm;                        // sorted position -> input index (uint32)
+    gbfmm::DevBuf flags, scan_out, scan_tmp, geom, errflag;
+    gbfmm::DevBuf rs_hist, rs_offs;            // radix sort histograms and offsets
+    gbfmm::DevBuf cur, nal, leaf_of;           // build state, node at level, leaf of particle
+    // nodes
+    int64_t n_nodes = 0, cap_nodes = 0;
+    int n_levels = 0;                          // levels 0 .. n_levels-1
+    std::vector<int> level_start;              // size n_levels + 1
+    gbfmm::DevBuf nfirst, ncount, nlevel, nparent, nchildf, nnchild;
+    gbfmm::DevBuf nM, nSx, nSy, nSz, nZx, nZy, nZz, nr2, nrmax;
+    // expansions
+    int mom_p = -1;
+    gbfmm::DevBuf mom;   // n_nodes x nmi(p)
+    gbfmm::DevBuf loc;   // n_nodes x (nmi(p) | 4 nmi(p-1))
+    gbfmm::DevBuf locp;  // standard locals for potentials of the conserving form
+    // lists
+    double list_theta = -1.0;
+    int64_t n_m2l = 0, n_p2p = 0;
+    gbfmm::DevBuf fr0, fr1, cnt, cnt_off;      // walk frontier
+    gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
+    gbfmm::DevBuf m2l_dir;                     // uint64 directed keys (tgt << b | src), sorted
+    gbfmm::DevBuf m2l_seg;                     // int64 [n_nodes + 1] segment starts per target
+    gbfmm::DevBuf p2p_dir, p2p_dval;           // uint64 keys + uint32 (pair << 1 | side), sorted
+    gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]
+    gbfmm::DevBuf p2p_off;                     // int64 [n_p2p + 1] partial offsets
+    gbfmm::DevBuf p2p_part;                    // double4 partials
+    gbfmm::DevBuf seg_cnt;
+    int id_bits = 0;
+    // results (sorted order) and output staging
+    gbfmm::DevBuf acc_s, pot_s;                // SoA: ax | ay | az
+    gbfmm::DevBuf out_stage;
+    gbfmm::DevBuf diag_tmp;
+    bool have_forces = false;
+    // timing
+    cudaEvent_t ev[2 * gbfmm::ST_COUNT] = {};
+    float stage_ms[gbfmm::ST_COUNT] = {};
+    bool stage_valid[gbfmm::ST_COUNT] = {};
+};
+
+namespace gbfmm {
+
+// buffers
+void ensure(DevBuf& b, size_t bytes);                              // grow, contents lost
+void ensure_keep(DevBuf& b, size_t bytes, cudaStream_t s);         // grow, contents kept
+void release(DevBuf& b);
+
+// scans (launch.cu); out must hold n + 1 entries, out[n] = total
+void scan_int(fmm_ctx* c, const int* in, int64_t n, int* out);
+void scan_i64(fmm_ctx* c, const int* in, int64_t n, long long* out);
+void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* out);
+void scan_cnt3(fmm_ctx* c, const Cnt3* in, int64_t n, Cnt3* out);
+// radix sort of keys [+ values] on bits [0, bits); result in place
+void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
+
+// tree (tree.cu)
+int build_tree(fmm_ctx* c, const double* x_dev, const double* m_dev);
+
+// walk (walk.cu)
+void run_walk(fmm_ctx* c, double theta);
+
+// expansions (expansion_p*.cu, dispatched in expansion.cu)
+void run_moments(fmm_ctx* c, int p);
+void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
+
+// particle-particle + final reduction (p2p.cu)
+void run_p2p(fmm_ctx* c, bool want_pot);
+void run_gather_out(fmm_ctx* c, int p, int variant, bool want_pot, double* acc_out, double* pot_out);
+void run_diagnostics(fmm_ctx* c, double* out6_host);
+
+void stage_begin(fmm_ctx* c, Stage s);
+void stage_end(fmm_ctx* c, Stage s);
+
+NodeView node_view(const fmm_ctx* c);
+
+}  // namespace gbfmm

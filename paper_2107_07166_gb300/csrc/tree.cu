@@ -1,0 +1,432 @@
+// Tree build: bounding cube, Morton keys, radix sort, breadth-first octree, centres of
+// mass and exact r_max (Sec. 2: nodes with COM Z and r_max of eq. mac_criterion).
+//
+// Every geometric quantity is computed with explicitly rounded IEEE operations
+// (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn) in a fixed order, so that keys, tree,
+// centres of mass, radii and the acceptance decisions of the walk are reproducible bit
+// for bit by any binary64 implementation using the same order:
+//   cube:  lo = per-axis minimum, side = max extent (1 if zero), scale = 2^21 / side
+//   key:   q_d = min(floor((x_d - lo_d) * scale), 2^21 - 1), bits interleaved x,y,z
+//   COM:   leaves sum m and m*X sequentially in sorted order; parents sum their
+//          children's sums in child order; Z = (sum m X) / M
+//   r_max: sqrt of the maximum over the node's particles of (dx*dx + dy*dy) + dz*dz
+#include <math.h>
+
+#include "fmm_device.cuh"
+#include "fmm_internal.h"
+
+namespace gbfmm {
+
+constexpr int MAX_LEVEL = 21;
+constexpr int TB = 256;
+
+// ------------------------------------------------------------------ cube + validation
+
+// Per-block min/max of each axis plus a flag for non-finite coordinates or bad masses.
+__global__ void bbox_partial_k(const double* __restrict__ x, const double* __restrict__ m, int64_t n,
+                               double* __restrict__ part, int* __restrict__ bad) {
+    __shared__ double smn[3][TB], smx[3][TB];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int b = 0;
+    for (int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
+        for (int d = 0; d < 3; d++) {
+            double v = x[3 * i + d];
+            if (!isfinite(v)) b = 1;
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+        double mm = m[i];
+        if (!(mm >= 0.0) || !isfinite(mm)) b = 1;
+    }
+    if (b) atomicOr(bad, 1);
+    for (int d = 0; d < 3; d++) {
+        smn[d][threadIdx.x] = mn[d];
+        smx[d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int s = TB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int d = 0; d < 3; d++) {
+                smn[d][threadIdx.x] = fmin(smn[d][threadIdx.x], smn[d][threadIdx.x + s]);
+                smx[d][threadIdx.x] = fmax(smx[d][threadIdx.x], smx[d][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; d++) {
+            part[6 * blockIdx.x + d] = smn[d][0];
+            part[6 * blockIdx.x + 3 + d] = smx[d][0];
+        }
+}
+
+// geom[0..2] = lo, geom[3] = side, geom[4] = scale
+__global__ void bbox_final_k(const double* __restrict__ part, int nb, double* __restrict__ geom) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mn[3], mx[3];
+    for (int d = 0; d < 3; d++) {
+        mn[d] = part[d];
+        mx[d] = part[3 + d];
+    }
+    for (int b = 1; b < nb; b++)
+        for (int d = 0; d < 3; d++) {
+            mn[d] = fmin(mn[d], part[6 * b + d]);
+            mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
+        }
+    double side = 0.0;
+    for (int d = 0; d < 3; d++) {
+        geom[d] = mn[d];
+        double e = __dsub_rn(mx[d], mn[d]);
+        if (e > side) side = e;
+    }
+    if (side == 0.0) side = 1.0;
+    geom[3] = side;
+    geom[4] = __ddiv_rn(2097152.0, side);
+}
+
+// ------------------------------------------------------------------ keys
+
+__device__ __forceinline__ uint64_t spread_bits3(uint64_t v) {
+    // place bit b of a 21-bit value at bit 3b
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x001f00000000ffffull;
+    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double x, double lo, double scale) {
+    double t = __dmul_rn(__dsub_rn(x, lo), scale);
+    double f = floor(t);
+    uint64_t q = (f <= 0.0) ? 0ull : (uint64_t)f;
+    return q > 2097151ull ? 2097151ull : q;
+}
+
+__global__ void keys_k(const double* __restrict__ x, int64_t n, const double* __restrict__ geom,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    double lo0 = geom[0], lo1 = geom[1], lo2 = geom[2], sc = geom[4];
+    uint64_t qx = quantise(x[3 * i], lo0, sc);
+    uint64_t qy = quantise(x[3 * i + 1], lo1, sc);
+    uint64_t qz = quantise(x[3 * i + 2], lo2, sc);
+    keys[i] = (spread_bits3(qx) << 2) | (spread_bits3(qy) << 1) | spread_bits3(qz);
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void gather_k(const double* __restrict__ x, const double* __restrict__ m,
+                         const uint32_t* __restrict__ perm, int64_t n, double* __restrict__ xs,
+                         double* __restrict__ ys, double* __restrict__ zs, double* __restrict__ ms) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    xs[i] = x[3 * j];
+    ys[i] = x[3 * j + 1];
+    zs[i] = x[3 * j + 2];
+    ms[i] = m[j];
+}
+
+// ------------------------------------------------------------------ octree, level by level
+
+// Boundary flags of the children of every splittable node at `level`: a particle starts
+// a child when it is the first of its node or its level+1 octant differs from the
+// previous particle's.  Also records the node of every particle at this level.
+__global__ void tree_mark_k(const uint64_t* __restrict__ keys, int n, int level, int leaf,
+                            const int* __restrict__ cur, const int* __restrict__ nfirst,
+                            const int* __restrict__ ncount, int* __restrict__ flag, int* __restrict__ nal_l) {
+    int i = blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    int c = cur[i];
+    nal_l[i] = c;
+    int f = 0;
+    if (c >= 0 && ncount[c] > leaf && level < MAX_LEVEL) {
+        int shift = 60 - 3 * level;
+        f = (i == nfirst[c]) || ((keys[i] >> shift) != (keys[i - 1] >> shift));
+    }
+    flag[i] = f;
+}
+
+__global__ void tree_emit_k(int n, int level, int leaf, int new_base, const int* __restrict__ flag,
+                            const int* __restrict__ pos, int* __restrict__ cur, int* __restrict__ nfirst,
+                            const int* __restrict__ ncount, int* __restrict__ nlevel, int* __restrict__ nparent,
+                            int* __restrict__ nchildf, int* __restrict__ nnchild, int* __restrict__ leaf_of) {
+    int i = blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    int c = cur[i];
+    if (c < 0) return;
+    if (!(ncount[c] > leaf && level < MAX_LEVEL)) {  // c is a leaf
+        leaf_of[i] = c;
+        cur[i] = -1;
+        return;
+    }
+    int id = new_base + pos[i] + flag[i] - 1;
+    if (flag[i]) {
+        nfirst[id] = i;
+        nlevel[id] = level + 1;
+        nparent[id] = c;
+        nchildf[id] = -1;
+        nnchild[id] = 0;
+        if (i == nfirst[c]) nchildf[c] = id;
+    }
+    cur[i] = id;
+}
+
+__global__ void tree_count_k(int new_base, int total, const int* __restrict__ nfirst, int* __restrict__ ncount,
+                             const int* __restrict__ nparent, const int* __restrict__ nchildf,
+                             int* __restrict__ nnchild) {
+    int t = blockIdx.x * TB + threadIdx.x;
+    if (t >= total) return;
+    int k = new_base + t;
+    int par = nparent[k];
+    bool last = (t + 1 == total) || (nparent[k + 1] != par);
+    int next = last ? nfirst[par] + ncount[par] : nfirst[k + 1];
+    ncount[k] = next - nfirst[k];
+    if (last) nnchild[par] = k - nchildf[par] + 1;
+}
+
+__global__ void tree_finish_k(int n, const int* __restrict__ cur, int* __restrict__ leaf_of) {
+    int i = blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    if (cur[i] >= 0) leaf_of[i] = cur[i];
+}
+
+__global__ void root_k(int n, int* nfirst, int* ncount, int* nlevel, int* nparent, int* nchildf, int* nnchild) {
+    nfirst[0] = 0;
+    ncount[0] = n;
+    nlevel[0] = 0;
+    nparent[0] = -1;
+    nchildf[0] = -1;
+    nnchild[0] = 0;
+}
+
+__global__ void fill_int_k(int* __restrict__ a, int64_t n, int v) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// ------------------------------------------------------------------ centres of mass
+
+__global__ void com_leaf_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                           const int* __restrict__ nnchild, const double* __restrict__ xs,
+                           const double* __restrict__ ys, const double* __restrict__ zs,
+                           const double* __restrict__ ms, double* __restrict__ M, double* __restrict__ Sx,
+                           double* __restrict__ Sy, double* __restrict__ Sz, double* __restrict__ Zx,
+                           double* __restrict__ Zy, double* __restrict__ Zz) {
+    int nd = blockIdx.x * TB + threadIdx.x;
+    if (nd >= nn || nnchild[nd] != 0) return;
+    int f = nfirst[nd], e = f + ncount[nd];
+    double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int i = f; i < e; i++) {
+        double mi = ms[i];
+        m = __dadd_rn(m, mi);
+        sx = __dadd_rn(sx, __dmul_rn(mi, xs[i]));
+        sy = __dadd_rn(sy, __dmul_rn(mi, ys[i]));
+        sz = __dadd_rn(sz, __dmul_rn(mi, zs[i]));
+    }
+    M[nd] = m;
+    Sx[nd] = sx;
+    Sy[nd] = sy;
+    Sz[nd] = sz;
+    bool ok = m > 0.0;
+    Zx[nd] = ok ? __ddiv_rn(sx, m) : xs[f];
+    Zy[nd] = ok ? __ddiv_rn(sy, m) : ys[f];
+    Zz[nd] = ok ? __ddiv_rn(sz, m) : zs[f];
+}
+
+__global__ void com_inner_k(int lo, int hi, const int* __restrict__ nfirst, const int* __restrict__ nchildf,
+                            const int* __restrict__ nnchild, const double* __restrict__ xs,
+                            const double* __restrict__ ys, const double* __restrict__ zs, double* __restrict__ M,
+                            double* __restrict__ Sx, double* __restrict__ Sy, double* __restrict__ Sz,
+                            double* __restrict__ Zx, double* __restrict__ Zy, double* __restrict__ Zz) {
+    int nd = lo + blockIdx.x * TB + threadIdx.x;
+    if (nd >= hi || nnchild[nd] == 0) return;
+    int c0 = nchildf[nd], c1 = c0 + nnchild[nd];
+    double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int c = c0; c < c1; c++) {
+        m = __dadd_rn(m, M[c]);
+        sx = __dadd_rn(sx, Sx[c]);
+        sy = __dadd_rn(sy, Sy[c]);
+        sz = __dadd_rn(sz, Sz[c]);
+    }
+    M[nd] = m;
+    Sx[nd] = sx;
+    Sy[nd] = sy;
+    Sz[nd] = sz;
+    int f = nfirst[nd];
+    bool ok = m > 0.0;
+    Zx[nd] = ok ? __ddiv_rn(sx, m) : xs[f];
+    Zy[nd] = ok ? __ddiv_rn(sy, m) : ys[f];
+    Zz[nd] = ok ? __ddiv_rn(sz, m) : zs[f];
+}
+
+// ------------------------------------------------------------------ r_max
+
+// For every level, each particle computes its squared distance to the COM of its node at
+// that level; equal nodes are contiguous in sorted order, so a segmented warp maximum
+// leaves one integer atomicMax (on the bit pattern of a non-negative double, which
+// orders like the value) per node and warp.  Max is order independent: bit exact.
+__global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const double* __restrict__ xs,
+                        const double* __restrict__ ys, const double* __restrict__ zs,
+                        const double* __restrict__ Zx, const double* __restrict__ Zy,
+                        const double* __restrict__ Zz, unsigned long long* __restrict__ r2bits) {
+    int i = blockIdx.x * TB + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    bool in = i < n;
+    double px = in ? xs[i] : 0.0, py = in ? ys[i] : 0.0, pz = in ? zs[i] : 0.0;
+    for (int l = 0; l < nlev; l++) {
+        int nd = in ? nal[(int64_t)l * n + i] : -1;
+        unsigned long long v = 0ull;
+        if (nd >= 0) {
+            double dx = __dsub_rn(px, Zx[nd]);
+            double dy = __dsub_rn(py, Zy[nd]);
+            double dz = __dsub_rn(pz, Zz[nd]);
+            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            v = (unsigned long long)__double_as_longlong(d2);
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            unsigned long long u = __shfl_down_sync(FULL, v, off);
+            int no = __shfl_down_sync(FULL, nd, off);
+            if (lane + off < 32 && no == nd && u > v) v = u;
+        }
+        int prev = __shfl_up_sync(FULL, nd, 1);
+        bool head = (lane == 0) || (prev != nd);
+        if (head && nd >= 0) atomicMax(&r2bits[nd], v);
+    }
+}
+
+__global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, double* __restrict__ rmax) {
+    int nd = blockIdx.x * TB + threadIdx.x;
+    if (nd < nn) rmax[nd] = __dsqrt_rn(__longlong_as_double((long long)r2bits[nd]));
+}
+
+// ------------------------------------------------------------------ host driver
+
+static void ensure_nodes(fmm_ctx* c, int64_t need) {
+    if (need <= c->cap_nodes) return;
+    int64_t cap = need + need / 2 + 1024;
+    size_t b = sizeof(int) * (size_t)cap;
+    ensure_keep(c->nfirst, b, c->stream);
+    ensure_keep(c->ncount, b, c->stream);
+    ensure_keep(c->nlevel, b, c->stream);
+    ensure_keep(c->nparent, b, c->stream);
+    ensure_keep(c->nchildf, b, c->stream);
+    ensure_keep(c->nnchild, b, c->stream);
+    c->cap_nodes = cap;
+}
+
+int build_tree(fmm_ctx* c, const double* x, const double* m) {
+    cudaStream_t s = c->stream;
+    int n = (int)c->N;
+    // a1: bounding cube and validation
+    int nb = (int)((c->N + TB - 1) / TB);
+    if (nb > 1024) nb = 1024;
+    ensure(c->geom, sizeof(double) * (size_t)(8 + 6 * nb));
+    ensure(c->errflag, sizeof(int) * 4);
+    double* geom = c->geom.as<double>();
+    double* part = geom + 8;
+    GB_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int) * 4, s));
+    bbox_partial_k<<<nb, TB, 0, s>>>(x, m, c->N, part, c->errflag.as<int>());
+    GB_LAUNCH("bbox_partial_k");
+    bbox_final_k<<<1, 32, 0, s>>>(part, nb, geom);
+    GB_LAUNCH("bbox_final_k");
+    int bad = 0;
+    GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (bad) return FMM_ERR_INVALID;
+    // a2: keys; a3: sort
+    ensure(c->keys0, sizeof(uint64_t) * (size_t)n);
+    ensure(c->vals0, sizeof(uint32_t) * (size_t)n);
+    keys_k<<<grid_for(n, TB), TB, 0, s>>>(x, n, geom, c->keys0.as<uint64_t>(), c->vals0.as<uint32_t>());
+    GB_LAUNCH("keys_k");
+    radix_sort(c, c->keys0, c->keys1, &c->vals0, &c->vals1, n, 63);
+    ensure(c->perm, sizeof(uint32_t) * (size_t)n);
+    GB_CUDA(cudaMemcpyAsync(c->perm.p, c->vals0.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    ensure(c->xs, sizeof(double) * (size_t)n);
+    ensure(c->ys, sizeof(double) * (size_t)n);
+    ensure(c->zs, sizeof(double) * (size_t)n);
+    ensure(c->ms, sizeof(double) * (size_t)n);
+    gather_k<<<grid_for(n, TB), TB, 0, s>>>(x, m, c->perm.as<uint32_t>(), n, c->xs.as<double>(),
+                                            c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>());
+    GB_LAUNCH("gather_k");
+    // a4: octree, level by level (breadth-first ids)
+    const uint64_t* keys = c->keys0.as<uint64_t>();
+    ensure_nodes(c, (int64_t)n / 4 + 64);
+    ensure(c->cur, sizeof(int) * (size_t)n);
+    ensure(c->flags, sizeof(int) * (size_t)n);
+    ensure(c->scan_out, sizeof(int) * (size_t)(n + 1));
+    ensure(c->leaf_of, sizeof(int) * (size_t)n);
+    ensure(c->nal, sizeof(int) * (size_t)n * (MAX_LEVEL + 1));
+    root_k<<<1, 1, 0, s>>>(n, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(), c->nparent.as<int>(),
+                           c->nchildf.as<int>(), c->nnchild.as<int>());
+    GB_LAUNCH("root_k");
+    fill_int_k<<<grid_for(n, TB), TB, 0, s>>>(c->cur.as<int>(), n, 0);
+    GB_LAUNCH("fill_int_k");
+    c->level_start.assign(1, 0);
+    c->level_start.push_back(1);
+    int64_t n_nodes = 1;
+    int level = 0;
+    for (;; level++) {
+        int* nal_l = c->nal.as<int>() + (int64_t)level * n;
+        tree_mark_k<<<grid_for(n, TB), TB, 0, s>>>(keys, n, level, c->leaf, c->cur.as<int>(), c->nfirst.as<int>(),
+                                                   c->ncount.as<int>(), c->flags.as<int>(), nal_l);
+        GB_LAUNCH("tree_mark_k");
+        if (level >= MAX_LEVEL) break;
+        scan_int(c, c->flags.as<int>(), n, c->scan_out.as<int>());
+        int total = 0;
+        GB_CUDA(cudaMemcpyAsync(&total, c->scan_out.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        if (total == 0) break;
+        ensure_nodes(c, n_nodes + total);
+        tree_emit_k<<<grid_for(n, TB), TB, 0, s>>>(n, level, c->leaf, (int)n_nodes, c->flags.as<int>(),
+                                                   c->scan_out.as<int>(), c->cur.as<int>(), c->nfirst.as<int>(),
+                                                   c->ncount.as<int>(), c->nlevel.as<int>(), c->nparent.as<int>(),
+                                                   c->nchildf.as<int>(), c->nnchild.as<int>(),
+                                                   c->leaf_of.as<int>());
+        GB_LAUNCH("tree_emit_k");
+        tree_count_k<<<grid_for(total, TB), TB, 0, s>>>((int)n_nodes, total, c->nfirst.as<int>(),
+                                                        c->ncount.as<int>(), c->nparent.as<int>(),
+                                                        c->nchildf.as<int>(), c->nnchild.as<int>());
+        GB_LAUNCH("tree_count_k");
+        n_nodes += total;
+        c->level_start.push_back((int)n_nodes);
+    }
+    // particles still holding a node sit in leaves of the deepest level
+    tree_finish_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->cur.as<int>(), c->leaf_of.as<int>());
+    GB_LAUNCH("tree_finish_k");
+    c->n_levels = (int)c->level_start.size() - 1;
+    c->n_nodes = n_nodes;
+    // centres of mass, bottom-up
+    int nn = (int)n_nodes;
+    size_t db = sizeof(double) * (size_t)nn;
+    for (DevBuf* b : {&c->nM, &c->nSx, &c->nSy, &c->nSz, &c->nZx, &c->nZy, &c->nZz, &c->nrmax}) ensure(*b, db);
+    ensure(c->nr2, sizeof(unsigned long long) * (size_t)nn);
+    com_leaf_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nfirst.as<int>(), c->ncount.as<int>(), c->nnchild.as<int>(),
+                                               c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
+                                               c->ms.as<double>(), c->nM.as<double>(), c->nSx.as<double>(),
+                                               c->nSy.as<double>(), c->nSz.as<double>(), c->nZx.as<double>(),
+                                               c->nZy.as<double>(), c->nZz.as<double>());
+    GB_LAUNCH("com_leaf_k");
+    for (int l = c->n_levels - 2; l >= 0; l--) {
+        int lo = c->level_start[l], hi = c->level_start[l + 1];
+        com_inner_k<<<grid_for(hi - lo, TB), TB, 0, s>>>(lo, hi, c->nfirst.as<int>(), c->nchildf.as<int>(),
+                                                         c->nnchild.as<int>(), c->xs.as<double>(),
+                                                         c->ys.as<double>(), c->zs.as<double>(), c->nM.as<double>(),
+                                                         c->nSx.as<double>(), c->nSy.as<double>(),
+                                                         c->nSz.as<double>(), c->nZx.as<double>(),
+                                                         c->nZy.as<double>(), c->nZz.as<double>());
+        GB_LAUNCH("com_inner_k");
+    }
+    // r_max
+    GB_CUDA(cudaMemsetAsync(c->nr2.p, 0, sizeof(unsigned long long) * (size_t)nn, s));
+    rmax2_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->nal.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+                                           c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
+                                           c->nZz.as<double>(), c->nr2.as<unsigned long long>());
+    GB_LAUNCH("rmax2_k");
+    rmax_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nr2.as<unsigned long long>(), c->nrmax.as<double>());
+    GB_LAUNCH("rmax_k");
+    return FMM_OK;
+}
+
+}  // namespace gbfmm

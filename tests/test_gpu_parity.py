@@ -1,0 +1,274 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Integer work (Morton keys, permutation, tree, interaction lists) and the IEEE-ordered
+geometry (node masses, centres of mass, r_max) must match bit for bit.  Forces and
+potentials must match within a relative L2 error of 1e-12 (binary64 throughout; the two
+sides differ only in summation order and in how the expansion tensors are formed)."""
+import numpy as np
+import pytest
+
+from paper_2107_07166_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def fmm(torch_cuda):
+    from paper_2107_07166_gb300 import fmm as F
+    F.load()
+    return F
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def run_gpu(fmm, torch, x, m, leaf, p, theta, variant, want_pot=True, device_arrays=True):
+    f = fmm.FMM(0)
+    N = x.shape[0]
+    if device_arrays:
+        xd, md = torch.from_numpy(x).cuda(), torch.from_numpy(m).cuda()
+        acc = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        pot = torch.empty(N, dtype=torch.float64, device="cuda") if want_pot else None
+    else:
+        xd, md = x, m
+        acc = np.empty((N, 3))
+        pot = np.empty(N) if want_pot else None
+    f.build(xd, md, leaf)
+    f.forces(p, theta, variant, acc, pot)
+    out = dict(f=f)
+    out["acc"] = acc.cpu().numpy() if hasattr(acc, "cpu") else acc
+    out["pot"] = (pot.cpu().numpy() if hasattr(pot, "cpu") else pot) if want_pot else None
+    return out
+
+
+def check_structure(f, r, N):
+    keys, perm, lo, side = f.get_keys()
+    assert np.array_equal(keys, r.keys)
+    assert np.array_equal(perm, r.perm)
+    assert np.array_equal(lo, r.lo) and side == r.side
+    t = f.get_tree()
+    for k in r.tree:
+        assert np.array_equal(t[k], r.tree[k]), k
+    M, Z, rmax = f.get_geometry()
+    assert np.array_equal(M, r.M)
+    assert np.array_equal(Z, r.Z)
+    assert np.array_equal(rmax, r.rmax)
+    m2l, p2p = f.get_lists()
+    assert np.array_equal(m2l, r.m2l)
+    assert np.array_equal(p2p, r.p2p)
+
+
+CASES = [
+    # name, generator, N, leaf, p, theta
+    ("plummer-4096-cfg", lambda n: synth.plummer(n, 1), 4096, 16, 2, 0.5),
+    ("plummer-ragged", lambda n: synth.plummer(n, 5), 3001, 7, 3, 0.6),
+    ("hernquist", lambda n: synth.hernquist(n, 6), 2500, 32, 4, 0.6),
+    ("disk", lambda n: synth.disk_bulge(n, 7), 4000, 24, 5, 0.7),
+    ("binary", lambda n: synth.binary(n // 2, 3, 4), 3000, 16, 6, 0.5),
+]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_parity_against_oracle(fmm, torch_cuda, orc, case, variant):
+    name, gen, N, leaf, p, theta = case
+    x, m = gen(N)
+    r = orc.run(x, m, leaf, p, theta, variant, want_pot=True)
+    g = run_gpu(fmm, torch_cuda, x, m, leaf, p, theta, variant)
+    check_structure(g["f"], r, N)
+    assert rel(g["acc"], r.acc) < TOL
+    assert rel(g["pot"], r.pot) < TOL
+    g["f"].close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_every_order(fmm, torch_cuda, orc, p):
+    x, m = synth.plummer(2048, 10 + p)
+    for variant in (0, 1):
+        r = orc.run(x, m, 12, p, 0.55, variant, want_pot=True, want_internals=False)
+        g = run_gpu(fmm, torch_cuda, x, m, 12, p, 0.55, variant)
+        assert rel(g["acc"], r.acc) < TOL, (p, variant)
+        assert rel(g["pot"], r.pot) < TOL, (p, variant)
+        g["f"].close()
+
+
+def test_theta_zero_equals_direct_sum(fmm, torch_cuda, orc):
+    x, m = synth.plummer(1500, 8)
+    a, ph = orc.direct(x, m)
+    for variant in (0, 1):
+        g = run_gpu(fmm, torch_cuda, x, m, 6, 3, 0.0, variant)
+        assert rel(g["acc"], a) < 1e-13
+        assert rel(g["pot"], ph) < 1e-13
+        g["f"].close()
+
+
+def test_host_and_device_buffers_agree(fmm, torch_cuda):
+    x, m = synth.plummer(3000, 9)
+    a = run_gpu(fmm, torch_cuda, x, m, 16, 4, 0.6, 1, device_arrays=True)
+    b = run_gpu(fmm, torch_cuda, x, m, 16, 4, 0.6, 1, device_arrays=False)
+    assert np.array_equal(a["acc"], b["acc"])
+    assert np.array_equal(a["pot"], b["pot"])
+
+
+def test_run_to_run_bitwise_identical(fmm, torch_cuda):
+    x, m = synth.plummer(20000, 12)
+    a = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, 1)
+    b = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, 1)
+    assert np.array_equal(a["acc"], b["acc"])
+    # the same context re-used with another p / theta / variant, then back
+    f = a["f"]
+    acc = np.empty((20000, 3))
+    f.forces(2, 0.4, 0, acc, None)
+    f.forces(4, 0.6, 1, acc, None)
+    assert np.array_equal(acc, a["acc"])
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 33])
+def test_tiny_inputs(fmm, torch_cuda, orc, N):
+    x, m = synth.plummer(max(N, 2), 30 + N)
+    x, m = np.ascontiguousarray(x[:N]), np.ascontiguousarray(m[:N])
+    for variant in (0, 1):
+        r = orc.run(x, m, 1, 2, 0.5, variant, want_pot=True)
+        g = run_gpu(fmm, torch_cuda, x, m, 1, 2, 0.5, variant)
+        check_structure(g["f"], r, N)
+        assert np.allclose(g["acc"], r.acc, rtol=1e-12, atol=1e-300)
+        g["f"].close()
+
+
+def test_coincident_and_massless_particles(fmm, torch_cuda, orc):
+    """Duplicated positions force leaves at the deepest level (21) holding more than
+    leaf_size particles; zero masses exercise the massless-node centre."""
+    rng = np.random.default_rng(4)
+    base = rng.normal(size=(300, 3))
+    x = np.concatenate([base, np.repeat(base[:3], 40, axis=0), np.zeros((45, 3))])
+    m = rng.random(x.shape[0])
+    m[::7] = 0.0
+    m[-45:] = 0.0
+    for variant in (0, 1):
+        r = orc.run(x, m, 4, 3, 0.5, variant, want_pot=True)
+        assert r.tree["level"].max() == 21
+        g = run_gpu(fmm, torch_cuda, x, m, 4, 3, 0.5, variant)
+        check_structure(g["f"], r, x.shape[0])
+        assert rel(g["acc"], r.acc) < TOL
+        assert rel(g["pot"], r.pot) < TOL
+        g["f"].close()
+
+
+def test_all_particles_identical(fmm, torch_cuda, orc):
+    x = np.ones((50, 3))
+    m = np.full(50, 0.02)
+    r = orc.run(x, m, 8, 2, 0.5, 0, want_pot=True)
+    g = run_gpu(fmm, torch_cuda, x, m, 8, 2, 0.5, 0)
+    check_structure(g["f"], r, 50)
+    assert np.all(g["acc"] == 0.0) and np.all(g["pot"] == 0.0)
+
+
+def test_diagnostics_and_conservation(fmm, torch_cuda):
+    x, m = synth.plummer(50000, 13)
+    for variant in (0, 1):
+        g = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, variant, want_pot=False)
+        F, T = g["f"].diagnostics()
+        a = g["acc"]
+        Fn = (m[:, None] * a).sum(0)
+        Tn = (m[:, None] * np.cross(x, a)).sum(0)
+        fs = (m * np.linalg.norm(a, axis=1)).sum()
+        ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+        assert np.allclose(F, Fn, rtol=0, atol=1e-13 * fs)
+        assert np.allclose(T, Tn, rtol=0, atol=1e-13 * ts)
+        assert np.linalg.norm(F) < 1e-14 * fs
+        if variant == 1:
+            assert np.linalg.norm(T) < 1e-14 * ts
+        else:
+            assert np.linalg.norm(T) > 1e-9 * ts
+        g["f"].close()
+
+
+def test_errors_leave_outputs_untouched(fmm, torch_cuda):
+    x, m = synth.plummer(1000, 14)
+    f = fmm.FMM(0)
+    acc = np.full((1000, 3), 7.0)
+    with pytest.raises(fmm.FMMError) as e:
+        f.forces(2, 0.5, 0, acc, None)          # before build
+    assert e.value.status == -2
+    f.build(x, m, 16)
+    for p, th, v in ((0, 0.5, 0), (fmm.P_MAX + 1, 0.5, 0), (2, 1.0, 0), (2, -0.1, 0), (2, 0.5, 3)):
+        with pytest.raises(fmm.FMMError) as e:
+            f.forces(p, th, v, acc, None)
+        assert e.value.status == -1
+    assert np.all(acc == 7.0)
+    bad = x.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(fmm.FMMError) as e:
+        f.build(bad, m, 16)
+    assert e.value.status == -1
+    mneg = m.copy()
+    mneg[3] = -1.0
+    with pytest.raises(fmm.FMMError):
+        f.build(x, mneg, 16)
+    f.close()
+
+
+# ------------------------------------------------------------- full-size workload
+
+def test_full_size_plummer_1m(fmm, torch_cuda, orc):
+    """The benchmark workload (Plummer N = 2^20, p = 4, theta = 0.6, leaf 32): structural
+    properties that hold at any size, conservation, and the error against the direct sum
+    on sampled targets."""
+    torch = torch_cuda
+    N = 1 << 20
+    x, m = synth.plummer(N, 2)
+    f = fmm.FMM(0)
+    xd, md = torch.from_numpy(x).cuda(), torch.from_numpy(m).cuda()
+    f.build(xd, md, 32)
+    keys, perm, lo, side = f.get_keys()
+    assert np.all(keys[1:] >= keys[:-1])
+    assert np.array_equal(np.sort(perm), np.arange(N))
+    t = f.get_tree()
+    leaves = t["nchild"] == 0
+    assert t["count"][leaves].sum() == N
+    assert np.all((t["count"][leaves] <= 32) | (t["level"][leaves] == 21))
+    rng = np.random.default_rng(0)
+    tg = rng.choice(N, 400, replace=False)
+    ad, _ = orc.direct_targets(x, m, tg)
+    for variant in (0, 1):
+        acc = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        f.forces(4, 0.6, variant, acc, None)
+        a = acc.cpu().numpy()
+        m2l, p2p = f.get_lists()
+        c = t["count"].astype(np.int64)
+        selfp = p2p[:, 0] == p2p[:, 1]
+        tot = (c[m2l[:, 0]] * c[m2l[:, 1]]).sum()
+        tot += np.where(selfp, c[p2p[:, 0]] * (c[p2p[:, 0]] - 1) // 2, c[p2p[:, 0]] * c[p2p[:, 1]]).sum()
+        assert tot == N * (N - 1) // 2                   # every particle pair exactly once
+        err = rel(a[tg], ad)
+        assert err < (2e-4 if variant == 0 else 1e-3), err
+        F, T = f.diagnostics()
+        fs = (m * np.linalg.norm(a, axis=1)).sum()
+        ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+        assert np.linalg.norm(F) < 1e-14 * fs
+        if variant == 1:
+            assert np.linalg.norm(T) < 1e-14 * ts
+    f.close()
+
+
+def test_medium_size_bitexact_lists(fmm, torch_cuda, orc):
+    """N = 2^17 Plummer at the benchmark's p, theta and leaf size: keys, tree and lists
+    bit-exact and forces within tolerance for the conserving variant."""
+    x, m = synth.plummer(1 << 17, 2)
+    r = orc.run(x, m, 32, 4, 0.6, 1, want_pot=False)
+    g = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, 1, want_pot=False)
+    check_structure(g["f"], r, 1 << 17)
+    assert rel(g["acc"], r.acc) < TOL
+    g["f"].close()
