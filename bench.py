@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="plummer-1m-conserving", N=1 << 20, seed=2, p=4, theta=0.6, leaf=32,
                 variant="conserving", precision="fp64")
 METRIC = "particles/s, AM-conserving FMM force eval, N=1M p=4 θ=0.6; force err; |Σx×F|"
-CPU_SAMPLE_N = 1 << 17          # oracle sample: same generator, p, theta, leaf; ~10-20 s of CPU
+CPU_SAMPLE_N = 1 << 19          # oracle sample: same generator, p, theta, leaf; ~15 s of CPU
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 
 

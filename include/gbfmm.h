@@ -72,7 +72,9 @@ enum {
 };
 
 /* Create a context on CUDA device `device` with arithmetic `precision` (FMM_FP64).
- * `cuda_stream` is a cudaStream_t to queue work on, or NULL for a private stream. */
+ * `cuda_stream` is the cudaStream_t to queue work on (cudaStreamLegacy and
+ * cudaStreamPerThread are accepted), or NULL for a private non-blocking stream.  Device
+ * outputs are complete once that stream has reached the end of the call's work. */
 GBFMM_API int fmm_create(fmm_ctx **out, int device, int precision, void *cuda_stream);
 
 /* Release the context and all device memory it holds.  NULL is accepted. */

@@ -116,11 +116,13 @@ class FMM:
 
     @staticmethod
     def _stream_ptr(stream):
+        """None -> private library stream; a torch stream or raw handle otherwise.  The
+        legacy default stream (handle 0) is passed as cudaStreamLegacy (1), because a NULL
+        handle asks the library for a private stream."""
         if stream is None:
             return None
-        if hasattr(stream, "cuda_stream"):
-            return C.c_void_p(stream.cuda_stream)
-        return C.c_void_p(int(stream))
+        h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        return C.c_void_p(h if h != 0 else 1)
 
     def close(self):
         if getattr(self, "h", None):
@@ -151,7 +153,7 @@ class FMM:
         self.N = n
 
     def forces(self, p: int, theta: float, variant: int, acc, pot=None):
-        if tuple(acc.shape) != (self.N, 3) or (pot is not None and tuple(pot.shape) != (self.N,)):
+        if self.N and (tuple(acc.shape) != (self.N, 3) or (pot is not None and tuple(pot.shape) != (self.N,))):
             raise ValueError("acc must be (N, 3) and pot (N,)")
         _check(self.lib.fmm_forces(self.h, int(p), float(theta), int(variant), _ptr(acc, np.float64),
                                    _ptr(pot, np.float64)), "fmm_forces")
