@@ -128,6 +128,33 @@ GBFMM_API int fmm_get_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p);
  * A stage that did not run in that call reports -1. */
 GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
 
+/* Largest N accepted by fmm_morton_sort_noalloc. */
+#define FMM_NOALLOC_MAX_N 131072
+
+/* Bounding cube, Morton keys and stable sort of fmm_build, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a service entry point.
+ *
+ * Who needs it: code that must not call cudaMalloc/cudaFree -- they can synchronise the
+ * whole device and are not allowed while a stream is being captured -- and hosts that
+ * hand out all device memory from their own pool or budget it up front.  The call
+ * allocates nothing: its scratch is one fixed array of about 2.1 MiB in the library's
+ * device image, which every GPU that loads the library holds until the process exits.
+ *
+ *   x: N x 3 row-major positions, device memory; 1 <= N <= FMM_NOALLOC_MAX_N.
+ *   keys_sorted[N] (device): the 63-bit Morton keys in stable sorted order.
+ *   perm[N] (device): input index of each sorted particle.
+ *   lo[3], side[1] (device, either may be NULL): the bounding cube.
+ *   cuda_stream: stream to queue the work on (NULL: the legacy default stream); the call
+ *   returns after that stream has finished it.
+ * Results equal those of fmm_build followed by fmm_get_keys on the same positions.
+ * Returns FMM_ERR_CAPACITY for N above the maximum, FMM_ERR_INVALID for NULL or host
+ * arrays, N < 1, or a non-finite coordinate (outputs are then unspecified).
+ * The first call on each device looks up the scratch array's address there; make that
+ * first call before any stream capture.  All calls share the one array, so calls whose
+ * GPU work overlaps (different streams or threads) race: serialise them. */
+GBFMM_API int fmm_morton_sort_noalloc(const double *x, int64_t N, uint64_t *keys_sorted, int64_t *perm,
+                                      double *lo, double *side, void *cuda_stream);
+
 /* Number of CUDA kernels this library has launched in this process so far (all contexts). */
 GBFMM_API int64_t fmm_kernel_launches(void);
 

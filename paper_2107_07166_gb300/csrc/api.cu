@@ -22,6 +22,10 @@ using namespace gbfmm;
 
 static thread_local std::string g_last_error;
 
+namespace gbfmm {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace gbfmm
+
 static int fail(int code, const std::string& msg) {
     g_last_error = msg;
     return code;

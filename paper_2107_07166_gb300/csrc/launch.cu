@@ -146,6 +146,21 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
     }
 }
 
+// One stable 8-bit pass of keys + 32-bit payloads on caller-provided buffers: hist and
+// offs hold 256 * ntiles + 1 entries, sums (256 * ntiles) / SCAN_TILE + 2.  Allocates nothing.
+void rs_pass_raw(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n, int shift,
+                 uint32_t* hist, int* offs, int* sums, cudaStream_t s) {
+    int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    int64_t nh = (int64_t)256 * ntiles;
+    int nst = (int)((nh + SCAN_TILE - 1) / SCAN_TILE);
+    rs_hist_k<<<ntiles, RS_BLOCK, 0, s>>>(kin, n, shift, hist, ntiles);
+    scan_tiles_k<int, int><<<nst, SCAN_BLOCK, 0, s>>>(reinterpret_cast<const int*>(hist), nh, sums);
+    scan_sums_k<int><<<1, SCAN_BLOCK, 0, s>>>(sums, nst);
+    scan_apply_k<int, int><<<nst, SCAN_BLOCK, 0, s>>>(reinterpret_cast<const int*>(hist), nh, sums, offs);
+    rs_scatter_k<true><<<ntiles, RS_BLOCK, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                   reinterpret_cast<const uint32_t*>(offs), ntiles);
+}
+
 void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits) {
     if (n <= 1 || bits <= 0) return;
     if (n >= (int64_t)1 << 31) throw FmmError{FMM_ERR_CAPACITY, "radix sort: more than 2^31 keys"};

@@ -28,7 +28,9 @@ P_MAX = 6
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_forces", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
-           "fmm_stage_times", "fmm_kernel_launches", "fmm_strerror", "fmm_last_error")
+           "fmm_stage_times", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_last_error")
+NOALLOC_MAX_N = 131072
 
 _lock = threading.Lock()
 _lib = None
@@ -63,6 +65,7 @@ def load(path: str = LIB_PATH):
             "fmm_get_geometry": (i32, [P, P, P, P]),
             "fmm_get_lists": (i32, [P, P, P]),
             "fmm_stage_times": (i32, [P, P, i32]),
+            "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
             "fmm_strerror": (C.c_char_p, [i32]),
             "fmm_last_error": (C.c_char_p, []),
