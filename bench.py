@@ -138,7 +138,11 @@ def run_gbfmm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.n:
+        W["N"] = args.n
+        W["workload"] = f"plummer-{args.n}-{args.variant}"
+    W["variant"] = args.variant
     N = W["N"]
     x, m = synth.plummer(N, W["seed"])
     xd = torch.from_numpy(x).to(dev)
@@ -146,7 +150,7 @@ def run_gbfmm(args):
     acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     f = fmm.FMM(local, fmm.FP64, stream)
-    variant = fmm.CONSERVING
+    variant = fmm.CONSERVING if args.variant == "conserving" else fmm.STANDARD
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -161,7 +165,7 @@ def run_gbfmm(args):
     # structure counts for the algorithmic work model (not timed)
     tree = f.get_tree()
     lists = f.get_lists()
-    work = algorithmic_flops(lists, tree["count"].astype(np.int64), W["p"], 1)
+    work = algorithmic_flops(lists, tree["count"].astype(np.int64), W["p"], variant)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -232,10 +236,11 @@ def run_gbfmm(args):
     peak = fp64_peak_tflops(2070.0)
     achieved = work[dom] / (stage_avg[dom] / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": f"{dom}_con_k" if dom == "m2l" else "p2p_k",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": ("m2l_con_k" if variant == 1 else "m2l_std_k") if dom == "m2l" else "p2p_k",
                 "peak_basis": "binary64 FMA rate derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz",
                 "sm_mhz_median": sm_mhz}
-    cpu = cpu_baseline() if (args.cpu_baseline and world == 1) else None
+    cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n) else None
     rng = np.random.default_rng(0)
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
@@ -318,6 +323,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--n", type=int, default=0, help="override N (profiling of a smaller case)")
+    ap.add_argument("--variant", default="conserving", choices=["conserving", "standard"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
