@@ -220,6 +220,7 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
         double* acc_d = acc_dev ? acc : c->out_stage.as<double>();
         double* pot_d = want_pot ? (pot_dev ? pot : c->out_stage.as<double>() + 3 * n) : nullptr;
         stage_begin(c, ST_L2P);
+        run_p2p_gather(c);
         run_finish_dispatch(c, p, variant, want_pot, acc_d, pot_d);
         stage_end(c, ST_L2P);
         if (!acc_dev)

@@ -57,58 +57,84 @@ __global__ void __launch_bounds__(EB) m2m_k(int lo, int hi, const int* __restric
     for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
 }
 
-// a8 M2L, standard: every cell accumulates D(Z_tgt - Z_src) contracted with the source
-// moments over its directed entries, in increasing source id (deterministic order).
+// a8 M2L, standard, one work item = up to M2L_CHUNK directed entries of one target cell
+// (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src).
+// The item's partial local goes to part[item]; m2l_reduce_k sums a cell's items in order.
 template <int P>
-__global__ void __launch_bounds__(EB) m2l_std_k(int nn, const uint64_t* __restrict__ dir,
-                                                const long long* __restrict__ seg, int bits,
+__global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __restrict__ items,
+                                                const uint64_t* __restrict__ dir, int bits,
                                                 const double* __restrict__ Zx, const double* __restrict__ Zy,
                                                 const double* __restrict__ Zz, const double* __restrict__ mom,
-                                                double* __restrict__ loc) {
+                                                double* __restrict__ part) {
     using E = Exp<P>;
-    int nd = blockIdx.x * EB + threadIdx.x;
-    if (nd >= nn) return;
+    int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
     double L[E::NM];
 #pragma unroll
     for (int k = 0; k < E::NM; k++) L[k] = 0.0;
-    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
-    long long e0 = seg[nd], e1 = seg[nd + 1];
-    for (long long e = e0; e < e1; e++) {
+    for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
         double D[E::NM];
         E::dtensor(zx - Zx[src], zy - Zy[src], zz - Zz[src], D);
         E::m2l_std(mom + (int64_t)src * E::NM, D, L);
     }
 #pragma unroll
-    for (int k = 0; k < E::NM; k++) loc[(int64_t)nd * E::NM + k] = L[k];
+    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = L[k];
 }
 
-// a8' M2L, conserving: S and U of the realigned pair forces
+// a8' M2L, conserving: S and U of the realigned pair forces, from conserving moments
 template <int P>
-__global__ void __launch_bounds__(EB) m2l_con_k(int nn, const uint64_t* __restrict__ dir,
-                                                const long long* __restrict__ seg, int bits,
+__global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __restrict__ items,
+                                                const uint64_t* __restrict__ dir, int bits,
                                                 const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz, const double* __restrict__ mom,
-                                                double* __restrict__ loc) {
+                                                const double* __restrict__ Zz, const double* __restrict__ cmom,
+                                                double* __restrict__ part) {
     using E = Exp<P>;
-    int nd = blockIdx.x * EB + threadIdx.x;
-    if (nd >= nn) return;
+    int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
     double SU[E::NSU];
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) SU[k] = 0.0;
-    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
-    long long e0 = seg[nd], e1 = seg[nd + 1];
-    for (long long e = e0; e < e1; e++) {
+    for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
         double rx = zx - Zx[src], ry = zy - Zy[src], rz = zz - Zz[src];
         double H[E::NQ];
         E::htensor(rx, ry, rz, H);
-        E::m2l_con(mom + (int64_t)src * E::NM, H, rx, ry, rz, SU);
+        E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
     }
 #pragma unroll
-    for (int k = 0; k < E::NSU; k++) loc[(int64_t)nd * E::NSU + k] = SU[k];
+    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = SU[k];
+}
+
+// a9: loc[x][k] = sum over the cell's items (full chunks in order, then the partial one)
+template <int NL>
+__global__ void m2l_reduce_k(int nn, const long long* __restrict__ fo, const long long* __restrict__ po,
+                             long long nfull, const double* __restrict__ part, double* __restrict__ loc) {
+    int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (t >= (int64_t)nn * NL) return;
+    int x = (int)(t / NL), k = (int)(t - (int64_t)x * NL);
+    double acc = 0.0;
+    for (long long i = fo[x]; i < fo[x + 1]; i++) acc += part[i * NL + k];
+    if (po[x + 1] > po[x]) acc += part[(nfull + po[x]) * NL + k];
+    loc[t] = acc;
+}
+
+// conserving source moments of every cell (formed once per moment build)
+template <int P>
+__global__ void __launch_bounds__(EB) con_moments_k(int nn, const double* __restrict__ mom, double* __restrict__ cmom) {
+    using E = Exp<P>;
+    int nd = blockIdx.x * EB + threadIdx.x;
+    if (nd >= nn) return;
+    double C[E::NSU];
+    E::con_moments(mom + (int64_t)nd * E::NM, C);
+#pragma unroll
+    for (int k = 0; k < E::NSU; k++) cmom[(int64_t)nd * E::NSU + k] = C[k];
 }
 
 // a10 L2L, one level: child += shift(parent) by s = Z_child - Z_parent
@@ -160,22 +186,19 @@ __global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __res
     }
 }
 
-// a11 + a13: far field at every particle from its leaf's locals, plus the P2P partials
-// of every directed entry of the leaf (increasing partner id), written in input order.
-//   part[] holds double4 (ax, ay, az, phi) per (pair, side, slot); pair k's block starts
-//   at off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+// a11 + a13: far field at every particle from its leaf's locals, plus the leaf's P2P item
+// sums (full chunks in order, then the partial one), written in input order.
 template <int P, int V>
 __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ leaf_of, const int* __restrict__ nfirst,
-                                               const int* __restrict__ ncount, const double* __restrict__ xs,
-                                               const double* __restrict__ ys, const double* __restrict__ zs,
-                                               const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                               const double* __restrict__ Zz, const double* __restrict__ loc,
-                                               const double* __restrict__ locp, const uint32_t* __restrict__ pdval,
-                                               const long long* __restrict__ pseg, const int2* __restrict__ pairs,
-                                               const long long* __restrict__ poff, const double4* __restrict__ part,
-                                               const uint32_t* __restrict__ perm, double* __restrict__ acc_s,
-                                               double* __restrict__ pot_s, double* __restrict__ acc_out,
-                                               double* __restrict__ pot_out) {
+                                               const double* __restrict__ xs, const double* __restrict__ ys,
+                                               const double* __restrict__ zs, const double* __restrict__ Zx,
+                                               const double* __restrict__ Zy, const double* __restrict__ Zz,
+                                               const double* __restrict__ loc, const double* __restrict__ locp,
+                                               const long long* __restrict__ fo, const long long* __restrict__ po,
+                                               long long nfull, const long long* __restrict__ islot,
+                                               const double4* __restrict__ ipart, const uint32_t* __restrict__ perm,
+                                               double* __restrict__ acc_s, double* __restrict__ pot_s,
+                                               double* __restrict__ acc_out, double* __restrict__ pot_out) {
     using E = Exp<P>;
     int i = blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
@@ -193,11 +216,15 @@ __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ le
         }
     }
     double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
-    for (long long e = pseg[lf]; e < pseg[lf + 1]; e++) {
-        uint32_t v = pdval[e];
-        uint32_t k = v >> 1;
-        long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
-        double4 q = part[o];
+    for (long long k = fo[lf]; k < fo[lf + 1]; k++) {
+        double4 q = ipart[islot[k] + slot];
+        px += q.x;
+        py += q.y;
+        pz += q.z;
+        pp += q.w;
+    }
+    if (po[lf + 1] > po[lf]) {
+        double4 q = ipart[islot[nfull + po[lf]] + slot];
         px += q.x;
         py += q.y;
         pz += q.z;
@@ -239,6 +266,9 @@ void run_moments_p(fmm_ctx* c) {
                                                       c->mom.as<double>());
         GB_LAUNCH("m2m_k");
     }
+    ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
+    con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
+    GB_LAUNCH("con_moments_k");
 }
 
 template <int P>
@@ -247,23 +277,37 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
     const uint64_t* dir = c->m2l_dir.as<uint64_t>();
-    const long long* seg = c->m2l_seg.as<long long>();
+    const ItemSet& it = c->m2l_items;
+    int64_t ni = it.n_items;
     bool std_locals = (variant == 0) || want_pot;
     stage_begin(c, ST_M2L);
+    int nl_max = E::NSU > E::NM ? E::NSU : E::NM;
+    ensure(c->m2l_part, sizeof(double) * (size_t)(ni > 0 ? ni : 1) * nl_max);
+    double* part = c->m2l_part.as<double>();
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
-        m2l_con_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, dir, seg, c->id_bits, c->nZx.as<double>(),
-                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
-                                                     c->loc.as<double>());
-        GB_LAUNCH("m2l_con_k");
+        if (ni > 0) {
+            m2l_con_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, c->nZx.as<double>(),
+                                                         c->nZy.as<double>(), c->nZz.as<double>(),
+                                                         c->cmom.as<double>(), part);
+            GB_LAUNCH("m2l_con_k");
+        }
+        m2l_reduce_k<E::NSU><<<grid_for((int64_t)nn * E::NSU, EB), EB, 0, s>>>(
+            nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, c->loc.as<double>());
+        GB_LAUNCH("m2l_reduce_k");
     }
     if (std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
-        m2l_std_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, dir, seg, c->id_bits, c->nZx.as<double>(),
-                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
-                                                     L.as<double>());
-        GB_LAUNCH("m2l_std_k");
+        if (ni > 0) {
+            m2l_std_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, c->nZx.as<double>(),
+                                                         c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
+                                                         part);
+            GB_LAUNCH("m2l_std_k");
+        }
+        m2l_reduce_k<E::NM><<<grid_for((int64_t)nn * E::NM, EB), EB, 0, s>>>(
+            nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, L.as<double>());
+        GB_LAUNCH("m2l_reduce_k");
     }
     stage_end(c, ST_M2L);
     stage_begin(c, ST_L2L);
@@ -290,14 +334,16 @@ template <int P>
 void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
     cudaStream_t s = c->stream;
     int n = (int)c->N;
+    const ItemSet& it = c->p2p_items;
+    int64_t ni = it.n_items;
     const double* locp = (variant == 1 && want_pot) ? c->locp.as<double>() : nullptr;
     auto args = [&](auto kern) {
         kern<<<grid_for(n, EB), EB, 0, s>>>(
-            n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
-            c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->loc.as<double>(),
-            locp, c->p2p_dval.as<uint32_t>(), c->p2p_seg.as<long long>(), c->p2p_pairs.as<int2>(),
-            c->p2p_off.as<long long>(), c->p2p_part.as<double4>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(),
-            c->pot_s.as<double>(), acc_out, want_pot ? pot_out : nullptr);
+            n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
+            c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->loc.as<double>(), locp,
+            it.fo.as<long long>(), it.po.as<long long>(), it.n_full, c->p2p_islot.as<long long>(),
+            c->p2p_ipart.as<double4>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
+            want_pot ? pot_out : nullptr);
     };
     if (variant == 0)
         args(finish_k<P, 0>);

@@ -47,6 +47,17 @@ struct NodeView {
     const double* rmax;
 };
 
+// Chunked work over per-cell segments (see build_items in walk.cu).
+struct ItemSet {
+    DevBuf items;   // int4 (cell, entry begin, entry end, -)
+    DevBuf fo, po;  // long long [n + 1]: full-chunk offsets, partial-chunk ranks
+    int64_t n_full = 0, n_items = 0;
+    int chunk = 0;
+};
+
+constexpr int M2L_CHUNK = 32;
+constexpr int P2P_CHUNK = 64;
+
 enum Stage {
     ST_BUILD = 0,   // bounding cube .. r_max
     ST_MOMENTS,     // P2M + M2M
@@ -100,6 +111,11 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_off;                     // int64 [n_p2p + 1] partial offsets
     gbfmm::DevBuf p2p_part;                    // double4 partials
     gbfmm::DevBuf seg_cnt;
+    gbfmm::ItemSet m2l_items, p2p_items;
+    gbfmm::DevBuf m2l_part;                    // M2L partial locals per item
+    gbfmm::DevBuf p2p_islot;                   // long long [items + 1]: slot offsets of P2P items
+    gbfmm::DevBuf p2p_ipart;                   // double4 per (P2P item, slot)
+    gbfmm::DevBuf cmom;                        // conserving source moments, n_nodes x 4 nmi(p-1)
     int id_bits = 0;
     // results (sorted order) and output staging
     gbfmm::DevBuf acc_s, pot_s;                // SoA: ax | ay | az
@@ -132,6 +148,7 @@ int build_tree(fmm_ctx* c, const double* x_dev, const double* m_dev);
 
 // walk (walk.cu)
 void run_walk(fmm_ctx* c, double theta);
+void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it);
 
 // expansions (expansion_p*.cu, dispatched in expansion.cu)
 void run_moments(fmm_ctx* c, int p);
@@ -139,6 +156,7 @@ void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
 
 // particle-particle + final reduction (p2p.cu)
 void run_p2p(fmm_ctx* c, bool want_pot);
+void run_p2p_gather(fmm_ctx* c);
 void run_gather_out(fmm_ctx* c, int p, int variant, bool want_pot, double* acc_out, double* pot_out);
 void run_diagnostics(fmm_ctx* c, double* out6_host);
 

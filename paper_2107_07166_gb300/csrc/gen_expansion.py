@@ -13,7 +13,9 @@ T (double, or float in mixed precision), for:
   htensor  h_alpha for |alpha| <= p-1 (kernel of the realigned force)
   m2l_std  L_gamma += sum_{|beta|+|gamma|<=p} M_beta D_{beta+gamma}       (eq. taylor)
   m2l_con  S_gamma += s_gamma,  U_gamma += R s_gamma + w_gamma with
-           s_gamma = sum M_beta h_{beta+gamma},  w_{i,gamma} = sum (beta_i+1) M_{beta+e_i} h_{beta+gamma}
+           s_gamma = sum M_beta h_{beta+gamma},  w_{i,gamma} = sum (beta_i+1) M_{beta+e_i} h_{beta+gamma};
+           the (beta_i+1) M_{beta+e_i} factors are formed once per cell (con_moments) and R is
+           folded into them per pair, so U_{i,gamma} += sum_beta (C_{i,beta} + R_i M_beta) h_{beta+gamma}
   p2m      M_alpha += m (-y)^alpha / alpha!
   m2m      M^P_alpha += sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta / beta!
   l2l      L'_gamma += sum_beta L_{gamma+beta} s^beta / beta!
@@ -157,26 +159,38 @@ def m2l_std(p):
     return L
 
 
+def con_moments(p):
+    q = p - 1
+    nq = nmi(q)
+    L = ["  /* conserving source moments: [M_b | (b_x+1) M_{b+e_x} | (b_y+1) M_{b+e_y} | (b_z+1) M_{b+e_z}], |b| <= p-1 */",
+         "  template <class T> __device__ __forceinline__ static void con_moments(const T* __restrict__ M, T* __restrict__ C) {"]
+    for b in mis(q):
+        bi = idx(b)
+        L.append(f"    C[{bi}] = M[{bi}];")
+        L.append(f"    C[{nq + bi}] = T({b[0] + 1}.0) * M[{idx((b[0] + 1, b[1], b[2]))}];")
+        L.append(f"    C[{2 * nq + bi}] = T({b[1] + 1}.0) * M[{idx((b[0], b[1] + 1, b[2]))}];")
+        L.append(f"    C[{3 * nq + bi}] = T({b[2] + 1}.0) * M[{idx((b[0], b[1], b[2] + 1))}];")
+    L.append("  }")
+    return L
+
+
 def m2l_con(p):
     q = p - 1
     nq = nmi(q)
-    L = ["  /* conserving M2L: s = sum M_beta h_{beta+gamma}; w_i = sum (beta_i+1) M_{beta+e_i} h_{beta+gamma};",
-         "     S += s, U_i += R_i s + w_i.  SU layout: [S (nq) | Ux | Uy | Uz] */",
-         "  template <class T, class A> __device__ __forceinline__ static void m2l_con(const T* __restrict__ M, const T* __restrict__ H, T rx, T ry, T rz, A* __restrict__ SU) {"]
-    for g in mis(q):
-        gi = idx(g)
-        rem = q - sum(g)
-        L.append(f"    {{ T s = T(0), wx = T(0), wy = T(0), wz = T(0);")
-        for b in mis(rem):
+    L = ["  /* conserving M2L from conserving moments C (see con_moments): with the per-pair",
+         "     M''_{i,b} = C_{i,b} + R_i M_b,  S_g += sum_b M_b h_{b+g},  U_{i,g} += sum_b M''_{i,b} h_{b+g}",
+         "     (= R_i s_g + w_{i,g}).  SU layout: [S (nq) | Ux | Uy | Uz] */",
+         "  template <class T, class A> __device__ __forceinline__ static void m2l_con(const T* __restrict__ C, const T* __restrict__ H, T rx, T ry, T rz, A* __restrict__ SU) {"]
+    for b in mis(q):
+        bi = idx(b)
+        rem = q - sum(b)
+        L.append(f"    {{ const T m = C[{bi}];")
+        L.append(f"      const T mx = fma_t(rx, m, C[{nq + bi}]), my = fma_t(ry, m, C[{2 * nq + bi}]), mz = fma_t(rz, m, C[{3 * nq + bi}]);")
+        for g in mis(rem):
+            gi = idx(g)
             hb = f"H[{idx((b[0] + g[0], b[1] + g[1], b[2] + g[2]))}]"
-            L.append(f"      s = fma_t(M[{idx(b)}], {hb}, s);")
-            L.append(f"      wx = fma_t(T({b[0] + 1}.0) * M[{idx((b[0] + 1, b[1], b[2]))}], {hb}, wx);")
-            L.append(f"      wy = fma_t(T({b[1] + 1}.0) * M[{idx((b[0], b[1] + 1, b[2]))}], {hb}, wy);")
-            L.append(f"      wz = fma_t(T({b[2] + 1}.0) * M[{idx((b[0], b[1], b[2] + 1))}], {hb}, wz);")
-        L.append(f"      SU[{gi}] += s;")
-        L.append(f"      SU[{nq + gi}] += fma_t(rx, s, wx);")
-        L.append(f"      SU[{2 * nq + gi}] += fma_t(ry, s, wy);")
-        L.append(f"      SU[{3 * nq + gi}] += fma_t(rz, s, wz);")
+            L.append(f"      SU[{gi}] = fma_t(m, {hb}, SU[{gi}]); SU[{nq + gi}] = fma_t(mx, {hb}, SU[{nq + gi}]);"
+                     f" SU[{2 * nq + gi}] = fma_t(my, {hb}, SU[{2 * nq + gi}]); SU[{3 * nq + gi}] = fma_t(mz, {hb}, SU[{3 * nq + gi}]);")
         L.append("    }")
     L.append("  }")
     return L
@@ -286,6 +300,7 @@ def header(p):
     out += radial_tensor(p, "d")
     out += radial_tensor(q, "h")
     out += m2l_std(p)
+    out += con_moments(p)
     out += m2l_con(p)
     out += p2m(p)
     out += m2m(p)

@@ -1,20 +1,25 @@
 // a12 mutual particle-particle interactions (eq. jia and its gradient) and a14 diagnostics.
 //
-// One warp per leaf pair of the P2P list.  For distinct leaves the smaller one is held
-// in lanes ("fixed", accumulators in registers) and the larger one is staged in shared
-// memory ("rotating"); in step s lane l meets rotating particle (l + s) mod n_rot, so
-// every particle pair is met exactly once and, within a step, no two lanes touch the
-// same rotating accumulator.  A self pair uses cyclic distances 1 .. n/2.  Each pair
-// force is applied to both partners (action = reaction).  The per-pair results go to a
-// partial buffer and are summed per particle, in increasing partner id, by the final
-// per-particle kernel: no floating-point atomics, run-to-run identical.
+// One warp per leaf pair (A, B) of the P2P list (A == B: a leaf with itself).  The
+// nA x nB particle pairs are spread flat over the 32 lanes, so lanes stay busy whatever
+// the leaf sizes (leaves hold ~10 particles on average): lane t of a round takes pair
+// (a, b) = (t / ncol, t % ncol) of a column panel, forms d = X_a - X_b, r^-1 and d r^-3
+// and stores them in a shared-memory panel.  Two passes then sum the panel with one lane
+// per (particle, component): rows give a_a = -sum_b m_b d r^-3 (phi_a = -sum_b m_b r^-1),
+// columns give a_b = +sum_a m_a d r^-3 (phi_b = -sum_a m_a r^-1).  Each pair force is
+// formed once and applied to both partners (action = reaction).  A self pair keeps a < b.
+// Results go to a per-(pair, side, slot) partial buffer that the final per-particle
+// kernels sum in increasing partner id: no floating-point atomics, run-to-run identical.
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 
 namespace gbfmm {
 
-constexpr int PB = 128;                // 4 warps
+constexpr int PB = 128;                 // 4 warps
 constexpr int PW = PB / 32;
+constexpr int PCOL = 16;                // panel columns
+constexpr int PROW = PCOL * 4 + 4;      // doubles per panel row: [col][comp], padded (row stride = 4 mod 16)
+constexpr int PANEL = 32 * PROW;        // doubles per warp panel
 
 struct PState {
     double x, y, z, m;
@@ -29,117 +34,109 @@ __device__ __forceinline__ bool pair_kernel(double dx, double dy, double dz, dou
     return true;
 }
 
+template <bool POT>
 __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restrict__ pairs,
                                             const long long* __restrict__ off, const int* __restrict__ nfirst,
                                             const int* __restrict__ ncount, const double* __restrict__ xs,
                                             const double* __restrict__ ys, const double* __restrict__ zs,
                                             const double* __restrict__ ms, double4* __restrict__ part) {
-    __shared__ PState sp[PW][32];
-    __shared__ double4 sa[PW][32];
+    extern __shared__ double smem[];
+    __shared__ PState sA[PW][32], sB[PW][32];
+    __shared__ double4 cacc[PW][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* F = smem + (size_t)w * PANEL;
+    double* cac = reinterpret_cast<double*>(&cacc[w][0]);
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
     for (int64_t k = gw; k < npairs; k += nw) {
         int2 pr = pairs[k];
         int A = pr.x, B = pr.y;
         int nA = ncount[A], nB = ncount[B], fA = nfirst[A], fB = nfirst[B];
         long long o = off[k];
-        if (A == B && nA <= 32) {
-            // ---- self pair
-            int n = nA;
-            double xi = 0, yi = 0, zi = 0, mi = 0;
-            if (lane < n) {
-                xi = xs[fA + lane];
-                yi = ys[fA + lane];
-                zi = zs[fA + lane];
-                mi = ms[fA + lane];
-                sp[w][lane] = PState{xi, yi, zi, mi};
-                sa[w][lane] = make_double4(0, 0, 0, 0);
-            }
+        bool self = A == B;
+        if (nA <= 32 && nB <= 32) {
+            if (lane < nA) sA[w][lane] = PState{xs[fA + lane], ys[fA + lane], zs[fA + lane], ms[fA + lane]};
+            if (lane < nB) sB[w][lane] = PState{xs[fB + lane], ys[fB + lane], zs[fB + lane], ms[fB + lane]};
+            cacc[w][lane] = make_double4(0.0, 0.0, 0.0, 0.0);
+            double racc[4] = {0.0, 0.0, 0.0, 0.0};  // row task tau = lane + 32 q: (a, comp) = (tau >> 2, tau & 3)
             __syncwarp();
-            double ax = 0, ay = 0, az = 0, ph = 0;
-            int half = n / 2;
-            for (int s = 1; s <= half; s++) {
-                bool act = lane < n && (2 * s < n || lane < half);
-                if (act) {
-                    int j = lane + s;
-                    if (j >= n) j -= n;
-                    PState q = sp[w][j];
-                    double dx = xi - q.x, dy = yi - q.y, dz = zi - q.z, ir, ir3;
-                    if (pair_kernel(dx, dy, dz, ir, ir3)) {
-                        double fb = q.m * ir3, fa = mi * ir3;
-                        ax -= fb * dx;
-                        ay -= fb * dy;
-                        az -= fb * dz;
-                        ph -= q.m * ir;
-                        double4 t = sa[w][j];
-                        t.x += fa * dx;
-                        t.y += fa * dy;
-                        t.z += fa * dz;
-                        t.w -= mi * ir;
-                        sa[w][j] = t;
+            for (int cb = 0; cb < nB; cb += PCOL) {
+                int ncol = min(PCOL, nB - cb);
+                int nint = nA * ncol;
+                // pair terms of the panel
+                for (int t = lane; t < nint; t += 32) {
+                    int a = t / ncol, bl = t - a * ncol, b = cb + bl;
+                    double fx = 0.0, fy = 0.0, fz = 0.0, fr = 0.0;
+                    if (!self || a < b) {
+                        PState pa = sA[w][a], pb = sB[w][b];
+                        double dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z, ir, ir3;
+                        if (pair_kernel(dx, dy, dz, ir, ir3)) {
+                            fx = dx * ir3;
+                            fy = dy * ir3;
+                            fz = dz * ir3;
+                            fr = ir;
+                        }
+                    }
+                    double* e = F + a * PROW + bl * 4;
+                    reinterpret_cast<double2*>(e)[0] = make_double2(fx, fy);
+                    reinterpret_cast<double2*>(e)[1] = make_double2(fz, fr);
+                }
+                __syncwarp();
+                // rows: sum_b m_b F[a][b]
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
+                    if (a < nA && (POT || c < 3)) {
+                        const double* row = F + a * PROW + c;
+                        double s = racc[q];
+                        for (int bl = 0; bl < ncol; bl++) s = fma(sB[w][cb + bl].m, row[bl * 4], s);
+                        racc[q] = s;
+                    }
+                }
+                // columns: sum_a m_a F[a][b]
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    int tau = lane + 32 * q, bl = tau >> 2, c = tau & 3;
+                    if (bl < ncol && (POT || c < 3)) {
+                        const double* col = F + bl * 4 + c;
+                        double s = 0.0;
+                        for (int a = 0; a < nA; a++) s = fma(sA[w][a].m, col[a * PROW], s);
+                        cac[(cb + bl) * 4 + c] += s;
                     }
                 }
                 __syncwarp();
             }
-            if (lane < n) {
-                double4 t = sa[w][lane];
-                part[o + lane] = make_double4(ax + t.x, ay + t.y, az + t.z, ph + t.w);
+            // write: rows are a_a = -sum (and phi_a = -sum); columns a_b = +sum, phi_b = -sum
+            double* pd = reinterpret_cast<double*>(part);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
+                if (a < nA) {
+                    double v = -racc[q];
+                    if (self) v += (c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c];
+                    pd[(o + a) * 4 + c] = (POT || c < 3) ? v : 0.0;
+                }
             }
-            __syncwarp();
-        } else if (A != B && nA <= 32 && nB <= 32) {
-            // ---- distinct leaves: smaller side fixed in lanes, larger side rotating
-            bool a_fixed = nA <= nB;
-            int nF = a_fixed ? nA : nB, nR = a_fixed ? nB : nA;
-            int fF = a_fixed ? fA : fB, fR = a_fixed ? fB : fA;
-            long long oF = a_fixed ? o : o + nA, oR = a_fixed ? o + nA : o;
-            if (lane < nR) {
-                sp[w][lane] = PState{xs[fR + lane], ys[fR + lane], zs[fR + lane], ms[fR + lane]};
-                sa[w][lane] = make_double4(0, 0, 0, 0);
-            }
-            double xi = 0, yi = 0, zi = 0, mi = 0;
-            if (lane < nF) {
-                xi = xs[fF + lane];
-                yi = ys[fF + lane];
-                zi = zs[fF + lane];
-                mi = ms[fF + lane];
-            }
-            __syncwarp();
-            double ax = 0, ay = 0, az = 0, ph = 0;
-            int j = lane;
-            for (int s = 0; s < nR; s++) {
-                if (lane < nF) {
-                    PState q = sp[w][j];
-                    double dx = xi - q.x, dy = yi - q.y, dz = zi - q.z, ir, ir3;
-                    if (pair_kernel(dx, dy, dz, ir, ir3)) {
-                        double fb = q.m * ir3, fa = mi * ir3;
-                        ax -= fb * dx;
-                        ay -= fb * dy;
-                        az -= fb * dz;
-                        ph -= q.m * ir;
-                        double4 t = sa[w][j];
-                        t.x += fa * dx;
-                        t.y += fa * dy;
-                        t.z += fa * dz;
-                        t.w -= mi * ir;
-                        sa[w][j] = t;
+            if (!self) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    int tau = lane + 32 * q, b = tau >> 2, c = tau & 3;
+                    if (b < nB) {
+                        double v = cac[b * 4 + c];
+                        pd[(o + nA + b) * 4 + c] = (c < 3) ? v : (POT ? -v : 0.0);
                     }
                 }
-                j = (j + 1 == nR) ? 0 : j + 1;
-                __syncwarp();
             }
-            if (lane < nF) part[oF + lane] = make_double4(ax, ay, az, ph);
-            if (lane < nR) part[oR + lane] = sa[w][lane];
             __syncwarp();
         } else {
             // ---- leaves above 32 particles (only at the deepest level): one side at a time
-            for (int side = 0; side < (A == B ? 1 : 2); side++) {
+            for (int side = 0; side < (self ? 1 : 2); side++) {
                 int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
                 long long oT = side ? o + nA : o;
                 for (int t = lane; t < nT; t += 32) {
                     double xi = xs[fT + t], yi = ys[fT + t], zi = zs[fT + t];
                     double ax = 0, ay = 0, az = 0, ph = 0;
                     for (int u = 0; u < nS; u++) {
-                        if (A == B && u == t) continue;
+                        if (self && u == t) continue;
                         double dx = xi - xs[fS + u], dy = yi - ys[fS + u], dz = zi - zs[fS + u], ir, ir3;
                         if (pair_kernel(dx, dy, dz, ir, ir3)) {
                             double fb = ms[fS + u] * ir3;
@@ -149,7 +146,7 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                             ph -= ms[fS + u] * ir;
                         }
                     }
-                    part[oT + t] = make_double4(ax, ay, az, ph);
+                    part[oT + t] = make_double4(ax, ay, az, POT ? ph : 0.0);
                 }
             }
         }
@@ -157,7 +154,6 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
 }
 
 void run_p2p(fmm_ctx* c, bool want_pot) {
-    (void)want_pot;
     cudaStream_t s = c->stream;
     long long total = 0;
     GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
@@ -171,12 +167,73 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     stage_begin(c, ST_P2P);
-    p2p_k<<<(unsigned)blocks, PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
-                                          c->nfirst.as<int>(), c->ncount.as<int>(), c->xs.as<double>(),
-                                          c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>(),
-                                          c->p2p_part.as<double4>());
+    size_t shm = sizeof(double) * (size_t)PANEL * PW;
+    auto kern = want_pot ? p2p_k<true> : p2p_k<false>;
+    GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
+                                           c->nfirst.as<int>(), c->ncount.as<int>(), c->xs.as<double>(),
+                                           c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>(),
+                                           c->p2p_part.as<double4>());
     GB_LAUNCH("p2p_k");
     stage_end(c, ST_P2P);
+}
+
+// a12/a13 first level: one warp per P2P work item (up to P2P_CHUNK directed entries of
+// one leaf); lane = particle slot of the leaf.  Sums the per-pair partials of the
+// item's entries (increasing partner id) into ipart[islot[item] + slot].
+//   part[] holds double4 (ax, ay, az, phi) per (pair, side, slot); pair k's block starts
+//   at off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+__global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
+                                                   const int* __restrict__ ncount, const uint32_t* __restrict__ pdval,
+                                                   const int2* __restrict__ pairs, const long long* __restrict__ poff,
+                                                   const double4* __restrict__ part,
+                                                   const long long* __restrict__ islot, double4* __restrict__ ipart) {
+    int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (it >= nitems) return;
+    int4 w = items[it];
+    int cnt = ncount[w.x];
+    for (int slot = lane; slot < cnt; slot += 32) {
+        double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
+        for (int e = w.y; e < w.z; e++) {
+            uint32_t v = pdval[e];
+            uint32_t k = v >> 1;
+            long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
+            double4 q = part[o];
+            px += q.x;
+            py += q.y;
+            pz += q.z;
+            pp += q.w;
+        }
+        ipart[islot[it] + slot] = make_double4(px, py, pz, pp);
+    }
+}
+
+// slot offsets of the P2P items: islot[i] = sum of the leaf sizes of items before i
+__global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, const int* __restrict__ ncount,
+                             long long* __restrict__ sizes) {
+    int64_t i = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (i < nitems) sizes[i] = ncount[items[i].x];
+}
+
+void run_p2p_gather(fmm_ctx* c) {
+    cudaStream_t s = c->stream;
+    const ItemSet& it = c->p2p_items;
+    int64_t ni = it.n_items;
+    ensure(c->p2p_islot, sizeof(long long) * (size_t)(ni + 1));
+    ensure(c->flags, sizeof(long long) * (size_t)(ni + 1));
+    item_slots_k<<<grid_for(ni, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(), c->flags.as<long long>());
+    GB_LAUNCH("item_slots_k");
+    scan_i64_from_i64(c, c->flags.as<long long>(), ni, c->p2p_islot.as<long long>());
+    long long nslots = 0;
+    GB_CUDA(cudaMemcpyAsync(&nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    ensure(c->p2p_ipart, sizeof(double4) * (size_t)(nslots > 0 ? nslots : 1));
+    p2p_gather_k<<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
+                                                       c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
+                                                       c->p2p_off.as<long long>(), c->p2p_part.as<double4>(),
+                                                       c->p2p_islot.as<long long>(), c->p2p_ipart.as<double4>());
+    GB_LAUNCH("p2p_gather_k");
 }
 
 // ------------------------------------------------------------------ diagnostics

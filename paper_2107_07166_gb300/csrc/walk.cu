@@ -127,6 +127,54 @@ __global__ void seg_count_k(const uint64_t* __restrict__ keys, int64_t n, int bi
     atomicAdd(&cnt[k >> bits], 1);  // integer counts: order independent
 }
 
+// Work items over segments seg[0..n]: every segment is cut into chunks of CH entries.
+// Full chunks come first (segment-major), then one partial chunk per segment that has a
+// remainder, so that warps see chunks of equal length.  fo/po (n + 1 entries) give each
+// segment's full-chunk range and partial-chunk rank.
+__global__ void items_count_k(const long long* __restrict__ seg, int n, int CH, int* __restrict__ nfull,
+                              int* __restrict__ npart) {
+    int x = blockIdx.x * WB + threadIdx.x;
+    if (x >= n) return;
+    long long deg = seg[x + 1] - seg[x];
+    nfull[x] = (int)(deg / CH);
+    npart[x] = (deg % CH) != 0;
+}
+
+__global__ void items_fill_k(const long long* __restrict__ seg, int n, int CH, const long long* __restrict__ fo,
+                             const long long* __restrict__ po, long long nfull_total, int4* __restrict__ items) {
+    int x = blockIdx.x * WB + threadIdx.x;
+    if (x >= n) return;
+    long long e0 = seg[x], e1 = seg[x + 1];
+    long long k0 = fo[x], nf = fo[x + 1] - k0;
+    for (long long k = 0; k < nf; k++)
+        items[k0 + k] = make_int4(x, (int)(e0 + k * CH), (int)(e0 + (k + 1) * CH), 0);
+    if (po[x + 1] > po[x]) items[nfull_total + po[x]] = make_int4(x, (int)(e0 + nf * CH), (int)e1, 0);
+}
+
+void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it) {
+    cudaStream_t s = c->stream;
+    ensure(c->seg_cnt, sizeof(int) * (size_t)(2 * n + 2));
+    int* nfull = c->seg_cnt.as<int>();
+    int* npart = nfull + n + 1;
+    ensure(it.fo, sizeof(long long) * (size_t)(n + 1));
+    ensure(it.po, sizeof(long long) * (size_t)(n + 1));
+    items_count_k<<<grid_for(n, WB), WB, 0, s>>>(seg, n, CH, nfull, npart);
+    GB_LAUNCH("items_count_k");
+    scan_i64(c, nfull, n, it.fo.as<long long>());
+    scan_i64(c, npart, n, it.po.as<long long>());
+    long long tot[2];
+    GB_CUDA(cudaMemcpyAsync(&tot[0], it.fo.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&tot[1], it.po.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    it.n_full = tot[0];
+    it.n_items = tot[0] + tot[1];
+    it.chunk = CH;
+    ensure(it.items, sizeof(int4) * (size_t)(it.n_items > 0 ? it.n_items : 1));
+    items_fill_k<<<grid_for(n, WB), WB, 0, s>>>(seg, n, CH, it.fo.as<long long>(), it.po.as<long long>(), it.n_full,
+                                                it.items.as<int4>());
+    GB_LAUNCH("items_fill_k");
+}
+
 static int bits_for(int64_t nn) {
     int b = 1;
     while (((int64_t)1 << b) <= nn) b++;  // ids < 2^b - 1 always
@@ -206,6 +254,9 @@ void run_walk(fmm_ctx* c, double theta) {
     seg_count_k<<<grid_for(np, WB), WB, 0, s>>>(c->p2p_dir.as<uint64_t>(), np, bits, c->seg_cnt.as<int>());
     GB_LAUNCH("seg_count_k");
     scan_i64(c, c->seg_cnt.as<int>(), nn, c->p2p_seg.as<long long>());
+    // work items: 32 M2L sources per chunk, 64 P2P entries per chunk
+    build_items(c, c->m2l_seg.as<long long>(), (int)nn, M2L_CHUNK, c->m2l_items);
+    build_items(c, c->p2p_seg.as<long long>(), (int)nn, P2P_CHUNK, c->p2p_items);
     c->list_theta = theta;
 }
 
