@@ -44,8 +44,9 @@ typedef struct fmm_ctx fmm_ctx;
 #define GBFMM_API
 #endif
 
-/* highest multipole order compiled into the library */
+/* highest multipole order compiled into the library, and into its FMM_DF64 mode */
 #define FMM_P_MAX 6
+#define FMM_DF64_P_MAX 5
 
 /* variants */
 enum {
@@ -53,10 +54,14 @@ enum {
     FMM_CONSERVING = 1 /* Sec. 3.2: every approximated pair force realigned onto the line X_a - Y_b */
 };
 
-/* arithmetic of the expansion and particle-particle kernels */
+/* arithmetic of the pair kernels (M2L and P2P); tree, moments, translations (M2M, L2L),
+ * L2P, accumulators and diagnostics are binary64 in every mode */
 enum {
-    FMM_FP64 = 0, /* all FMM arithmetic in IEEE binary64 */
-    FMM_MIXED = 1 /* reserved: binary32 M2L/P2P with binary64 translations and accumulators */
+    FMM_FP64 = 0,  /* M2L and P2P in IEEE binary64 */
+    FMM_MIXED = 1, /* M2L and P2P in binary32 (separations formed in double-float first),
+                      per-pair and per-chunk partials summed in binary64 */
+    FMM_DF64 = 2   /* M2L and P2P in double-float arithmetic on the binary32 units (two binary32
+                      words, ~48-bit significand): binary64-level results at the binary32 issue rate */
 };
 
 /* status codes */
@@ -71,7 +76,8 @@ enum {
     FMM_ERR_TIMEOUT = -6   /* reserved for bounded device waits */
 };
 
-/* Create a context on CUDA device `device` with arithmetic `precision` (FMM_FP64).
+/* Create a context on CUDA device `device` with arithmetic `precision` (FMM_FP64,
+ * FMM_MIXED or FMM_DF64).
  * `cuda_stream` is the cudaStream_t to queue work on (cudaStreamLegacy and
  * cudaStreamPerThread are accepted), or NULL for a private non-blocking stream.  Device
  * outputs are complete once that stream has reached the end of the call's work. */

@@ -31,7 +31,14 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    gen = os.path.join(CSRC, "gen")
+    own = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu")]
+    generated = [os.path.join(gen, f) for f in os.listdir(gen) if f.endswith(".cu")] if os.path.isdir(gen) else []
+    # heaviest translation units (highest order) first, so the parallel build ends sooner
+    def cost(f):
+        b = os.path.basename(f)
+        return -int(b[len("expansion_p")]) if b.startswith("expansion_p") else 0
+    return sorted(own + generated, key=lambda f: (cost(f), f))
 
 
 def _stale(obj, deps):
@@ -49,13 +56,13 @@ def build(verbose: bool = False, jobs: int | None = None, extra_flags=None) -> s
     flags = NVCC_FLAGS + list(extra_flags or [])
     cmds = []
     objs = []
-    for src in sources():
-        s = os.path.join(CSRC, src)
+    for s in sources():
+        src = os.path.basename(s)
         o = os.path.join(BUILD, src[:-3] + ".o")
         objs.append(o)
         deps = [s] + headers
         if src.startswith("expansion_p"):
-            deps.append(os.path.join(CSRC, "gen", "exp_" + src[len("expansion_"):-3] + ".cuh"))
+            deps.append(os.path.join(CSRC, "gen", "exp_p" + src[len("expansion_p")] + ".cuh"))
         if _stale(o, deps):
             cmds.append([nvcc(), *ARCH, *flags, "-I", INCLUDE, "-c", s, "-o", o])
     jobs = jobs or max(2, os.cpu_count() or 2)

@@ -86,7 +86,8 @@ int64_t fmm_kernel_launches(void) { return (int64_t)launches(); }
 
 int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
     if (!out) return fail(FMM_ERR_INVALID, "fmm_create: out is NULL");
-    if (precision != FMM_FP64) return fail(FMM_ERR_INVALID, "fmm_create: only FMM_FP64 is available");
+    if (precision != FMM_FP64 && precision != FMM_MIXED && precision != FMM_DF64)
+        return fail(FMM_ERR_INVALID, "fmm_create: unknown precision");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -125,7 +126,10 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nrmax, &c->mom, &c->loc, &c->locp, &c->fr0,
                           &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
                           &c->p2p_dir, &c->p2p_dval, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
-                          &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp};
+                          &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
+                          &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
+                          &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
+                          &c->zst, &c->momT, &c->cmomT};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -163,6 +167,7 @@ int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_
         c->have_forces = false;
         c->mom_p = -1;
         c->list_theta = -1.0;
+        c->pos_valid = false;
         c->N = N;
         c->leaf = leaf_size;
         const double* xd = x;
@@ -192,6 +197,8 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
     if (!c->built) return fail(FMM_ERR_STATE, "fmm_forces: call fmm_build first");
     if (p < 1 || p > FMM_P_MAX) return fail(FMM_ERR_INVALID, "fmm_forces: p must be in [1, FMM_P_MAX]");
     if (!(theta >= 0.0 && theta < 1.0)) return fail(FMM_ERR_INVALID, "fmm_forces: theta must be in [0, 1)");
+    if (c->precision == FMM_DF64 && p > FMM_DF64_P_MAX)
+        return fail(FMM_ERR_INVALID, "fmm_forces: FMM_DF64 supports p <= FMM_DF64_P_MAX");
     if (variant != FMM_STANDARD && variant != FMM_CONSERVING)
         return fail(FMM_ERR_INVALID, "fmm_forces: unknown variant");
     if (!acc) return fail(FMM_ERR_INVALID, "fmm_forces: acc is required");

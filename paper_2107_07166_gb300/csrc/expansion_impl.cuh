@@ -11,6 +11,7 @@
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
+#include "prec.cuh"
 
 namespace gbfmm {
 
@@ -58,71 +59,98 @@ __global__ void __launch_bounds__(EB) m2m_k(int lo, int hi, const int* __restric
 }
 
 // a8 M2L, standard, one work item = up to M2L_CHUNK directed entries of one target cell
-// (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src).
+// (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src),
+// in the pair-kernel type T; centres are stored as S = Prec<T>::S and R is formed in S.
 // The item's partial local goes to part[item]; m2l_reduce_k sums a cell's items in order.
-template <int P>
+template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __restrict__ items,
                                                 const uint64_t* __restrict__ dir, int bits,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz, const double* __restrict__ mom,
-                                                double* __restrict__ part) {
+                                                const typename Prec<T>::S* __restrict__ zst,
+                                                const T* __restrict__ mom, T* __restrict__ part) {
     using E = Exp<P>;
+    using S = typename Prec<T>::S;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
-    double L[E::NM];
+    T L[E::NM];
 #pragma unroll
-    for (int k = 0; k < E::NM; k++) L[k] = 0.0;
-    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
+    for (int k = 0; k < E::NM; k++) L[k] = T(0);
+    S zx = zst[3 * w.x], zy = zst[3 * w.x + 1], zz = zst[3 * w.x + 2];
     uint64_t mask = (1ull << bits) - 1ull;
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        double D[E::NM];
-        E::dtensor(zx - Zx[src], zy - Zy[src], zz - Zz[src], D);
+        T rx = Prec<T>::narrow(zx - zst[3 * src]), ry = Prec<T>::narrow(zy - zst[3 * src + 1]);
+        T rz = Prec<T>::narrow(zz - zst[3 * src + 2]);
+        T D[E::NM];
+        E::dtensor(rx, ry, rz, D);
         E::m2l_std(mom + (int64_t)src * E::NM, D, L);
     }
 #pragma unroll
-    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = L[k];
+    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = Prec<T>::to_g(L[k]);
 }
 
 // a8' M2L, conserving: S and U of the realigned pair forces, from conserving moments
-template <int P>
+template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __restrict__ items,
                                                 const uint64_t* __restrict__ dir, int bits,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz, const double* __restrict__ cmom,
-                                                double* __restrict__ part) {
+                                                const typename Prec<T>::S* __restrict__ zst,
+                                                const T* __restrict__ cmom, T* __restrict__ part) {
     using E = Exp<P>;
+    using S = typename Prec<T>::S;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
-    double SU[E::NSU];
+    T SU[E::NSU];
 #pragma unroll
-    for (int k = 0; k < E::NSU; k++) SU[k] = 0.0;
-    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
+    for (int k = 0; k < E::NSU; k++) SU[k] = T(0);
+    S zx = zst[3 * w.x], zy = zst[3 * w.x + 1], zz = zst[3 * w.x + 2];
     uint64_t mask = (1ull << bits) - 1ull;
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        double rx = zx - Zx[src], ry = zy - Zy[src], rz = zz - Zz[src];
-        double H[E::NQ];
+        T rx = Prec<T>::narrow(zx - zst[3 * src]), ry = Prec<T>::narrow(zy - zst[3 * src + 1]);
+        T rz = Prec<T>::narrow(zz - zst[3 * src + 2]);
+        T H[E::NQ];
         E::htensor(rx, ry, rz, H);
         E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
     }
 #pragma unroll
-    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = SU[k];
+    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::to_g(SU[k]);
 }
 
-// a9: loc[x][k] = sum over the cell's items (full chunks in order, then the partial one)
-template <int NL>
+// a9: loc[x][k] = sum over the cell's items (full chunks in order, then the partial one),
+// accumulated in binary64
+__device__ __forceinline__ double as_double(double v) { return v; }
+__device__ __forceinline__ double as_double(float v) { return (double)v; }
+__device__ __forceinline__ double as_double(df64 v) { return to_double(v); }
+
+template <int NL, class T>
 __global__ void m2l_reduce_k(int nn, const long long* __restrict__ fo, const long long* __restrict__ po,
-                             long long nfull, const double* __restrict__ part, double* __restrict__ loc) {
+                             long long nfull, const T* __restrict__ part, double* __restrict__ loc) {
     int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (t >= (int64_t)nn * NL) return;
     int x = (int)(t / NL), k = (int)(t - (int64_t)x * NL);
     double acc = 0.0;
-    for (long long i = fo[x]; i < fo[x + 1]; i++) acc += part[i * NL + k];
-    if (po[x + 1] > po[x]) acc += part[(nfull + po[x]) * NL + k];
+    for (long long i = fo[x]; i < fo[x + 1]; i++) acc += as_double(part[i * NL + k]);
+    if (po[x + 1] > po[x]) acc += as_double(part[(nfull + po[x]) * NL + k]);
     loc[t] = acc;
+}
+
+// binary64 arrays converted to the pair-kernel / storage types
+template <class T>
+__global__ void convert_k(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (i < n) out[i] = to_kernel(in[i], T());
+}
+
+template <class S>
+__global__ void pack_centres_k(int nn, const double* __restrict__ Zx, const double* __restrict__ Zy,
+                               const double* __restrict__ Zz, S* __restrict__ zst) {
+    int i = blockIdx.x * EB + threadIdx.x;
+    if (i < nn) {
+        zst[3 * i] = to_storage(Zx[i], S());
+        zst[3 * i + 1] = to_storage(Zy[i], S());
+        zst[3 * i + 2] = to_storage(Zz[i], S());
+    }
 }
 
 // conserving source moments of every cell (formed once per moment build)
@@ -188,7 +216,7 @@ __global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __res
 
 // a11 + a13: far field at every particle from its leaf's locals, plus the leaf's P2P item
 // sums (full chunks in order, then the partial one), written in input order.
-template <int P, int V>
+template <int P, int V, class G>
 __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ leaf_of, const int* __restrict__ nfirst,
                                                const double* __restrict__ xs, const double* __restrict__ ys,
                                                const double* __restrict__ zs, const double* __restrict__ Zx,
@@ -196,7 +224,7 @@ __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ le
                                                const double* __restrict__ loc, const double* __restrict__ locp,
                                                const long long* __restrict__ fo, const long long* __restrict__ po,
                                                long long nfull, const long long* __restrict__ islot,
-                                               const double4* __restrict__ ipart, const uint32_t* __restrict__ perm,
+                                               const Quad<G>* __restrict__ ipart, const uint32_t* __restrict__ perm,
                                                double* __restrict__ acc_s, double* __restrict__ pot_s,
                                                double* __restrict__ acc_out, double* __restrict__ pot_out) {
     using E = Exp<P>;
@@ -217,18 +245,18 @@ __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ le
     }
     double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
     for (long long k = fo[lf]; k < fo[lf + 1]; k++) {
-        double4 q = ipart[islot[k] + slot];
-        px += q.x;
-        py += q.y;
-        pz += q.z;
-        pp += q.w;
+        Quad<G> q = ipart[islot[k] + slot];
+        px += as_double(q.x);
+        py += as_double(q.y);
+        pz += as_double(q.z);
+        pp += as_double(q.w);
     }
     if (po[lf + 1] > po[lf]) {
-        double4 q = ipart[islot[nfull + po[lf]] + slot];
-        px += q.x;
-        py += q.y;
-        pz += q.z;
-        pp += q.w;
+        Quad<G> q = ipart[islot[nfull + po[lf]] + slot];
+        px += as_double(q.x);
+        py += as_double(q.y);
+        pz += as_double(q.z);
+        pp += as_double(q.w);
     }
     ax += px;
     ay += py;
@@ -269,30 +297,56 @@ void run_moments_p(fmm_ctx* c) {
     ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
     con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
     GB_LAUNCH("con_moments_k");
+    // copies in the pair-kernel type and centres in the storage type
+    if (c->precision == FMM_FP64) {
+        ensure(c->zst, sizeof(double) * 3 * (size_t)nn);
+        pack_centres_k<double><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nZx.as<double>(), c->nZy.as<double>(),
+                                                               c->nZz.as<double>(), c->zst.as<double>());
+        GB_LAUNCH("pack_centres_k");
+    } else {
+        ensure(c->zst, sizeof(df64) * 3 * (size_t)nn);
+        pack_centres_k<df64><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nZx.as<double>(), c->nZy.as<double>(),
+                                                             c->nZz.as<double>(), c->zst.as<df64>());
+        GB_LAUNCH("pack_centres_k");
+        int64_t nm = (int64_t)nn * E::NM, nc = (int64_t)nn * E::NSU;
+        if (c->precision == FMM_DF64) {
+            ensure(c->momT, sizeof(df64) * (size_t)nm);
+            ensure(c->cmomT, sizeof(df64) * (size_t)nc);
+            convert_k<df64><<<grid_for(nm, EB), EB, 0, s>>>(nm, c->mom.as<double>(), c->momT.as<df64>());
+            convert_k<df64><<<grid_for(nc, EB), EB, 0, s>>>(nc, c->cmom.as<double>(), c->cmomT.as<df64>());
+        } else {
+            ensure(c->momT, sizeof(float) * (size_t)nm);
+            ensure(c->cmomT, sizeof(float) * (size_t)nc);
+            convert_k<float><<<grid_for(nm, EB), EB, 0, s>>>(nm, c->mom.as<double>(), c->momT.as<float>());
+            convert_k<float><<<grid_for(nc, EB), EB, 0, s>>>(nc, c->cmom.as<double>(), c->cmomT.as<float>());
+        }
+        GB_LAUNCH("convert_k");
+    }
 }
 
-template <int P>
-void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
+template <int P, class T>
+void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     using E = Exp<P>;
+    using S = typename Prec<T>::S;
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
     const uint64_t* dir = c->m2l_dir.as<uint64_t>();
     const ItemSet& it = c->m2l_items;
     int64_t ni = it.n_items;
-    bool std_locals = (variant == 0) || want_pot;
-    stage_begin(c, ST_M2L);
+    bool native = c->precision == FMM_FP64;
+    const T* mom = native ? c->mom.as<T>() : c->momT.as<T>();
+    const T* cmom = native ? c->cmom.as<T>() : c->cmomT.as<T>();
+    const S* zst = c->zst.as<S>();
     int nl_max = E::NSU > E::NM ? E::NSU : E::NM;
-    ensure(c->m2l_part, sizeof(double) * (size_t)(ni > 0 ? ni : 1) * nl_max);
-    double* part = c->m2l_part.as<double>();
+    ensure(c->m2l_part, sizeof(T) * (size_t)(ni > 0 ? ni : 1) * nl_max);
+    T* part = c->m2l_part.as<T>();
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
-            m2l_con_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, c->nZx.as<double>(),
-                                                         c->nZy.as<double>(), c->nZz.as<double>(),
-                                                         c->cmom.as<double>(), part);
+            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zst, cmom, part);
             GB_LAUNCH("m2l_con_k");
         }
-        m2l_reduce_k<E::NSU><<<grid_for((int64_t)nn * E::NSU, EB), EB, 0, s>>>(
+        m2l_reduce_k<E::NSU, T><<<grid_for((int64_t)nn * E::NSU, EB), EB, 0, s>>>(
             nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, c->loc.as<double>());
         GB_LAUNCH("m2l_reduce_k");
     }
@@ -300,15 +354,26 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
         if (ni > 0) {
-            m2l_std_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, c->nZx.as<double>(),
-                                                         c->nZy.as<double>(), c->nZz.as<double>(), c->mom.as<double>(),
-                                                         part);
+            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zst, mom, part);
             GB_LAUNCH("m2l_std_k");
         }
-        m2l_reduce_k<E::NM><<<grid_for((int64_t)nn * E::NM, EB), EB, 0, s>>>(
+        m2l_reduce_k<E::NM, T><<<grid_for((int64_t)nn * E::NM, EB), EB, 0, s>>>(
             nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, L.as<double>());
         GB_LAUNCH("m2l_reduce_k");
     }
+}
+
+template <int P>
+void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
+    cudaStream_t s = c->stream;
+    bool std_locals = (variant == 0) || want_pot;
+    stage_begin(c, ST_M2L);
+    if (c->precision == FMM_FP64)
+        m2l_launch<P, double>(c, variant, std_locals);
+    else if (c->precision == FMM_DF64) {
+        if constexpr (P <= FMM_DF64_P_MAX) m2l_launch<P, df64>(c, variant, std_locals);
+    } else
+        m2l_launch<P, float>(c, variant, std_locals);
     stage_end(c, ST_M2L);
     stage_begin(c, ST_L2L);
     for (int l = 1; l < c->n_levels; l++) {
@@ -330,31 +395,45 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     stage_end(c, ST_L2L);
 }
 
-template <int P>
-void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
+template <int P, class G>
+static void finish_launch(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
     cudaStream_t s = c->stream;
     int n = (int)c->N;
     const ItemSet& it = c->p2p_items;
-    int64_t ni = it.n_items;
     const double* locp = (variant == 1 && want_pot) ? c->locp.as<double>() : nullptr;
     auto args = [&](auto kern) {
         kern<<<grid_for(n, EB), EB, 0, s>>>(
             n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
             c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->loc.as<double>(), locp,
             it.fo.as<long long>(), it.po.as<long long>(), it.n_full, c->p2p_islot.as<long long>(),
-            c->p2p_ipart.as<double4>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
+            c->p2p_ipart.as<Quad<G>>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
             want_pot ? pot_out : nullptr);
     };
     if (variant == 0)
-        args(finish_k<P, 0>);
+        args(finish_k<P, 0, G>);
     else
-        args(finish_k<P, 1>);
+        args(finish_k<P, 1, G>);
     GB_LAUNCH("finish_k");
 }
 
+template <int P>
+void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
+    if (c->precision == FMM_DF64)
+        finish_launch<P, df64>(c, variant, want_pot, acc_out, pot_out);
+    else
+        finish_launch<P, double>(c, variant, want_pot, acc_out, pot_out);
+}
+
+// One translation unit per order instantiates the order's stages; the M2L launches of
+// each arithmetic type get translation units of their own (compiled in parallel).
 #define GBFMM_INSTANTIATE(P)                                                                             \
+    extern template void m2l_launch<P, double>(fmm_ctx*, int, bool);                                    \
+    extern template void m2l_launch<P, float>(fmm_ctx*, int, bool);                                     \
+    extern template void m2l_launch<P, df64>(fmm_ctx*, int, bool);                                      \
     template void run_moments_p<P>(fmm_ctx*);                                                           \
     template void run_far_field_p<P>(fmm_ctx*, int, bool);                                              \
     template void run_finish_p<P>(fmm_ctx*, int, bool, double*, double*);
+
+#define GBFMM_INSTANTIATE_M2L(P, T) template void m2l_launch<P, T>(fmm_ctx*, int, bool);
 
 }  // namespace gbfmm

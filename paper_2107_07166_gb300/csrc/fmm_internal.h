@@ -116,6 +116,10 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_islot;                   // long long [items + 1]: slot offsets of P2P items
     gbfmm::DevBuf p2p_ipart;                   // double4 per (P2P item, slot)
     gbfmm::DevBuf cmom;                        // conserving source moments, n_nodes x 4 nmi(p-1)
+    gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
+    bool pos_valid = false;
+    gbfmm::DevBuf zst;                         // node centres in the storage type (3 per node)
+    gbfmm::DevBuf momT, cmomT;                 // moments in the pair-kernel type
     int id_bits = 0;
     // results (sorted order) and output staging
     gbfmm::DevBuf acc_s, pot_s;                // SoA: ax | ay | az

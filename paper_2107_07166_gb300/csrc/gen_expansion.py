@@ -33,6 +33,7 @@ import sys
 from fractions import Fraction
 
 PMAX = 6  # orders compiled into the library
+DF64_PMAX = 5  # highest order of the double-float M2L (p = 6 takes minutes to compile)
 
 
 def mis(p):
@@ -313,14 +314,29 @@ def header(p):
     return "\n".join(out) + "\n"
 
 
+def _write(path, txt):
+    if not os.path.exists(path) or open(path).read() != txt:
+        with open(path, "w") as f:
+            f.write(txt)
+
+
 def main(outdir):
+    """Writes gen/exp_p{p}.cuh and the translation units that instantiate them:
+    expansion_p{p}.cu (moments, translations, L2P) and expansion_p{p}_{type}.cu (M2L of one
+    arithmetic type), so that the heavy instantiations compile in parallel."""
     os.makedirs(outdir, exist_ok=True)
     for p in range(1, PMAX + 1):
-        path = os.path.join(outdir, f"exp_p{p}.cuh")
-        txt = header(p)
-        if not os.path.exists(path) or open(path).read() != txt:
-            with open(path, "w") as f:
-                f.write(txt)
+        _write(os.path.join(outdir, f"exp_p{p}.cuh"), header(p))
+        inc = f'#include "exp_p{p}.cuh"\n#include "../expansion_impl.cuh"\n'
+        _write(os.path.join(outdir, f"expansion_p{p}.cu"),
+               f"// generated: expansion stages of order p = {p}\n" + inc +
+               f"namespace gbfmm {{\nGBFMM_INSTANTIATE({p})\n}}\n")
+        for tname, t in (("f64", "double"), ("f32", "float"), ("df64", "df64")):
+            if t == "df64" and p > DF64_PMAX:
+                continue
+            _write(os.path.join(outdir, f"expansion_p{p}_{tname}.cu"),
+                   f"// generated: M2L of order p = {p} in {t}\n" + inc +
+                   f"namespace gbfmm {{\nGBFMM_INSTANTIATE_M2L({p}, {t})\n}}\n")
 
 
 if __name__ == "__main__":

@@ -12,6 +12,8 @@
 // kernels sum in increasing partner id: no floating-point atomics, run-to-run identical.
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
+#include "fmm_math.cuh"
+#include "prec.cuh"
 
 namespace gbfmm {
 
@@ -21,31 +23,26 @@ constexpr int PCOL = 16;                // panel columns
 constexpr int PROW = PCOL * 4 + 4;      // doubles per panel row: [col][comp], padded (row stride = 4 mod 16)
 constexpr int PANEL = 32 * PROW;        // doubles per warp panel
 
+template <class S>
 struct PState {
-    double x, y, z, m;
+    S x, y, z, m;
 };
 
-// pair force pieces: d = Xa - Xb, returns m-free factors
-__device__ __forceinline__ bool pair_kernel(double dx, double dy, double dz, double& ir, double& ir3) {
-    double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 == 0.0) return false;  // coincident particles do not interact
-    ir = rsqrt(r2);
-    ir3 = ir * ir * ir;
-    return true;
-}
-
-template <bool POT>
+// The pair kernel in arithmetic T over positions stored as S = Prec<T>::S.
+template <class T, bool POT>
 __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restrict__ pairs,
                                             const long long* __restrict__ off, const int* __restrict__ nfirst,
-                                            const int* __restrict__ ncount, const double* __restrict__ xs,
-                                            const double* __restrict__ ys, const double* __restrict__ zs,
-                                            const double* __restrict__ ms, double4* __restrict__ part) {
-    extern __shared__ double smem[];
-    __shared__ PState sA[PW][32], sB[PW][32];
-    __shared__ double4 cacc[PW][32];
+                                            const int* __restrict__ ncount,
+                                            const PState<typename Prec<T>::S>* __restrict__ pos,
+                                            Quad<typename Prec<T>::G>* __restrict__ part) {
+    using S = typename Prec<T>::S;
+    using G = typename Prec<T>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PState<S> sA[PW][32], sB[PW][32];
+    __shared__ Quad<T> cacc[PW][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* F = smem + (size_t)w * PANEL;
-    double* cac = reinterpret_cast<double*>(&cacc[w][0]);
+    T* F = reinterpret_cast<T*>(smem_raw) + (size_t)w * PANEL;
+    T* cac = reinterpret_cast<T*>(&cacc[w][0]);
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
     for (int64_t k = gw; k < npairs; k += nw) {
         int2 pr = pairs[k];
@@ -54,31 +51,38 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
         long long o = off[k];
         bool self = A == B;
         if (nA <= 32 && nB <= 32) {
-            if (lane < nA) sA[w][lane] = PState{xs[fA + lane], ys[fA + lane], zs[fA + lane], ms[fA + lane]};
-            if (lane < nB) sB[w][lane] = PState{xs[fB + lane], ys[fB + lane], zs[fB + lane], ms[fB + lane]};
-            cacc[w][lane] = make_double4(0.0, 0.0, 0.0, 0.0);
-            double racc[4] = {0.0, 0.0, 0.0, 0.0};  // row task tau = lane + 32 q: (a, comp) = (tau >> 2, tau & 3)
+            if (lane < nA) sA[w][lane] = pos[fA + lane];
+            if (lane < nB) sB[w][lane] = pos[fB + lane];
+            cacc[w][lane] = Quad<T>{T(0), T(0), T(0), T(0)};
+            T racc[4] = {T(0), T(0), T(0), T(0)};  // row task tau = lane + 32 q: (a, comp) = (tau >> 2, tau & 3)
             __syncwarp();
             for (int cb = 0; cb < nB; cb += PCOL) {
                 int ncol = min(PCOL, nB - cb);
                 int nint = nA * ncol;
-                // pair terms of the panel
+                // pair terms of the panel: d = X_a - X_b (formed in the storage type), r^-1, d r^-3
                 for (int t = lane; t < nint; t += 32) {
                     int a = t / ncol, bl = t - a * ncol, b = cb + bl;
-                    double fx = 0.0, fy = 0.0, fz = 0.0, fr = 0.0;
+                    T fx = T(0), fy = T(0), fz = T(0), fr = T(0);
                     if (!self || a < b) {
-                        PState pa = sA[w][a], pb = sB[w][b];
-                        double dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z, ir, ir3;
-                        if (pair_kernel(dx, dy, dz, ir, ir3)) {
+                        const PState<S>& pa = sA[w][a];
+                        const PState<S>& pb = sB[w][b];
+                        T dx = Prec<T>::narrow(pa.x - pb.x), dy = Prec<T>::narrow(pa.y - pb.y);
+                        T dz = Prec<T>::narrow(pa.z - pb.z);
+                        T r2 = dx * dx + dy * dy + dz * dz;
+                        if (!is_zero(r2)) {
+                            T ir = rsqrt_t(r2);
+                            T ir3 = ir * ir * ir;
                             fx = dx * ir3;
                             fy = dy * ir3;
                             fz = dz * ir3;
                             fr = ir;
                         }
                     }
-                    double* e = F + a * PROW + bl * 4;
-                    reinterpret_cast<double2*>(e)[0] = make_double2(fx, fy);
-                    reinterpret_cast<double2*>(e)[1] = make_double2(fz, fr);
+                    T* e = F + a * PROW + bl * 4;
+                    e[0] = fx;
+                    e[1] = fy;
+                    e[2] = fz;
+                    e[3] = fr;
                 }
                 __syncwarp();
                 // rows: sum_b m_b F[a][b]
@@ -86,10 +90,10 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 for (int q = 0; q < 4; q++) {
                     int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
                     if (a < nA && (POT || c < 3)) {
-                        const double* row = F + a * PROW + c;
-                        double s = racc[q];
-                        for (int bl = 0; bl < ncol; bl++) s = fma(sB[w][cb + bl].m, row[bl * 4], s);
-                        racc[q] = s;
+                        const T* row = F + a * PROW + c;
+                        T sum = racc[q];
+                        for (int bl = 0; bl < ncol; bl++) sum = fma_t(Prec<T>::mass(sB[w][cb + bl].m), row[bl * 4], sum);
+                        racc[q] = sum;
                     }
                 }
                 // columns: sum_a m_a F[a][b]
@@ -97,23 +101,23 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 for (int q = 0; q < 2; q++) {
                     int tau = lane + 32 * q, bl = tau >> 2, c = tau & 3;
                     if (bl < ncol && (POT || c < 3)) {
-                        const double* col = F + bl * 4 + c;
-                        double s = 0.0;
-                        for (int a = 0; a < nA; a++) s = fma(sA[w][a].m, col[a * PROW], s);
-                        cac[(cb + bl) * 4 + c] += s;
+                        const T* col = F + bl * 4 + c;
+                        T sum = cac[(cb + bl) * 4 + c];
+                        for (int a = 0; a < nA; a++) sum = fma_t(Prec<T>::mass(sA[w][a].m), col[a * PROW], sum);
+                        cac[(cb + bl) * 4 + c] = sum;
                     }
                 }
                 __syncwarp();
             }
             // write: rows are a_a = -sum (and phi_a = -sum); columns a_b = +sum, phi_b = -sum
-            double* pd = reinterpret_cast<double*>(part);
+            G* pd = reinterpret_cast<G*>(part);
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
                 if (a < nA) {
-                    double v = -racc[q];
-                    if (self) v += (c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c];
-                    pd[(o + a) * 4 + c] = (POT || c < 3) ? v : 0.0;
+                    T v = -racc[q];
+                    if (self) v = v + ((c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c]);
+                    pd[(o + a) * 4 + c] = (POT || c < 3) ? Prec<T>::to_g(v) : G(0);
                 }
             }
             if (!self) {
@@ -121,8 +125,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 for (int q = 0; q < 4; q++) {
                     int tau = lane + 32 * q, b = tau >> 2, c = tau & 3;
                     if (b < nB) {
-                        double v = cac[b * 4 + c];
-                        pd[(o + nA + b) * 4 + c] = (c < 3) ? v : (POT ? -v : 0.0);
+                        T v = cac[b * 4 + c];
+                        pd[(o + nA + b) * 4 + c] = (c < 3) ? Prec<T>::to_g(v) : (POT ? Prec<T>::to_g(-v) : G(0));
                     }
                 }
             }
@@ -133,79 +137,114 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
                 long long oT = side ? o + nA : o;
                 for (int t = lane; t < nT; t += 32) {
-                    double xi = xs[fT + t], yi = ys[fT + t], zi = zs[fT + t];
-                    double ax = 0, ay = 0, az = 0, ph = 0;
+                    PState<S> pt = pos[fT + t];
+                    T ax = T(0), ay = T(0), az = T(0), ph = T(0);
                     for (int u = 0; u < nS; u++) {
                         if (self && u == t) continue;
-                        double dx = xi - xs[fS + u], dy = yi - ys[fS + u], dz = zi - zs[fS + u], ir, ir3;
-                        if (pair_kernel(dx, dy, dz, ir, ir3)) {
-                            double fb = ms[fS + u] * ir3;
-                            ax -= fb * dx;
-                            ay -= fb * dy;
-                            az -= fb * dz;
-                            ph -= ms[fS + u] * ir;
+                        PState<S> ps = pos[fS + u];
+                        T dx = Prec<T>::narrow(pt.x - ps.x), dy = Prec<T>::narrow(pt.y - ps.y);
+                        T dz = Prec<T>::narrow(pt.z - ps.z);
+                        T r2 = dx * dx + dy * dy + dz * dz;
+                        if (!is_zero(r2)) {
+                            T ir = rsqrt_t(r2);
+                            T fb = Prec<T>::mass(ps.m) * (ir * ir * ir);
+                            ax = fma_t(-fb, dx, ax);
+                            ay = fma_t(-fb, dy, ay);
+                            az = fma_t(-fb, dz, az);
+                            ph = fma_t(-Prec<T>::mass(ps.m), ir, ph);
                         }
                     }
-                    part[oT + t] = make_double4(ax, ay, az, POT ? ph : 0.0);
+                    part[oT + t] = Quad<G>{Prec<T>::to_g(ax), Prec<T>::to_g(ay), Prec<T>::to_g(az),
+                                           POT ? Prec<T>::to_g(ph) : G(0)};
                 }
             }
         }
     }
 }
 
-void run_p2p(fmm_ctx* c, bool want_pot) {
+// packed (x, y, z, m) of every sorted particle in the storage type S
+template <class S>
+__global__ void pack_pos_k(int n, const double* __restrict__ xs, const double* __restrict__ ys,
+                           const double* __restrict__ zs, const double* __restrict__ ms, PState<S>* __restrict__ pos) {
+    int i = blockIdx.x * PB + threadIdx.x;
+    if (i < n)
+        pos[i] = PState<S>{to_storage(xs[i], S()), to_storage(ys[i], S()), to_storage(zs[i], S()),
+                           to_storage(ms[i], S())};
+}
+
+template <class T>
+static void p2p_launch(fmm_ctx* c, bool want_pot) {
+    using S = typename Prec<T>::S;
+    using G = typename Prec<T>::G;
     cudaStream_t s = c->stream;
+    int n = (int)c->N;
+    if (!c->pos_valid) {
+        ensure(c->pos4, sizeof(PState<S>) * (size_t)n);
+        pack_pos_k<S><<<grid_for(n, PB), PB, 0, s>>>(n, c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
+                                                   c->ms.as<double>(), c->pos4.as<PState<S>>());
+        GB_LAUNCH("pack_pos_k");
+        c->pos_valid = true;
+    }
     long long total = 0;
     GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
                             cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    ensure(c->p2p_part, sizeof(double4) * (size_t)(total > 0 ? total : 1));
+    ensure(c->p2p_part, sizeof(Quad<G>) * (size_t)(total > 0 ? total : 1));
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int64_t blocks = (c->n_p2p + PW - 1) / PW;
     int64_t cap = (int64_t)dev_sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    stage_begin(c, ST_P2P);
-    size_t shm = sizeof(double) * (size_t)PANEL * PW;
-    auto kern = want_pot ? p2p_k<true> : p2p_k<false>;
+    size_t shm = sizeof(T) * (size_t)PANEL * PW;
+    auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;
     GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    stage_begin(c, ST_P2P);
     kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
-                                           c->nfirst.as<int>(), c->ncount.as<int>(), c->xs.as<double>(),
-                                           c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>(),
-                                           c->p2p_part.as<double4>());
+                                           c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
+                                           c->p2p_part.as<Quad<G>>());
     GB_LAUNCH("p2p_k");
     stage_end(c, ST_P2P);
+}
+
+void run_p2p(fmm_ctx* c, bool want_pot) {
+    if (c->precision == FMM_FP64)
+        p2p_launch<double>(c, want_pot);
+    else if (c->precision == FMM_DF64)
+        p2p_launch<df64>(c, want_pot);
+    else
+        p2p_launch<float>(c, want_pot);
 }
 
 // a12/a13 first level: one warp per P2P work item (up to P2P_CHUNK directed entries of
 // one leaf); lane = particle slot of the leaf.  Sums the per-pair partials of the
 // item's entries (increasing partner id) into ipart[islot[item] + slot].
-//   part[] holds double4 (ax, ay, az, phi) per (pair, side, slot); pair k's block starts
-//   at off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+//   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
+//   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+template <class G>
 __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
                                                    const int* __restrict__ ncount, const uint32_t* __restrict__ pdval,
                                                    const int2* __restrict__ pairs, const long long* __restrict__ poff,
-                                                   const double4* __restrict__ part,
-                                                   const long long* __restrict__ islot, double4* __restrict__ ipart) {
+                                                   const Quad<G>* __restrict__ part,
+                                                   const long long* __restrict__ islot, Quad<G>* __restrict__ ipart) {
     int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (it >= nitems) return;
     int4 w = items[it];
     int cnt = ncount[w.x];
     for (int slot = lane; slot < cnt; slot += 32) {
-        double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
+        Quad<G> acc{G(0), G(0), G(0), G(0)};
         for (int e = w.y; e < w.z; e++) {
             uint32_t v = pdval[e];
             uint32_t k = v >> 1;
             long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
-            double4 q = part[o];
-            px += q.x;
-            py += q.y;
-            pz += q.z;
-            pp += q.w;
+            Quad<G> q = part[o];
+            acc.x = acc.x + q.x;
+            acc.y = acc.y + q.y;
+            acc.z = acc.z + q.z;
+            acc.w = acc.w + q.w;
         }
-        ipart[islot[it] + slot] = make_double4(px, py, pz, pp);
+        ipart[islot[it] + slot] = acc;
     }
 }
 
@@ -216,7 +255,8 @@ __global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, con
     if (i < nitems) sizes[i] = ncount[items[i].x];
 }
 
-void run_p2p_gather(fmm_ctx* c) {
+template <class G>
+static void gather_launch(fmm_ctx* c) {
     cudaStream_t s = c->stream;
     const ItemSet& it = c->p2p_items;
     int64_t ni = it.n_items;
@@ -228,12 +268,19 @@ void run_p2p_gather(fmm_ctx* c) {
     long long nslots = 0;
     GB_CUDA(cudaMemcpyAsync(&nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    ensure(c->p2p_ipart, sizeof(double4) * (size_t)(nslots > 0 ? nslots : 1));
-    p2p_gather_k<<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
-                                                       c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
-                                                       c->p2p_off.as<long long>(), c->p2p_part.as<double4>(),
-                                                       c->p2p_islot.as<long long>(), c->p2p_ipart.as<double4>());
+    ensure(c->p2p_ipart, sizeof(Quad<G>) * (size_t)(nslots > 0 ? nslots : 1));
+    p2p_gather_k<G><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
+                                                          c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
+                                                          c->p2p_off.as<long long>(), c->p2p_part.as<Quad<G>>(),
+                                                          c->p2p_islot.as<long long>(), c->p2p_ipart.as<Quad<G>>());
     GB_LAUNCH("p2p_gather_k");
+}
+
+void run_p2p_gather(fmm_ctx* c) {
+    if (c->precision == FMM_DF64)
+        gather_launch<df64>(c);
+    else
+        gather_launch<double>(c);
 }
 
 // ------------------------------------------------------------------ diagnostics

@@ -23,8 +23,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbfmm.so")
 
 STANDARD, CONSERVING = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 P_MAX = 6
+DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_forces", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",

@@ -34,13 +34,13 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def new_ctx(fmm, torch):
+def new_ctx(fmm, torch, precision=0):
     """A context queued on torch's current stream, so tensor reads are ordered after it."""
-    return fmm.FMM(0, stream=torch.cuda.current_stream())
+    return fmm.FMM(0, precision=precision, stream=torch.cuda.current_stream())
 
 
-def run_gpu(fmm, torch, x, m, leaf, p, theta, variant, want_pot=True, device_arrays=True):
-    f = new_ctx(fmm, torch)
+def run_gpu(fmm, torch, x, m, leaf, p, theta, variant, want_pot=True, device_arrays=True, precision=0):
+    f = new_ctx(fmm, torch, precision)
     N = x.shape[0]
     if device_arrays:
         xd, md = torch.from_numpy(x).cuda(), torch.from_numpy(m).cuda()
@@ -279,3 +279,56 @@ def test_medium_size_bitexact_lists(fmm, torch_cuda, orc):
     check_structure(g["f"], r, 1 << 17)
     assert rel(g["acc"], r.acc) < TOL
     g["f"].close()
+
+
+# ------------------------------------------------------------- arithmetic modes
+
+# FMM_DF64 (double-float pair kernels) must meet the binary64 bound; FMM_MIXED (binary32
+# pair kernels, binary64 translations and accumulators) is held to a stated bound.
+MODE_TOL = {2: TOL, 1: 2e-5}
+
+
+@pytest.mark.parametrize("precision", [2, 1], ids=["df64", "mixed"])
+@pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_precision_modes(fmm, torch_cuda, orc, case, precision):
+    name, gen, N, leaf, p, theta = case
+    x, m = gen(N)
+    for variant in (0, 1):
+        r = orc.run(x, m, leaf, p, theta, variant, want_pot=True)
+        g = run_gpu(fmm, torch_cuda, x, m, leaf, p, theta, variant, precision=precision)
+        check_structure(g["f"], r, N)
+        ea, ep = rel(g["acc"], r.acc), rel(g["pot"], r.pot)
+        assert ea < MODE_TOL[precision], (name, variant, ea)
+        assert ep < MODE_TOL[precision], (name, variant, ep)
+        F, T = g["f"].diagnostics()
+        a = g["acc"]
+        fs = (m * np.linalg.norm(a, axis=1)).sum()
+        ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+        lim = 1e-14 if precision == 2 else 1e-6
+        assert np.linalg.norm(F) < lim * fs
+        if variant == 1:
+            assert np.linalg.norm(T) < lim * ts
+        g["f"].close()
+
+
+def test_df64_every_order_and_full_size_sample(fmm, torch_cuda, orc):
+    for p in range(1, fmm.DF64_P_MAX + 1):
+        x, m = synth.plummer(2048, 40 + p)
+        for variant in (0, 1):
+            r = orc.run(x, m, 12, p, 0.55, variant, want_pot=False, want_internals=False)
+            g = run_gpu(fmm, torch_cuda, x, m, 12, p, 0.55, variant, want_pot=False, precision=2)
+            assert rel(g["acc"], r.acc) < TOL, (p, variant)
+            g["f"].close()
+    f = new_ctx(fmm, torch_cuda, 2)
+    f.build(*synth.plummer(1000, 3), 16)
+    with pytest.raises(fmm.FMMError) as e:
+        f.forces(fmm.DF64_P_MAX + 1, 0.5, 0, np.empty((1000, 3)), None)
+    assert e.value.status == -1
+
+
+def test_df64_matches_fp64_at_benchmark_size(fmm, torch_cuda):
+    """N = 2^20, p = 4, theta = 0.6, conserving: double-float against binary64 on the GPU."""
+    x, m = synth.plummer(1 << 20, 2)
+    a = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, 1, want_pot=False, precision=0)
+    b = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, 1, want_pot=False, precision=2)
+    assert rel(b["acc"], a["acc"]) < TOL
