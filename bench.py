@@ -143,13 +143,15 @@ def run_gbfmm(args):
         W["N"] = args.n
         W["workload"] = f"plummer-{args.n}-{args.variant}"
     W["variant"] = args.variant
+    W["precision"] = args.precision
     N = W["N"]
     x, m = synth.plummer(N, W["seed"])
     xd = torch.from_numpy(x).to(dev)
     md = torch.from_numpy(m).to(dev)
     acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    f = fmm.FMM(local, fmm.FP64, stream)
+    prec = {"fp64": fmm.FP64, "df64": fmm.DF64, "mixed": fmm.MIXED}[args.precision]
+    f = fmm.FMM(local, prec, stream)
     variant = fmm.CONSERVING if args.variant == "conserving" else fmm.STANDARD
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
@@ -221,6 +223,17 @@ def run_gbfmm(args):
     # accuracy and conservation of the timed configuration
     Fsum, Tsum = f.diagnostics()
     a = acc.cpu().numpy()
+    err = {"vs_direct_sampled": sampled_direct_error(torch, dev, x, m, a)}
+    if prec != fmm.FP64:     # the binary64 mode on the same input, untimed
+        g = fmm.FMM(local, fmm.FP64, stream)
+        ref = torch.empty_like(acc)
+        with torch.cuda.stream(stream):
+            g.build(xd, md, W["leaf"])
+            g.forces(W["p"], W["theta"], variant, ref, None)
+        stream.synchronize()
+        r = ref.cpu().numpy()
+        err["vs_fp64_gpu"] = float(np.linalg.norm(a - r) / np.linalg.norm(r))
+        g.close()
     ts = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum())
     fsum = float((m * np.linalg.norm(a, axis=1)).sum())
 
@@ -245,13 +258,15 @@ def run_gbfmm(args):
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer sphere)",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[args.precision],
+        "data": "synthetic (seeded Plummer sphere)",
         "config": {"workload": W["workload"], "N": N, "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
                    "variant": W["variant"], "precision": W["precision"], "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
         "work": {"n_m2l_pairs": work["n_m2l"], "n_p2p_particle_pairs": work["n_pp"],
                  "m2l_flops": work["m2l"], "p2p_flops": work["p2p"]},
+        "force_err_rel_l2": err,
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
         "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
@@ -265,6 +280,24 @@ def run_gbfmm(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return line
+
+
+def sampled_direct_error(torch, dev, x, m, a, n_targets=400):
+    """Relative L2 error of accelerations a (N x 3) against the direct sum (eq. jia) on
+    n_targets sampled particles, evaluated with plain binary64 tensor operations."""
+    rng = np.random.default_rng(0)
+    tg = rng.choice(x.shape[0], n_targets, replace=False)
+    X = torch.from_numpy(x).to(dev)
+    M = torch.from_numpy(m).to(dev)
+    ref = torch.zeros((n_targets, 3), dtype=torch.float64, device=dev)
+    for i0 in range(0, n_targets, 16):
+        t = torch.from_numpy(tg[i0:i0 + 16]).to(dev)
+        d = X[t][:, None, :] - X[None, :, :]                      # (16, N, 3)
+        r2 = (d * d).sum(-1)
+        inv3 = torch.where(r2 > 0, r2.rsqrt() ** 3, torch.zeros_like(r2))
+        ref[i0:i0 + 16] = -(M[None, :, None] * d * inv3[..., None]).sum(1)
+    ref = ref.cpu().numpy()
+    return float(np.linalg.norm(a[tg] - ref) / np.linalg.norm(ref))
 
 
 def oracle_sample_rate():
@@ -325,6 +358,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--n", type=int, default=0, help="override N (profiling of a smaller case)")
     ap.add_argument("--variant", default="conserving", choices=["conserving", "standard"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "mixed"],
+                    help="arithmetic of the pair kernels (M2L, P2P)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
