@@ -65,22 +65,22 @@ __global__ void __launch_bounds__(EB) m2m_k(int lo, int hi, const int* __restric
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __restrict__ items,
                                                 const uint64_t* __restrict__ dir, int bits,
-                                                const typename Prec<T>::S* __restrict__ zst,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz,
                                                 const T* __restrict__ mom, T* __restrict__ part) {
     using E = Exp<P>;
-    using S = typename Prec<T>::S;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
     T L[E::NM];
 #pragma unroll
     for (int k = 0; k < E::NM; k++) L[k] = T(0);
-    S zx = zst[3 * w.x], zy = zst[3 * w.x + 1], zz = zst[3 * w.x + 2];
+    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        T rx = Prec<T>::narrow(zx - zst[3 * src]), ry = Prec<T>::narrow(zy - zst[3 * src + 1]);
-        T rz = Prec<T>::narrow(zz - zst[3 * src + 2]);
+        // R = Z_tgt - Z_src in binary64, then narrowed to the kernel type
+        T rx = to_kernel(zx - Zx[src], T()), ry = to_kernel(zy - Zy[src], T()), rz = to_kernel(zz - Zz[src], T());
         T D[E::NM];
         E::dtensor(rx, ry, rz, D);
         E::m2l_std(mom + (int64_t)src * E::NM, D, L);
@@ -93,22 +93,22 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __restrict__ items,
                                                 const uint64_t* __restrict__ dir, int bits,
-                                                const typename Prec<T>::S* __restrict__ zst,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz,
                                                 const T* __restrict__ cmom, T* __restrict__ part) {
     using E = Exp<P>;
-    using S = typename Prec<T>::S;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
     T SU[E::NSU];
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) SU[k] = T(0);
-    S zx = zst[3 * w.x], zy = zst[3 * w.x + 1], zz = zst[3 * w.x + 2];
+    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        T rx = Prec<T>::narrow(zx - zst[3 * src]), ry = Prec<T>::narrow(zy - zst[3 * src + 1]);
-        T rz = Prec<T>::narrow(zz - zst[3 * src + 2]);
+        // R = Z_tgt - Z_src in binary64, then narrowed to the kernel type
+        T rx = to_kernel(zx - Zx[src], T()), ry = to_kernel(zy - Zy[src], T()), rz = to_kernel(zz - Zz[src], T());
         T H[E::NQ];
         E::htensor(rx, ry, rz, H);
         E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
@@ -140,17 +140,6 @@ template <class T>
 __global__ void convert_k(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (i < n) out[i] = to_kernel(in[i], T());
-}
-
-template <class S>
-__global__ void pack_centres_k(int nn, const double* __restrict__ Zx, const double* __restrict__ Zy,
-                               const double* __restrict__ Zz, S* __restrict__ zst) {
-    int i = blockIdx.x * EB + threadIdx.x;
-    if (i < nn) {
-        zst[3 * i] = to_storage(Zx[i], S());
-        zst[3 * i + 1] = to_storage(Zy[i], S());
-        zst[3 * i + 2] = to_storage(Zz[i], S());
-    }
 }
 
 // conserving source moments of every cell (formed once per moment build)
@@ -297,17 +286,8 @@ void run_moments_p(fmm_ctx* c) {
     ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
     con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
     GB_LAUNCH("con_moments_k");
-    // copies in the pair-kernel type and centres in the storage type
-    if (c->precision == FMM_FP64) {
-        ensure(c->zst, sizeof(double) * 3 * (size_t)nn);
-        pack_centres_k<double><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nZx.as<double>(), c->nZy.as<double>(),
-                                                               c->nZz.as<double>(), c->zst.as<double>());
-        GB_LAUNCH("pack_centres_k");
-    } else {
-        ensure(c->zst, sizeof(df64) * 3 * (size_t)nn);
-        pack_centres_k<df64><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nZx.as<double>(), c->nZy.as<double>(),
-                                                             c->nZz.as<double>(), c->zst.as<df64>());
-        GB_LAUNCH("pack_centres_k");
+    // moments in the pair-kernel type
+    if (c->precision != FMM_FP64) {
         int64_t nm = (int64_t)nn * E::NM, nc = (int64_t)nn * E::NSU;
         if (c->precision == FMM_DF64) {
             ensure(c->momT, sizeof(df64) * (size_t)nm);
@@ -327,7 +307,6 @@ void run_moments_p(fmm_ctx* c) {
 template <int P, class T>
 void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     using E = Exp<P>;
-    using S = typename Prec<T>::S;
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
     const uint64_t* dir = c->m2l_dir.as<uint64_t>();
@@ -336,14 +315,15 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     bool native = c->precision == FMM_FP64;
     const T* mom = native ? c->mom.as<T>() : c->momT.as<T>();
     const T* cmom = native ? c->cmom.as<T>() : c->cmomT.as<T>();
-    const S* zst = c->zst.as<S>();
+    const double *zx = c->nZx.as<double>(), *zy = c->nZy.as<double>(), *zz = c->nZz.as<double>();
     int nl_max = E::NSU > E::NM ? E::NSU : E::NM;
     ensure(c->m2l_part, sizeof(T) * (size_t)(ni > 0 ? ni : 1) * nl_max);
     T* part = c->m2l_part.as<T>();
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
-            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zst, cmom, part);
+            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zx, zy, zz, cmom,
+                                                            part);
             GB_LAUNCH("m2l_con_k");
         }
         m2l_reduce_k<E::NSU, T><<<grid_for((int64_t)nn * E::NSU, EB), EB, 0, s>>>(
@@ -354,7 +334,8 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
         if (ni > 0) {
-            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zst, mom, part);
+            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zx, zy, zz, mom,
+                                                            part);
             GB_LAUNCH("m2l_std_k");
         }
         m2l_reduce_k<E::NM, T><<<grid_for((int64_t)nn * E::NM, EB), EB, 0, s>>>(

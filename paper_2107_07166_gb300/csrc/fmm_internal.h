@@ -118,7 +118,6 @@ struct fmm_ctx {
     gbfmm::DevBuf cmom;                        // conserving source moments, n_nodes x 4 nmi(p-1)
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     bool pos_valid = false;
-    gbfmm::DevBuf zst;                         // node centres in the storage type (3 per node)
     gbfmm::DevBuf momT, cmomT;                 // moments in the pair-kernel type
     int id_bits = 0;
     // results (sorted order) and output staging

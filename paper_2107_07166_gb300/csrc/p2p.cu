@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                                             const long long* __restrict__ off, const int* __restrict__ nfirst,
                                             const int* __restrict__ ncount,
                                             const PState<typename Prec<T>::S>* __restrict__ pos,
+                                            const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                            const double* __restrict__ Zz,
                                             Quad<typename Prec<T>::G>* __restrict__ part) {
     using S = typename Prec<T>::S;
     using G = typename Prec<T>::G;
@@ -50,8 +52,15 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
         int nA = ncount[A], nB = ncount[B], fA = nfirst[A], fB = nfirst[B];
         long long o = off[k];
         bool self = A == B;
+        // positions are stored relative to their leaf's centre; the pair's centre
+        // separation R = Z_A - Z_B is formed in binary64 and folded into the A side
+        S rx = to_storage(Zx[A] - Zx[B], S()), ry = to_storage(Zy[A] - Zy[B], S());
+        S rz = to_storage(Zz[A] - Zz[B], S());
         if (nA <= 32 && nB <= 32) {
-            if (lane < nA) sA[w][lane] = pos[fA + lane];
+            if (lane < nA) {
+                PState<S> q = pos[fA + lane];
+                sA[w][lane] = PState<S>{rx + q.x, ry + q.y, rz + q.z, q.m};
+            }
             if (lane < nB) sB[w][lane] = pos[fB + lane];
             cacc[w][lane] = Quad<T>{T(0), T(0), T(0), T(0)};
             T racc[4] = {T(0), T(0), T(0), T(0)};  // row task tau = lane + 32 q: (a, comp) = (tau >> 2, tau & 3)
@@ -136,8 +145,10 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
             for (int side = 0; side < (self ? 1 : 2); side++) {
                 int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
                 long long oT = side ? o + nA : o;
+                S sx = side ? -rx : rx, sy = side ? -ry : ry, sz = side ? -rz : rz;
                 for (int t = lane; t < nT; t += 32) {
                     PState<S> pt = pos[fT + t];
+                    pt = PState<S>{sx + pt.x, sy + pt.y, sz + pt.z, pt.m};
                     T ax = T(0), ay = T(0), az = T(0), ph = T(0);
                     for (int u = 0; u < nS; u++) {
                         if (self && u == t) continue;
@@ -162,14 +173,20 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
     }
 }
 
-// packed (x, y, z, m) of every sorted particle in the storage type S
+// packed (x - Z_leaf, y - Z_leaf, z - Z_leaf, m) of every sorted particle in the storage
+// type S: offsets from the leaf centre keep double-float positions accurate to ~2^-48 of
+// the leaf size rather than of the coordinate
 template <class S>
-__global__ void pack_pos_k(int n, const double* __restrict__ xs, const double* __restrict__ ys,
-                           const double* __restrict__ zs, const double* __restrict__ ms, PState<S>* __restrict__ pos) {
+__global__ void pack_pos_k(int n, const int* __restrict__ leaf_of, const double* __restrict__ xs,
+                           const double* __restrict__ ys, const double* __restrict__ zs,
+                           const double* __restrict__ ms, const double* __restrict__ Zx,
+                           const double* __restrict__ Zy, const double* __restrict__ Zz, PState<S>* __restrict__ pos) {
     int i = blockIdx.x * PB + threadIdx.x;
-    if (i < n)
-        pos[i] = PState<S>{to_storage(xs[i], S()), to_storage(ys[i], S()), to_storage(zs[i], S()),
-                           to_storage(ms[i], S())};
+    if (i < n) {
+        int l = leaf_of[i];
+        pos[i] = PState<S>{to_storage(xs[i] - Zx[l], S()), to_storage(ys[i] - Zy[l], S()),
+                           to_storage(zs[i] - Zz[l], S()), to_storage(ms[i], S())};
+    }
 }
 
 template <class T>
@@ -180,8 +197,9 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     int n = (int)c->N;
     if (!c->pos_valid) {
         ensure(c->pos4, sizeof(PState<S>) * (size_t)n);
-        pack_pos_k<S><<<grid_for(n, PB), PB, 0, s>>>(n, c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
-                                                   c->ms.as<double>(), c->pos4.as<PState<S>>());
+        pack_pos_k<S><<<grid_for(n, PB), PB, 0, s>>>(n, c->leaf_of.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+                                                   c->zs.as<double>(), c->ms.as<double>(), c->nZx.as<double>(),
+                                                   c->nZy.as<double>(), c->nZz.as<double>(), c->pos4.as<PState<S>>());
         GB_LAUNCH("pack_pos_k");
         c->pos_valid = true;
     }
@@ -202,6 +220,7 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     stage_begin(c, ST_P2P);
     kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
                                            c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
+                                           c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
                                            c->p2p_part.as<Quad<G>>());
     GB_LAUNCH("p2p_k");
     stage_end(c, ST_P2P);
