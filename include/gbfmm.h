@@ -129,6 +129,14 @@ GBFMM_API int fmm_get_geometry(fmm_ctx *c, double *M, double *Z, double *rmax);
  * m2l[n_m2l x 2], p2p[n_p2p x 2] (self pairs (A, A) included) */
 GBFMM_API int fmm_get_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p);
 
+/* Initial sizes (entries) of the dual-tree walk's buffers: frontier, M2L pairs, P2P pairs.
+ * Without this call they start at 4N, 16N and 4N.  A walk that outgrows a buffer is run
+ * again with larger buffers (see fmm_walk_retries); the results do not depend on the
+ * sizes.  Invalidates cached lists. */
+GBFMM_API int fmm_set_walk_capacity(fmm_ctx *c, int64_t frontier, int64_t m2l, int64_t p2p);
+/* Number of walks this context has re-run after a buffer overflow. */
+GBFMM_API int fmm_walk_retries(fmm_ctx *c, int64_t *retries);
+
 /* Device time in milliseconds of each stage of the last build/forces call, measured
  * with CUDA events on the context's stream: [build, moments, walk, m2l, l2l, p2p, l2p].
  * A stage that did not run in that call reports -1. */

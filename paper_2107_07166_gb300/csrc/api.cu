@@ -169,6 +169,12 @@ int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_
         c->list_theta = -1.0;
         c->pos_valid = false;
         c->N = N;
+        // walk buffers: start from sizes that fit the usual lists (the walk grows them)
+        if (!c->caps_user) {
+            c->cap_m2l = std::max<int64_t>(c->cap_m2l, 16 * N + 4096);
+            c->cap_p2p = std::max<int64_t>(c->cap_p2p, 4 * N + 4096);
+            c->cap_fr = std::max<int64_t>(c->cap_fr, 4 * N + 4096);
+        }
         c->leaf = leaf_size;
         const double* xd = x;
         const double* md = m;
@@ -379,6 +385,23 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
         }
         return FMM_OK;
     });
+}
+
+int fmm_set_walk_capacity(fmm_ctx* c, int64_t frontier, int64_t m2l, int64_t p2p) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_walk_capacity: NULL context");
+    if (frontier < 1 || m2l < 1 || p2p < 1) return fail(FMM_ERR_INVALID, "fmm_set_walk_capacity: sizes must be >= 1");
+    c->cap_fr = frontier;
+    c->cap_m2l = m2l;
+    c->cap_p2p = p2p;
+    c->caps_user = true;
+    c->list_theta = -1.0;
+    return FMM_OK;
+}
+
+int fmm_walk_retries(fmm_ctx* c, int64_t* retries) {
+    if (!c || !retries) return fail(FMM_ERR_INVALID, "fmm_walk_retries: NULL argument");
+    *retries = c->walk_retries;
+    return FMM_OK;
 }
 
 int fmm_stage_times(fmm_ctx* c, double* ms, int n) {

@@ -102,7 +102,10 @@ struct fmm_ctx {
     // lists
     double list_theta = -1.0;
     int64_t n_m2l = 0, n_p2p = 0;
-    gbfmm::DevBuf fr0, fr1, cnt, cnt_off;      // walk frontier
+    gbfmm::DevBuf fr0, fr1, cnt, cnt_off;      // walk frontier and counters
+    int64_t cap_fr = 1 << 16, cap_m2l = 1 << 16, cap_p2p = 1 << 16;   // walk buffer sizes (grow only)
+    bool caps_user = false;                    // sizes set by fmm_set_walk_capacity
+    int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
     gbfmm::DevBuf m2l_dir;                     // uint64 directed keys (tgt << b | src), sorted
     gbfmm::DevBuf m2l_seg;                     // int64 [n_nodes + 1] segment starts per target

@@ -8,11 +8,17 @@
 //               otherwise split A or B into its children: a leaf is never split; between
 //               two inner nodes the larger r_max is split, ties -> larger count, then
 //               lower id.
-// The rule is symmetric in (A, B), so the emitted pair set is unique.  Each frontier
-// step counts every item's outputs, scans the counts and writes the outputs at their
-// offsets, so the emission order is deterministic too.  The lists are then expanded
-// into directed entries (target, source) and radix-sorted: every cell sees its partners
-// in increasing id order, which is also the canonical (min id, max id) order.
+// The rule is symmetric in (A, B), so the emitted pair set is unique.  The lists are then
+// expanded into directed entries (target, source) and radix-sorted: every cell sees its
+// partners in increasing id order, which is also the canonical (min id, max id) order,
+// and every later sum runs in that order.  The order in which a frontier step emits its
+// outputs therefore cannot change any result, so one kernel per step claims output
+// slots with warp-aggregated integer atomics, and the host launches a fixed number of
+// steps (2 x levels + 2 bounds the recursion depth) without waiting between them.  The
+// counters keep counting past the buffers' capacity; one read at the end detects an
+// overflow and the walk is run again with buffers of the reported sizes.
+#include <algorithm>
+
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 
@@ -55,39 +61,82 @@ __device__ __forceinline__ int decide(const NodeView& nv, int2 it, double theta,
     return 0;
 }
 
-__global__ void walk_count_k(const int2* __restrict__ fr, int nf, NodeView nv, double theta, Cnt3* __restrict__ cnt) {
-    int i = blockIdx.x * WB + threadIdx.x;
-    if (i >= nf) return;
-    int nnew = 0;
-    bool sa = false;
-    int d = decide(nv, fr[i], theta, &nnew, &sa);
-    cnt[i] = Cnt3{d == 0 ? nnew : 0, d == 1 ? 1 : 0, d == 2 ? 1 : 0};
+struct WalkCounters {
+    int nf[2];       // frontier sizes (read by the step of that parity, appended by the other)
+    int n_m2l, n_p2p;
+};
+
+__device__ __forceinline__ int warp_claim(int* counter, int want, unsigned lane_lt) {
+    // exclusive prefix of `want` over the warp and one atomic per warp
+    int incl = want;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(FULL, incl, d);
+        if ((int)(threadIdx.x & 31) >= d) incl += o;
+    }
+    int total = __shfl_sync(FULL, incl, 31);
+    int base = 0;
+    if ((threadIdx.x & 31) == 31 && total > 0) base = atomicAdd(counter, total);
+    base = __shfl_sync(FULL, base, 31);
+    (void)lane_lt;
+    return base + incl - want;
 }
 
-__global__ void walk_emit_k(const int2* __restrict__ fr, int nf, NodeView nv, double theta,
-                            const Cnt3* __restrict__ off, int2* __restrict__ fr_out, int2* __restrict__ m2l,
-                            int2* __restrict__ p2p) {
-    int i = blockIdx.x * WB + threadIdx.x;
-    if (i >= nf) return;
-    int2 it = fr[i];
-    int nnew = 0;
-    bool sa = false;
-    int d = decide(nv, it, theta, &nnew, &sa);
-    Cnt3 o = off[i];
-    if (d == 1) {
-        m2l[o.b] = it;
-    } else if (d == 2) {
-        p2p[o.c] = it;
-    } else if (it.x == it.y) {
-        int c0 = nv.child_first[it.x], nc = nv.nchild[it.x];
-        int k = o.a;
-        for (int a = 0; a < nc; a++)
-            for (int b = a; b < nc; b++) fr_out[k++] = make_int2(c0 + a, c0 + b);
-    } else {
-        int S = sa ? it.x : it.y;
-        int c0 = nv.child_first[S], nc = nv.nchild[S];
-        for (int a = 0; a < nc; a++) fr_out[o.a + a] = sa ? make_int2(c0 + a, it.y) : make_int2(it.x, c0 + a);
+__global__ void walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out, WalkCounters* __restrict__ cnt,
+                            int par, NodeView nv, double theta, int2* __restrict__ m2l, int cap_m2l,
+                            int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
+    int nf = min(cnt->nf[par], cap_fr);  // a frontier beyond the buffer was not stored (retried)
+    int lane = threadIdx.x & 31;
+    int64_t warp0 = ((int64_t)blockIdx.x * WB + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * WB) >> 5;
+    for (int64_t base = warp0 * 32; base < nf; base += nwarps * 32) {
+        int64_t i = base + lane;
+        int2 it = make_int2(0, 0);
+        int d = -1, nnew = 0;
+        bool sa = false;
+        if (i < nf) {
+            it = fr_in[i];
+            d = decide(nv, it, theta, &nnew, &sa);
+        }
+        int om = warp_claim(&cnt->n_m2l, d == 1 ? 1 : 0, 0);
+        int op = warp_claim(&cnt->n_p2p, d == 2 ? 1 : 0, 0);
+        int of = warp_claim(&cnt->nf[par ^ 1], d == 0 ? nnew : 0, 0);
+        if (d == 1) {
+            if (om < cap_m2l) m2l[om] = it;
+        } else if (d == 2) {
+            if (op < cap_p2p) p2p[op] = it;
+        } else if (d == 0) {
+            if (it.x == it.y) {
+                int c0 = nv.child_first[it.x], nc = nv.nchild[it.x];
+                int k = of;
+                for (int a = 0; a < nc; a++)
+                    for (int b = a; b < nc; b++, k++)
+                        if (k < cap_fr) fr_out[k] = make_int2(c0 + a, c0 + b);
+            } else {
+                int S = sa ? it.x : it.y;
+                int c0 = nv.child_first[S], nc = nv.nchild[S];
+                for (int a = 0; a < nc; a++)
+                    if (of + a < cap_fr) fr_out[of + a] = sa ? make_int2(c0 + a, it.y) : make_int2(it.x, c0 + a);
+            }
+        }
     }
+}
+
+// prepares the next step: its input count is this step's output, its output starts at 0;
+// frontier overflow is recorded in *over (the largest frontier seen)
+__global__ void walk_advance_k(WalkCounters* cnt, int par, int* max_fr) {
+    int nxt = cnt->nf[par ^ 1];
+    if (nxt > *max_fr) *max_fr = nxt;
+    cnt->nf[par] = 0;
+}
+
+__global__ void walk_init_k(WalkCounters* cnt, int2* fr0, int* max_fr) {
+    cnt->nf[0] = 1;
+    cnt->nf[1] = 0;
+    cnt->n_m2l = 0;
+    cnt->n_p2p = 0;
+    *max_fr = 1;
+    fr0[0] = make_int2(0, 0);
 }
 
 // directed M2L entries: (A -> B) and (B -> A) for every mutual pair
@@ -119,12 +168,21 @@ __global__ void p2p_dir_k(const int2* __restrict__ pairs, int64_t n, int bits, u
     }
 }
 
-__global__ void seg_count_k(const uint64_t* __restrict__ keys, int64_t n, int bits, int* __restrict__ cnt) {
-    int64_t i = (int64_t)blockIdx.x * WB + threadIdx.x;
-    if (i >= n) return;
-    uint64_t k = keys[i];
-    if (k == (1ull << (2 * bits)) - 1ull) return;
-    atomicAdd(&cnt[k >> bits], 1);  // integer counts: order independent
+// seg[x] = first sorted entry whose target is >= x (binary search), x in [0, nn]
+__global__ void seg_bounds_k(const uint64_t* __restrict__ keys, int64_t n, int bits, int nn,
+                             long long* __restrict__ seg) {
+    int x = blockIdx.x * WB + threadIdx.x;
+    if (x > nn) return;
+    uint64_t key = (uint64_t)x << bits;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    seg[x] = lo;
 }
 
 // Work items over segments seg[0..n]: every segment is cut into chunks of CH entries.
@@ -185,37 +243,54 @@ void run_walk(fmm_ctx* c, double theta) {
     cudaStream_t s = c->stream;
     NodeView nv = node_view(c);
     int64_t nn = c->n_nodes;
-    // frontier starts with Self(root)
-    int64_t cap_fr = 4096;
-    ensure(c->fr0, sizeof(int2) * (size_t)cap_fr);
-    int2 root = make_int2(0, 0);
-    GB_CUDA(cudaMemcpyAsync(c->fr0.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
-    int64_t nf = 1, n_m2l = 0, n_p2p = 0;
-    while (nf > 0) {
-        if (nf >= ((int64_t)1 << 31)) throw FmmError{FMM_ERR_CAPACITY, "walk frontier above 2^31"};
-        ensure(c->cnt, sizeof(Cnt3) * (size_t)nf);
-        ensure(c->cnt_off, sizeof(Cnt3) * (size_t)(nf + 1));
-        walk_count_k<<<grid_for(nf, WB), WB, 0, s>>>(c->fr0.as<int2>(), (int)nf, nv, theta, c->cnt.as<Cnt3>());
-        GB_LAUNCH("walk_count_k");
-        scan_cnt3(c, c->cnt.as<Cnt3>(), nf, c->cnt_off.as<Cnt3>());
-        Cnt3 tot;
-        GB_CUDA(cudaMemcpyAsync(&tot, c->cnt_off.as<Cnt3>() + nf, sizeof(Cnt3), cudaMemcpyDeviceToHost, s));
+    // fixed number of steps, no host round trip between them; one retry if a buffer overflowed
+    int steps = 2 * c->n_levels + 2;
+    int dev_sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int grid = dev_sms * 8;
+    int64_t n_m2l = 0, n_p2p = 0;
+    for (int attempt = 0;; attempt++) {
+        int64_t cap_fr = c->cap_fr, cap_m2l = c->cap_m2l, cap_p2p = c->cap_p2p;
+        ensure(c->fr0, sizeof(int2) * (size_t)cap_fr);
+        ensure(c->fr1, sizeof(int2) * (size_t)cap_fr);
+        ensure(c->m2l_pairs, sizeof(int2) * (size_t)cap_m2l);
+        ensure(c->p2p_pairs, sizeof(int2) * (size_t)cap_p2p);
+        ensure(c->cnt, sizeof(WalkCounters) + 16);
+        WalkCounters* cnt = reinterpret_cast<WalkCounters*>(c->cnt.p);
+        int* max_fr = reinterpret_cast<int*>(cnt + 1);
+        walk_init_k<<<1, 1, 0, s>>>(cnt, c->fr0.as<int2>(), max_fr);
+        GB_LAUNCH("walk_init_k");
+        for (int k = 0; k < steps; k++) {
+            int par = k & 1;
+            int2* fin = par ? c->fr1.as<int2>() : c->fr0.as<int2>();
+            int2* fout = par ? c->fr0.as<int2>() : c->fr1.as<int2>();
+            walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, nv, theta, c->m2l_pairs.as<int2>(), (int)cap_m2l,
+                                            c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr);
+            GB_LAUNCH("walk_step_k");
+            walk_advance_k<<<1, 1, 0, s>>>(cnt, par, max_fr);
+            GB_LAUNCH("walk_advance_k");
+        }
+        WalkCounters h;
+        int hmax = 0;
+        GB_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(WalkCounters), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&hmax, max_fr, sizeof(int), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
-        if ((int64_t)n_m2l + tot.b >= ((int64_t)1 << 31) || (int64_t)n_p2p + tot.c >= ((int64_t)1 << 30))
-            throw FmmError{FMM_ERR_CAPACITY, "interaction lists above 2^31 entries"};
-        ensure(c->fr1, sizeof(int2) * (size_t)(tot.a > 0 ? tot.a : 1));
-        ensure_keep(c->m2l_pairs, sizeof(int2) * (size_t)(n_m2l + tot.b + 1), s);
-        ensure_keep(c->p2p_pairs, sizeof(int2) * (size_t)(n_p2p + tot.c + 1), s);
-        walk_emit_k<<<grid_for(nf, WB), WB, 0, s>>>(c->fr0.as<int2>(), (int)nf, nv, theta, c->cnt_off.as<Cnt3>(),
-                                                    c->fr1.as<int2>(), c->m2l_pairs.as<int2>() + n_m2l,
-                                                    c->p2p_pairs.as<int2>() + n_p2p);
-        GB_LAUNCH("walk_emit_k");
-        n_m2l += tot.b;
-        n_p2p += tot.c;
-        nf = tot.a;
-        DevBuf t = c->fr0;
-        c->fr0 = c->fr1;
-        c->fr1 = t;
+        if (h.nf[0] != 0 || h.nf[1] != 0) throw FmmError{FMM_ERR_CAPACITY, "walk did not finish in 2 x levels + 2 steps"};
+        bool over = h.n_m2l > cap_m2l || h.n_p2p > cap_p2p || hmax > cap_fr;
+        if (h.n_m2l < 0 || h.n_p2p < 0 || hmax < 0) throw FmmError{FMM_ERR_CAPACITY, "walk counters above 2^31"};
+        if (over) {
+            // a truncated frontier under-reports what the later steps need: grow each
+            // overflowing buffer to at least twice its size and try again
+            if (attempt >= 10) throw FmmError{FMM_ERR_CAPACITY, "walk buffers still overflow after 10 retries"};
+            if (h.n_m2l > cap_m2l) c->cap_m2l = std::max<int64_t>(2 * cap_m2l, (int64_t)h.n_m2l + h.n_m2l / 8);
+            if (h.n_p2p > cap_p2p) c->cap_p2p = std::max<int64_t>(2 * cap_p2p, (int64_t)h.n_p2p + h.n_p2p / 8);
+            if (hmax > cap_fr) c->cap_fr = std::max<int64_t>(2 * cap_fr, (int64_t)hmax + hmax / 8);
+            c->walk_retries++;
+            continue;
+        }
+        n_m2l = h.n_m2l;
+        n_p2p = h.n_p2p;
+        break;
     }
     c->n_m2l = n_m2l;
     c->n_p2p = n_p2p;
@@ -224,19 +299,15 @@ void run_walk(fmm_ctx* c, double theta) {
     // M2L: directed entries sorted by (target, source)
     int64_t nd = 2 * n_m2l;
     ensure(c->m2l_dir, sizeof(uint64_t) * (size_t)(nd > 0 ? nd : 1));
-    ensure(c->seg_cnt, sizeof(int) * (size_t)(nn + 1));
     ensure(c->m2l_seg, sizeof(long long) * (size_t)(nn + 1));
     if (n_m2l > 0) {
         m2l_dir_k<<<grid_for(n_m2l, WB), WB, 0, s>>>(c->m2l_pairs.as<int2>(), n_m2l, bits, c->m2l_dir.as<uint64_t>());
         GB_LAUNCH("m2l_dir_k");
         radix_sort(c, c->m2l_dir, c->keys1, nullptr, nullptr, nd, 2 * bits);
     }
-    GB_CUDA(cudaMemsetAsync(c->seg_cnt.p, 0, sizeof(int) * (size_t)nn, s));
-    if (nd > 0) {
-        seg_count_k<<<grid_for(nd, WB), WB, 0, s>>>(c->m2l_dir.as<uint64_t>(), nd, bits, c->seg_cnt.as<int>());
-        GB_LAUNCH("seg_count_k");
-    }
-    scan_i64(c, c->seg_cnt.as<int>(), nn, c->m2l_seg.as<long long>());
+    seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->m2l_dir.as<uint64_t>(), nd, bits, (int)nn,
+                                                    c->m2l_seg.as<long long>());
+    GB_LAUNCH("seg_bounds_k");
     // P2P: directed entries with payload (pair << 1 | side), plus partial offsets
     int64_t np = 2 * n_p2p;
     ensure(c->p2p_dir, sizeof(uint64_t) * (size_t)np);
@@ -250,10 +321,9 @@ void run_walk(fmm_ctx* c, double theta) {
     GB_LAUNCH("p2p_dir_k");
     scan_i64_from_i64(c, c->flags.as<long long>(), n_p2p, c->p2p_off.as<long long>());
     radix_sort(c, c->p2p_dir, c->keys1, &c->p2p_dval, &c->vals1, np, 2 * bits);
-    GB_CUDA(cudaMemsetAsync(c->seg_cnt.p, 0, sizeof(int) * (size_t)nn, s));
-    seg_count_k<<<grid_for(np, WB), WB, 0, s>>>(c->p2p_dir.as<uint64_t>(), np, bits, c->seg_cnt.as<int>());
-    GB_LAUNCH("seg_count_k");
-    scan_i64(c, c->seg_cnt.as<int>(), nn, c->p2p_seg.as<long long>());
+    seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->p2p_dir.as<uint64_t>(), np, bits, (int)nn,
+                                                    c->p2p_seg.as<long long>());
+    GB_LAUNCH("seg_bounds_k");
     // work items: 32 M2L sources per chunk, 64 P2P entries per chunk
     build_items(c, c->m2l_seg.as<long long>(), (int)nn, M2L_CHUNK, c->m2l_items);
     build_items(c, c->p2p_seg.as<long long>(), (int)nn, P2P_CHUNK, c->p2p_items);

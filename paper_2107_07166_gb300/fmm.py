@@ -29,7 +29,7 @@ DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_forces", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
-           "fmm_stage_times", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_stage_times", "fmm_set_walk_capacity", "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -66,6 +66,8 @@ def load(path: str = LIB_PATH):
             "fmm_get_geometry": (i32, [P, P, P, P]),
             "fmm_get_lists": (i32, [P, P, P]),
             "fmm_stage_times": (i32, [P, P, i32]),
+            "fmm_set_walk_capacity": (i32, [P, i64, i64, i64]),
+            "fmm_walk_retries": (i32, [P, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
             "fmm_strerror": (C.c_char_p, [i32]),
@@ -203,6 +205,14 @@ class FMM:
         p2p = np.zeros((c["n_p2p"], 2), np.int32)
         _check(self.lib.fmm_get_lists(self.h, _ptr(m2l), _ptr(p2p)), "fmm_get_lists")
         return m2l, p2p
+
+    def set_walk_capacity(self, frontier: int, m2l: int, p2p: int):
+        _check(self.lib.fmm_set_walk_capacity(self.h, int(frontier), int(m2l), int(p2p)), "fmm_set_walk_capacity")
+
+    def walk_retries(self) -> int:
+        r = np.zeros(1, np.int64)
+        _check(self.lib.fmm_walk_retries(self.h, _ptr(r)), "fmm_walk_retries")
+        return int(r[0])
 
     def stage_times(self):
         ms = np.zeros(len(STAGES))

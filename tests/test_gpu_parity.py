@@ -200,6 +200,23 @@ def test_diagnostics_and_conservation(fmm, torch_cuda):
         g["f"].close()
 
 
+def test_walk_retries_after_buffer_overflow(fmm, torch_cuda, orc):
+    """Tiny walk buffers force the overflow path: the walk is re-run with larger buffers
+    and the lists and forces are those of an ordinary run."""
+    x, m = synth.plummer(6000, 17)
+    r = orc.run(x, m, 8, 3, 0.5, 1, want_pot=False)
+    f = new_ctx(fmm, torch_cuda)
+    f.set_walk_capacity(16, 16, 16)
+    f.build(x, m, 8)
+    acc = np.empty((6000, 3))
+    f.forces(3, 0.5, 1, acc, None)
+    assert f.walk_retries() >= 3
+    m2l, p2p = f.get_lists()
+    assert np.array_equal(m2l, r.m2l) and np.array_equal(p2p, r.p2p)
+    assert rel(acc, r.acc) < TOL
+    f.close()
+
+
 def test_errors_leave_outputs_untouched(fmm, torch_cuda):
     x, m = synth.plummer(1000, 14)
     f = new_ctx(fmm, torch_cuda)
