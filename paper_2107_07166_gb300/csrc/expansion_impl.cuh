@@ -111,7 +111,22 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
         T rx = to_kernel(zx - Zx[src], T()), ry = to_kernel(zy - Zy[src], T()), rz = to_kernel(zz - Zz[src], T());
         T H[E::NQ];
         E::htensor(rx, ry, rz, H);
-        E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
+        if constexpr (sizeof(T) == 4) {
+            // binary32: the source block (4 nmi(p-1) floats, a multiple of 4) in 16-byte loads
+            T Cs[E::NSU];
+            const float4* src4 = reinterpret_cast<const float4*>(cmom + (int64_t)src * E::NSU);
+#pragma unroll
+            for (int k = 0; k < E::NSU / 4; k++) {
+                float4 v = src4[k];
+                Cs[4 * k] = v.x;
+                Cs[4 * k + 1] = v.y;
+                Cs[4 * k + 2] = v.z;
+                Cs[4 * k + 3] = v.w;
+            }
+            E::m2l_con(Cs, H, rx, ry, rz, SU);
+        } else {
+            E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
+        }
     }
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::to_g(SU[k]);
@@ -399,10 +414,10 @@ static void finish_launch(fmm_ctx* c, int variant, bool want_pot, double* acc_ou
 
 template <int P>
 void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
-    if (c->precision == FMM_DF64)
-        finish_launch<P, df64>(c, variant, want_pot, acc_out, pot_out);
-    else
+    if (c->precision == FMM_FP64)
         finish_launch<P, double>(c, variant, want_pot, acc_out, pot_out);
+    else
+        finish_launch<P, df64>(c, variant, want_pot, acc_out, pot_out);
 }
 
 // One translation unit per order instantiates the order's stages; the M2L launches of

@@ -19,9 +19,14 @@ namespace gbfmm {
 
 constexpr int PB = 128;                 // 4 warps
 constexpr int PW = PB / 32;
-constexpr int PCOL = 16;                // panel columns
-constexpr int PROW = PCOL * 4 + 4;      // doubles per panel row: [col][comp], padded (row stride = 4 mod 16)
-constexpr int PANEL = 32 * PROW;        // doubles per warp panel
+// panel columns: 8-byte types use 8 columns so that four warps of panels leave room for
+// four blocks per SM; 4-byte types use 16
+template <class T>
+struct Panel {
+    static constexpr int COLS = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int ROW = COLS * 4 + 4;  // elements per panel row: [col][comp], padded (stride = 4 mod 16)
+    static constexpr int SIZE = 32 * ROW;     // elements per warp panel
+};
 
 template <class S>
 struct PState {
@@ -34,11 +39,11 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                                             const long long* __restrict__ off, const int* __restrict__ nfirst,
                                             const int* __restrict__ ncount,
                                             const PState<typename Prec<T>::S>* __restrict__ pos,
-                                            const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                            const double* __restrict__ Zz,
+                                            const typename Prec<T>::S* __restrict__ sep,
                                             Quad<typename Prec<T>::G>* __restrict__ part) {
     using S = typename Prec<T>::S;
     using G = typename Prec<T>::G;
+    constexpr int PCOL = Panel<T>::COLS, PROW = Panel<T>::ROW, PANEL = Panel<T>::SIZE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PState<S> sA[PW][32], sB[PW][32];
     __shared__ Quad<T> cacc[PW][32];
@@ -53,9 +58,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
         long long o = off[k];
         bool self = A == B;
         // positions are stored relative to their leaf's centre; the pair's centre
-        // separation R = Z_A - Z_B is formed in binary64 and folded into the A side
-        S rx = to_storage(Zx[A] - Zx[B], S()), ry = to_storage(Zy[A] - Zy[B], S());
-        S rz = to_storage(Zz[A] - Zz[B], S());
+        // separation R = Z_A - Z_B (formed in binary64 by p2p_sep_k) is folded into the A side
+        S rx = sep[3 * k], ry = sep[3 * k + 1], rz = sep[3 * k + 2];
         if (nA <= 32 && nB <= 32) {
             if (lane < nA) {
                 PState<S> q = pos[fA + lane];
@@ -68,9 +72,11 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
             for (int cb = 0; cb < nB; cb += PCOL) {
                 int ncol = min(PCOL, nB - cb);
                 int nint = nA * ncol;
+                float rcol = 1.0f / (float)ncol;
                 // pair terms of the panel: d = X_a - X_b (formed in the storage type), r^-1, d r^-3
                 for (int t = lane; t < nint; t += 32) {
-                    int a = t / ncol, bl = t - a * ncol, b = cb + bl;
+                    int a = __float2int_rz(((float)t + 0.5f) * rcol);  // t / ncol, exact for t < 2^12
+                    int bl = t - a * ncol, b = cb + bl;
                     T fx = T(0), fy = T(0), fz = T(0), fr = T(0);
                     if (!self || a < b) {
                         const PState<S>& pa = sA[w][a];
@@ -173,6 +179,20 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
     }
 }
 
+// centre separation Z_A - Z_B of every P2P pair, formed in binary64 once per pair and
+// stored in the storage type (one thread per pair: the pair kernel's lanes would all
+// repeat this binary64 work)
+template <class S>
+__global__ void p2p_sep_k(int64_t npairs, const int2* __restrict__ pairs, const double* __restrict__ Zx,
+                          const double* __restrict__ Zy, const double* __restrict__ Zz, S* __restrict__ sep) {
+    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (k >= npairs) return;
+    int2 p = pairs[k];
+    sep[3 * k] = to_storage(Zx[p.x] - Zx[p.y], S());
+    sep[3 * k + 1] = to_storage(Zy[p.x] - Zy[p.y], S());
+    sep[3 * k + 2] = to_storage(Zz[p.x] - Zz[p.y], S());
+}
+
 // packed (x - Z_leaf, y - Z_leaf, z - Z_leaf, m) of every sorted particle in the storage
 // type S: offsets from the leaf centre keep double-float positions accurate to ~2^-48 of
 // the leaf size rather than of the coordinate
@@ -214,14 +234,17 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     int64_t cap = (int64_t)dev_sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    size_t shm = sizeof(T) * (size_t)PANEL * PW;
+    ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
+    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
+                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
+    GB_LAUNCH("p2p_sep_k");
+    size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
     auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;
     GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     stage_begin(c, ST_P2P);
     kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
                                            c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
-                                           c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
-                                           c->p2p_part.as<Quad<G>>());
+                                           c->p2p_sep.as<S>(), c->p2p_part.as<Quad<G>>());
     GB_LAUNCH("p2p_k");
     stage_end(c, ST_P2P);
 }
@@ -296,10 +319,10 @@ static void gather_launch(fmm_ctx* c) {
 }
 
 void run_p2p_gather(fmm_ctx* c) {
-    if (c->precision == FMM_DF64)
-        gather_launch<df64>(c);
-    else
+    if (c->precision == FMM_FP64)
         gather_launch<double>(c);
+    else
+        gather_launch<df64>(c);
 }
 
 // ------------------------------------------------------------------ diagnostics

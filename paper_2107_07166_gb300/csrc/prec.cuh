@@ -8,8 +8,9 @@
 // Positions and cell centres are stored as binary64 in FMM_FP64 and as double-float
 // otherwise ("storage type" S).  Differences X_a - X_b and Z_A - Z_B are formed in S and
 // only then narrowed to T, so binary32 pair kernels still see separations accurate to
-// their own rounding.  Per-pair and per-chunk partial sums are kept in G (double for
-// binary64 and binary32, double-float for df64) and reduced in a fixed order.
+// their own rounding.  Per-pair and per-chunk partial sums are kept in G (binary64 for
+// binary64, double-float otherwise, so that no binary64 conversion sits in the binary32
+// pair kernels) and reduced in a fixed order; the per-particle totals are binary64.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -45,12 +46,12 @@ struct Prec<df64> {
 template <>
 struct Prec<float> {
     using S = df64;
-    using G = double;
+    using G = df64;  // per-pair partials kept as double-float: no binary64 converts in the pair kernel
     __device__ static float narrow(df64 v) { return __fadd_rn(v.hi, v.lo); }
     __device__ static float mass(df64 m) { return __fadd_rn(m.hi, m.lo); }
-    __device__ static double to_g(float v) { return (double)v; }
-    __device__ static double g_to_double(double v) { return v; }
-    __device__ static double g_add(double a, double b) { return a + b; }
+    __device__ static df64 to_g(float v) { return df64(v, 0.f); }
+    __device__ static double g_to_double(df64 v) { return to_double(v); }
+    __device__ static df64 g_add(df64 a, df64 b) { return a + b; }
 };
 
 __device__ __forceinline__ double to_storage(double v, double) { return v; }
