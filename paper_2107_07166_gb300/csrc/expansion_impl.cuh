@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
         E::m2l_std(mom + (int64_t)src * E::NM, D, L);
     }
 #pragma unroll
-    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = Prec<T>::to_g(L[k]);
+    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = Prec<T>::fin(L[k]);
 }
 
 // a8' M2L, conserving: S and U of the realigned pair forces, from conserving moments
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
         }
     }
 #pragma unroll
-    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::to_g(SU[k]);
+    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::fin(SU[k]);
 }
 
 // a9: loc[x][k] = sum over the cell's items (full chunks in order, then the partial one),

@@ -18,6 +18,7 @@
 
 namespace gbfmm {
 
+// fin(v): a finished value of type T (double-float normalised) for storage
 template <class T>
 struct Prec;
 
@@ -25,6 +26,7 @@ template <>
 struct Prec<double> {
     using S = double;  // storage of positions, masses and centres
     using G = double;  // partial sums
+    __device__ static double fin(double v) { return v; }
     __device__ static double narrow(double v) { return v; }
     __device__ static double mass(double m) { return m; }
     __device__ static double to_g(double v) { return v; }
@@ -36,6 +38,7 @@ template <>
 struct Prec<df64> {
     using S = df64;
     using G = df64;
+    __device__ static df64 fin(df64 v) { return norm(v); }
     __device__ static df64 narrow(df64 v) { return v; }
     __device__ static df64 mass(df64 m) { return m; }
     __device__ static df64 to_g(df64 v) { return norm(v); }
@@ -47,6 +50,7 @@ template <>
 struct Prec<float> {
     using S = df64;
     using G = df64;  // per-pair partials kept as double-float: no binary64 converts in the pair kernel
+    __device__ static float fin(float v) { return v; }
     __device__ static float narrow(df64 v) { return __fadd_rn(v.hi, v.lo); }
     __device__ static float mass(df64 m) { return __fadd_rn(m.hi, m.lo); }
     __device__ static df64 to_g(float v) { return df64(v, 0.f); }
