@@ -38,25 +38,6 @@ __global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfir
     for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
 }
 
-// a6 M2M: inner nodes of one level from their children (c = Z_child - Z_parent)
-template <int P>
-__global__ void __launch_bounds__(EB) m2m_k(int lo, int hi, const int* __restrict__ nchildf,
-                                            const int* __restrict__ nnchild, const double* __restrict__ Zx,
-                                            const double* __restrict__ Zy, const double* __restrict__ Zz,
-                                            double* __restrict__ mom) {
-    using E = Exp<P>;
-    int nd = lo + blockIdx.x * EB + threadIdx.x;
-    if (nd >= hi || nnchild[nd] == 0) return;
-    double M[E::NM];
-#pragma unroll
-    for (int k = 0; k < E::NM; k++) M[k] = 0.0;
-    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
-    int c0 = nchildf[nd], c1 = c0 + nnchild[nd];
-    for (int ch = c0; ch < c1; ch++)
-        E::m2m(mom + (int64_t)ch * E::NM, Zx[ch] - zx, Zy[ch] - zy, Zz[ch] - zz, M);
-#pragma unroll
-    for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
-}
 
 // a8 M2L, standard, one work item = up to M2L_CHUNK directed entries of one target cell
 // (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src),
@@ -169,54 +150,158 @@ __global__ void __launch_bounds__(EB) con_moments_k(int nn, const double* __rest
     for (int k = 0; k < E::NSU; k++) cmom[(int64_t)nd * E::NSU + k] = C[k];
 }
 
-// a10 L2L, one level: child += shift(parent) by s = Z_child - Z_parent
-template <int P>
-__global__ void __launch_bounds__(EB) l2l_std_k(int lo, int hi, const int* __restrict__ nparent,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz, double* __restrict__ loc) {
-    using E = Exp<P>;
-    int nd = lo + blockIdx.x * EB + threadIdx.x;
-    if (nd >= hi) return;
-    int par = nparent[nd];
-    double L[E::NM];
-#pragma unroll
-    for (int k = 0; k < E::NM; k++) L[k] = loc[(int64_t)nd * E::NM + k];
-    E::l2l(loc + (int64_t)par * E::NM, Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par], L);
-#pragma unroll
-    for (int k = 0; k < E::NM; k++) loc[(int64_t)nd * E::NM + k] = L[k];
+// ---- coefficient-parallel translations: one warp per node, lanes over output coefficients.
+// On GB300 a warp's binary64 instructions issue at one per 16 SM cycles, so a level whose
+// threads each run a long serial chain takes the chain's length in time; spreading the
+// coefficients over lanes shortens every chain ~NM-fold.
+
+// position of multi-index (ax, ay, az) in the degree-major order (ax, then ay descending)
+__device__ __forceinline__ int mi_index(int ax, int ay, int az) {
+    int n = ax + ay + az, j = n - ax;
+    return n * (n + 1) * (n + 2) / 6 + j * (j + 1) / 2 + (j - ay);
 }
 
-template <int P>
-__global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __restrict__ nparent,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz, double* __restrict__ loc) {
-    using E = Exp<P>;
-    constexpr int NQ = E::NQ;
-    int nd = lo + blockIdx.x * EB + threadIdx.x;
-    if (nd >= hi) return;
-    int par = nparent[nd];
-    double sx = Zx[nd] - Zx[par], sy = Zy[nd] - Zy[par], sz = Zz[nd] - Zz[par];
-    const double* Lp = loc + (int64_t)par * E::NSU;
-    double* Lc = loc + (int64_t)nd * E::NSU;
-    double sh[NQ];
-#pragma unroll
-    for (int k = 0; k < NQ; k++) sh[k] = 0.0;
-    E::l2l_q(Lp, sx, sy, sz, sh);  // shifted parent S
-    double t[NQ];
-#pragma unroll
-    for (int k = 0; k < NQ; k++) t[k] = Lc[k] + sh[k];
-#pragma unroll
-    for (int k = 0; k < NQ; k++) Lc[k] = t[k];
-    const double s3[3] = {sx, sy, sz};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-#pragma unroll
-        for (int k = 0; k < NQ; k++) t[k] = Lc[(d + 1) * NQ + k];
-        E::l2l_q(Lp + (d + 1) * NQ, sx, sy, sz, t);
-#pragma unroll
-        for (int k = 0; k < NQ; k++) Lc[(d + 1) * NQ + k] = fma(s3[d], sh[k], t[k]);
+__device__ __forceinline__ void mi_decode(int k, int& ax, int& ay, int& az) {
+    int n = 0;
+    while ((n + 1) * (n + 2) * (n + 3) / 6 <= k) n++;
+    int rem = k - n * (n + 1) * (n + 2) / 6, j = 0;
+    while ((j + 1) * (j + 2) / 2 <= rem) j++;
+    ay = j - (rem - j * (j + 1) / 2);
+    ax = n - j;
+    az = n - ax - ay;
+}
+
+// w[b] = v^b / b! for |b| <= p, written by the warp's lanes into shared memory
+template <int NMP>
+__device__ __forceinline__ void fill_mono(double vx, double vy, double vz, double* w, int lane) {
+    for (int k = lane; k < NMP; k += 32) {
+        int bx, by, bz;
+        mi_decode(k, bx, by, bz);
+        double t = 1.0, f = 1.0;
+        for (int e = 1; e <= bx; e++) t *= vx, f *= e;
+        for (int e = 1; e <= by; e++) t *= vy, f *= e;
+        for (int e = 1; e <= bz; e++) t *= vz, f *= e;
+        w[k] = t / f;
     }
 }
+
+constexpr int TWB = 128;  // translation blocks: 4 warps
+constexpr int TWW = TWB / 32;
+
+// a6 M2M: M^P_alpha = sum_children sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta/beta!
+template <int P>
+__global__ void __launch_bounds__(TWB) m2m_warp_k(int lo, int hi, const int* __restrict__ nchildf,
+                                                  const int* __restrict__ nnchild, const double* __restrict__ Zx,
+                                                  const double* __restrict__ Zy, const double* __restrict__ Zz,
+                                                  double* __restrict__ mom) {
+    using E = Exp<P>;
+    constexpr int NM = E::NM, PER = (NM + 31) / 32;
+    __shared__ double ws[TWW][NM];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
+    if (nd >= hi || nnchild[nd] == 0) return;  // warp-uniform
+    double acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; q++) acc[q] = 0.0;
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    int c0 = nchildf[nd], c1 = c0 + nnchild[nd];
+    for (int ch = c0; ch < c1; ch++) {
+        fill_mono<NM>(-(Zx[ch] - zx), -(Zy[ch] - zy), -(Zz[ch] - zz), ws[w], lane);
+        __syncwarp();
+        const double* Mc = mom + (int64_t)ch * NM;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            int k = lane + 32 * q;
+            if (k < NM) {
+                int ax, ay, az;
+                mi_decode(k, ax, ay, az);
+                double s = acc[q];
+                for (int bx = 0; bx <= ax; bx++)
+                    for (int by = 0; by <= ay; by++)
+                        for (int bz = 0; bz <= az; bz++)
+                            s = fma(Mc[mi_index(ax - bx, ay - by, az - bz)], ws[w][mi_index(bx, by, bz)], s);
+                acc[q] = s;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < PER; q++)
+        if (lane + 32 * q < NM) mom[(int64_t)nd * NM + lane + 32 * q] = acc[q];
+}
+
+// a10 L2L standard: L_child[g] += sum_{|g+b|<=p} L_parent[g+b] s^b/b!, s = Z_child - Z_parent
+template <int P>
+__global__ void __launch_bounds__(TWB) l2l_std_warp_k(int lo, int hi, const int* __restrict__ nparent,
+                                                      const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                      const double* __restrict__ Zz, double* __restrict__ loc) {
+    using E = Exp<P>;
+    constexpr int NM = E::NM, PER = (NM + 31) / 32;
+    __shared__ double ws[TWW][NM];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
+    if (nd >= hi) return;
+    int par = nparent[nd];
+    fill_mono<NM>(Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par], ws[w], lane);
+    __syncwarp();
+    const double* Lp = loc + (int64_t)par * NM;
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        int k = lane + 32 * q;
+        if (k < NM) {
+            int gx, gy, gz;
+            mi_decode(k, gx, gy, gz);
+            int rem = P - (gx + gy + gz);
+            double s = loc[(int64_t)nd * NM + k];
+            for (int bx = 0; bx <= rem; bx++)
+                for (int by = 0; by <= rem - bx; by++)
+                    for (int bz = 0; bz <= rem - bx - by; bz++)
+                        s = fma(Lp[mi_index(gx + bx, gy + by, gz + bz)], ws[w][mi_index(bx, by, bz)], s);
+            loc[(int64_t)nd * NM + k] = s;
+        }
+    }
+}
+
+// a10 L2L conserving: S' = shift(S), U'_i = shift(U_i) + s_i shift(S) (degree p-1)
+template <int P>
+__global__ void __launch_bounds__(TWB) l2l_con_warp_k(int lo, int hi, const int* __restrict__ nparent,
+                                                      const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                      const double* __restrict__ Zz, double* __restrict__ loc) {
+    using E = Exp<P>;
+    constexpr int NQ = E::NQ, NSU = E::NSU, PER = (NSU + 31) / 32, Q = P - 1;
+    __shared__ double ws[TWW][NQ];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
+    if (nd >= hi) return;
+    int par = nparent[nd];
+    double sv[3] = {Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par]};
+    fill_mono<NQ>(sv[0], sv[1], sv[2], ws[w], lane);
+    __syncwarp();
+    const double* Lp = loc + (int64_t)par * NSU;
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        int t = lane + 32 * q;
+        if (t < NSU) {
+            int comp = t / NQ, k = t - comp * NQ;
+            int gx, gy, gz;
+            mi_decode(k, gx, gy, gz);
+            int rem = Q - (gx + gy + gz);
+            double sh = 0.0, su = 0.0;
+            for (int bx = 0; bx <= rem; bx++)
+                for (int by = 0; by <= rem - bx; by++)
+                    for (int bz = 0; bz <= rem - bx - by; bz++) {
+                        int src = mi_index(gx + bx, gy + by, gz + bz);
+                        double wb = ws[w][mi_index(bx, by, bz)];
+                        sh = fma(Lp[src], wb, sh);
+                        if (comp > 0) su = fma(Lp[comp * NQ + src], wb, su);
+                    }
+            double v = loc[(int64_t)nd * NSU + t] + (comp == 0 ? sh : fma(sv[comp - 1], sh, su));
+            loc[(int64_t)nd * NSU + t] = v;
+        }
+    }
+}
+
+
 
 // a11 + a13: far field at every particle from its leaf's locals, plus the leaf's P2P item
 // sums (full chunks in order, then the partial one), written in input order.
@@ -293,10 +378,10 @@ void run_moments_p(fmm_ctx* c) {
     GB_LAUNCH("p2m_k");
     for (int l = c->n_levels - 2; l >= 0; l--) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
-        m2m_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nchildf.as<int>(), c->nnchild.as<int>(),
-                                                      c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
-                                                      c->mom.as<double>());
-        GB_LAUNCH("m2m_k");
+        m2m_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
+            lo, hi, c->nchildf.as<int>(), c->nnchild.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(),
+            c->nZz.as<double>(), c->mom.as<double>());
+        GB_LAUNCH("m2m_warp_k");
     }
     ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
     con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
@@ -375,17 +460,17 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     for (int l = 1; l < c->n_levels; l++) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
         if (variant == 1) {
-            l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
-                                                              c->nZy.as<double>(), c->nZz.as<double>(),
-                                                              c->loc.as<double>());
-            GB_LAUNCH("l2l_con_k");
+            l2l_con_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
+                lo, hi, c->nparent.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                c->loc.as<double>());
+            GB_LAUNCH("l2l_con_warp_k");
         }
         if (std_locals) {
             DevBuf& L = variant == 0 ? c->loc : c->locp;
-            l2l_std_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
-                                                              c->nZy.as<double>(), c->nZz.as<double>(),
-                                                              L.as<double>());
-            GB_LAUNCH("l2l_std_k");
+            l2l_std_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
+                lo, hi, c->nparent.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                L.as<double>());
+            GB_LAUNCH("l2l_std_warp_k");
         }
     }
     stage_end(c, ST_L2L);
