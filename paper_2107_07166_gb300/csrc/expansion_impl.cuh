@@ -171,17 +171,23 @@ __device__ __forceinline__ void mi_decode(int k, int& ax, int& ay, int& az) {
     az = n - ax - ay;
 }
 
+// 1/e for the small integers of factorials (constants, no binary64 division)
+__device__ __forceinline__ double recip_small(int e) {
+    return e == 1 ? 1.0 : e == 2 ? 0.5 : e == 3 ? 1.0 / 3.0 : e == 4 ? 0.25 : e == 5 ? 0.2 : e == 6 ? 1.0 / 6.0
+         : e == 7 ? 1.0 / 7.0 : 0.125;
+}
+
 // w[b] = v^b / b! for |b| <= p, written by the warp's lanes into shared memory
 template <int NMP>
 __device__ __forceinline__ void fill_mono(double vx, double vy, double vz, double* w, int lane) {
     for (int k = lane; k < NMP; k += 32) {
         int bx, by, bz;
         mi_decode(k, bx, by, bz);
-        double t = 1.0, f = 1.0;
-        for (int e = 1; e <= bx; e++) t *= vx, f *= e;
-        for (int e = 1; e <= by; e++) t *= vy, f *= e;
-        for (int e = 1; e <= bz; e++) t *= vz, f *= e;
-        w[k] = t / f;
+        double t = 1.0;
+        for (int e = 1; e <= bx; e++) t *= vx * recip_small(e);
+        for (int e = 1; e <= by; e++) t *= vy * recip_small(e);
+        for (int e = 1; e <= bz; e++) t *= vz * recip_small(e);
+        w[k] = t;
     }
 }
 
