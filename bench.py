@@ -242,6 +242,54 @@ def run_gbfmm(args):
     ts = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum())
     fsum = float((m * np.linalg.norm(a, axis=1)).sum())
 
+    # the other arithmetic modes of the pair kernels on the same input (same timing method)
+    modes = {}
+    if args.modes and world == 1:
+        for name in ("fp64", "df64", "mixed"):
+            if name == args.precision:
+                continue
+            pm = {"fp64": fmm.FP64, "df64": fmm.DF64, "mixed": fmm.MIXED}[name]
+            h = fmm.FMM(local, pm, stream)
+            out = torch.empty_like(acc)
+
+            def st():
+                h.build(xd, md, W["leaf"])
+                h.forces(W["p"], W["theta"], variant, out, None)
+
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    st()
+            stream.synchronize()
+            ts_ = []
+            for _ in range(max(3, min(args.steps, 5))):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st()
+                e1.record(stream)
+                e1.synchronize()
+                ts_.append(e0.elapsed_time(e1))
+            o = out.cpu().numpy()
+            ref = a if args.precision == "fp64" else None
+            if ref is None:
+                g = fmm.FMM(local, fmm.FP64, stream)
+                rr = torch.empty_like(acc)
+                with torch.cuda.stream(stream):
+                    g.build(xd, md, W["leaf"])
+                    g.forces(W["p"], W["theta"], variant, rr, None)
+                stream.synchronize()
+                ref = rr.cpu().numpy()
+                g.close()
+            tm = statistics.mean(ts_)
+            modes[name] = {"value": N / (tm / 1e3), "ms_per_step": tm,
+                           "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[name],
+                           "force_err_vs_fp64_gpu": float(np.linalg.norm(o - ref) / np.linalg.norm(ref)),
+                           "stage_ms": {k: round(v, 4) for k, v in h.stage_times().items()}}
+            h.close()
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -280,6 +328,7 @@ def run_gbfmm(args):
         "force_err_rel_l2": err,
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
+        "modes": modes or None,
         "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
                 "d2h_bytes_per_step": int(24 * N)},
         "gpu_launches": int(launches),
@@ -371,6 +420,8 @@ def main():
     ap.add_argument("--variant", default="conserving", choices=["conserving", "standard"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "mixed"],
                     help="arithmetic of the pair kernels (M2L, P2P)")
+    ap.add_argument("--no-modes", dest="modes", action="store_false",
+                    help="skip timing the other arithmetic modes on the same input")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
