@@ -194,6 +194,10 @@ __device__ __forceinline__ void fill_mono(double vx, double vy, double vz, doubl
 constexpr int TWB = 128;  // translation blocks: 4 warps
 constexpr int TWW = TWB / 32;
 
+// Dependent binary64 instructions are slow to retire on GB300, so every lane keeps
+// several independent accumulators (one per child for M2M, four interleaved partial
+// sums for L2L) and adds them in a fixed order at the end.
+
 // a6 M2M: M^P_alpha = sum_children sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta/beta!
 template <int P>
 __global__ void __launch_bounds__(TWB) m2m_warp_k(int lo, int hi, const int* __restrict__ nchildf,
@@ -202,38 +206,44 @@ __global__ void __launch_bounds__(TWB) m2m_warp_k(int lo, int hi, const int* __r
                                                   double* __restrict__ mom) {
     using E = Exp<P>;
     constexpr int NM = E::NM, PER = (NM + 31) / 32;
-    __shared__ double ws[TWW][NM];
+    __shared__ double ws[TWW][8][NM];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
     if (nd >= hi || nnchild[nd] == 0) return;  // warp-uniform
-    double acc[PER];
-#pragma unroll
-    for (int q = 0; q < PER; q++) acc[q] = 0.0;
+    int c0 = nchildf[nd], nc = nnchild[nd];
     double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
-    int c0 = nchildf[nd], c1 = c0 + nnchild[nd];
-    for (int ch = c0; ch < c1; ch++) {
-        fill_mono<NM>(-(Zx[ch] - zx), -(Zy[ch] - zy), -(Zz[ch] - zz), ws[w], lane);
-        __syncwarp();
-        const double* Mc = mom + (int64_t)ch * NM;
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            int k = lane + 32 * q;
-            if (k < NM) {
-                int ax, ay, az;
-                mi_decode(k, ax, ay, az);
-                double s = acc[q];
-                for (int bx = 0; bx <= ax; bx++)
-                    for (int by = 0; by <= ay; by++)
-                        for (int bz = 0; bz <= az; bz++)
-                            s = fma(Mc[mi_index(ax - bx, ay - by, az - bz)], ws[w][mi_index(bx, by, bz)], s);
-                acc[q] = s;
-            }
-        }
-        __syncwarp();
+    // monomials (-c)^b / b! of every child
+    for (int t = lane; t < nc * NM; t += 32) {
+        int ch = t / NM, k = t - ch * NM;
+        int bx, by, bz;
+        mi_decode(k, bx, by, bz);
+        double vx = -(Zx[c0 + ch] - zx), vy = -(Zy[c0 + ch] - zy), vz = -(Zz[c0 + ch] - zz);
+        double tx = 1.0, ty = 1.0, tz = 1.0;
+        for (int e = 1; e <= bx; e++) tx *= vx * recip_small(e);
+        for (int e = 1; e <= by; e++) ty *= vy * recip_small(e);
+        for (int e = 1; e <= bz; e++) tz *= vz * recip_small(e);
+        ws[w][ch][k] = tx * ty * tz;
     }
+    __syncwarp();
+    const double* Mc = mom + (int64_t)c0 * NM;
 #pragma unroll
-    for (int q = 0; q < PER; q++)
-        if (lane + 32 * q < NM) mom[(int64_t)nd * NM + lane + 32 * q] = acc[q];
+    for (int q = 0; q < PER; q++) {
+        int k = lane + 32 * q;
+        if (k < NM) {
+            int ax, ay, az;
+            mi_decode(k, ax, ay, az);
+            double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int bx = 0; bx <= ax; bx++)
+                for (int by = 0; by <= ay; by++)
+                    for (int bz = 0; bz <= az; bz++) {
+                        int r = mi_index(ax - bx, ay - by, az - bz), b = mi_index(bx, by, bz);
+#pragma unroll
+                        for (int ch = 0; ch < 8; ch++)
+                            if (ch < nc) acc[ch] = fma(Mc[(int64_t)ch * NM + r], ws[w][ch][b], acc[ch]);
+                    }
+            mom[(int64_t)nd * NM + k] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        }
+    }
 }
 
 // a10 L2L standard: L_child[g] += sum_{|g+b|<=p} L_parent[g+b] s^b/b!, s = Z_child - Z_parent
@@ -258,12 +268,13 @@ __global__ void __launch_bounds__(TWB) l2l_std_warp_k(int lo, int hi, const int*
             int gx, gy, gz;
             mi_decode(k, gx, gy, gz);
             int rem = P - (gx + gy + gz);
-            double s = loc[(int64_t)nd * NM + k];
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            int j = 0;
             for (int bx = 0; bx <= rem; bx++)
                 for (int by = 0; by <= rem - bx; by++)
-                    for (int bz = 0; bz <= rem - bx - by; bz++)
-                        s = fma(Lp[mi_index(gx + bx, gy + by, gz + bz)], ws[w][mi_index(bx, by, bz)], s);
-            loc[(int64_t)nd * NM + k] = s;
+                    for (int bz = 0; bz <= rem - bx - by; bz++, j++)
+                        acc[j & 3] = fma(Lp[mi_index(gx + bx, gy + by, gz + bz)], ws[w][mi_index(bx, by, bz)], acc[j & 3]);
+            loc[(int64_t)nd * NM + k] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
     }
 }
@@ -292,22 +303,21 @@ __global__ void __launch_bounds__(TWB) l2l_con_warp_k(int lo, int hi, const int*
             int gx, gy, gz;
             mi_decode(k, gx, gy, gz);
             int rem = Q - (gx + gy + gz);
-            double sh = 0.0, su = 0.0;
+            double sh[2] = {0.0, 0.0}, su[2] = {0.0, 0.0};
+            int j = 0;
             for (int bx = 0; bx <= rem; bx++)
                 for (int by = 0; by <= rem - bx; by++)
-                    for (int bz = 0; bz <= rem - bx - by; bz++) {
+                    for (int bz = 0; bz <= rem - bx - by; bz++, j++) {
                         int src = mi_index(gx + bx, gy + by, gz + bz);
                         double wb = ws[w][mi_index(bx, by, bz)];
-                        sh = fma(Lp[src], wb, sh);
-                        if (comp > 0) su = fma(Lp[comp * NQ + src], wb, su);
+                        sh[j & 1] = fma(Lp[src], wb, sh[j & 1]);
+                        if (comp > 0) su[j & 1] = fma(Lp[comp * NQ + src], wb, su[j & 1]);
                     }
-            double v = loc[(int64_t)nd * NSU + t] + (comp == 0 ? sh : fma(sv[comp - 1], sh, su));
-            loc[(int64_t)nd * NSU + t] = v;
+            double shv = sh[0] + sh[1], suv = su[0] + su[1];
+            loc[(int64_t)nd * NSU + t] += (comp == 0 ? shv : fma(sv[comp - 1], shv, suv));
         }
     }
 }
-
-
 
 // a11 + a13: far field at every particle from its leaf's locals, plus the leaf's P2P item
 // sums (full chunks in order, then the partial one), written in input order.
