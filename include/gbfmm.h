@@ -151,7 +151,7 @@ GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
  * Who needs it: code that must not call cudaMalloc/cudaFree -- they can synchronise the
  * whole device and are not allowed while a stream is being captured -- and hosts that
  * hand out all device memory from their own pool or budget it up front.  The call
- * allocates nothing: its scratch is one fixed array of about 2.1 MiB in the library's
+ * allocates nothing: its scratch is one fixed array of about 2.2 MiB in the library's
  * device image, which every GPU that loads the library holds until the process exits.
  *
  *   x: N x 3 row-major positions, device memory; 1 <= N <= FMM_NOALLOC_MAX_N.

@@ -116,12 +116,14 @@ __global__ void scan_apply_k(const In* __restrict__ in, int64_t n, const T* __re
 }
 
 // ------------------------------------------------------------------ radix sort
-// Stable least-significant-digit sort of 64-bit keys with optional 32-bit payloads.
+// Stable least-significant-digit sort of 64-bit keys with optional 32-bit payloads,
+// RS_BITS-bit digits (9: seven passes for 63-bit Morton keys, four for 36-bit list keys).
 // Each pass: per-tile digit histograms (digit-major so that one exclusive scan gives
 // every tile's output offset), then a stable scatter whose in-tile ranks come from
 // warp match masks, in the original order (warp-major, then chunk, then lane).
 
 constexpr int RS_BLOCK = 256, RS_ITEMS = 16, RS_TILE = RS_BLOCK * RS_ITEMS, RS_WARPS = RS_BLOCK / 32;
+constexpr int RS_BITS = 9, RS_BINS = 1 << RS_BITS;
 
 __global__ void rs_hist_k(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
                           int ntiles);

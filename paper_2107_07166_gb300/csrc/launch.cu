@@ -76,20 +76,20 @@ void scan_cnt3(fmm_ctx* c, const Cnt3* in, int64_t n, Cnt3* out) { scan_impl<Cnt
 
 __global__ void rs_hist_k(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
                           int ntiles) {
-    __shared__ uint32_t sh[256];
-    for (int i = threadIdx.x; i < 256; i += RS_BLOCK) sh[i] = 0;
+    __shared__ uint32_t sh[RS_BINS];
+    for (int i = threadIdx.x; i < RS_BINS; i += RS_BLOCK) sh[i] = 0;
     __syncthreads();
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
 #pragma unroll 4
     for (int j = 0; j < RS_ITEMS; j++) {
         int64_t i = base + j * 32 + lane;
-        unsigned d = (i < n) ? (unsigned)((keys[i] >> shift) & 255u) : 256u;
+        unsigned d = (i < n) ? (unsigned)((keys[i] >> shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
         unsigned peers = __match_any_sync(FULL, d);
-        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[d], (uint32_t)__popc(peers));
+        if (d < (unsigned)RS_BINS && lane == __ffs(peers) - 1) atomicAdd(&sh[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += RS_BLOCK) hist[(int64_t)d * ntiles + blockIdx.x] = sh[d];
+    for (int d = threadIdx.x; d < RS_BINS; d += RS_BLOCK) hist[(int64_t)d * ntiles + blockIdx.x] = sh[d];
 }
 
 template <bool V>
@@ -98,10 +98,10 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
                                                          uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          int64_t n, int shift, const uint32_t* __restrict__ offs,
                                                          int ntiles) {
-    __shared__ uint32_t wcnt[RS_WARPS][256];
-    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+    __shared__ uint32_t dbase[RS_BINS];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BLOCK) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_BLOCK) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
     uint64_t k[RS_ITEMS];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
         bool ok = i < n;
         k[j] = ok ? kin[i] : 0ull;
         if (V) v[j] = ok ? vin[i] : 0u;
-        unsigned d = ok ? (unsigned)((k[j] >> shift) & 255u) : 256u;
+        unsigned d = ok ? (unsigned)((k[j] >> shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
         unsigned peers = __match_any_sync(FULL, d);
         uint32_t r = 0;
         if (ok) r = wcnt[warp][d] + (uint32_t)__popc(peers & lt);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
         rank[j] = r;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += RS_BLOCK) {
+    for (int d = threadIdx.x; d < RS_BINS; d += RS_BLOCK) {
         uint32_t s = 0;
         for (int w = 0; w < RS_WARPS; w++) {
             uint32_t t = wcnt[w][d];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
     for (int j = 0; j < RS_ITEMS; j++) {
         int64_t i = base + j * 32 + lane;
         if (i < n) {
-            unsigned d = (unsigned)((k[j] >> shift) & 255u);
+            unsigned d = (unsigned)((k[j] >> shift) & (RS_BINS - 1));
             uint32_t pos = dbase[d] + wcnt[warp][d] + rank[j];
             kout[pos] = k[j];
             if (V) vout[pos] = v[j];
@@ -146,12 +146,13 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
     }
 }
 
-// One stable 8-bit pass of keys + 32-bit payloads on caller-provided buffers: hist and
-// offs hold 256 * ntiles + 1 entries, sums (256 * ntiles) / SCAN_TILE + 2.  Allocates nothing.
+// One stable RS_BITS-bit pass of keys + 32-bit payloads on caller-provided buffers: hist
+// and offs hold RS_BINS * ntiles + 1 entries, sums (RS_BINS * ntiles) / SCAN_TILE + 2.
+// Allocates nothing.
 void rs_pass_raw(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n, int shift,
                  uint32_t* hist, int* offs, int* sums, cudaStream_t s) {
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
-    int64_t nh = (int64_t)256 * ntiles;
+    int64_t nh = (int64_t)RS_BINS * ntiles;
     int nst = (int)((nh + SCAN_TILE - 1) / SCAN_TILE);
     rs_hist_k<<<ntiles, RS_BLOCK, 0, s>>>(kin, n, shift, hist, ntiles);
     scan_tiles_k<int, int><<<nst, SCAN_BLOCK, 0, s>>>(reinterpret_cast<const int*>(hist), nh, sums);
@@ -167,19 +168,19 @@ void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     ensure(keys_tmp, sizeof(uint64_t) * (size_t)n);
     if (vals) ensure(*vals_tmp, sizeof(uint32_t) * (size_t)n);
-    ensure(c->rs_hist, sizeof(uint32_t) * (size_t)(256 * ntiles + 1));
-    ensure(c->rs_offs, sizeof(int) * (size_t)(256 * ntiles + 1));
+    ensure(c->rs_hist, sizeof(uint32_t) * (size_t)(RS_BINS * ntiles + 1));
+    ensure(c->rs_offs, sizeof(int) * (size_t)(RS_BINS * ntiles + 1));
     uint64_t* ka = keys.as<uint64_t>();
     uint64_t* kb = keys_tmp.as<uint64_t>();
     uint32_t* va = vals ? vals->as<uint32_t>() : nullptr;
     uint32_t* vb = vals ? vals_tmp->as<uint32_t>() : nullptr;
-    int passes = (bits + 7) / 8;
+    int passes = (bits + RS_BITS - 1) / RS_BITS;
     for (int ps = 0; ps < passes; ps++) {
-        int shift = 8 * ps;
+        int shift = RS_BITS * ps;
         uint32_t* hist = c->rs_hist.as<uint32_t>();
         rs_hist_k<<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, n, shift, hist, ntiles);
         GB_LAUNCH("rs_hist_k");
-        scan_int(c, reinterpret_cast<const int*>(hist), (int64_t)256 * ntiles, c->rs_offs.as<int>());
+        scan_int(c, reinterpret_cast<const int*>(hist), (int64_t)RS_BINS * ntiles, c->rs_offs.as<int>());
         const uint32_t* offs = reinterpret_cast<const uint32_t*>(c->rs_offs.as<int>());
         if (vals)
             rs_scatter_k<true><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, offs, ntiles);

@@ -28,7 +28,7 @@ namespace {
 constexpr int64_t NA_MAX_N = FMM_NOALLOC_MAX_N;                     // particles per call
 constexpr int NA_TB = 256;                                          // bbox block size
 constexpr int NA_MAX_TILES = (int)(NA_MAX_N / RS_TILE);             // 32 sort tiles
-constexpr int NA_HIST = 256 * NA_MAX_TILES + 1;
+constexpr int NA_HIST = RS_BINS * NA_MAX_TILES + 1;
 constexpr int NA_MAX_BB = (int)(NA_MAX_N / NA_TB);                  // 512 bbox blocks
 
 constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
@@ -42,7 +42,7 @@ constexpr size_t OFF_SUMS = OFF_OFFS + al256(sizeof(int) * NA_HIST);
 constexpr size_t OFF_PART = OFF_SUMS + al256(sizeof(int) * 64);
 constexpr size_t OFF_GEOM = OFF_PART + al256(sizeof(double) * 6 * NA_MAX_BB);
 constexpr size_t OFF_FLAG = OFF_GEOM + al256(sizeof(double) * 8);
-constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_FLAG + al256(sizeof(int) * 4);   // ~2.1 MiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_FLAG + al256(sizeof(int) * 4);   // ~2.2 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -114,7 +114,7 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
         base = g_na_addr[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    uint64_t* keys_a = keys_sorted;  // eight passes: the result lands back in keys_a
+    uint64_t* keys_a = keys_sorted;
     uint64_t* keys_b = reinterpret_cast<uint64_t*>(base + OFF_KEYS_B);
     uint32_t* vals_a = reinterpret_cast<uint32_t*>(base + OFF_VALS_A);
     uint32_t* vals_b = reinterpret_cast<uint32_t*>(base + OFF_VALS_B);
@@ -133,12 +133,13 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
     e = cudaMemsetAsync(vals_a, 0, sizeof(double) * (size_t)N, s);
     if (e != cudaSuccess) return FMM_ERR_CUDA;
     bbox_partial_k<<<nb, NA_TB, 0, s>>>(x, reinterpret_cast<const double*>(vals_a), N, part, flag);
-    bbox_final_k<<<1, 32, 0, s>>>(part, nb, geom);
+    bbox_final_k<<<1, 512, 0, s>>>(part, nb, geom);
     // a2: keys and identity payload
     keys_k<<<(unsigned)((N + NA_TB - 1) / NA_TB), NA_TB, 0, s>>>(x, N, geom, keys_a, vals_a);
-    // a3: eight stable 8-bit passes over 63-bit keys
-    for (int ps = 0; ps < 8; ps++) {
-        rs_pass_raw(keys_a, vals_a, keys_b, vals_b, N, 8 * ps, hist, offs, sums, s);
+    // a3: stable RS_BITS-bit passes over the 63-bit keys
+    int passes = (63 + RS_BITS - 1) / RS_BITS;
+    for (int ps = 0; ps < passes; ps++) {
+        rs_pass_raw(keys_a, vals_a, keys_b, vals_b, N, RS_BITS * ps, hist, offs, sums, s);
         uint64_t* tk = keys_a;
         keys_a = keys_b;
         keys_b = tk;
@@ -146,6 +147,9 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
         vals_a = vals_b;
         vals_b = tv;
     }
+    if (keys_a != keys_sorted &&
+        cudaMemcpyAsync(keys_sorted, keys_a, sizeof(uint64_t) * (size_t)N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return FMM_ERR_CUDA;
     widen_perm_k<<<(unsigned)((N + NA_TB - 1) / NA_TB), NA_TB, 0, s>>>(vals_a, N, perm);
     if (lo && (e = cudaMemcpyAsync(lo, geom, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return FMM_ERR_CUDA;

@@ -59,23 +59,35 @@ __global__ void bbox_partial_k(const double* __restrict__ x, const double* __res
         }
 }
 
-// geom[0..2] = lo, geom[3] = side, geom[4] = scale
-__global__ void bbox_final_k(const double* __restrict__ part, int nb, double* __restrict__ geom) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double mn[3], mx[3];
-    for (int d = 0; d < 3; d++) {
-        mn[d] = part[d];
-        mx[d] = part[3 + d];
-    }
-    for (int b = 1; b < nb; b++)
+// geom[0..2] = lo, geom[3] = side, geom[4] = scale.  One block, a tree over the partials
+// (min and max are exact, so the grouping does not matter).
+constexpr int BFB = 512;
+__global__ void __launch_bounds__(BFB) bbox_final_k(const double* __restrict__ part, int nb, double* __restrict__ geom) {
+    __shared__ double smn[3][BFB], smx[3][BFB];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nb; b += BFB)
         for (int d = 0; d < 3; d++) {
             mn[d] = fmin(mn[d], part[6 * b + d]);
             mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
         }
+    for (int d = 0; d < 3; d++) {
+        smn[d][threadIdx.x] = mn[d];
+        smx[d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int st = BFB / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int d = 0; d < 3; d++) {
+                smn[d][threadIdx.x] = fmin(smn[d][threadIdx.x], smn[d][threadIdx.x + st]);
+                smx[d][threadIdx.x] = fmax(smx[d][threadIdx.x], smx[d][threadIdx.x + st]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     double side = 0.0;
     for (int d = 0; d < 3; d++) {
-        geom[d] = mn[d];
-        double e = __dsub_rn(mx[d], mn[d]);
+        geom[d] = smn[d][0];
+        double e = __dsub_rn(smx[d][0], smn[d][0]);
         if (e > side) side = e;
     }
     if (side == 0.0) side = 1.0;
@@ -329,7 +341,7 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     GB_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int) * 4, s));
     bbox_partial_k<<<nb, TB, 0, s>>>(x, m, c->N, part, c->errflag.as<int>());
     GB_LAUNCH("bbox_partial_k");
-    bbox_final_k<<<1, 32, 0, s>>>(part, nb, geom);
+    bbox_final_k<<<1, BFB, 0, s>>>(part, nb, geom);
     GB_LAUNCH("bbox_final_k");
     int bad = 0;
     GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
