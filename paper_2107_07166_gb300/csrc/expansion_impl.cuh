@@ -150,172 +150,91 @@ __global__ void __launch_bounds__(EB) con_moments_k(int nn, const double* __rest
     for (int k = 0; k < E::NSU; k++) cmom[(int64_t)nd * E::NSU + k] = C[k];
 }
 
-// ---- coefficient-parallel translations: one warp per node, lanes over output coefficients.
-// On GB300 a warp's binary64 instructions issue at one per 16 SM cycles, so a level whose
-// threads each run a long serial chain takes the chain's length in time; spreading the
-// coefficients over lanes shortens every chain ~NM-fold.
-
-// position of multi-index (ax, ay, az) in the degree-major order (ax, then ay descending)
-__device__ __forceinline__ int mi_index(int ax, int ay, int az) {
-    int n = ax + ay + az, j = n - ax;
-    return n * (n + 1) * (n + 2) / 6 + j * (j + 1) / 2 + (j - ay);
-}
-
-__device__ __forceinline__ void mi_decode(int k, int& ax, int& ay, int& az) {
-    int n = 0;
-    while ((n + 1) * (n + 2) * (n + 3) / 6 <= k) n++;
-    int rem = k - n * (n + 1) * (n + 2) / 6, j = 0;
-    while ((j + 1) * (j + 2) / 2 <= rem) j++;
-    ay = j - (rem - j * (j + 1) / 2);
-    ax = n - j;
-    az = n - ax - ay;
-}
-
-// 1/e for the small integers of factorials (constants, no binary64 division)
-__device__ __forceinline__ double recip_small(int e) {
-    return e == 1 ? 1.0 : e == 2 ? 0.5 : e == 3 ? 1.0 / 3.0 : e == 4 ? 0.25 : e == 5 ? 0.2 : e == 6 ? 1.0 / 6.0
-         : e == 7 ? 1.0 / 7.0 : 0.125;
-}
-
-// w[b] = v^b / b! for |b| <= p, written by the warp's lanes into shared memory
-template <int NMP>
-__device__ __forceinline__ void fill_mono(double vx, double vy, double vz, double* w, int lane) {
-    for (int k = lane; k < NMP; k += 32) {
-        int bx, by, bz;
-        mi_decode(k, bx, by, bz);
-        double t = 1.0;
-        for (int e = 1; e <= bx; e++) t *= vx * recip_small(e);
-        for (int e = 1; e <= by; e++) t *= vy * recip_small(e);
-        for (int e = 1; e <= bz; e++) t *= vz * recip_small(e);
-        w[k] = t;
-    }
-}
-
-constexpr int TWB = 128;  // translation blocks: 4 warps
-constexpr int TWW = TWB / 32;
-
-// Dependent binary64 instructions are slow to retire on GB300, so every lane keeps
-// several independent accumulators (one per child for M2M, four interleaved partial
-// sums for L2L) and adds them in a fixed order at the end.
-
-// a6 M2M: M^P_alpha = sum_children sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta/beta!
+// a6 M2M in two steps per level: one thread per (parent, child) shifts the child's
+// moments to the parent centre (straight-line, independent accumulators), then one thread
+// per (parent, coefficient) adds the children's shifted moments in child order.  A single
+// thread per parent would run one long binary64 chain per level, which on GB300 sets the
+// level's time.
 template <int P>
-__global__ void __launch_bounds__(TWB) m2m_warp_k(int lo, int hi, const int* __restrict__ nchildf,
-                                                  const int* __restrict__ nnchild, const double* __restrict__ Zx,
-                                                  const double* __restrict__ Zy, const double* __restrict__ Zz,
-                                                  double* __restrict__ mom) {
+__global__ void __launch_bounds__(EB) m2m_child_k(int lo, int hi, int cfirst, const int* __restrict__ nparent,
+                                                  const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                  const double* __restrict__ Zz, const double* __restrict__ mom,
+                                                  double* __restrict__ shifted) {
     using E = Exp<P>;
-    constexpr int NM = E::NM, PER = (NM + 31) / 32;
-    __shared__ double ws[TWW][8][NM];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
-    if (nd >= hi || nnchild[nd] == 0) return;  // warp-uniform
-    int c0 = nchildf[nd], nc = nnchild[nd];
-    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
-    // monomials (-c)^b / b! of every child
-    for (int t = lane; t < nc * NM; t += 32) {
-        int ch = t / NM, k = t - ch * NM;
-        int bx, by, bz;
-        mi_decode(k, bx, by, bz);
-        double vx = -(Zx[c0 + ch] - zx), vy = -(Zy[c0 + ch] - zy), vz = -(Zz[c0 + ch] - zz);
-        double tx = 1.0, ty = 1.0, tz = 1.0;
-        for (int e = 1; e <= bx; e++) tx *= vx * recip_small(e);
-        for (int e = 1; e <= by; e++) ty *= vy * recip_small(e);
-        for (int e = 1; e <= bz; e++) tz *= vz * recip_small(e);
-        ws[w][ch][k] = tx * ty * tz;
-    }
-    __syncwarp();
-    const double* Mc = mom + (int64_t)c0 * NM;
+    // children of the parents in [lo, hi) are the nodes [cfirst, cfirst + gridDim-covered)
+    int ch = cfirst + blockIdx.x * EB + threadIdx.x;
+    if (ch >= hi) return;
+    int par = nparent[ch];
+    double M[E::NM];
 #pragma unroll
-    for (int q = 0; q < PER; q++) {
-        int k = lane + 32 * q;
-        if (k < NM) {
-            int ax, ay, az;
-            mi_decode(k, ax, ay, az);
-            double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int bx = 0; bx <= ax; bx++)
-                for (int by = 0; by <= ay; by++)
-                    for (int bz = 0; bz <= az; bz++) {
-                        int r = mi_index(ax - bx, ay - by, az - bz), b = mi_index(bx, by, bz);
+    for (int k = 0; k < E::NM; k++) M[k] = 0.0;
+    E::m2m(mom + (int64_t)ch * E::NM, Zx[ch] - Zx[par], Zy[ch] - Zy[par], Zz[ch] - Zz[par], M);
 #pragma unroll
-                        for (int ch = 0; ch < 8; ch++)
-                            if (ch < nc) acc[ch] = fma(Mc[(int64_t)ch * NM + r], ws[w][ch][b], acc[ch]);
-                    }
-            mom[(int64_t)nd * NM + k] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-        }
-    }
+    for (int k = 0; k < E::NM; k++) shifted[(int64_t)(ch - cfirst) * E::NM + k] = M[k];
+    (void)lo;
 }
 
-// a10 L2L standard: L_child[g] += sum_{|g+b|<=p} L_parent[g+b] s^b/b!, s = Z_child - Z_parent
 template <int P>
-__global__ void __launch_bounds__(TWB) l2l_std_warp_k(int lo, int hi, const int* __restrict__ nparent,
-                                                      const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                      const double* __restrict__ Zz, double* __restrict__ loc) {
+__global__ void m2m_sum_k(int lo, int hi, int cfirst, const int* __restrict__ nchildf, const int* __restrict__ nnchild,
+                          const double* __restrict__ shifted, double* __restrict__ mom) {
     using E = Exp<P>;
-    constexpr int NM = E::NM, PER = (NM + 31) / 32;
-    __shared__ double ws[TWW][NM];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
+    int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (t >= (int64_t)(hi - lo) * E::NM) return;
+    int nd = lo + (int)(t / E::NM), k = (int)(t - (int64_t)(nd - lo) * E::NM);
+    int nc = nnchild[nd];
+    if (nc == 0) return;
+    int c0 = nchildf[nd] - cfirst;
+    double s = 0.0;
+    for (int c = 0; c < nc; c++) s += shifted[(int64_t)(c0 + c) * E::NM + k];
+    mom[(int64_t)nd * E::NM + k] = s;
+}
+
+// a10 L2L, one level: child += shift(parent) by s = Z_child - Z_parent
+template <int P>
+__global__ void __launch_bounds__(EB) l2l_std_k(int lo, int hi, const int* __restrict__ nparent,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, double* __restrict__ loc) {
+    using E = Exp<P>;
+    int nd = lo + blockIdx.x * EB + threadIdx.x;
     if (nd >= hi) return;
     int par = nparent[nd];
-    fill_mono<NM>(Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par], ws[w], lane);
-    __syncwarp();
-    const double* Lp = loc + (int64_t)par * NM;
+    double L[E::NM];
 #pragma unroll
-    for (int q = 0; q < PER; q++) {
-        int k = lane + 32 * q;
-        if (k < NM) {
-            int gx, gy, gz;
-            mi_decode(k, gx, gy, gz);
-            int rem = P - (gx + gy + gz);
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            int j = 0;
-            for (int bx = 0; bx <= rem; bx++)
-                for (int by = 0; by <= rem - bx; by++)
-                    for (int bz = 0; bz <= rem - bx - by; bz++, j++)
-                        acc[j & 3] = fma(Lp[mi_index(gx + bx, gy + by, gz + bz)], ws[w][mi_index(bx, by, bz)], acc[j & 3]);
-            loc[(int64_t)nd * NM + k] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        }
-    }
+    for (int k = 0; k < E::NM; k++) L[k] = loc[(int64_t)nd * E::NM + k];
+    E::l2l(loc + (int64_t)par * E::NM, Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par], L);
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) loc[(int64_t)nd * E::NM + k] = L[k];
 }
 
-// a10 L2L conserving: S' = shift(S), U'_i = shift(U_i) + s_i shift(S) (degree p-1)
 template <int P>
-__global__ void __launch_bounds__(TWB) l2l_con_warp_k(int lo, int hi, const int* __restrict__ nparent,
-                                                      const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                      const double* __restrict__ Zz, double* __restrict__ loc) {
+__global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __restrict__ nparent,
+                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                const double* __restrict__ Zz, double* __restrict__ loc) {
     using E = Exp<P>;
-    constexpr int NQ = E::NQ, NSU = E::NSU, PER = (NSU + 31) / 32, Q = P - 1;
-    __shared__ double ws[TWW][NQ];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int nd = lo + (int)(((int64_t)blockIdx.x * TWB + threadIdx.x) >> 5);
+    constexpr int NQ = E::NQ;
+    int nd = lo + blockIdx.x * EB + threadIdx.x;
     if (nd >= hi) return;
     int par = nparent[nd];
-    double sv[3] = {Zx[nd] - Zx[par], Zy[nd] - Zy[par], Zz[nd] - Zz[par]};
-    fill_mono<NQ>(sv[0], sv[1], sv[2], ws[w], lane);
-    __syncwarp();
-    const double* Lp = loc + (int64_t)par * NSU;
+    double sx = Zx[nd] - Zx[par], sy = Zy[nd] - Zy[par], sz = Zz[nd] - Zz[par];
+    const double* Lp = loc + (int64_t)par * E::NSU;
+    double* Lc = loc + (int64_t)nd * E::NSU;
+    double sh[NQ];
 #pragma unroll
-    for (int q = 0; q < PER; q++) {
-        int t = lane + 32 * q;
-        if (t < NSU) {
-            int comp = t / NQ, k = t - comp * NQ;
-            int gx, gy, gz;
-            mi_decode(k, gx, gy, gz);
-            int rem = Q - (gx + gy + gz);
-            double sh[2] = {0.0, 0.0}, su[2] = {0.0, 0.0};
-            int j = 0;
-            for (int bx = 0; bx <= rem; bx++)
-                for (int by = 0; by <= rem - bx; by++)
-                    for (int bz = 0; bz <= rem - bx - by; bz++, j++) {
-                        int src = mi_index(gx + bx, gy + by, gz + bz);
-                        double wb = ws[w][mi_index(bx, by, bz)];
-                        sh[j & 1] = fma(Lp[src], wb, sh[j & 1]);
-                        if (comp > 0) su[j & 1] = fma(Lp[comp * NQ + src], wb, su[j & 1]);
-                    }
-            double shv = sh[0] + sh[1], suv = su[0] + su[1];
-            loc[(int64_t)nd * NSU + t] += (comp == 0 ? shv : fma(sv[comp - 1], shv, suv));
-        }
+    for (int k = 0; k < NQ; k++) sh[k] = 0.0;
+    E::l2l_q(Lp, sx, sy, sz, sh);  // shifted parent S
+    double t[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; k++) t[k] = Lc[k] + sh[k];
+#pragma unroll
+    for (int k = 0; k < NQ; k++) Lc[k] = t[k];
+    const double s3[3] = {sx, sy, sz};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) t[k] = Lc[(d + 1) * NQ + k];
+        E::l2l_q(Lp + (d + 1) * NQ, sx, sy, sz, t);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) Lc[(d + 1) * NQ + k] = fma(s3[d], sh[k], t[k]);
     }
 }
 
@@ -394,10 +313,17 @@ void run_moments_p(fmm_ctx* c) {
     GB_LAUNCH("p2m_k");
     for (int l = c->n_levels - 2; l >= 0; l--) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
-        m2m_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
-            lo, hi, c->nchildf.as<int>(), c->nnchild.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(),
-            c->nZz.as<double>(), c->mom.as<double>());
-        GB_LAUNCH("m2m_warp_k");
+        // the children of level l are exactly level l + 1
+        int c_lo = c->level_start[l + 1], c_hi = c->level_start[l + 2];
+        ensure(c->m2m_tmp, sizeof(double) * (size_t)(c_hi - c_lo) * E::NM);
+        m2m_child_k<P><<<grid_for(c_hi - c_lo, EB), EB, 0, s>>>(lo, c_hi, c_lo, c->nparent.as<int>(),
+                                                                c->nZx.as<double>(), c->nZy.as<double>(),
+                                                                c->nZz.as<double>(), c->mom.as<double>(),
+                                                                c->m2m_tmp.as<double>());
+        GB_LAUNCH("m2m_child_k");
+        m2m_sum_k<P><<<grid_for((int64_t)(hi - lo) * E::NM, EB), EB, 0, s>>>(
+            lo, hi, c_lo, c->nchildf.as<int>(), c->nnchild.as<int>(), c->m2m_tmp.as<double>(), c->mom.as<double>());
+        GB_LAUNCH("m2m_sum_k");
     }
     ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
     con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
@@ -476,17 +402,17 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     for (int l = 1; l < c->n_levels; l++) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
         if (variant == 1) {
-            l2l_con_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
-                lo, hi, c->nparent.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
-                c->loc.as<double>());
-            GB_LAUNCH("l2l_con_warp_k");
+            l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
+                                                              c->nZy.as<double>(), c->nZz.as<double>(),
+                                                              c->loc.as<double>());
+            GB_LAUNCH("l2l_con_k");
         }
         if (std_locals) {
             DevBuf& L = variant == 0 ? c->loc : c->locp;
-            l2l_std_warp_k<P><<<grid_for((int64_t)(hi - lo) * 32, TWB), TWB, 0, s>>>(
-                lo, hi, c->nparent.as<int>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
-                L.as<double>());
-            GB_LAUNCH("l2l_std_warp_k");
+            l2l_std_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
+                                                              c->nZy.as<double>(), c->nZz.as<double>(),
+                                                              L.as<double>());
+            GB_LAUNCH("l2l_std_k");
         }
     }
     stage_end(c, ST_L2L);

@@ -17,6 +17,8 @@ T (double, or float in mixed precision), for:
            the (beta_i+1) M_{beta+e_i} factors are formed once per cell (con_moments) and R is
            folded into them per pair, so U_{i,gamma} += sum_beta (C_{i,beta} + R_i M_beta) h_{beta+gamma}
   p2m      M_alpha += m (-y)^alpha / alpha!
+  m2m      M^P_alpha += sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta / beta!
+  l2l      L'_gamma += sum_beta L_{gamma+beta} s^beta / beta!
   l2p      standard: a_i = -sum_{|g|<=p-1} L_{g+e_i} x^g/g!, phi = sum L_g x^g/g!
            conserving: a = x S(x) + U(x)
 
@@ -207,6 +209,42 @@ def p2m(p):
     return L
 
 
+def m2m(p):
+    L = ["  /* M^P_alpha += sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta/beta!,  c = Z_child - Z_parent */",
+         "  template <class T> __device__ __forceinline__ static void m2m(const T* __restrict__ Mc, T cx, T cy, T cz, T* __restrict__ Mp) {"]
+    body = []
+    emit_monomials(body, ("(-cx)", "(-cy)", "(-cz)"), p, name="w", scale_fact=True)
+    L += ["  " + b for b in body]
+    for a in mis(p):
+        terms = []
+        for b in mis(sum(a)):
+            if b[0] <= a[0] and b[1] <= a[1] and b[2] <= a[2]:
+                r = (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+                terms.append((r, b))
+        expr = f"Mp[{idx(a)}]"
+        for r, b in terms:
+            expr = f"fma_t(Mc[{idx(r)}], {mono_expr('w', b)}, {expr})"
+        L.append(f"    Mp[{idx(a)}] = {expr};")
+    L.append("  }")
+    return L
+
+
+def l2l_poly(p, name):
+    L = [f"  /* L'_gamma += sum_beta L_{{gamma+beta}} s^beta/beta!  (|gamma+beta| <= {p}) */",
+         f"  template <class T> __device__ __forceinline__ static void {name}(const T* __restrict__ Lp, T sx, T sy, T sz, T* __restrict__ Lc) {{"]
+    body = []
+    emit_monomials(body, ("sx", "sy", "sz"), p, name="w", scale_fact=True)
+    L += ["  " + b for b in body]
+    for g in mis(p):
+        expr = f"Lc[{idx(g)}]"
+        for b in mis(p - sum(g)):
+            s = (g[0] + b[0], g[1] + b[1], g[2] + b[2])
+            expr = f"fma_t(Lp[{idx(s)}], {mono_expr('w', b)}, {expr})"
+        L.append(f"    Lc[{idx(g)}] = {expr};")
+    L.append("  }")
+    return L
+
+
 def l2p_std(p):
     L = ["  /* standard L2P: a_i = -sum_{|g|<=p-1} L_{g+e_i} x^g/g!;  phi = sum_g L_g x^g/g! */",
          "  template <class T> __device__ __forceinline__ static void l2p_std(const T* __restrict__ Lc, T xx, T xy, T xz, T& ax, T& ay, T& az, T& phi) {"]
@@ -266,6 +304,9 @@ def header(p):
     out += con_moments(p)
     out += m2l_con(p)
     out += p2m(p)
+    out += m2m(p)
+    out += l2l_poly(p, "l2l")
+    out += l2l_poly(q, "l2l_q")
     out += l2p_std(p)
     out += l2p_con(p)
     out.append("};")
