@@ -242,6 +242,23 @@ def run_gbfmm(args):
     ts = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum())
     fsum = float((m * np.linalg.norm(a, axis=1)).sum())
 
+    # momentum drift over leapfrog steps (the workload's drift run), untimed
+    leap = None
+    if args.leapfrog > 0 and world == 1:
+        _, _, v0 = synth.plummer(N, W["seed"], velocities=True)
+        xl = torch.from_numpy(x).to(dev)
+        vl = torch.from_numpy(v0).to(dev)
+        t0 = time.perf_counter()
+        dg = f.leapfrog(xl, vl, md, W["leaf"], W["p"], W["theta"], variant, 1e-3, args.leapfrog)
+        tl = time.perf_counter() - t0
+        Pm, Lm = dg[:, :3], dg[:, 3:]
+        pscale = float((m * np.linalg.norm(v0, axis=1)).sum())
+        lscale = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(v0, axis=1)).sum())
+        leap = {"steps": args.leapfrog, "dt": 1e-3, "seconds": tl,
+                "max_dP_rel": float(np.abs(Pm - Pm[0]).max() / pscale),
+                "max_dL_rel": float(np.abs(Lm - Lm[0]).max() / lscale),
+                "norm": "|sum m v - initial| / sum m|v|, |sum m x x v - initial| / sum m|x||v|"}
+
     # the other arithmetic modes of the pair kernels on the same input (same timing method)
     modes = {}
     if args.modes and world == 1:
@@ -329,6 +346,7 @@ def run_gbfmm(args):
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
         "modes": modes or None,
+        "leapfrog": leap,
         "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
                 "d2h_bytes_per_step": int(24 * N)},
         "gpu_launches": int(launches),
@@ -420,6 +438,7 @@ def main():
     ap.add_argument("--variant", default="conserving", choices=["conserving", "standard"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "mixed"],
                     help="arithmetic of the pair kernels (M2L, P2P)")
+    ap.add_argument("--leapfrog", type=int, default=100, help="KDK steps of the momentum-drift run (0: skip)")
     ap.add_argument("--no-modes", dest="modes", action="store_false",
                     help="skip timing the other arithmetic modes on the same input")
     args = ap.parse_args()

@@ -107,6 +107,16 @@ GBFMM_API int fmm_build(fmm_ctx *c, const double *x, const double *m, int64_t N,
  * mutual P2P, deterministic reductions (no floating-point atomics). */
 GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
 
+/* Kick-drift-kick leapfrog with this context's forces, for momentum-drift runs.
+ *   x, v: N x 3 row-major positions and velocities (host or device), advanced in place;
+ *   m: N masses.  Every step: v += a dt/2, x += v dt, rebuild (leaf_size), forces
+ *   (p, theta, variant), v += a dt/2.  All state stays on the device between steps.
+ *   diag: (nsteps + 1) x 6 doubles (host or device, or NULL): total linear momentum
+ *   sum m v and angular momentum sum m x x v before the first step and after each step,
+ *   summed in a fixed order.  Leaves the context built on the final positions. */
+GBFMM_API int fmm_leapfrog(fmm_ctx *c, double *x, double *v, const double *m, int64_t N, int leaf_size, int p,
+                           double theta, int variant, double dt, int nsteps, double *diag);
+
 /* Diagnostics of the last fmm_forces (eqs. netforce, total_torque), float64,
  * summed in a fixed order:  sum_ma = sum_a m_a acc_a,  sum_mxa = sum_a m_a X_a x acc_a. */
 GBFMM_API int fmm_diagnostics(fmm_ctx *c, double sum_ma[3], double sum_mxa[3]);

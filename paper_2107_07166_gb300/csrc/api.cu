@@ -129,7 +129,8 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
-                          &c->momT, &c->cmomT, &c->p2p_sep, &c->m2m_tmp};
+                          &c->momT, &c->cmomT, &c->p2p_sep, &c->m2m_tmp, &c->lf_x, &c->lf_v,
+                          &c->lf_m, &c->lf_a, &c->lf_diag};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);

@@ -120,6 +120,7 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_ipart;                   // double4 per (P2P item, slot)
     gbfmm::DevBuf cmom;                        // conserving source moments, n_nodes x 4 nmi(p-1)
     gbfmm::DevBuf m2m_tmp;                     // shifted child moments of one level
+    gbfmm::DevBuf lf_x, lf_v, lf_m, lf_a, lf_diag;  // leapfrog state (input order)
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     gbfmm::DevBuf p2p_sep;                     // centre separation of every P2P pair, storage type
     bool pos_valid = false;

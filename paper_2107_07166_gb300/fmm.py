@@ -29,7 +29,7 @@ DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_forces", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
-           "fmm_stage_times", "fmm_set_walk_capacity", "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
             "fmm_get_lists": (i32, [P, P, P]),
             "fmm_stage_times": (i32, [P, P, i32]),
             "fmm_set_walk_capacity": (i32, [P, i64, i64, i64]),
+            "fmm_leapfrog": (i32, [P, P, P, P, i64, i32, i32, dbl, i32, dbl, i32, P]),
             "fmm_walk_retries": (i32, [P, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
@@ -205,6 +206,18 @@ class FMM:
         p2p = np.zeros((c["n_p2p"], 2), np.int32)
         _check(self.lib.fmm_get_lists(self.h, _ptr(m2l), _ptr(p2p)), "fmm_get_lists")
         return m2l, p2p
+
+    def leapfrog(self, x, v, m, leaf_size: int, p: int, theta: float, variant: int, dt: float, nsteps: int,
+                 diag=None):
+        """nsteps kick-drift-kick steps; x and v (N x 3) are advanced in place.  Returns the
+        (nsteps + 1) x 6 momenta [sum m v, sum m x x v] as numpy if diag is None."""
+        n = int(x.shape[0])
+        out = np.zeros((nsteps + 1, 6)) if diag is None else diag
+        _check(self.lib.fmm_leapfrog(self.h, _ptr(x, np.float64), _ptr(v, np.float64), _ptr(m, np.float64), n,
+                                     int(leaf_size), int(p), float(theta), int(variant), float(dt), int(nsteps),
+                                     _ptr(out, np.float64)), "fmm_leapfrog")
+        self.N = n
+        return out
 
     def set_walk_capacity(self, frontier: int, m2l: int, p2p: int):
         _check(self.lib.fmm_set_walk_capacity(self.h, int(frontier), int(m2l), int(p2p)), "fmm_set_walk_capacity")
