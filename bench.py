@@ -123,6 +123,12 @@ def algorithmic_flops(counts, tree_counts, p, variant):
             "per_m2l_pair": per_m2l}
 
 
+# DRAM bytes (read + write) per unit of the dominant kernels, from one ncu --set full
+# capture of the current kernels at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md),
+# scaled here by the units of the timed launch: per mutual M2L pair, per particle pair.
+NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 68.3, ("p2p_k", "fp64"): 5.25}
+
+
 def fp64_peak_tflops(sm_mhz: float) -> float:
     """binary64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops."""
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
@@ -325,9 +331,14 @@ def run_gbfmm(args):
                  + ("; the double-float kernels run on the binary32 units and are rated against the binary64 "
                     "peak they replace" if args.precision == "df64" else ""))
     achieved = work[dom] / (stage_avg[dom] / 1e3) / 1e12
+    kname = ("m2l_con_k" if variant == 1 else "m2l_std_k") if dom == "m2l" else "p2p_k"
+    per_unit = NCU_TRAFFIC_PER_UNIT.get((kname, args.precision)) if W["p"] == 4 else None
+    units = work["n_m2l"] if dom == "m2l" else work["n_pp"]
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": ("m2l_con_k" if variant == 1 else "m2l_std_k") if dom == "m2l" else "p2p_k",
+                "frac": round(achieved / peak, 4),
+                "traffic": (round(per_unit * units) if per_unit else None),
+                "traffic_basis": ("ncu dram bytes per unit at N=2^19, scaled to this launch" if per_unit else None),
+                "kernel": kname,
                 "peak_basis": basis, "sm_mhz_median": sm_mhz}
     cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n) else None
     rng = np.random.default_rng(0)
