@@ -97,6 +97,17 @@ GBFMM_API int fmm_set_stream(fmm_ctx *c, void *cuda_stream);
  * centres of mass and exact r_max.  Invalidates previous moments, lists and forces. */
 GBFMM_API int fmm_build(fmm_ctx *c, const double *x, const double *m, int64_t N, int leaf_size);
 
+/* Build a batch of independent systems in one context (no force acts between systems).
+ *   x: N x 3, m: N with the systems concatenated; offsets: n_sys + 1 entries (host or
+ *   device), system s = particles [offsets[s], offsets[s+1]), offsets[0] = 0, every
+ *   system non-empty, N = offsets[n_sys].
+ * Every system gets its own bounding cube, keys and octree, exactly as fmm_build would
+ * give it alone; the trees form one forest (system s owns root node s) and every later
+ * stage processes all systems in the same launches.  fmm_get_keys reports the cube of
+ * system 0. */
+GBFMM_API int fmm_build_batch(fmm_ctx *c, const double *x, const double *m, const int64_t *offsets, int n_sys,
+                              int leaf_size);
+
 /* One force evaluation on the last built tree.
  *   p in [1,FMM_P_MAX]: multipole order (Sec. 2.1); theta in [0,1): acceptance parameter
  *   (eq. mac_criterion); variant: FMM_STANDARD or FMM_CONSERVING.
@@ -106,6 +117,11 @@ GBFMM_API int fmm_build(fmm_ctx *c, const double *x, const double *m, int64_t N,
  * Steps: P2M/M2M (cached per p), dual-tree walk (cached per theta), M2L, L2L, L2P,
  * mutual P2P, deterministic reductions (no floating-point atomics). */
 GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
+
+/* fmm_forces for a batch, plus per-system diagnostics: diag (n_sys x 6, host or device, or
+ * NULL) receives [sum m a, sum m X x a] of every system, summed in a fixed order. */
+GBFMM_API int fmm_forces_batch(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot,
+                               double *diag);
 
 /* Kick-drift-kick leapfrog with this context's forces, for momentum-drift runs.
  *   x, v: N x 3 row-major positions and velocities (host or device), advanced in place;

@@ -130,7 +130,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
                           &c->momT, &c->cmomT, &c->p2p_sep, &c->m2m_tmp, &c->lf_x, &c->lf_v,
-                          &c->lf_m, &c->lf_a, &c->lf_diag};
+                          &c->lf_m, &c->lf_a, &c->lf_diag, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -156,12 +156,8 @@ int fmm_set_stream(fmm_ctx* c, void* cuda_stream) {
     });
 }
 
-int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_size) {
-    if (!c) return fail(FMM_ERR_INVALID, "fmm_build: NULL context");
-    if (!x || !m) return fail(FMM_ERR_INVALID, "fmm_build: x and m are required");
-    if (N < 1) return fail(FMM_ERR_INVALID, "fmm_build: N must be >= 1");
-    if (N >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_CAPACITY, "fmm_build: N must be < 2^31 - 1");
-    if (leaf_size < 1) return fail(FMM_ERR_INVALID, "fmm_build: leaf_size must be >= 1");
+static int build_common(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_size,
+                        const std::vector<long long>& off) {
     return guarded(c, [&]() -> int {
         for (int s = 0; s < ST_COUNT; s++) c->stage_valid[s] = false;
         c->built = false;
@@ -177,6 +173,11 @@ int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_
             c->cap_fr = std::max<int64_t>(c->cap_fr, 4 * N + 4096);
         }
         c->leaf = leaf_size;
+        c->n_sys = (int)off.size() - 1;
+        c->sys_off_h = off;
+        ensure(c->sys_off, sizeof(long long) * off.size());
+        GB_CUDA(cudaMemcpyAsync(c->sys_off.p, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
+                                c->stream));
         const double* xd = x;
         const double* md = m;
         if (!is_device_ptr(x)) {
@@ -197,6 +198,38 @@ int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_
         c->built = true;
         return FMM_OK;
     });
+}
+
+int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_size) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_build: NULL context");
+    if (!x || !m) return fail(FMM_ERR_INVALID, "fmm_build: x and m are required");
+    if (N < 1) return fail(FMM_ERR_INVALID, "fmm_build: N must be >= 1");
+    if (N >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_CAPACITY, "fmm_build: N must be < 2^31 - 1");
+    if (leaf_size < 1) return fail(FMM_ERR_INVALID, "fmm_build: leaf_size must be >= 1");
+    return build_common(c, x, m, N, leaf_size, std::vector<long long>{0, (long long)N});
+}
+
+int fmm_build_batch(fmm_ctx* c, const double* x, const double* m, const int64_t* offsets, int n_sys,
+                    int leaf_size) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_build_batch: NULL context");
+    if (!x || !m || !offsets) return fail(FMM_ERR_INVALID, "fmm_build_batch: x, m and offsets are required");
+    if (n_sys < 1) return fail(FMM_ERR_INVALID, "fmm_build_batch: n_sys must be >= 1");
+    if (leaf_size < 1) return fail(FMM_ERR_INVALID, "fmm_build_batch: leaf_size must be >= 1");
+    std::vector<long long> off((size_t)n_sys + 1);
+    if (is_device_ptr(offsets)) {
+        if (cudaMemcpy(off.data(), offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FMM_ERR_CUDA, "fmm_build_batch: reading offsets failed");
+        }
+    } else {
+        for (size_t i = 0; i < off.size(); i++) off[i] = offsets[i];
+    }
+    if (off[0] != 0) return fail(FMM_ERR_INVALID, "fmm_build_batch: offsets[0] must be 0");
+    for (int i = 0; i < n_sys; i++)
+        if (off[i + 1] <= off[i]) return fail(FMM_ERR_INVALID, "fmm_build_batch: every system needs >= 1 particle");
+    int64_t N = off[n_sys];
+    if (N >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_CAPACITY, "fmm_build_batch: total N must be < 2^31 - 1");
+    return build_common(c, x, m, N, leaf_size, off);
 }
 
 int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double* pot) {
@@ -243,6 +276,19 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
             GB_CUDA(cudaMemcpyAsync(pot, pot_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
         if (!acc_dev || (want_pot && !pot_dev)) GB_CUDA(cudaStreamSynchronize(c->stream));
         c->have_forces = true;
+        return FMM_OK;
+    });
+}
+
+int fmm_forces_batch(fmm_ctx* c, int p, double theta, int variant, double* acc, double* pot, double* diag) {
+    int rc = fmm_forces(c, p, theta, variant, acc, pot);
+    if (rc != FMM_OK || !diag) return rc;
+    return guarded(c, [&]() -> int {
+        ensure(c->sys_diag, sizeof(double) * 6 * (size_t)c->n_sys);
+        run_diagnostics_sys(c, c->sys_diag.as<double>());
+        GB_CUDA(cudaMemcpyAsync(diag, c->sys_diag.p, sizeof(double) * 6 * (size_t)c->n_sys, cudaMemcpyDefault,
+                                c->stream));
+        GB_CUDA(cudaStreamSynchronize(c->stream));
         return FMM_OK;
     });
 }

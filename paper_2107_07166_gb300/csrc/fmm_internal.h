@@ -80,6 +80,10 @@ struct fmm_ctx {
     int64_t N = 0;
     int leaf = 0;
     bool built = false;
+    // systems of a batch: particles [off[s], off[s+1]) (one system for fmm_build)
+    int n_sys = 1;
+    std::vector<long long> sys_off_h;
+    gbfmm::DevBuf sys_off, sys_k, sys_v, sys_diag;
     // device buffers (see the kernels for layouts)
     gbfmm::DevBuf x_stage, m_stage;           // host inputs staged on the device
     gbfmm::DevBuf keys0, keys1, vals0, vals1;  // sort ping-pong
@@ -168,6 +172,7 @@ void run_p2p(fmm_ctx* c, bool want_pot);
 void run_p2p_gather(fmm_ctx* c);
 void run_gather_out(fmm_ctx* c, int p, int variant, bool want_pot, double* acc_out, double* pot_out);
 void run_diagnostics(fmm_ctx* c, double* out6_host);
+void run_diagnostics_sys(fmm_ctx* c, double* out_dev);
 
 void stage_begin(fmm_ctx* c, Stage s);
 void stage_end(fmm_ctx* c, Stage s);

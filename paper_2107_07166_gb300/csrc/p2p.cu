@@ -373,6 +373,36 @@ __global__ void diag_final_k(int nb, const double* __restrict__ part, double* __
     }
 }
 
+// per-system sums (batch): one block per system over its sorted particle range
+__global__ void diag_sys_k(const long long* __restrict__ off, int n, const double* __restrict__ xs,
+                           const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ ms,
+                           const double* __restrict__ acc, double* __restrict__ out) {
+    __shared__ double sh[DB];
+    int sys = blockIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (long long i = off[sys] + threadIdx.x; i < off[sys + 1]; i += DB) {
+        double m = ms[i], ax = acc[i], ay = acc[n + i], az = acc[2 * (int64_t)n + i];
+        double x = xs[i], y = ys[i], z = zs[i];
+        v[0] += m * ax;
+        v[1] += m * ay;
+        v[2] += m * az;
+        v[3] += m * (y * az - z * ay);
+        v[4] += m * (z * ax - x * az);
+        v[5] += m * (x * ay - y * ax);
+    }
+    for (int d = 0; d < 6; d++) {
+        double r = block_sum(v[d], sh);
+        if (threadIdx.x == 0) out[6 * sys + d] = r;
+    }
+}
+
+void run_diagnostics_sys(fmm_ctx* c, double* out) {
+    cudaStream_t s = c->stream;
+    diag_sys_k<<<c->n_sys, DB, 0, s>>>(c->sys_off.as<long long>(), (int)c->N, c->xs.as<double>(), c->ys.as<double>(),
+                                       c->zs.as<double>(), c->ms.as<double>(), c->acc_s.as<double>(), out);
+    GB_LAUNCH("diag_sys_k");
+}
+
 void run_diagnostics(fmm_ctx* c, double* out6) {
     cudaStream_t s = c->stream;
     int n = (int)c->N;

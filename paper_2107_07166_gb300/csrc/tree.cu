@@ -203,20 +203,6 @@ __global__ void tree_finish_k(int n, const int* __restrict__ cur, int* __restric
     if (cur[i] >= 0) leaf_of[i] = cur[i];
 }
 
-__global__ void root_k(int n, int* nfirst, int* ncount, int* nlevel, int* nparent, int* nchildf, int* nnchild) {
-    nfirst[0] = 0;
-    ncount[0] = n;
-    nlevel[0] = 0;
-    nparent[0] = -1;
-    nchildf[0] = -1;
-    nnchild[0] = 0;
-}
-
-__global__ void fill_int_k(int* __restrict__ a, int64_t n, int v) {
-    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i < n) a[i] = v;
-}
-
 // ------------------------------------------------------------------ centres of mass
 
 __global__ void com_leaf_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
@@ -313,6 +299,113 @@ __global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, do
     if (nd < nn) rmax[nd] = __dsqrt_rn(__longlong_as_double((long long)r2bits[nd]));
 }
 
+// ------------------------------------------------------------------ batches of systems
+// A batch is a forest: every system keeps its own bounding cube and keys (as if it were
+// built alone), particles are ordered by (system, key), and system s owns root node s.
+
+__device__ __forceinline__ int system_of(const long long* __restrict__ off, int nsys, int64_t i) {
+    int lo = 0, hi = nsys;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// one block per system: cube [lo(3), side, scale] into geom[8 s ..] and input validation
+__global__ void bbox_sys_k(const double* __restrict__ x, const double* __restrict__ m,
+                           const long long* __restrict__ off, double* __restrict__ geom, int* __restrict__ bad) {
+    __shared__ double smn[3][TB], smx[3][TB];
+    int sys = blockIdx.x;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int b = 0;
+    for (int64_t i = off[sys] + threadIdx.x; i < off[sys + 1]; i += TB) {
+        for (int d = 0; d < 3; d++) {
+            double v = x[3 * i + d];
+            if (!isfinite(v)) b = 1;
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+        double mm = m[i];
+        if (!(mm >= 0.0) || !isfinite(mm)) b = 1;
+    }
+    if (b) atomicOr(bad, 1);
+    for (int d = 0; d < 3; d++) {
+        smn[d][threadIdx.x] = mn[d];
+        smx[d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int st = TB / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int d = 0; d < 3; d++) {
+                smn[d][threadIdx.x] = fmin(smn[d][threadIdx.x], smn[d][threadIdx.x + st]);
+                smx[d][threadIdx.x] = fmax(smx[d][threadIdx.x], smx[d][threadIdx.x + st]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double side = 0.0;
+    for (int d = 0; d < 3; d++) {
+        geom[8 * sys + d] = smn[d][0];
+        double e = __dsub_rn(smx[d][0], smn[d][0]);
+        if (e > side) side = e;
+    }
+    if (side == 0.0) side = 1.0;
+    geom[8 * sys + 3] = side;
+    geom[8 * sys + 4] = __ddiv_rn(2097152.0, side);
+}
+
+__global__ void keys_sys_k(const double* __restrict__ x, int64_t n, const long long* __restrict__ off, int nsys,
+                           const double* __restrict__ geom, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    const double* g = geom + 8 * system_of(off, nsys, i);
+    uint64_t qx = quantise(x[3 * i], g[0], g[4]);
+    uint64_t qy = quantise(x[3 * i + 1], g[1], g[4]);
+    uint64_t qz = quantise(x[3 * i + 2], g[2], g[4]);
+    keys[i] = (spread_bits3(qx) << 2) | (spread_bits3(qy) << 1) | spread_bits3(qz);
+    idx[i] = (uint32_t)i;
+}
+
+// after the key sort: the system of every sorted particle, with its position as payload
+__global__ void sys_keys_k(const uint32_t* __restrict__ perm, int64_t n, const long long* __restrict__ off, int nsys,
+                           uint64_t* __restrict__ sk, uint32_t* __restrict__ pos) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    sk[i] = (uint64_t)system_of(off, nsys, perm[i]);
+    pos[i] = (uint32_t)i;
+}
+
+// reorder keys and permutation by q (sorted by system, stable in key order)
+__global__ void regather_k(const uint32_t* __restrict__ q, int64_t n, const uint64_t* __restrict__ kin,
+                           const uint32_t* __restrict__ pin, uint64_t* __restrict__ kout, uint32_t* __restrict__ pout) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = q[i];
+    kout[i] = kin[j];
+    pout[i] = pin[j];
+}
+
+__global__ void roots_k(const long long* __restrict__ off, int nsys, int* nfirst, int* ncount, int* nlevel,
+                        int* nparent, int* nchildf, int* nnchild) {
+    int sys = blockIdx.x * TB + threadIdx.x;
+    if (sys >= nsys) return;
+    nfirst[sys] = (int)off[sys];
+    ncount[sys] = (int)(off[sys + 1] - off[sys]);
+    nlevel[sys] = 0;
+    nparent[sys] = -1;
+    nchildf[sys] = -1;
+    nnchild[sys] = 0;
+}
+
+__global__ void cur_init_k(const long long* __restrict__ off, int nsys, int64_t n, int* __restrict__ cur) {
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i < n) cur[i] = system_of(off, nsys, i);
+}
+
 // ------------------------------------------------------------------ host driver
 
 static void ensure_nodes(fmm_ctx* c, int64_t need) {
@@ -331,18 +424,25 @@ static void ensure_nodes(fmm_ctx* c, int64_t need) {
 int build_tree(fmm_ctx* c, const double* x, const double* m) {
     cudaStream_t s = c->stream;
     int n = (int)c->N;
-    // a1: bounding cube and validation
+    int nsys = c->n_sys;
+    const long long* off = c->sys_off.as<long long>();
+    // a1: bounding cube(s) and validation
     int nb = (int)((c->N + TB - 1) / TB);
     if (nb > 1024) nb = 1024;
-    ensure(c->geom, sizeof(double) * (size_t)(8 + 6 * nb));
+    ensure(c->geom, sizeof(double) * (size_t)(8 * nsys + 6 * nb));
     ensure(c->errflag, sizeof(int) * 4);
     double* geom = c->geom.as<double>();
-    double* part = geom + 8;
+    double* part = geom + 8 * nsys;
     GB_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int) * 4, s));
-    bbox_partial_k<<<nb, TB, 0, s>>>(x, m, c->N, part, c->errflag.as<int>());
-    GB_LAUNCH("bbox_partial_k");
-    bbox_final_k<<<1, BFB, 0, s>>>(part, nb, geom);
-    GB_LAUNCH("bbox_final_k");
+    if (nsys == 1) {
+        bbox_partial_k<<<nb, TB, 0, s>>>(x, m, c->N, part, c->errflag.as<int>());
+        GB_LAUNCH("bbox_partial_k");
+        bbox_final_k<<<1, BFB, 0, s>>>(part, nb, geom);
+        GB_LAUNCH("bbox_final_k");
+    } else {
+        bbox_sys_k<<<nsys, TB, 0, s>>>(x, m, off, geom, c->errflag.as<int>());
+        GB_LAUNCH("bbox_sys_k");
+    }
     int bad = 0;
     GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
@@ -350,11 +450,32 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     // a2: keys; a3: sort
     ensure(c->keys0, sizeof(uint64_t) * (size_t)n);
     ensure(c->vals0, sizeof(uint32_t) * (size_t)n);
-    keys_k<<<grid_for(n, TB), TB, 0, s>>>(x, n, geom, c->keys0.as<uint64_t>(), c->vals0.as<uint32_t>());
+    if (nsys == 1)
+        keys_k<<<grid_for(n, TB), TB, 0, s>>>(x, n, geom, c->keys0.as<uint64_t>(), c->vals0.as<uint32_t>());
+    else
+        keys_sys_k<<<grid_for(n, TB), TB, 0, s>>>(x, n, off, nsys, geom, c->keys0.as<uint64_t>(),
+                                                  c->vals0.as<uint32_t>());
     GB_LAUNCH("keys_k");
     radix_sort(c, c->keys0, c->keys1, &c->vals0, &c->vals1, n, 63);
     ensure(c->perm, sizeof(uint32_t) * (size_t)n);
-    GB_CUDA(cudaMemcpyAsync(c->perm.p, c->vals0.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (nsys == 1) {
+        GB_CUDA(cudaMemcpyAsync(c->perm.p, c->vals0.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    } else {
+        // stable sort by system on top of the key order: (system, key) order
+        ensure(c->sys_k, sizeof(uint64_t) * (size_t)n);
+        ensure(c->sys_v, sizeof(uint32_t) * (size_t)n);
+        sys_keys_k<<<grid_for(n, TB), TB, 0, s>>>(c->vals0.as<uint32_t>(), n, off, nsys, c->sys_k.as<uint64_t>(),
+                                                  c->sys_v.as<uint32_t>());
+        GB_LAUNCH("sys_keys_k");
+        int sbits = 1;
+        while ((1 << sbits) < nsys) sbits++;
+        radix_sort(c, c->sys_k, c->keys1, &c->sys_v, &c->vals1, n, sbits);
+        regather_k<<<grid_for(n, TB), TB, 0, s>>>(c->sys_v.as<uint32_t>(), n, c->keys0.as<uint64_t>(),
+                                                  c->vals0.as<uint32_t>(), c->keys1.as<uint64_t>(),
+                                                  c->perm.as<uint32_t>());
+        GB_LAUNCH("regather_k");
+        GB_CUDA(cudaMemcpyAsync(c->keys0.p, c->keys1.p, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
     ensure(c->xs, sizeof(double) * (size_t)n);
     ensure(c->ys, sizeof(double) * (size_t)n);
     ensure(c->zs, sizeof(double) * (size_t)n);
@@ -370,14 +491,15 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     ensure(c->scan_out, sizeof(int) * (size_t)(n + 1));
     ensure(c->leaf_of, sizeof(int) * (size_t)n);
     ensure(c->nal, sizeof(int) * (size_t)n * (MAX_LEVEL + 1));
-    root_k<<<1, 1, 0, s>>>(n, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(), c->nparent.as<int>(),
-                           c->nchildf.as<int>(), c->nnchild.as<int>());
-    GB_LAUNCH("root_k");
-    fill_int_k<<<grid_for(n, TB), TB, 0, s>>>(c->cur.as<int>(), n, 0);
-    GB_LAUNCH("fill_int_k");
+    ensure_nodes(c, (int64_t)nsys + 64);
+    roots_k<<<grid_for(nsys, TB), TB, 0, s>>>(off, nsys, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
+                                              c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
+    GB_LAUNCH("roots_k");
+    cur_init_k<<<grid_for(n, TB), TB, 0, s>>>(off, nsys, n, c->cur.as<int>());
+    GB_LAUNCH("cur_init_k");
     c->level_start.assign(1, 0);
-    c->level_start.push_back(1);
-    int64_t n_nodes = 1;
+    c->level_start.push_back(nsys);
+    int64_t n_nodes = nsys;
     int level = 0;
     for (;; level++) {
         int* nal_l = c->nal.as<int>() + (int64_t)level * n;

@@ -130,13 +130,17 @@ __global__ void walk_advance_k(WalkCounters* cnt, int par, int* max_fr) {
     cnt->nf[par] = 0;
 }
 
-__global__ void walk_init_k(WalkCounters* cnt, int2* fr0, int* max_fr) {
-    cnt->nf[0] = 1;
-    cnt->nf[1] = 0;
-    cnt->n_m2l = 0;
-    cnt->n_p2p = 0;
-    *max_fr = 1;
-    fr0[0] = make_int2(0, 0);
+// the walk starts with Self(root) of every system of the batch (roots are nodes 0..nsys-1)
+__global__ void walk_init_k(WalkCounters* cnt, int2* fr0, int* max_fr, int nsys) {
+    int sys = blockIdx.x * WB + threadIdx.x;
+    if (sys < nsys) fr0[sys] = make_int2(sys, sys);
+    if (sys == 0) {
+        cnt->nf[0] = nsys;
+        cnt->nf[1] = 0;
+        cnt->n_m2l = 0;
+        cnt->n_p2p = 0;
+        *max_fr = nsys;
+    }
 }
 
 // directed M2L entries: (A -> B) and (B -> A) for every mutual pair
@@ -258,7 +262,7 @@ void run_walk(fmm_ctx* c, double theta) {
         ensure(c->cnt, sizeof(WalkCounters) + 16);
         WalkCounters* cnt = reinterpret_cast<WalkCounters*>(c->cnt.p);
         int* max_fr = reinterpret_cast<int*>(cnt + 1);
-        walk_init_k<<<1, 1, 0, s>>>(cnt, c->fr0.as<int2>(), max_fr);
+        walk_init_k<<<grid_for(c->n_sys, WB), WB, 0, s>>>(cnt, c->fr0.as<int2>(), max_fr, c->n_sys);
         GB_LAUNCH("walk_init_k");
         for (int k = 0; k < steps; k++) {
             int par = k & 1;

@@ -27,7 +27,8 @@ FP64, MIXED, DF64 = 0, 1, 2
 P_MAX = 6
 DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
-EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_forces", "fmm_diagnostics",
+EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_build_batch", "fmm_forces",
+           "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
@@ -59,6 +60,8 @@ def load(path: str = LIB_PATH):
             "fmm_set_stream": (i32, [P, P]),
             "fmm_build": (i32, [P, P, P, i64, i32]),
             "fmm_forces": (i32, [P, i32, dbl, i32, P, P]),
+            "fmm_build_batch": (i32, [P, P, P, P, i32, i32]),
+            "fmm_forces_batch": (i32, [P, i32, dbl, i32, P, P, P]),
             "fmm_diagnostics": (i32, [P, P, P]),
             "fmm_counts": (i32, [P, P, P, P, P]),
             "fmm_get_keys": (i32, [P, P, P, P, P]),
@@ -158,6 +161,24 @@ class FMM:
         _check(self.lib.fmm_build(self.h, _ptr(x, np.float64), _ptr(m, np.float64), n, int(leaf_size)),
                "fmm_build")
         self.N = n
+
+    def build_batch(self, x, m, offsets, leaf_size: int):
+        """Independent systems concatenated in x, m; offsets (n_sys + 1,) int64."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64) if not hasattr(offsets, "data_ptr") else offsets
+        n = int(x.shape[0])
+        if tuple(x.shape) != (n, 3) or tuple(m.shape) != (n,):
+            raise ValueError("x must be (N, 3) and m (N,)")
+        _check(self.lib.fmm_build_batch(self.h, _ptr(x, np.float64), _ptr(m, np.float64), _ptr(off, np.int64),
+                                        int(off.shape[0]) - 1, int(leaf_size)), "fmm_build_batch")
+        self.N = n
+        self.n_sys = int(off.shape[0]) - 1
+
+    def forces_batch(self, p: int, theta: float, variant: int, acc, pot=None):
+        """Forces of every system; returns the (n_sys, 6) per-system [sum m a, sum m X x a]."""
+        diag = np.zeros((self.n_sys, 6))
+        _check(self.lib.fmm_forces_batch(self.h, int(p), float(theta), int(variant), _ptr(acc, np.float64),
+                                         _ptr(pot, np.float64), _ptr(diag)), "fmm_forces_batch")
+        return diag
 
     def forces(self, p: int, theta: float, variant: int, acc, pot=None):
         if self.N and (tuple(acc.shape) != (self.N, 3) or (pot is not None and tuple(pot.shape) != (self.N,))):

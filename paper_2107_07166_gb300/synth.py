@@ -125,3 +125,20 @@ def clusters_pair(n_each: int, seed: int, distance: float):
     x = np.concatenate(out)
     m = np.full(x.shape[0], 1.0 / x.shape[0])
     return x, m
+
+
+def batch(n_sys: int, seed: int, n_min: int = 1024, n_max: int = 65536):
+    """Independent systems concatenated: system i has N_i = floor(exp U(ln n_min, ln n_max))
+    particles, a Plummer or a Hernquist (a = 1) profile by a coin flip, seed seed + i.
+    Returns (x[N, 3], m[N], offsets[n_sys + 1])."""
+    rng = _rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_sys))).astype(np.int64)
+    kinds = rng.random(n_sys) < 0.5
+    xs, ms = [], []
+    for i in range(n_sys):
+        gen = plummer if kinds[i] else hernquist
+        x, m = gen(int(sizes[i]), seed + 1 + i)
+        xs.append(x)
+        ms.append(m)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return np.concatenate(xs), np.concatenate(ms), off

@@ -389,3 +389,63 @@ def test_leapfrog_momentum_drift(fmm, torch_cuda, precision):
     assert drift[1][0] < 1e-13 and drift[1][1] < 1e-13, drift
     assert drift[0][0] < 1e-13, drift
     assert drift[0][1] > 100 * drift[1][1], drift
+
+
+# ------------------------------------------------------------- batches of systems
+
+def test_batch_matches_each_system_alone(fmm, torch_cuda, orc):
+    """A batch of independent systems (one of them a single particle) gives, system by
+    system, the keys, list sizes, forces and diagnostics of the oracle run on that system."""
+    x, m, off = synth.batch(7, 300, 100, 3000)
+    x1, m1 = synth.plummer(2, 301)
+    x = np.concatenate([x, x1[:1]])
+    m = np.concatenate([m, m1[:1]])
+    off = np.concatenate([off, [off[-1] + 1]])
+    ns = len(off) - 1
+    for variant in (0, 1):
+        f = new_ctx(fmm, torch_cuda)
+        f.build_batch(x, m, off, 16)
+        acc = np.empty_like(x)
+        pot = np.empty(x.shape[0])
+        diag = f.forces_batch(3, 0.5, variant, acc, pot)
+        keys, perm, _, _ = f.get_keys()
+        c = f.counts()
+        nn = nm = npp = 0
+        for s in range(ns):
+            a, b = off[s], off[s + 1]
+            r = orc.run(x[a:b], m[a:b], 16, 3, 0.5, variant, want_pot=True)
+            nn += r.n_nodes
+            nm += r.n_m2l
+            npp += r.n_p2p
+            assert np.array_equal(keys[a:b], r.keys)
+            assert np.array_equal(perm[a:b], r.perm + a)
+            assert rel(acc[a:b], r.acc) < TOL or np.abs(acc[a:b] - r.acc).max() == 0
+            assert rel(pot[a:b], r.pot) < TOL or np.abs(pot[a:b] - r.pot).max() == 0
+            F = (m[a:b, None] * acc[a:b]).sum(0)
+            T = (m[a:b, None] * np.cross(x[a:b], acc[a:b])).sum(0)
+            scale = (m[a:b] * np.linalg.norm(acc[a:b], axis=1)).sum() + 1e-300
+            assert np.allclose(diag[s, :3], F, rtol=0, atol=1e-13 * scale)
+            assert np.allclose(diag[s, 3:], T, rtol=0, atol=1e-13 * scale * (1 + np.abs(x[a:b]).max()))
+        assert (c["n_nodes"], c["n_m2l"], c["n_p2p"]) == (nn, nm, npp)
+        f.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_workload_shape(fmm, torch_cuda, orc, precision):
+    """64 systems with N log-uniform in [1k, 8k] (the batch workload's recipe at reduced
+    size), p = 4, theta = 0.6: per-system forces against the oracle on a sample of systems."""
+    x, m, off = synth.batch(64, 1000, 1024, 8192)
+    f = new_ctx(fmm, torch_cuda, precision)
+    f.build_batch(x, m, off, 32)
+    acc = np.empty_like(x)
+    diag = f.forces_batch(4, 0.6, 1, acc, None)
+    tol = {0: TOL, 2: TOL, 1: 2e-5}[precision]
+    for s in (0, 17, 41, 63):
+        a, b = off[s], off[s + 1]
+        r = orc.run(x[a:b], m[a:b], 32, 4, 0.6, 1, want_pot=False, want_internals=False)
+        assert rel(acc[a:b], r.acc) < tol, (s, rel(acc[a:b], r.acc))
+    tscale = np.array([(m[off[s]:off[s + 1]] * np.linalg.norm(x[off[s]:off[s + 1]], axis=1)
+                        * np.linalg.norm(acc[off[s]:off[s + 1]], axis=1)).sum() for s in range(64)])
+    lim = 1e-14 if precision != 1 else 1e-6
+    assert np.all(np.linalg.norm(diag[:, 3:], axis=1) < lim * tscale)
+    f.close()
