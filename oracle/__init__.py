@@ -22,7 +22,13 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-STANDARD, CONSERVING = 0, 1
+STANDARD, CONSERVING, CONSERVING_PAPER0 = 0, 1, 2
+
+
+def expansion_order(p: int, variant: int) -> int:
+    """Order of the moments (and standard locals) a run carries: p, except for the
+    literal order-0 realigned form, which needs the second moments of eq. aaB0."""
+    return 2 if variant == CONSERVING_PAPER0 else p
 
 
 def build(force: bool = False) -> str:
@@ -244,13 +250,14 @@ def run(x, m, leaf_size, p, theta, variant=STANDARD, want_pot=True, want_interna
             Z = np.zeros((nn, 3))
             rmax = np.zeros(nn)
             lib.orc_get_geometry(h, _p(M), _p(Z), _p(rmax))
-            mom = np.zeros((nn, nmi(p)))
+            pe = expansion_order(p, variant)
+            mom = np.zeros((nn, nmi(pe)))
             lib.orc_get_moments(h, _p(mom))
             m2l = np.zeros((nm2l, 2), dtype=np.int32)
             p2p = np.zeros((np2p, 2), dtype=np.int32)
             lib.orc_get_lists(h, _p(m2l), _p(p2p))
-            L = np.zeros((nn, nmi(p)))
-            SU = np.zeros((nn, 4 * nmi(p - 1)))
+            L = np.zeros((nn, nmi(pe)))
+            SU = np.zeros((nn, 4 * nmi(pe - 1)))
             got = lib.orc_get_locals(h, _p(L), _p(SU))
             r.__dict__.update(keys=keys_s, perm=perm, lo=lo, side=float(side[0]), tree=tree, M=M, Z=Z,
                               rmax=rmax, moments=mom, m2l=m2l, p2p=p2p,

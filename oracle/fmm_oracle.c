@@ -34,6 +34,15 @@
  *       W_{i,g}   = sum_{|b|+|g|<=p-1} (beta_i + 1) M_{beta+e_i} h_{beta+gamma}(R)
  *       U_gamma   = R S_gamma + W_gamma
  *       a(x)      = x S(x) + U(x).
+ * Literal order-0 realigned form (Sec. 3.2, eqs. realign2, nab-expansion, aaB0;
+ * variant 2, API order p = 1): every pair force is -m_b/R^2 times the expanded
+ * unit vector (n + delta)(1 - n.delta), delta = (x_a - y_b)/R, n = R/|R|; summed
+ * over b with sum m_b y_b = 0 this is
+ *       a(x) = -(M/R^2) [n + x_perp/R - (n.x) x/R^2] + Qbar n / R^4,
+ *       Qbar = sum_b m_b y_b y_b^T (raw second moment, trace included),
+ * a polynomial of degree 1 in x written as x S(x) + U(x).  It needs moments up to
+ * order 2, so the run carries order-2 moments (and, for the potential, the
+ * standard order-2 locals) and degree-1 conserving locals.
  */
 #include <math.h>
 #include <stdint.h>
@@ -497,6 +506,42 @@ static void m2l_conserving(orc_t *o, int64_t tgt, int64_t src) {
     }
 }
 
+/* literal order-0 realigned M2L (eq. aaB0): the terms of
+ *   a(x) = -(M/R^2) [n + x/R - (n.x) n/R - (n.x) x/R^2] + Qbar n / R^4
+ * sorted into x S(x) + U(x) with S, U of degree 1:
+ *   S_0 = -M/R^3            S_{e_j} = M n_j / R^4
+ *   U_{i,0} = -M n_i/R^2 + (Qbar n)_i / R^4      U_{i,e_j} = M n_i n_j / R^3
+ * with M = M_0 and Qbar_ij = sum m y_i y_j read from the raw moments
+ * (Qbar_ii = 2 M_{2e_i}, Qbar_ij = M_{e_i+e_j} for i != j). */
+static void m2l_paper0(orc_t *o, int64_t tgt, int64_t src) {
+    double R[3];
+    for (int d = 0; d < 3; d++) R[d] = o->Z[3 * tgt + d] - o->Z[3 * src + d];
+    double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    double n[3] = {R[0] / r, R[1] / r, R[2] / r};
+    const double *Ms = o->mom + src * o->nmom;
+    double M = Ms[0];
+    double Q[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            int e[3] = {0, 0, 0};
+            e[i] += 1;
+            e[j] += 1;
+            double v = Ms[g_idx[e[0]][e[1]][e[2]]];
+            Q[i][j] = (i == j) ? 2.0 * v : v;
+        }
+    double r2 = r * r, r3 = r2 * r, r4 = r2 * r2;
+    int nq = orc_nmi(1); /* 1, x, y, z */
+    double *S = o->SU + tgt * o->nloc;
+    double *U = S + nq;
+    S[0] += -M / r3;
+    for (int j = 0; j < 3; j++) S[1 + j] += M * n[j] / r4;
+    for (int i = 0; i < 3; i++) {
+        double Qn = Q[i][0] * n[0] + Q[i][1] * n[1] + Q[i][2] * n[2];
+        U[i * nq] += -M * n[i] / r2 + Qn / r4;
+        for (int j = 0; j < 3; j++) U[i * nq + 1 + j] += M * n[i] * n[j] / r3;
+    }
+}
+
 /* L2L (polynomial shift): L'_gamma += sum_{|gamma+beta|<=p} L_{gamma+beta} s^beta/beta!, s = Z_c - Z_P */
 static void l2l_poly(int p, const double *Lp, double *Lc, const double *w) {
     int n = orc_nmi(p);
@@ -561,11 +606,17 @@ static void p2p_pair(orc_t *o, int64_t a, int64_t b, double *acc, double *pot) {
 
 void orc_free(orc_t *o);
 
-/* Full evaluation.  x: N x 3 input order, m: N.  variant 0 standard, 1 conserving. */
+/* Full evaluation.  x: N x 3 input order, m: N.  variant 0 standard, 1 conserving,
+ * 2 literal order-0 realigned (p must be 1; carried internally at expansion order 2:
+ * order-2 moments, degree-1 conserving locals, standard order-2 potential). */
 orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p, double theta, int variant,
                int want_pot) {
     orc_tables();
-    if (N < 1 || leaf_size < 1 || p < 1 || p > ORC_PMAX) return NULL;
+    if (N < 1 || leaf_size < 1 || p < 1 || p > ORC_PMAX || variant < 0 || variant > 2) return NULL;
+    if (variant == 2) {
+        if (p != 1) return NULL;
+        p = 2;
+    }
     orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
     o->N = N;
     o->leaf_size = leaf_size;
@@ -608,7 +659,7 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
     /* a8 M2L (both partners of each mutual pair), a9 accumulation in list order */
     int need_L = (variant == 0) || want_pot;
     if (need_L) o->L = (double *)calloc((size_t)nn * o->nmom, 8);
-    if (variant == 1) o->SU = (double *)calloc((size_t)nn * o->nloc, 8);
+    if (variant >= 1) o->SU = (double *)calloc((size_t)nn * o->nloc, 8);
     for (int64_t k = 0; k < o->n_m2l; k++) {
         int32_t A = o->m2l[2 * k], B = o->m2l[2 * k + 1];
         if (need_L) {
@@ -619,6 +670,10 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
             m2l_conserving(o, A, B);
             m2l_conserving(o, B, A);
         }
+        if (variant == 2) {
+            m2l_paper0(o, A, B);
+            m2l_paper0(o, B, A);
+        }
     }
     /* a10 L2L, parents before children (breadth-first order) */
     double w[ORC_NMI_MAX];
@@ -628,7 +683,7 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
         for (int d = 0; d < 3; d++) s[d] = o->Z[3 * n + d] - o->Z[3 * P + d];
         mono_over_fact(p, s, w);
         if (need_L) l2l_poly(p, o->L + P * o->nmom, o->L + n * o->nmom, w);
-        if (variant == 1) {
+        if (variant >= 1) {
             int q = p - 1, nq = orc_nmi(q);
             double *Sc = o->SU + n * o->nloc;
             const double *Sp = o->SU + P * o->nloc;
@@ -892,6 +947,7 @@ void orc_l2l(int p, const double *s, const double *Lp, double *Lc) {
 void orc_cell_pair(int p, int variant, const double *ZA, const double *XA, int64_t nA, const double *ZB,
                    const double *YB, const double *mB, int64_t nB, double *acc, double *pot) {
     orc_tables();
+    if (variant == 2) p = 2; /* literal order-0 form: order-2 moments, degree-1 locals */
     orc_t o;
     memset(&o, 0, sizeof(o));
     double Z[6] = {ZA[0], ZA[1], ZA[2], ZB[0], ZB[1], ZB[2]};
@@ -906,6 +962,7 @@ void orc_cell_pair(int p, int variant, const double *ZA, const double *XA, int64
     orc_p2m(p, ZB, YB, mB, nB, o.mom + o.nmom);
     m2l_standard(&o, 0, 1);
     if (variant == 1) m2l_conserving(&o, 0, 1);
+    if (variant == 2) m2l_paper0(&o, 0, 1);
     for (int64_t a = 0; a < nA; a++) {
         double xv[3];
         for (int d = 0; d < 3; d++) xv[d] = XA[3 * a + d] - ZA[d];

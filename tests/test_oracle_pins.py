@@ -474,3 +474,77 @@ def test_plummer_potential_profile(orc):
         s = (rad > lo) & (rad < hi)
         want = (-1 / np.sqrt(rad[s] ** 2 + 1)).mean()
         assert r.pot[s].mean() == pytest.approx(want, rel=0.02)
+
+
+# ---------------------------------------------------------------- literal order-0 realigned form
+
+def _paper0_pairwise(ZA, XA, ZB, YB, mB):
+    """Per-pair sum of eqs. realign2 and nab-expansion: a_a = sum_b -(m_b/R^2) (n + delta)
+    (1 - n.delta), delta = ((X_a - Z_A) - (Y_b - Z_B)) / R, n = R/|R|, R = Z_A - Z_B."""
+    R = ZA - ZB
+    r = np.linalg.norm(R)
+    n = R / r
+    out = np.zeros_like(XA)
+    for a in range(XA.shape[0]):
+        delta = ((XA[a] - ZA)[None, :] - (YB - ZB)) / r
+        nd = delta @ n
+        out[a] = (-(mB / r ** 2)[:, None] * (n[None, :] + delta) * (1.0 - nd)[:, None]).sum(0)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_paper0_closed_form_equals_pairwise_expansion(orc, seed):
+    """The cell form of eq. aaB0 (monopole, x_perp, (n.x)x and Qbar terms) equals the
+    particle-by-particle sum of the expanded realigned pair forces it was derived from,
+    given that Z_B is the centre of mass of B (the dipole vanishes)."""
+    rng = np.random.default_rng(40 + seed)
+    XA = rng.normal(size=(7, 3)) * 0.3
+    YB = rng.normal(size=(11, 3)) * 0.4 + rng.normal(size=3) * 3.0 + np.array([4.0, 0.0, 0.0])
+    mB = rng.random(11) + 0.1
+    ZA = XA.mean(0) + 0.03
+    ZB = (mB[:, None] * YB).sum(0) / mB.sum()
+    a1, _ = orc.cell_pair(1, 2, ZA, XA, ZB, YB, mB)
+    a2 = _paper0_pairwise(ZA, XA, ZB, YB, mB)
+    assert rel(a1, a2) < 1e-13
+
+
+def test_paper0_single_source_is_central_and_first_order(orc):
+    """With one source particle (Qbar = 0) every force lies on X_a - Y_b, and its error
+    against Newton falls linearly with the separation (the expansion is of order 0 in
+    magnitude and 1 in direction)."""
+    rng = np.random.default_rng(3)
+    XA = rng.normal(size=(6, 3)) * 0.2
+    errs = []
+    for dist in (4.0, 8.0, 16.0, 32.0):
+        YB = np.array([[dist, 0.3, -0.2]])
+        mB = np.array([1.7])
+        a, _ = orc.cell_pair(1, 2, XA.mean(0), XA, YB[0], YB, mB)
+        d = XA - YB
+        assert np.abs(np.cross(a, d)).max() <= 1e-14 * np.abs(a).max() * np.abs(d).max()
+        exact = -mB[0] * d / (np.linalg.norm(d, axis=1) ** 3)[:, None]
+        errs.append(rel(a, exact))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.7 < q < 2.3 for q in ratios), ratios
+
+
+def test_paper0_run_conserves_momenta(orc):
+    """The literal order-0 realigned form conserves linear and angular momentum in the
+    full FMM (pair forces central and antisymmetric), at roundoff."""
+    x, m = synth.plummer(3000, 11)
+    a, _ = orc.direct(x, m, want_pot=False)
+    errs = []
+    for th in (0.3, 0.6):
+        r = orc.run(x, m, 16, 1, th, 2, want_pot=False, want_internals=False)
+        f, t = _net(x, m, r.acc)
+        assert f < 1e-14 and t < 1e-14, (th, f, t)
+        s = orc.run(x, m, 16, 1, th, 0, want_pot=False, want_internals=False)
+        errs.append(rel(r.acc, a))
+        # same order as the standard monopole expansion (Sec. 3.1 vs Sec. 3.2)
+        assert rel(s.acc, a) < errs[-1] < 2 * rel(s.acc, a), (th, errs[-1], rel(s.acc, a))
+    assert errs[0] < errs[1]
+
+
+def test_paper0_requires_order_one(orc):
+    x, m = synth.plummer(100, 1)
+    with pytest.raises(ValueError):
+        orc.run(x, m, 16, 2, 0.5, 2)
