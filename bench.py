@@ -30,6 +30,19 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="plummer-1m-conserving", N=1 << 20, seed=2, p=4, theta=0.6, leaf=32,
                 variant="conserving", precision="fp64")
+# further synthetic workloads (sizes and orders of the paper-shaped test set); the default
+# line is plummer1m
+WORKLOADS = {
+    "plummer1m": WORKLOAD,
+    "plummer4k": dict(workload="plummer-4096", N=4096, seed=1, p=2, theta=0.5, leaf=16, variant="conserving",
+                      precision="fp64", gen="plummer"),
+    "binary4m": dict(workload="binary-2x2m", N=1 << 22, seed=3, p=6, theta=0.7, leaf=32, variant="conserving",
+                     precision="mixed", gen="binary"),
+    "batch512": dict(workload="batch-512-systems", N=None, seed=1000, p=4, theta=0.6, leaf=32,
+                     variant="conserving", precision="mixed", gen="batch", n_sys=512),
+    "disk16m": dict(workload="disk-bulge-16m", N=1 << 24, seed=5, p=5, theta=0.7, leaf=32, variant="conserving",
+                    precision="mixed", gen="disk", leapfrog=20),
+}
 METRIC = "particles/s, AM-conserving FMM force eval, N=1M p=4 θ=0.6; force err; |Σx×F|"
 CPU_SAMPLE_N = 1 << 19          # oracle sample: same generator, p, theta, leaf; ~15 s of CPU
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
@@ -149,14 +162,28 @@ def run_gbfmm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    W = dict(WORKLOAD)
+    W = dict(WORKLOADS[args.workload])
     if args.n:
         W["N"] = args.n
         W["workload"] = f"plummer-{args.n}-{args.variant}"
-    W["variant"] = args.variant
-    W["precision"] = args.precision
+    if args.variant_set:
+        W["variant"] = args.variant
+    if args.precision_set or args.workload == "plummer1m":
+        W["precision"] = args.precision
+    args.precision = W["precision"]
+    args.variant = W["variant"]
+    gen = W.get("gen", "plummer")
+    offsets = None
+    if gen == "binary":
+        x, m = synth.binary(W["N"] // 2, W["seed"], W["seed"] + 1)
+    elif gen == "disk":
+        x, m = synth.disk_bulge(W["N"], W["seed"])
+    elif gen == "batch":
+        x, m, offsets = synth.batch(W["n_sys"], W["seed"])
+        W["N"] = int(offsets[-1])
+    else:
+        x, m = synth.plummer(W["N"], W["seed"])
     N = W["N"]
-    x, m = synth.plummer(N, W["seed"])
     xd = torch.from_numpy(x).to(dev)
     md = torch.from_numpy(m).to(dev)
     acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
@@ -167,7 +194,10 @@ def run_gbfmm(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        f.build(xd, md, W["leaf"])
+        if offsets is not None:
+            f.build_batch(xd, md, offsets, W["leaf"])
+        else:
+            f.build(xd, md, W["leaf"])
         f.forces(W["p"], W["theta"], variant, acc, None)
 
     with torch.cuda.stream(stream):
@@ -225,7 +255,10 @@ def run_gbfmm(args):
     for _ in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        f.build(xh, mh, W["leaf"])
+        if offsets is not None:
+            f.build_batch(xh, mh, offsets, W["leaf"])
+        else:
+            f.build(xh, mh, W["leaf"])
         f.forces(W["p"], W["theta"], variant, acch, None)
         torch.cuda.synchronize(dev)
         e2e_t.append(time.perf_counter() - t0)
@@ -234,12 +267,15 @@ def run_gbfmm(args):
     # accuracy and conservation of the timed configuration
     Fsum, Tsum = f.diagnostics()
     a = acc.cpu().numpy()
-    err = {"vs_direct_sampled": sampled_direct_error(torch, dev, x, m, a)}
+    err = {"vs_direct_sampled": sampled_direct_error(torch, dev, x, m, a, offsets=offsets)}
     if prec != fmm.FP64:     # the binary64 mode on the same input, untimed
         g = fmm.FMM(local, fmm.FP64, stream)
         ref = torch.empty_like(acc)
         with torch.cuda.stream(stream):
-            g.build(xd, md, W["leaf"])
+            if offsets is not None:
+                g.build_batch(xd, md, offsets, W["leaf"])
+            else:
+                g.build(xd, md, W["leaf"])
             g.forces(W["p"], W["theta"], variant, ref, None)
         stream.synchronize()
         r = ref.cpu().numpy()
@@ -250,24 +286,28 @@ def run_gbfmm(args):
 
     # momentum drift over leapfrog steps (the workload's drift run), untimed
     leap = None
-    if args.leapfrog > 0 and world == 1:
-        _, _, v0 = synth.plummer(N, W["seed"], velocities=True)
+    lf_steps = W.get("leapfrog", args.leapfrog) if args.leapfrog > 0 else 0
+    if lf_steps > 0 and world == 1 and gen in ("plummer", "disk"):
+        if gen == "disk":
+            _, _, v0 = synth.disk_bulge(N, W["seed"], velocities=True)
+        else:
+            _, _, v0 = synth.plummer(N, W["seed"], velocities=True)
         xl = torch.from_numpy(x).to(dev)
         vl = torch.from_numpy(v0).to(dev)
         t0 = time.perf_counter()
-        dg = f.leapfrog(xl, vl, md, W["leaf"], W["p"], W["theta"], variant, 1e-3, args.leapfrog)
+        dg = f.leapfrog(xl, vl, md, W["leaf"], W["p"], W["theta"], variant, 1e-3, lf_steps)
         tl = time.perf_counter() - t0
         Pm, Lm = dg[:, :3], dg[:, 3:]
         pscale = float((m * np.linalg.norm(v0, axis=1)).sum())
         lscale = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(v0, axis=1)).sum())
-        leap = {"steps": args.leapfrog, "dt": 1e-3, "seconds": tl,
+        leap = {"steps": lf_steps, "dt": 1e-3, "seconds": tl,
                 "max_dP_rel": float(np.abs(Pm - Pm[0]).max() / pscale),
                 "max_dL_rel": float(np.abs(Lm - Lm[0]).max() / lscale),
                 "norm": "|sum m v - initial| / sum m|v|, |sum m x x v - initial| / sum m|x||v|"}
 
     # the other arithmetic modes of the pair kernels on the same input (same timing method)
     modes = {}
-    if args.modes and world == 1:
+    if args.modes and world == 1 and args.workload == "plummer1m" and not args.n:
         for name in ("fp64", "df64", "mixed"):
             if name == args.precision:
                 continue
@@ -340,14 +380,18 @@ def run_gbfmm(args):
                 "traffic_basis": ("ncu dram bytes per unit at N=2^19, scaled to this launch" if per_unit else None),
                 "kernel": kname,
                 "peak_basis": basis, "sm_mhz_median": sm_mhz}
-    cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n) else None
+    cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n and args.workload == "plummer1m") else None
     rng = np.random.default_rng(0)
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[args.precision],
-        "data": "synthetic (seeded Plummer sphere)",
-        "config": {"workload": W["workload"], "N": N, "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
+        "data": {"plummer": "synthetic (seeded Plummer sphere)",
+                 "binary": "synthetic (seeded binary of two Plummer spheres, 10 apart)",
+                 "disk": "synthetic (seeded exponential disk + Hernquist bulge)",
+                 "batch": "synthetic (seeded batch of Plummer/Hernquist systems, log-uniform sizes)"}[gen],
+        "config": {"workload": W["workload"], "N": N, "n_systems": (len(offsets) - 1 if offsets is not None else 1),
+                   "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
                    "variant": W["variant"], "precision": W["precision"], "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
@@ -371,20 +415,32 @@ def run_gbfmm(args):
     return line
 
 
-def sampled_direct_error(torch, dev, x, m, a, n_targets=400):
+def sampled_direct_error(torch, dev, x, m, a, n_targets=400, offsets=None):
     """Relative L2 error of accelerations a (N x 3) against the direct sum (eq. jia) on
-    n_targets sampled particles, evaluated with plain binary64 tensor operations."""
+    n_targets sampled particles, evaluated with plain binary64 tensor operations.  With
+    offsets (a batch of independent systems) each target sums over its own system only."""
     rng = np.random.default_rng(0)
-    tg = rng.choice(x.shape[0], n_targets, replace=False)
+    tg = np.sort(rng.choice(x.shape[0], n_targets, replace=False))
     X = torch.from_numpy(x).to(dev)
     M = torch.from_numpy(m).to(dev)
     ref = torch.zeros((n_targets, 3), dtype=torch.float64, device=dev)
-    for i0 in range(0, n_targets, 16):
-        t = torch.from_numpy(tg[i0:i0 + 16]).to(dev)
-        d = X[t][:, None, :] - X[None, :, :]                      # (16, N, 3)
+    if offsets is not None:
+        sys_of = np.searchsorted(offsets, tg, side="right") - 1
+        for k, t in enumerate(tg):
+            lo, hi = int(offsets[sys_of[k]]), int(offsets[sys_of[k] + 1])
+            d = X[int(t)][None, :] - X[lo:hi]
+            r2 = (d * d).sum(-1)
+            inv3 = torch.where(r2 > 0, r2.rsqrt() ** 3, torch.zeros_like(r2))
+            ref[k] = -(M[lo:hi, None] * d * inv3[:, None]).sum(0)
+        ref = ref.cpu().numpy()
+        return float(np.linalg.norm(a[tg] - ref) / np.linalg.norm(ref))
+    ch = max(1, min(16, (1 << 25) // x.shape[0]))               # targets per chunk
+    for i0 in range(0, n_targets, ch):
+        t = torch.from_numpy(tg[i0:i0 + ch]).to(dev)
+        d = X[t][:, None, :] - X[None, :, :]                      # (ch, N, 3)
         r2 = (d * d).sum(-1)
         inv3 = torch.where(r2 > 0, r2.rsqrt() ** 3, torch.zeros_like(r2))
-        ref[i0:i0 + 16] = -(M[None, :, None] * d * inv3[..., None]).sum(1)
+        ref[i0:i0 + ch] = -(M[None, :, None] * d * inv3[..., None]).sum(1)
     ref = ref.cpu().numpy()
     return float(np.linalg.norm(a[tg] - ref) / np.linalg.norm(ref))
 
@@ -446,13 +502,19 @@ def main():
     ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--n", type=int, default=0, help="override N (profiling of a smaller case)")
-    ap.add_argument("--variant", default="conserving", choices=["conserving", "standard"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "mixed"],
+    ap.add_argument("--workload", default="plummer1m", choices=sorted(WORKLOADS),
+                    help="plummer1m (default line) or another synthetic workload")
+    ap.add_argument("--variant", default=None, choices=["conserving", "standard"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "df64", "mixed"],
                     help="arithmetic of the pair kernels (M2L, P2P)")
     ap.add_argument("--leapfrog", type=int, default=100, help="KDK steps of the momentum-drift run (0: skip)")
     ap.add_argument("--no-modes", dest="modes", action="store_false",
                     help="skip timing the other arithmetic modes on the same input")
     args = ap.parse_args()
+    args.variant_set = args.variant is not None
+    args.precision_set = args.precision is not None
+    args.variant = args.variant or "conserving"
+    args.precision = args.precision or "fp64"
     if args.impl == "reference":
         run_reference(args)
         return

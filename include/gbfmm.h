@@ -50,8 +50,11 @@ typedef struct fmm_ctx fmm_ctx;
 
 /* variants */
 enum {
-    FMM_STANDARD = 0,  /* Sec. 2: symmetric Taylor expansion (eq. taylor), forces a = -grad phi */
-    FMM_CONSERVING = 1 /* Sec. 3.2: every approximated pair force realigned onto the line X_a - Y_b */
+    FMM_STANDARD = 0,   /* Sec. 2: symmetric Taylor expansion (eq. taylor), forces a = -grad phi */
+    FMM_CONSERVING = 1, /* Sec. 3.2: every approximated pair force realigned onto the line X_a - Y_b */
+    FMM_CONSERVING_PAPER0 = 2 /* Sec. 3.2, eqs. realign2 and aaB0, p = 1 only: zeroth-order magnitude
+                                 times the first-order expanded unit vector, summed into monopole,
+                                 x_perp, (n.x) x and second-moment terms (moments carried to order 2) */
 };
 
 /* arithmetic of the pair kernels (M2L and P2P); tree, moments, translations (M2M, L2L),
@@ -110,10 +113,12 @@ GBFMM_API int fmm_build_batch(fmm_ctx *c, const double *x, const double *m, cons
 
 /* One force evaluation on the last built tree.
  *   p in [1,FMM_P_MAX]: multipole order (Sec. 2.1); theta in [0,1): acceptance parameter
- *   (eq. mac_criterion); variant: FMM_STANDARD or FMM_CONSERVING.
+ *   (eq. mac_criterion); variant: FMM_STANDARD, FMM_CONSERVING, or FMM_CONSERVING_PAPER0
+ *   (which needs p = 1, else FMM_ERR_INVALID).
  *   acc: N x 3 row-major output accelerations (required).
  *   pot: N output potentials, or NULL to skip them.  For FMM_CONSERVING the potential
- *   is the standard order-p potential (a realigned force field has no potential).
+ *   is the standard order-p potential (a realigned force field has no potential); for
+ *   FMM_CONSERVING_PAPER0 it is the standard order-2 potential of the moments it carries.
  * Steps: P2M/M2M (cached per p), dual-tree walk (cached per theta), M2L, L2L, L2P,
  * mutual P2P, deterministic reductions (no floating-point atomics). */
 GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);

@@ -129,7 +129,8 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
-                          &c->momT, &c->cmomT, &c->p2p_sep, &c->m2m_tmp, &c->lf_x, &c->lf_v,
+                          &c->momT, &c->nk, &c->zhl, &c->m2l_kpart, &c->p2p_sep, &c->m2m_tmp,
+                          &c->lf_x, &c->lf_v,
                           &c->lf_m, &c->lf_a, &c->lf_diag, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
@@ -239,9 +240,13 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
     if (!(theta >= 0.0 && theta < 1.0)) return fail(FMM_ERR_INVALID, "fmm_forces: theta must be in [0, 1)");
     if (c->precision == FMM_DF64 && p > FMM_DF64_P_MAX)
         return fail(FMM_ERR_INVALID, "fmm_forces: FMM_DF64 supports p <= FMM_DF64_P_MAX");
-    if (variant != FMM_STANDARD && variant != FMM_CONSERVING)
+    if (variant != FMM_STANDARD && variant != FMM_CONSERVING && variant != FMM_CONSERVING_PAPER0)
         return fail(FMM_ERR_INVALID, "fmm_forces: unknown variant");
+    if (variant == FMM_CONSERVING_PAPER0 && p != 1)
+        return fail(FMM_ERR_INVALID, "fmm_forces: FMM_CONSERVING_PAPER0 needs p = 1");
     if (!acc) return fail(FMM_ERR_INVALID, "fmm_forces: acc is required");
+    // the literal order-0 form reads the second moments (eq. aaB0): expansion order 2
+    if (variant == FMM_CONSERVING_PAPER0) p = 2;
     return guarded(c, [&]() -> int {
         for (int s = ST_MOMENTS; s < ST_COUNT; s++) c->stage_valid[s] = false;
         bool want_pot = pot != nullptr;

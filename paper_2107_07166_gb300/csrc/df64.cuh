@@ -108,5 +108,15 @@ __device__ __forceinline__ df64 to_df(double d) {
 }
 
 __device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+// multiplication by a power of two f: both words scale exactly (barring underflow of lo)
+__device__ __forceinline__ df64 scale_t(df64 a, float f) { return df64(a.hi * f, a.lo * f); }
+// a * f * c for a power of two f and a small integer c: the high word's product is split
+// exactly (TwoProd), the low word's carries the usual double-word error (left unnormalised)
+__device__ __forceinline__ df64 scale_c_t(df64 a, float f, float c) {
+    float h = a.hi * f;
+    float p = h * c;
+    float e = fmaf(h, c, -p);
+    return df64(p, fmaf(a.lo * f, c, e));
+}
 
 }  // namespace gbfmm

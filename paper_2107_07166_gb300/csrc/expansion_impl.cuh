@@ -5,9 +5,32 @@
 // Layouts (device, node ids breadth-first):
 //   mom[n * NM + k]     raw moments M_alpha about Z_n, alpha in generated order
 //   loc[n * NM + k]     standard locals L_gamma                       (variant 0)
-//   loc[n * NSU + k]    conserving locals [S | Ux | Uy | Uz]          (variant 1)
+//   loc[n * NSU + k]    conserving locals [S | Ux | Uy | Uz]          (variants 1 and 2)
 //   m2l_dir[e]          directed entry tgt << bits | src, sorted; m2l_seg[n] = first entry of n
+//
+// Range scaling of the binary32 and double-float M2L (their exponent range is binary32's).
+// A tensor of order n at separation R grows like R^-(n+1) (R^-(n+3) for the conserving
+// kernel), which leaves the binary32 range for close, small cells (R ~ 1e-5 at p = 6),
+// and the moments of small cells underflow.  These modes therefore work in powers of two:
+//   * node n stores its moments in units of s_n = 2^k_n, k_n = floor(log2 r_max,n):
+//     Mt_beta = M_beta s_n^-|beta| (exact power-of-two scaling in binary64, then narrowed);
+//   * an M2L item (one target, up to M2L_CHUNK sources) works in units of
+//     s_I = 2^k_I <= its nearest source separation;
+//   * each entry takes its tensor at R' = R / 2^k_e with k_e = floor(log2 |R|_inf), so
+//     |R'|_inf is in [1, 2) and no monomial of the tensor leaves the range, and moves it to
+//     item units by homogeneity, T_alpha(R / s_I) = v^(|alpha|+1) T_alpha(R') (v^(|alpha|+3)
+//     for the conserving kernel), v = 2^(k_I - k_e) <= 1;
+//   * a source's moments are multiplied on load by (s_n / s_I)^|beta| (saturated at 2^100:
+//     a source that far beyond the item's nearest one contributes below binary32 resolution);
+//   * the item's partial locals carry s_I^(|gamma|+1) (standard), s_I^(|gamma|+3) (S) or
+//     s_I^(|gamma|+2) (U); the binary64 reduction removes the factor exactly.
+// Every factor is a power of two, so the scaling itself adds no rounding.  binary64 (FMM_FP64)
+// is unscaled.  The binary32 separation is formed from double-float centres (two binary32
+// words per coordinate) with an error-free subtraction, so no binary64 arithmetic sits in the
+// binary32 kernel.
 #pragma once
+#include <type_traits>
+
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
@@ -39,72 +62,249 @@ __global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfir
 }
 
 
+// ---- range scaling helpers (binary32 and double-float kernels)
+
+// floor(log2(max(|x|, |y|, |z|))) from the binary32 exponent, clamped to [-100, 100]
+__device__ __forceinline__ int sep_exp(float x, float y, float z) {
+    float m = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+    int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;
+    return min(100, max(-100, e));
+}
+
+// 2^e as binary32, e in [-126, 127]
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
+
+// Z_a - Z_b from double-float centres, rounded to binary32: (ah - bh) + (al - bl).  When
+// the centres are close (the case that cancels), ah - bh is exact by Sterbenz's lemma;
+// otherwise its rounding is within binary32's own 2^-24 of |Z_a - Z_b|
+__device__ __forceinline__ float dsep(float ah, float al, float bh, float bl) {
+    return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
+}
+
+// 2^e as binary64 for |e| <= 1022
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// the item unit exponent: min over the item's sources of floor(log2 |R|_inf)
+__device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint64_t* __restrict__ dir, uint64_t mask,
+                                        const float4* __restrict__ zh, const float4* __restrict__ zl) {
+    float4 ah = zh[tgt], al = zl[tgt];
+    int k = 100;
+    for (int e = e0; e < e1; e++) {
+        int src = (int)(dir[e] & mask);
+        float4 bh = zh[src], bl = zl[src];
+        k = min(k, sep_exp(dsep(ah.x, al.x, bh.x, bl.x), dsep(ah.y, al.y, bh.y, bl.y), dsep(ah.z, al.z, bh.z, bl.z)));
+    }
+    return k;
+}
+
+// degree of multi-index number j in the generated order (by degree)
+__host__ __device__ constexpr int mi_deg(int j) {
+    int n = 0;
+    while (j >= (n + 1) * (n + 2) * (n + 3) / 6) n++;
+    return n;
+}
+
+// v^n for n < NF (v a power of two <= 1; underflow to zero is harmless here)
+template <int NF>
+__device__ __forceinline__ void pow_table(float v, float* w) {
+    w[0] = 1.f;
+#pragma unroll
+    for (int n = 1; n < NF; n++) w[n] = w[n - 1] * v;
+}
+
+// f[n] = 2^(e n), n < NF, saturated at 2^100
+template <int NF>
+__device__ __forceinline__ void moment_factors(int e, float* f) {
+    float t = pow2f(min(100, max(-126, e)));
+    f[0] = 1.f;
+#pragma unroll
+    for (int n = 1; n < NF; n++) f[n] = fminf(f[n - 1] * t, 0x1p100f);
+}
+
+// R = Z_tgt - Z_src in the kernel type: binary64 from the binary64 centres; double-float
+// from the binary64 difference; binary32 from the double-float centres
+template <class T>
+struct SepOf;
+template <>
+struct SepOf<double> {
+    __device__ static void get(const double* Zx, const double* Zy, const double* Zz, const float4*, const float4*,
+                               int tgt, int src, double& rx, double& ry, double& rz) {
+        rx = Zx[tgt] - Zx[src];
+        ry = Zy[tgt] - Zy[src];
+        rz = Zz[tgt] - Zz[src];
+    }
+    __device__ static float approx(double v) { return (float)v; }
+};
+template <>
+struct SepOf<df64> {
+    __device__ static void get(const double* Zx, const double* Zy, const double* Zz, const float4*, const float4*,
+                               int tgt, int src, df64& rx, df64& ry, df64& rz) {
+        rx = to_df(Zx[tgt] - Zx[src]);
+        ry = to_df(Zy[tgt] - Zy[src]);
+        rz = to_df(Zz[tgt] - Zz[src]);
+    }
+    __device__ static float approx(df64 v) { return v.hi; }
+};
+template <>
+struct SepOf<float> {
+    __device__ static void get(const double*, const double*, const double*, const float4* zh, const float4* zl,
+                               int tgt, int src, float& rx, float& ry, float& rz) {
+        float4 ah = zh[tgt], al = zl[tgt], bh = zh[src], bl = zl[src];
+        rx = dsep(ah.x, al.x, bh.x, bl.x);
+        ry = dsep(ah.y, al.y, bh.y, bl.y);
+        rz = dsep(ah.z, al.z, bh.z, bl.z);
+    }
+    __device__ static float approx(float v) { return v; }
+};
+
+// one M2L entry's geometry in the scaled modes: R' = R 2^-k_e (|R'|_inf in [1, 2)), the
+// item-unit separation R'' = R' 2^(k_e - k_I), v = 2^(k_I - k_e); returns k_e
+template <class T>
+__device__ __forceinline__ int entry_units(T& rx, T& ry, T& rz, int kI, T& ux, T& uy, T& uz, float& v) {
+    int ke = sep_exp(SepOf<T>::approx(rx), SepOf<T>::approx(ry), SepOf<T>::approx(rz));
+    float se = pow2f(-ke);
+    rx = scale_t(rx, se);
+    ry = scale_t(ry, se);
+    rz = scale_t(rz, se);
+    int d = ke - kI;  // >= 0 by the choice of k_I
+    v = pow2f(-min(d, 126));
+    float up = pow2f(min(d, 100));
+    ux = scale_t(rx, up);
+    uy = scale_t(ry, up);
+    uz = scale_t(rz, up);
+    return ke;
+}
+
+// N (a multiple of 4) binary32 values in 16-byte loads
+template <int N>
+__device__ __forceinline__ void load_f4(const float* __restrict__ src, float* dst) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int k = 0; k < N / 4; k++) {
+        float4 v = s4[k];
+        dst[4 * k] = v.x;
+        dst[4 * k + 1] = v.y;
+        dst[4 * k + 2] = v.z;
+        dst[4 * k + 3] = v.w;
+    }
+}
+
+// geometry of the M2L kernels
+struct M2LGeom {
+    const double *Zx, *Zy, *Zz;  // binary64 centres
+    const float4 *zh, *zl;       // double-float centres (scaled modes)
+    const int* nk;               // per-node moment unit exponent (scaled modes)
+};
+
 // a8 M2L, standard, one work item = up to M2L_CHUNK directed entries of one target cell
 // (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src),
-// in the pair-kernel type T; centres are stored as S = Prec<T>::S and R is formed in S.
-// The item's partial local goes to part[item]; m2l_reduce_k sums a cell's items in order.
+// in the pair-kernel type T.  The item's partial local goes to part[item] (and its unit
+// exponent to kpart[item] in the scaled modes); m2l_reduce_k sums a cell's items in order.
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __restrict__ items,
-                                                const uint64_t* __restrict__ dir, int bits,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz,
-                                                const T* __restrict__ mom, T* __restrict__ part) {
+                                                const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                                const T* __restrict__ mom, T* __restrict__ part,
+                                                int* __restrict__ kpart) {
     using E = Exp<P>;
+    constexpr bool SC = !std::is_same<T, double>::value;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
     T L[E::NM];
 #pragma unroll
     for (int k = 0; k < E::NM; k++) L[k] = T(0);
-    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
+    int kI = 0;
+    if constexpr (SC) {
+        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kpart[it] = kI;
+    }
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        // R = Z_tgt - Z_src in binary64, then narrowed to the kernel type
-        T rx = to_kernel(zx - Zx[src], T()), ry = to_kernel(zy - Zy[src], T()), rz = to_kernel(zz - Zz[src], T());
+        T rx, ry, rz;
+        SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
         T D[E::NM];
-        E::dtensor(rx, ry, rz, D);
-        E::m2l_std(mom + (int64_t)src * E::NM, D, L);
+        if constexpr (SC) {
+            T ux, uy, uz;
+            float v;
+            entry_units(rx, ry, rz, kI, ux, uy, uz, v);
+            E::dtensor(rx, ry, rz, D);
+            float vp[P + 2];
+            pow_table<P + 2>(v, vp);
+#pragma unroll
+            for (int k = 0; k < E::NM; k++) D[k] = scale_t(D[k], vp[mi_deg(k) + 1]);
+            float f[P + 1];
+            moment_factors<P + 1>(g.nk[src] - kI, f);
+            if constexpr (sizeof(T) == 4) {
+                T Ms[E::NMP];
+                load_f4<E::NMP>(mom + (int64_t)src * E::NMP, Ms);
+                E::m2l_std_s(Ms, f, D, L);
+            } else {
+                E::m2l_std_s(mom + (int64_t)src * E::NMP, f, D, L);
+            }
+        } else {
+            E::dtensor(rx, ry, rz, D);
+            E::m2l_std(mom + (int64_t)src * E::NM, D, L);
+        }
     }
 #pragma unroll
     for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = Prec<T>::fin(L[k]);
 }
 
-// a8' M2L, conserving: S and U of the realigned pair forces, from conserving moments
+// a8' M2L, conserving: S and U of the realigned pair forces; binary64 reads the conserving
+// moments of con_moments_k, the scaled modes read the raw moments (padded, range-scaled)
+// and form the conserving ones on load
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __restrict__ items,
-                                                const uint64_t* __restrict__ dir, int bits,
-                                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                                const double* __restrict__ Zz,
-                                                const T* __restrict__ cmom, T* __restrict__ part) {
+                                                const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                                const T* __restrict__ cmom, T* __restrict__ part,
+                                                int* __restrict__ kpart) {
     using E = Exp<P>;
+    constexpr bool SC = !std::is_same<T, double>::value;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
     T SU[E::NSU];
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) SU[k] = T(0);
-    double zx = Zx[w.x], zy = Zy[w.x], zz = Zz[w.x];
     uint64_t mask = (1ull << bits) - 1ull;
+    int kI = 0;
+    if constexpr (SC) {
+        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kpart[it] = kI;
+    }
     for (int e = w.y; e < w.z; e++) {
         int src = (int)(dir[e] & mask);
-        // R = Z_tgt - Z_src in binary64, then narrowed to the kernel type
-        T rx = to_kernel(zx - Zx[src], T()), ry = to_kernel(zy - Zy[src], T()), rz = to_kernel(zz - Zz[src], T());
+        T rx, ry, rz;
+        SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
         T H[E::NQ];
-        E::htensor(rx, ry, rz, H);
-        if constexpr (sizeof(T) == 4) {
-            // binary32: the source block (4 nmi(p-1) floats, a multiple of 4) in 16-byte loads
-            T Cs[E::NSU];
-            const float4* src4 = reinterpret_cast<const float4*>(cmom + (int64_t)src * E::NSU);
+        if constexpr (SC) {
+            T ux, uy, uz;
+            float v;
+            entry_units(rx, ry, rz, kI, ux, uy, uz, v);
+            E::htensor(rx, ry, rz, H);
+            float vp[P + 3];
+            pow_table<P + 3>(v, vp);
 #pragma unroll
-            for (int k = 0; k < E::NSU / 4; k++) {
-                float4 v = src4[k];
-                Cs[4 * k] = v.x;
-                Cs[4 * k + 1] = v.y;
-                Cs[4 * k + 2] = v.z;
-                Cs[4 * k + 3] = v.w;
-            }
-            E::m2l_con(Cs, H, rx, ry, rz, SU);
+            for (int k = 0; k < E::NQ; k++) H[k] = scale_t(H[k], vp[mi_deg(k) + 3]);
+            rx = ux;
+            ry = uy;
+            rz = uz;
+        } else {
+            E::htensor(rx, ry, rz, H);
+        }
+        if constexpr (sizeof(T) == 4) {
+            // binary32: the raw moments (padded to a multiple of 4 floats) in 16-byte loads;
+            // the conserving moments are formed from them on load
+            T Ms[E::NMP];
+            load_f4<E::NMP>(cmom + (int64_t)src * E::NMP, Ms);
+            float f[P + 1];
+            moment_factors<P + 1>(g.nk[src] - kI, f);
+            E::m2l_con_m(Ms, f, H, rx, ry, rz, SU);
+        } else if constexpr (SC) {
+            float f[P + 1];
+            moment_factors<P + 1>(g.nk[src] - kI, f);
+            E::m2l_con_m(cmom + (int64_t)src * E::NMP, f, H, rx, ry, rz, SU);
         } else {
             E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
         }
@@ -113,29 +313,142 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::fin(SU[k]);
 }
 
+// a8'' M2L, literal order-0 realigned form (eq. aaB0), run at expansion order 2: from the
+// raw moments of the source (M = M_0, Qbar_ii = 2 M_{2e_i}, Qbar_ij = M_{e_i+e_j}) the
+// degree-1 conserving locals of
+//   a(x) = -(M/R^2) [n + x/R - (n.x) n/R - (n.x) x/R^2] + Qbar n / R^4 = x S(x) + U(x):
+//   S_0 = -M/R^3, S_{e_j} = M n_j/R^4, U_{i,0} = -M n_i/R^2 + (Qbar n)_i/R^4,
+//   U_{i,e_j} = M n_i n_j/R^3.
+// Moment order (10 entries): 1 | x y z | xx xy xz yy yz zz; locals [S | Ux | Uy | Uz], 4 each.
+template <class T>
+__global__ void __launch_bounds__(EB) m2l_p0_k(int64_t nitems, const int4* __restrict__ items,
+                                               const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                               const T* __restrict__ mom, T* __restrict__ part,
+                                               int* __restrict__ kpart) {
+    constexpr bool SC = !std::is_same<T, double>::value;
+    constexpr int NM = SC ? 12 : 10, NQ = 4, NSU = 16;  // moment stride: padded in the scaled modes
+    int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
+    T SU[NSU];
+#pragma unroll
+    for (int k = 0; k < NSU; k++) SU[k] = T(0);
+    uint64_t mask = (1ull << bits) - 1ull;
+    int kI = 0;
+    if constexpr (SC) {
+        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kpart[it] = kI;
+    }
+    for (int e = w.y; e < w.z; e++) {
+        int src = (int)(dir[e] & mask);
+        T r[3];
+        SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, r[0], r[1], r[2]);
+        // scaled modes: the terms are formed in entry units (|R'| ~ 1) and moved to item
+        // units by v^(length power): S_0 ~ R^-3, S_ej ~ R^-4, U_i0 ~ R^-2, U_iej ~ R^-3
+        float w2 = 1.f, w3 = 1.f, w4 = 1.f, f2 = 1.f;
+        if constexpr (SC) {
+            T ux, uy, uz;
+            float v;
+            int ke = entry_units(r[0], r[1], r[2], kI, ux, uy, uz, v);
+            w2 = v * v;
+            w3 = w2 * v;
+            w4 = w2 * w2;
+            float f[3];
+            moment_factors<3>(g.nk[src] - ke, f);  // Qbar in entry units
+            f2 = f[2];
+        }
+        T ir = rsqrt_t(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        T n[3] = {r[0] * ir, r[1] * ir, r[2] * ir};
+        const T* Ms = mom + (int64_t)src * NM;
+        T M = Ms[0];
+        T q[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) q[k] = scale_t(Ms[4 + k], f2);
+        T two = T(2);
+        T Q[3][3] = {{two * q[0], q[1], q[2]}, {q[1], two * q[3], q[4]}, {q[2], q[4], two * q[5]}};
+        T ir2 = ir * ir;
+        T mi3 = M * (ir2 * ir), mi4 = M * (ir2 * ir2), ir4 = ir2 * ir2;
+        SU[0] = SU[0] - scale_t(mi3, w3);
+#pragma unroll
+        for (int j = 0; j < 3; j++) SU[1 + j] = SU[1 + j] + scale_t(mi4 * n[j], w4);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            T Qn = Q[i][0] * n[0] + Q[i][1] * n[1] + Q[i][2] * n[2];
+            SU[NQ * (i + 1)] = SU[NQ * (i + 1)] + scale_t(Qn * ir4 - (M * ir2) * n[i], w2);
+            T mn = mi3 * n[i];
+#pragma unroll
+            for (int j = 0; j < 3; j++) SU[NQ * (i + 1) + 1 + j] = SU[NQ * (i + 1) + 1 + j] + scale_t(mn * n[j], w3);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NSU; k++) part[it * NSU + k] = Prec<T>::fin(SU[k]);
+}
+
 // a9: loc[x][k] = sum over the cell's items (full chunks in order, then the partial one),
-// accumulated in binary64
+// accumulated in binary64; in the scaled modes each item's unit 2^k_I is removed exactly
+// (coefficient k carries 2^(k_I d(k)), d from out_deg)
 __device__ __forceinline__ double as_double(double v) { return v; }
 __device__ __forceinline__ double as_double(float v) { return (double)v; }
 __device__ __forceinline__ double as_double(df64 v) { return to_double(v); }
 
-template <int NL, class T>
+// power of the length unit carried by local coefficient k: standard L_gamma ~ length^-(|gamma|+1);
+// conserving S_gamma ~ length^-(|gamma|+3), U_gamma ~ length^-(|gamma|+2)
+template <int KIND, int NQ>
+__device__ __forceinline__ int out_deg(int k) {
+    if (KIND == 0) return mi_deg(k) + 1;
+    return k < NQ ? mi_deg(k) + 3 : mi_deg(k % NQ) + 2;
+}
+
+template <int NL, int NQ, int KIND, class T>
 __global__ void m2l_reduce_k(int nn, const long long* __restrict__ fo, const long long* __restrict__ po,
-                             long long nfull, const T* __restrict__ part, double* __restrict__ loc) {
+                             long long nfull, const T* __restrict__ part, const int* __restrict__ kpart,
+                             double* __restrict__ loc) {
+    constexpr bool SC = !std::is_same<T, double>::value;
     int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (t >= (int64_t)nn * NL) return;
     int x = (int)(t / NL), k = (int)(t - (int64_t)x * NL);
+    int d = SC ? out_deg<KIND, NQ>(k) : 0;
     double acc = 0.0;
-    for (long long i = fo[x]; i < fo[x + 1]; i++) acc += as_double(part[i * NL + k]);
-    if (po[x + 1] > po[x]) acc += as_double(part[(nfull + po[x]) * NL + k]);
+    for (long long i = fo[x]; i < fo[x + 1]; i++) {
+        double v = as_double(part[i * NL + k]);
+        acc += SC ? v * pow2d(-kpart[i] * d) : v;
+    }
+    if (po[x + 1] > po[x]) {
+        long long i = nfull + po[x];
+        double v = as_double(part[i * NL + k]);
+        acc += SC ? v * pow2d(-kpart[i] * d) : v;
+    }
     loc[t] = acc;
 }
 
-// binary64 arrays converted to the pair-kernel / storage types
-template <class T>
-__global__ void convert_k(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
-    int64_t i = (int64_t)blockIdx.x * EB + threadIdx.x;
-    if (i < n) out[i] = to_kernel(in[i], T());
+// moments of every node in the pair-kernel type, in units of 2^k_n (k_n = floor(log2 r_max)
+// for r_max > 0; a node with r_max = 0 has all particles at its centre, so its moments
+// beyond the mass vanish and any unit serves), padded to NMP per node, plus the
+// double-float centres: one thread per (node, padded coefficient)
+template <int P, class T>
+__global__ void scale_moments_k(int nn, const double* __restrict__ mom, const double* __restrict__ rmax,
+                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                const double* __restrict__ Zz, T* __restrict__ momT, int* __restrict__ nk,
+                                float4* __restrict__ zh, float4* __restrict__ zl) {
+    using E = Exp<P>;
+    int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (t >= (int64_t)nn * E::NMP) return;
+    int n = (int)(t / E::NMP), k = (int)(t - (int64_t)n * E::NMP);
+    double r = rmax[n];
+    int kn = r > 0.0 ? max(-120, min(120, ilogb(r))) : 0;
+    momT[t] = k < E::NM ? to_kernel(mom[(int64_t)n * E::NM + k] * pow2d(-kn * mi_deg(k)), T()) : T(0);
+    if (k == 0) {
+        nk[n] = kn;
+        double z[3] = {Zx[n], Zy[n], Zz[n]};
+        float h[3], l[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            h[i] = (float)z[i];
+            l[i] = (float)(z[i] - (double)h[i]);
+        }
+        zh[n] = make_float4(h[0], h[1], h[2], 0.f);
+        zl[n] = make_float4(l[0], l[1], l[2], 0.f);
+    }
 }
 
 // conserving source moments of every cell (formed once per moment build)
@@ -325,25 +638,31 @@ void run_moments_p(fmm_ctx* c) {
             lo, hi, c_lo, c->nchildf.as<int>(), c->nnchild.as<int>(), c->m2m_tmp.as<double>(), c->mom.as<double>());
         GB_LAUNCH("m2m_sum_k");
     }
-    ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
-    con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
-    GB_LAUNCH("con_moments_k");
-    // moments in the pair-kernel type
-    if (c->precision != FMM_FP64) {
-        int64_t nm = (int64_t)nn * E::NM, nc = (int64_t)nn * E::NSU;
-        if (c->precision == FMM_DF64) {
-            ensure(c->momT, sizeof(df64) * (size_t)nm);
-            ensure(c->cmomT, sizeof(df64) * (size_t)nc);
-            convert_k<df64><<<grid_for(nm, EB), EB, 0, s>>>(nm, c->mom.as<double>(), c->momT.as<df64>());
-            convert_k<df64><<<grid_for(nc, EB), EB, 0, s>>>(nc, c->cmom.as<double>(), c->cmomT.as<df64>());
-        } else {
-            ensure(c->momT, sizeof(float) * (size_t)nm);
-            ensure(c->cmomT, sizeof(float) * (size_t)nc);
-            convert_k<float><<<grid_for(nm, EB), EB, 0, s>>>(nm, c->mom.as<double>(), c->momT.as<float>());
-            convert_k<float><<<grid_for(nc, EB), EB, 0, s>>>(nc, c->cmom.as<double>(), c->cmomT.as<float>());
-        }
-        GB_LAUNCH("convert_k");
+    if (c->precision == FMM_FP64) {
+        ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
+        con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
+        GB_LAUNCH("con_moments_k");
+        return;
     }
+    // the scaled modes: raw moments in the pair-kernel type, range-scaled and padded, and
+    // the double-float centres
+    int64_t nmp = (int64_t)nn * E::NMP;
+    ensure(c->nk, sizeof(int) * (size_t)nn);
+    ensure(c->zhl, sizeof(float4) * 2 * (size_t)nn);
+    float4* zh = c->zhl.as<float4>();
+    auto launch = [&](auto* mT) {
+        scale_moments_k<P><<<grid_for(nmp, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->nrmax.as<double>(),
+                                                            c->nZx.as<double>(), c->nZy.as<double>(),
+                                                            c->nZz.as<double>(), mT, c->nk.as<int>(), zh, zh + nn);
+    };
+    if (c->precision == FMM_DF64) {
+        ensure(c->momT, sizeof(df64) * (size_t)nmp);
+        launch(c->momT.as<df64>());
+    } else {
+        ensure(c->momT, sizeof(float) * (size_t)nmp);
+        launch(c->momT.as<float>());
+    }
+    GB_LAUNCH("scale_moments_k");
 }
 
 template <int P, class T>
@@ -356,33 +675,53 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     int64_t ni = it.n_items;
     bool native = c->precision == FMM_FP64;
     const T* mom = native ? c->mom.as<T>() : c->momT.as<T>();
-    const T* cmom = native ? c->cmom.as<T>() : c->cmomT.as<T>();
-    const double *zx = c->nZx.as<double>(), *zy = c->nZy.as<double>(), *zz = c->nZz.as<double>();
+    const T* cmom = native ? c->cmom.as<T>() : c->momT.as<T>();  // scaled modes: raw moments
+    M2LGeom g{c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), nullptr, nullptr, nullptr};
+    if (!native) {
+        g.zh = c->zhl.as<float4>();
+        g.zl = g.zh + nn;
+        g.nk = c->nk.as<int>();
+    }
     int nl_max = E::NSU > E::NM ? E::NSU : E::NM;
     ensure(c->m2l_part, sizeof(T) * (size_t)(ni > 0 ? ni : 1) * nl_max);
+    ensure(c->m2l_kpart, sizeof(int) * (size_t)(ni > 0 ? ni : 1));
     T* part = c->m2l_part.as<T>();
+    int* kpart = c->m2l_kpart.as<int>();
+    auto reduce = [&](auto kern, int NL, double* out) {
+        kern<<<grid_for((int64_t)nn * NL, EB), EB, 0, s>>>(nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full,
+                                                          part, kpart, out);
+        GB_LAUNCH("m2l_reduce_k");
+    };
+    if (variant == 2) {
+        // the literal order-0 realigned form runs at expansion order 2 only
+        if constexpr (P == 2) {
+            ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
+            if (ni > 0) {
+                m2l_p0_k<T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, mom, part,
+                                                            kpart);
+                GB_LAUNCH("m2l_p0_k");
+            }
+            reduce(m2l_reduce_k<E::NSU, E::NQ, 1, T>, E::NSU, c->loc.as<double>());
+        }
+    }
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
-            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zx, zy, zz, cmom,
-                                                            part);
+            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, cmom, part,
+                                                            kpart);
             GB_LAUNCH("m2l_con_k");
         }
-        m2l_reduce_k<E::NSU, T><<<grid_for((int64_t)nn * E::NSU, EB), EB, 0, s>>>(
-            nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, c->loc.as<double>());
-        GB_LAUNCH("m2l_reduce_k");
+        reduce(m2l_reduce_k<E::NSU, E::NQ, 1, T>, E::NSU, c->loc.as<double>());
     }
     if (std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
         if (ni > 0) {
-            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, zx, zy, zz, mom,
-                                                            part);
+            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, mom, part,
+                                                            kpart);
             GB_LAUNCH("m2l_std_k");
         }
-        m2l_reduce_k<E::NM, T><<<grid_for((int64_t)nn * E::NM, EB), EB, 0, s>>>(
-            nn, it.fo.as<long long>(), it.po.as<long long>(), it.n_full, part, L.as<double>());
-        GB_LAUNCH("m2l_reduce_k");
+        reduce(m2l_reduce_k<E::NM, E::NQ, 0, T>, E::NM, L.as<double>());
     }
 }
 
@@ -401,7 +740,7 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     stage_begin(c, ST_L2L);
     for (int l = 1; l < c->n_levels; l++) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
-        if (variant == 1) {
+        if (variant != 0) {
             l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
                                                               c->nZy.as<double>(), c->nZz.as<double>(),
                                                               c->loc.as<double>());
@@ -423,7 +762,7 @@ static void finish_launch(fmm_ctx* c, int variant, bool want_pot, double* acc_ou
     cudaStream_t s = c->stream;
     int n = (int)c->N;
     const ItemSet& it = c->p2p_items;
-    const double* locp = (variant == 1 && want_pot) ? c->locp.as<double>() : nullptr;
+    const double* locp = (variant != 0 && want_pot) ? c->locp.as<double>() : nullptr;
     auto args = [&](auto kern) {
         kern<<<grid_for(n, EB), EB, 0, s>>>(
             n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),

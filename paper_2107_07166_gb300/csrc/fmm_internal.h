@@ -128,7 +128,10 @@ struct fmm_ctx {
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     gbfmm::DevBuf p2p_sep;                     // centre separation of every P2P pair, storage type
     bool pos_valid = false;
-    gbfmm::DevBuf momT, cmomT;                 // moments in the pair-kernel type
+    gbfmm::DevBuf momT;                        // raw moments in the pair-kernel type (range-scaled, padded)
+    gbfmm::DevBuf nk;                          // per-node moment unit exponent (scaled modes)
+    gbfmm::DevBuf zhl;                         // double-float node centres: float4 hi[n] | lo[n]
+    gbfmm::DevBuf m2l_kpart;                   // per-item unit exponent of the M2L partials
     int id_bits = 0;
     // results (sorted order) and output staging
     gbfmm::DevBuf acc_s, pot_s;                // SoA: ax | ay | az

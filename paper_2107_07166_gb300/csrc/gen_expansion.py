@@ -160,6 +160,21 @@ def m2l_std(p):
     return L
 
 
+def m2l_std_s(p):
+    """m2l_std with the source moments rescaled on load: M_beta * f[|beta|]."""
+    L = ["  /* as m2l_std, with every moment multiplied on load by f[|beta|] (a power of two) */",
+         "  template <class T, class A> __device__ __forceinline__ static void m2l_std_s(const T* __restrict__ M, const float* __restrict__ f, const T* __restrict__ D, A* __restrict__ Lc) {"]
+    for b in mis(p):
+        rem = p - sum(b)
+        L.append(f"    {{ const T mb = scale_t(M[{idx(b)}], f[{sum(b)}]);")
+        for g in mis(rem):
+            s = (b[0] + g[0], b[1] + g[1], b[2] + g[2])
+            L.append(f"      Lc[{idx(g)}] = fma_t(mb, D[{idx(s)}], Lc[{idx(g)}]);")
+        L.append("    }")
+    L.append("  }")
+    return L
+
+
 def con_moments(p):
     q = p - 1
     nq = nmi(q)
@@ -187,6 +202,62 @@ def m2l_con(p):
         rem = q - sum(b)
         L.append(f"    {{ const T m = C[{bi}];")
         L.append(f"      const T mx = fma_t(rx, m, C[{nq + bi}]), my = fma_t(ry, m, C[{2 * nq + bi}]), mz = fma_t(rz, m, C[{3 * nq + bi}]);")
+        for g in mis(rem):
+            gi = idx(g)
+            hb = f"H[{idx((b[0] + g[0], b[1] + g[1], b[2] + g[2]))}]"
+            L.append(f"      SU[{gi}] = fma_t(m, {hb}, SU[{gi}]); SU[{nq + gi}] = fma_t(mx, {hb}, SU[{nq + gi}]);"
+                     f" SU[{2 * nq + gi}] = fma_t(my, {hb}, SU[{2 * nq + gi}]); SU[{3 * nq + gi}] = fma_t(mz, {hb}, SU[{3 * nq + gi}]);")
+        L.append("    }")
+    L.append("  }")
+    return L
+
+
+def m2l_con_s(p):
+    """m2l_con with the conserving moments rescaled on load: the M_b block by f[|b|], the
+    (b_i + 1) M_{b+e_i} blocks by f[|b| + 1]."""
+    q = p - 1
+    nq = nmi(q)
+    L = ["  /* as m2l_con, with C_b multiplied on load by f[|b|] and C_{i,b} by f[|b|+1] (powers of two) */",
+         "  template <class T, class A> __device__ __forceinline__ static void m2l_con_s(const T* __restrict__ C, const float* __restrict__ f, const T* __restrict__ H, T rx, T ry, T rz, A* __restrict__ SU) {"]
+    for b in mis(q):
+        bi = idx(b)
+        rem = q - sum(b)
+        nb, nb1 = sum(b), sum(b) + 1
+        L.append(f"    {{ const T m = scale_t(C[{bi}], f[{nb}]);")
+        L.append(f"      const T mx = fma_t(rx, m, scale_t(C[{nq + bi}], f[{nb1}])), my = fma_t(ry, m, scale_t(C[{2 * nq + bi}], f[{nb1}])),"
+                 f" mz = fma_t(rz, m, scale_t(C[{3 * nq + bi}], f[{nb1}]));")
+        for g in mis(rem):
+            gi = idx(g)
+            hb = f"H[{idx((b[0] + g[0], b[1] + g[1], b[2] + g[2]))}]"
+            L.append(f"      SU[{gi}] = fma_t(m, {hb}, SU[{gi}]); SU[{nq + gi}] = fma_t(mx, {hb}, SU[{nq + gi}]);"
+                     f" SU[{2 * nq + gi}] = fma_t(my, {hb}, SU[{2 * nq + gi}]); SU[{3 * nq + gi}] = fma_t(mz, {hb}, SU[{3 * nq + gi}]);")
+        L.append("    }")
+    L.append("  }")
+    return L
+
+
+def m2l_con_m(p):
+    """Conserving M2L that forms the conserving moments from the raw moments on load:
+    C_b = M_b f[|b|], C_{i,b} = (b_i + 1) M_{b+e_i} f[|b|+1] (f powers of two).  Reads nmi(p)
+    values per source instead of 4 nmi(p-1)."""
+    q = p - 1
+    nq = nmi(q)
+    L = ["  /* as m2l_con, reading the raw moments M (|a| <= p): C_b = M_b f[|b|] and",
+         "     C_{i,b} = (b_i+1) M_{b+e_i} f[|b|+1] are formed on load */",
+         "  template <class T, class A> __device__ __forceinline__ static void m2l_con_m(const T* __restrict__ M, const float* __restrict__ f, const T* __restrict__ H, T rx, T ry, T rz, A* __restrict__ SU) {"]
+    def w(b, d):
+        e = list(b)
+        e[d] += 1
+        c = b[d] + 1
+        n = sum(b) + 1
+        if c == 1:
+            return f"scale_t(M[{idx(tuple(e))}], f[{n}])"
+        return f"scale_c_t(M[{idx(tuple(e))}], f[{n}], {c}.f)"
+    for b in mis(q):
+        bi = idx(b)
+        rem = q - sum(b)
+        L.append(f"    {{ const T m = scale_t(M[{bi}], f[{sum(b)}]);")
+        L.append(f"      const T mx = fma_t(rx, m, {w(b, 0)}), my = fma_t(ry, m, {w(b, 1)}), mz = fma_t(rz, m, {w(b, 2)});")
         for g in mis(rem):
             gi = idx(g)
             hb = f"H[{idx((b[0] + g[0], b[1] + g[1], b[2] + g[2]))}]"
@@ -296,13 +367,17 @@ def header(p):
            f"template <> struct Exp<{p}> {{",
            f"  static constexpr int P = {p};",
            f"  static constexpr int NM = {nmi(p)};   // moments / standard locals",
+           f"  static constexpr int NMP = {(nmi(p) + 3) // 4 * 4};   // moments padded to 16 bytes (binary32 storage)",
            f"  static constexpr int NQ = {nmi(q)};   // conserving scalar local S (|gamma| <= p-1)",
            f"  static constexpr int NSU = {4 * nmi(q)};  // conserving locals S, Ux, Uy, Uz"]
     out += radial_tensor(p, "d")
     out += radial_tensor(q, "h")
     out += m2l_std(p)
+    out += m2l_std_s(p)
     out += con_moments(p)
     out += m2l_con(p)
+    out += m2l_con_s(p)
+    out += m2l_con_m(p)
     out += p2m(p)
     out += m2m(p)
     out += l2l_poly(p, "l2l")

@@ -40,9 +40,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                                             const int* __restrict__ ncount,
                                             const PState<typename Prec<T>::S>* __restrict__ pos,
                                             const typename Prec<T>::S* __restrict__ sep,
-                                            Quad<typename Prec<T>::G>* __restrict__ part) {
+                                            Quad<T>* __restrict__ part) {
     using S = typename Prec<T>::S;
-    using G = typename Prec<T>::G;
     constexpr int PCOL = Panel<T>::COLS, PROW = Panel<T>::ROW, PANEL = Panel<T>::SIZE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PState<S> sA[PW][32], sB[PW][32];
@@ -81,8 +80,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     if (!self || a < b) {
                         const PState<S>& pa = sA[w][a];
                         const PState<S>& pb = sB[w][b];
-                        T dx = Prec<T>::narrow(pa.x - pb.x), dy = Prec<T>::narrow(pa.y - pb.y);
-                        T dz = Prec<T>::narrow(pa.z - pb.z);
+                        T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y);
+                        T dz = Prec<T>::sep(pa.z, pb.z);
                         T r2 = dx * dx + dy * dy + dz * dz;
                         if (!is_zero(r2)) {
                             T ir = rsqrt_t(r2);
@@ -125,14 +124,14 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 __syncwarp();
             }
             // write: rows are a_a = -sum (and phi_a = -sum); columns a_b = +sum, phi_b = -sum
-            G* pd = reinterpret_cast<G*>(part);
+            T* pd = reinterpret_cast<T*>(part);
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
                 if (a < nA) {
                     T v = -racc[q];
                     if (self) v = v + ((c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c]);
-                    pd[(o + a) * 4 + c] = (POT || c < 3) ? Prec<T>::to_g(v) : G(0);
+                    pd[(o + a) * 4 + c] = (POT || c < 3) ? Prec<T>::fin(v) : T(0);
                 }
             }
             if (!self) {
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     int tau = lane + 32 * q, b = tau >> 2, c = tau & 3;
                     if (b < nB) {
                         T v = cac[b * 4 + c];
-                        pd[(o + nA + b) * 4 + c] = (c < 3) ? Prec<T>::to_g(v) : (POT ? Prec<T>::to_g(-v) : G(0));
+                        pd[(o + nA + b) * 4 + c] = (c < 3) ? Prec<T>::fin(v) : (POT ? Prec<T>::fin(-v) : T(0));
                     }
                 }
             }
@@ -159,8 +158,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     for (int u = 0; u < nS; u++) {
                         if (self && u == t) continue;
                         PState<S> ps = pos[fS + u];
-                        T dx = Prec<T>::narrow(pt.x - ps.x), dy = Prec<T>::narrow(pt.y - ps.y);
-                        T dz = Prec<T>::narrow(pt.z - ps.z);
+                        T dx = Prec<T>::sep(pt.x, ps.x), dy = Prec<T>::sep(pt.y, ps.y);
+                        T dz = Prec<T>::sep(pt.z, ps.z);
                         T r2 = dx * dx + dy * dy + dz * dz;
                         if (!is_zero(r2)) {
                             T ir = rsqrt_t(r2);
@@ -171,8 +170,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                             ph = fma_t(-Prec<T>::mass(ps.m), ir, ph);
                         }
                     }
-                    part[oT + t] = Quad<G>{Prec<T>::to_g(ax), Prec<T>::to_g(ay), Prec<T>::to_g(az),
-                                           POT ? Prec<T>::to_g(ph) : G(0)};
+                    part[oT + t] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
+                                           POT ? Prec<T>::fin(ph) : T(0)};
                 }
             }
         }
@@ -212,7 +211,6 @@ __global__ void pack_pos_k(int n, const int* __restrict__ leaf_of, const double*
 template <class T>
 static void p2p_launch(fmm_ctx* c, bool want_pot) {
     using S = typename Prec<T>::S;
-    using G = typename Prec<T>::G;
     cudaStream_t s = c->stream;
     int n = (int)c->N;
     if (!c->pos_valid) {
@@ -227,7 +225,7 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
                             cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    ensure(c->p2p_part, sizeof(Quad<G>) * (size_t)(total > 0 ? total : 1));
+    ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int64_t blocks = (c->n_p2p + PW - 1) / PW;
@@ -244,7 +242,7 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     stage_begin(c, ST_P2P);
     kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
                                            c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
-                                           c->p2p_sep.as<S>(), c->p2p_part.as<Quad<G>>());
+                                           c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
     GB_LAUNCH("p2p_k");
     stage_end(c, ST_P2P);
 }
@@ -263,11 +261,15 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
 // item's entries (increasing partner id) into ipart[islot[item] + slot].
 //   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
 //   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
-template <class G>
+__device__ __forceinline__ double to_acc(double v, double) { return v; }
+__device__ __forceinline__ df64 to_acc(df64 v, df64) { return v; }
+__device__ __forceinline__ df64 to_acc(float v, df64) { return df64(v, 0.f); }
+
+template <class G, class PT>
 __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
                                                    const int* __restrict__ ncount, const uint32_t* __restrict__ pdval,
                                                    const int2* __restrict__ pairs, const long long* __restrict__ poff,
-                                                   const Quad<G>* __restrict__ part,
+                                                   const Quad<PT>* __restrict__ part,
                                                    const long long* __restrict__ islot, Quad<G>* __restrict__ ipart) {
     int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -280,11 +282,11 @@ __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* _
             uint32_t v = pdval[e];
             uint32_t k = v >> 1;
             long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
-            Quad<G> q = part[o];
-            acc.x = acc.x + q.x;
-            acc.y = acc.y + q.y;
-            acc.z = acc.z + q.z;
-            acc.w = acc.w + q.w;
+            Quad<PT> q = part[o];
+            acc.x = acc.x + to_acc(q.x, G());
+            acc.y = acc.y + to_acc(q.y, G());
+            acc.z = acc.z + to_acc(q.z, G());
+            acc.w = acc.w + to_acc(q.w, G());
         }
         ipart[islot[it] + slot] = acc;
     }
@@ -297,7 +299,7 @@ __global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, con
     if (i < nitems) sizes[i] = ncount[items[i].x];
 }
 
-template <class G>
+template <class G, class PT>
 static void gather_launch(fmm_ctx* c) {
     cudaStream_t s = c->stream;
     const ItemSet& it = c->p2p_items;
@@ -311,18 +313,20 @@ static void gather_launch(fmm_ctx* c) {
     GB_CUDA(cudaMemcpyAsync(&nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     ensure(c->p2p_ipart, sizeof(Quad<G>) * (size_t)(nslots > 0 ? nslots : 1));
-    p2p_gather_k<G><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
-                                                          c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
-                                                          c->p2p_off.as<long long>(), c->p2p_part.as<Quad<G>>(),
-                                                          c->p2p_islot.as<long long>(), c->p2p_ipart.as<Quad<G>>());
+    p2p_gather_k<G, PT><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
+                                                              c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
+                                                              c->p2p_off.as<long long>(), c->p2p_part.as<Quad<PT>>(),
+                                                              c->p2p_islot.as<long long>(), c->p2p_ipart.as<Quad<G>>());
     GB_LAUNCH("p2p_gather_k");
 }
 
 void run_p2p_gather(fmm_ctx* c) {
     if (c->precision == FMM_FP64)
-        gather_launch<double>(c);
+        gather_launch<double, double>(c);
+    else if (c->precision == FMM_DF64)
+        gather_launch<df64, df64>(c);
     else
-        gather_launch<df64>(c);
+        gather_launch<df64, float>(c);
 }
 
 // ------------------------------------------------------------------ diagnostics

@@ -6,11 +6,12 @@
 //                (FMM_MIXED)
 //
 // Positions and cell centres are stored as binary64 in FMM_FP64 and as double-float
-// otherwise ("storage type" S).  Differences X_a - X_b and Z_A - Z_B are formed in S and
-// only then narrowed to T, so binary32 pair kernels still see separations accurate to
-// their own rounding.  Per-pair and per-chunk partial sums are kept in G (binary64 for
-// binary64, double-float otherwise, so that no binary64 conversion sits in the binary32
-// pair kernels) and reduced in a fixed order; the per-particle totals are binary64.
+// otherwise ("storage type" S).  Differences X_a - X_b are formed from the S operands to
+// the accuracy of T (sep), so binary32 pair kernels still see separations accurate to
+// their own rounding.  The pair kernel's per-(leaf pair, particle) partials are stored in
+// T; the per-item sums over them are kept in G (binary64 for binary64, double-float
+// otherwise, so that no binary64 conversion sits in the binary32 kernels) and reduced in a
+// fixed order; the per-particle totals are binary64.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -25,37 +26,31 @@ struct Prec;
 template <>
 struct Prec<double> {
     using S = double;  // storage of positions, masses and centres
-    using G = double;  // partial sums
+    using G = double;  // item-level partial sums
+    __device__ static double sep(double a, double b) { return a - b; }
     __device__ static double fin(double v) { return v; }
-    __device__ static double narrow(double v) { return v; }
     __device__ static double mass(double m) { return m; }
-    __device__ static double to_g(double v) { return v; }
-    __device__ static double g_to_double(double v) { return v; }
-    __device__ static double g_add(double a, double b) { return a + b; }
 };
 
 template <>
 struct Prec<df64> {
     using S = df64;
     using G = df64;
+    __device__ static df64 sep(df64 a, df64 b) { return a - b; }
     __device__ static df64 fin(df64 v) { return norm(v); }
-    __device__ static df64 narrow(df64 v) { return v; }
     __device__ static df64 mass(df64 m) { return m; }
-    __device__ static df64 to_g(df64 v) { return norm(v); }
-    __device__ static double g_to_double(df64 v) { return to_double(v); }
-    __device__ static df64 g_add(df64 a, df64 b) { return a + b; }
 };
 
 template <>
 struct Prec<float> {
     using S = df64;
-    using G = df64;  // per-pair partials kept as double-float: no binary64 converts in the pair kernel
+    using G = df64;  // item-level sums of the binary32 pair partials kept as double-float
+    // a - b rounded to binary32 from double-float operands: (a.hi - b.hi) + (a.lo - b.lo).
+    // When a and b are close the high-word difference is exact (Sterbenz); otherwise its
+    // rounding is within binary32's own 2^-24 of the result.
+    __device__ static float sep(df64 a, df64 b) { return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)); }
     __device__ static float fin(float v) { return v; }
-    __device__ static float narrow(df64 v) { return __fadd_rn(v.hi, v.lo); }
-    __device__ static float mass(df64 m) { return __fadd_rn(m.hi, m.lo); }
-    __device__ static df64 to_g(float v) { return df64(v, 0.f); }
-    __device__ static double g_to_double(df64 v) { return to_double(v); }
-    __device__ static df64 g_add(df64 a, df64 b) { return a + b; }
+    __device__ static float mass(df64 m) { return m.hi; }  // hi is m rounded to binary32
 };
 
 __device__ __forceinline__ double to_storage(double v, double) { return v; }

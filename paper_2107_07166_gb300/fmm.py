@@ -22,7 +22,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbfmm.so")
 
-STANDARD, CONSERVING = 0, 1
+STANDARD, CONSERVING, CONSERVING_PAPER0 = 0, 1, 2
 FP64, MIXED, DF64 = 0, 1, 2
 P_MAX = 6
 DF64_P_MAX = 5

@@ -70,9 +70,12 @@ def hernquist(n: int, seed: int, a: float = 1.0, mass: float = 1.0, u_max: float
 
 
 def disk_bulge(n: int, seed: int, rd: float = 1.0, z0: float = 0.1, f_disk: float = 0.8,
-               a_bulge: float = 0.2):
+               a_bulge: float = 0.2, velocities: bool = False):
     """Exponential disk (surface density ~ exp(-R/rd), cut at 10 rd; vertical
-    sech^2(z/z0)) holding f_disk of the mass, plus a Hernquist bulge.  Total mass 1."""
+    sech^2(z/z0)) holding f_disk of the mass, plus a Hernquist bulge.  Total mass 1.
+    With velocities, disk particles rotate on circular orbits about z at the speed
+    sqrt(M(<r) / r) of the spherically averaged enclosed mass and bulge particles get an
+    isotropic direction at half that speed: a rotating galaxy with net angular momentum."""
     rng = _rng(seed)
     nd = int(round(f_disk * n))
     nb = n - nd
@@ -95,7 +98,20 @@ def disk_bulge(n: int, seed: int, rd: float = 1.0, z0: float = 0.1, f_disk: floa
     xb = rb[:, None] * _isotropic(rng, nb)
     x = np.concatenate([xd, xb], axis=0)
     m = np.concatenate([np.full(nd, f_disk / max(nd, 1)), np.full(nb, (1.0 - f_disk) / max(nb, 1))])
-    return _centre(x, m), m
+    x = _centre(x, m)
+    if not velocities:
+        return x, m
+    r = np.linalg.norm(x, axis=1)
+    order = np.argsort(r, kind="stable")
+    menc = np.empty(n)
+    menc[order] = np.cumsum(m[order])
+    vc = np.sqrt(menc / np.maximum(r, 1e-12))
+    v = np.zeros_like(x)
+    v[:nd, 0] = -vc[:nd] * np.sin(ph)
+    v[:nd, 1] = vc[:nd] * np.cos(ph)
+    v[nd:] = (0.5 * vc[nd:])[:, None] * _isotropic(rng, nb)
+    v -= (m[:, None] * v).sum(axis=0) / m.sum()
+    return x, m, v
 
 
 def binary(n_each: int, seed_a: int, seed_b: int, separation: float = 10.0):

@@ -449,3 +449,96 @@ def test_batch_workload_shape(fmm, torch_cuda, orc, precision):
     lim = 1e-14 if precision != 1 else 1e-6
     assert np.all(np.linalg.norm(diag[:, 3:], axis=1) < lim * tscale)
     f.close()
+
+
+# ------------------------------------------------------------- literal order-0 realigned form
+
+@pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_paper0_parity_against_oracle(fmm, torch_cuda, orc, case):
+    """FMM_CONSERVING_PAPER0 (eq. aaB0, p = 1) against the oracle in every arithmetic mode,
+    with the same trees and lists, and momentum conservation of the result."""
+    name, gen, N, leaf, _, theta = case
+    x, m = gen(N)
+    r = orc.run(x, m, leaf, 1, theta, fmm.CONSERVING_PAPER0, want_pot=True)
+    for precision in (0, 2, 1):
+        g = run_gpu(fmm, torch_cuda, x, m, leaf, 1, theta, fmm.CONSERVING_PAPER0, precision=precision)
+        check_structure(g["f"], r, N)
+        tol = TOL if precision != 1 else MODE_TOL[1]
+        assert rel(g["acc"], r.acc) < tol, (name, precision)
+        assert rel(g["pot"], r.pot) < tol, (name, precision)
+        F, T = g["f"].diagnostics()
+        a = g["acc"]
+        fs = (m * np.linalg.norm(a, axis=1)).sum()
+        ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+        lim = 1e-6 if precision == 1 else 1e-14
+        assert np.linalg.norm(F) < lim * fs and np.linalg.norm(T) < lim * ts, (name, precision)
+        g["f"].close()
+
+
+def test_paper0_needs_order_one(fmm, torch_cuda):
+    x, m = synth.plummer(1000, 14)
+    f = new_ctx(fmm, torch_cuda)
+    f.build(x, m, 16)
+    acc = np.full((1000, 3), 7.0)
+    for p in (0, 2, 4):
+        with pytest.raises(fmm.FMMError) as e:
+            f.forces(p, 0.5, fmm.CONSERVING_PAPER0, acc, None)
+        assert e.value.status == -1
+    assert np.all(acc == 7.0)
+    # after the order-2 moments of the literal form, an ordinary p = 1 run is unaffected
+    f.forces(1, 0.5, fmm.CONSERVING_PAPER0, acc, None)
+    a1 = acc.copy()
+    f.forces(1, 0.5, fmm.STANDARD, acc, None)
+    g = new_ctx(fmm, torch_cuda)
+    g.build(x, m, 16)
+    b = np.empty((1000, 3))
+    g.forces(1, 0.5, fmm.STANDARD, b, None)
+    assert np.array_equal(acc, b)
+    assert not np.array_equal(a1, b)
+    f.close()
+    g.close()
+
+
+# ------------------------------------------------------------- range of the binary32 kernels
+
+def _close_pair_set(n=3000, seed=21, gap=1e-9):
+    """A Plummer set plus two particles a distance gap apart on either side of the plane
+    between the root's children, each alone in its leaf at leaf size 1, so that their
+    cells meet in M2L at a separation where R^-(p+2) leaves the binary32 range."""
+    x, m = synth.plummer(n, seed)
+    lo = x.min(0)
+    side = (x.max(0) - lo).max()
+    b = lo[0] + 0.5 * side          # the plane between the root's children in x
+    pair = np.array([[b - 0.5 * gap, 0.1, 0.1], [b + 0.5 * gap, 0.1, 0.1]])
+    x = np.concatenate([x, pair])
+    m = np.concatenate([m, [1.0 / n, 1.0 / n]])
+    return x, m
+
+
+@pytest.mark.parametrize("precision", [2, 1], ids=["df64", "mixed"])
+def test_scaled_modes_survive_close_cells(fmm, torch_cuda, orc, precision):
+    """Cells a billionth apart in M2L: the range-scaled binary32 / double-float kernels stay
+    finite and within the mode's bound of the oracle."""
+    x, m = _close_pair_set()
+    for variant, p in ((1, 5), (0, 4)):
+        r = orc.run(x, m, 1, p, 0.6, variant, want_pot=False, want_internals=False)
+        g = run_gpu(fmm, torch_cuda, x, m, 1, p, 0.6, variant, want_pot=False, precision=precision)
+        assert np.isfinite(g["acc"]).all()
+        assert rel(g["acc"], r.acc) < MODE_TOL[precision], (variant, rel(g["acc"], r.acc))
+        # the rest of the set, away from the pair's enormous mutual force
+        assert rel(g["acc"][:-2], r.acc[:-2]) < MODE_TOL[precision], variant
+        g["f"].close()
+
+
+@pytest.mark.parametrize("precision", [0, 2, 1], ids=["fp64", "df64", "mixed"])
+def test_power_of_two_rescaling_is_exact(fmm, torch_cuda, precision):
+    """Scaling positions by 2^30 scales accelerations by 2^-60: trees, moments and the
+    range-scaled kernels see the same numbers up to the power of two."""
+    x, m = synth.hernquist(5000, 23)
+    s = 2.0 ** 30
+    for variant in (0, 1):
+        a = run_gpu(fmm, torch_cuda, x, m, 16, 4, 0.6, variant, want_pot=False, precision=precision)
+        b = run_gpu(fmm, torch_cuda, x * s, m, 16, 4, 0.6, variant, want_pot=False, precision=precision)
+        assert rel(b["acc"] * s * s, a["acc"]) < 1e-13, (variant, rel(b["acc"] * s * s, a["acc"]))
+        a["f"].close()
+        b["f"].close()
