@@ -305,6 +305,43 @@ def run_gbfmm(args):
                 "max_dL_rel": float(np.abs(Lm - Lm[0]).max() / lscale),
                 "norm": "|sum m v - initial| / sum m|v|, |sum m x x v - initial| / sum m|x||v|"}
 
+    # the other variant on the same input and tree (same timing method): the cost of
+    # realignment is the conserving time over the standard time
+    variants = {}
+    if args.modes and world == 1:
+        other = fmm.STANDARD if variant == fmm.CONSERVING else fmm.CONSERVING
+        out = torch.empty_like(acc)
+
+        def sv():
+            if offsets is not None:
+                f.build_batch(xd, md, offsets, W["leaf"])
+            else:
+                f.build(xd, md, W["leaf"])
+            f.forces(W["p"], W["theta"], other, out, None)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                sv()
+        stream.synchronize()
+        ts_ = []
+        for _ in range(max(3, min(args.steps, 5))):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv()
+            e1.record(stream)
+            e1.synchronize()
+            ts_.append(e0.elapsed_time(e1))
+        tm = statistics.mean(ts_)
+        o = out.cpu().numpy()
+        variants["standard" if other == fmm.STANDARD else "conserving"] = {
+            "value": N / (tm / 1e3), "ms_per_step": tm,
+            "force_err_rel_l2": {"vs_direct_sampled": sampled_direct_error(torch, dev, x, m, o, offsets=offsets)},
+            "stage_ms": {k: round(v, 4) for k, v in f.stage_times().items()}}
+
     # the other arithmetic modes of the pair kernels on the same input (same timing method)
     modes = {}
     if args.modes and world == 1 and args.workload == "plummer1m" and not args.n:
@@ -400,6 +437,7 @@ def run_gbfmm(args):
         "force_err_rel_l2": err,
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
+        "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,
         "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),

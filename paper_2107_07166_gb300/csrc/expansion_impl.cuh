@@ -423,13 +423,11 @@ __global__ void m2l_reduce_k(int nn, const long long* __restrict__ fo, const lon
 
 // moments of every node in the pair-kernel type, in units of 2^k_n (k_n = floor(log2 r_max)
 // for r_max > 0; a node with r_max = 0 has all particles at its centre, so its moments
-// beyond the mass vanish and any unit serves), padded to NMP per node, plus the
-// double-float centres: one thread per (node, padded coefficient)
+// beyond the mass vanish and any unit serves), padded to NMP per node: one thread per
+// (node, padded coefficient)
 template <int P, class T>
 __global__ void scale_moments_k(int nn, const double* __restrict__ mom, const double* __restrict__ rmax,
-                                const double* __restrict__ Zx, const double* __restrict__ Zy,
-                                const double* __restrict__ Zz, T* __restrict__ momT, int* __restrict__ nk,
-                                float4* __restrict__ zh, float4* __restrict__ zl) {
+                                T* __restrict__ momT, int* __restrict__ nk) {
     using E = Exp<P>;
     int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (t >= (int64_t)nn * E::NMP) return;
@@ -437,18 +435,7 @@ __global__ void scale_moments_k(int nn, const double* __restrict__ mom, const do
     double r = rmax[n];
     int kn = r > 0.0 ? max(-120, min(120, ilogb(r))) : 0;
     momT[t] = k < E::NM ? to_kernel(mom[(int64_t)n * E::NM + k] * pow2d(-kn * mi_deg(k)), T()) : T(0);
-    if (k == 0) {
-        nk[n] = kn;
-        double z[3] = {Zx[n], Zy[n], Zz[n]};
-        float h[3], l[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            h[i] = (float)z[i];
-            l[i] = (float)(z[i] - (double)h[i]);
-        }
-        zh[n] = make_float4(h[0], h[1], h[2], 0.f);
-        zl[n] = make_float4(l[0], l[1], l[2], 0.f);
-    }
+    if (k == 0) nk[n] = kn;
 }
 
 // conserving source moments of every cell (formed once per moment build)
@@ -644,16 +631,12 @@ void run_moments_p(fmm_ctx* c) {
         GB_LAUNCH("con_moments_k");
         return;
     }
-    // the scaled modes: raw moments in the pair-kernel type, range-scaled and padded, and
-    // the double-float centres
+    // the scaled modes: raw moments in the pair-kernel type, range-scaled and padded
     int64_t nmp = (int64_t)nn * E::NMP;
     ensure(c->nk, sizeof(int) * (size_t)nn);
-    ensure(c->zhl, sizeof(float4) * 2 * (size_t)nn);
-    float4* zh = c->zhl.as<float4>();
     auto launch = [&](auto* mT) {
-        scale_moments_k<P><<<grid_for(nmp, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->nrmax.as<double>(),
-                                                            c->nZx.as<double>(), c->nZy.as<double>(),
-                                                            c->nZz.as<double>(), mT, c->nk.as<int>(), zh, zh + nn);
+        scale_moments_k<P><<<grid_for(nmp, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->nrmax.as<double>(), mT,
+                                                            c->nk.as<int>());
     };
     if (c->precision == FMM_DF64) {
         ensure(c->momT, sizeof(df64) * (size_t)nmp);

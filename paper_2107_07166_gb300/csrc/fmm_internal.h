@@ -45,6 +45,8 @@ struct NodeView {
     const double* Zy;
     const double* Zz;
     const double* rmax;
+    const float4* zh;  // (hi(Z), r_max rounded up) in binary32
+    const float4* zl;  // (lo(Z), 0)
 };
 
 // Chunked work over per-cell segments (see build_items in walk.cu).
@@ -130,7 +132,7 @@ struct fmm_ctx {
     bool pos_valid = false;
     gbfmm::DevBuf momT;                        // raw moments in the pair-kernel type (range-scaled, padded)
     gbfmm::DevBuf nk;                          // per-node moment unit exponent (scaled modes)
-    gbfmm::DevBuf zhl;                         // double-float node centres: float4 hi[n] | lo[n]
+    gbfmm::DevBuf zhl;                         // double-float node centres: float4 hi[n] | lo[n] (build)
     gbfmm::DevBuf m2l_kpart;                   // per-item unit exponent of the M2L partials
     int id_bits = 0;
     // results (sorted order) and output staging

@@ -224,7 +224,8 @@ void stage_end(fmm_ctx* c, Stage s) {
 NodeView node_view(const fmm_ctx* c) {
     return NodeView{c->nfirst.as<int>(), c->ncount.as<int>(),  c->nparent.as<int>(),
                     c->nchildf.as<int>(), c->nnchild.as<int>(), c->nZx.as<double>(),
-                    c->nZy.as<double>(),  c->nZz.as<double>(),  c->nrmax.as<double>()};
+                    c->nZy.as<double>(),  c->nZz.as<double>(),  c->nrmax.as<double>(),
+                    c->zhl.as<float4>(),  c->zhl.as<float4>() + c->n_nodes};
 }
 
 }  // namespace gbfmm

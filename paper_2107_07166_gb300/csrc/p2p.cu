@@ -18,6 +18,9 @@
 namespace gbfmm {
 
 constexpr int PB = 128;                 // 4 warps
+#ifndef RING_ALL
+#define RING_ALL 0
+#endif
 constexpr int PW = PB / 32;
 // panel columns: 8-byte types use 8 columns so that four warps of panels leave room for
 // four blocks per SM; 4-byte types use 16
@@ -28,10 +31,54 @@ struct Panel {
     static constexpr int SIZE = 32 * ROW;     // elements per warp panel
 };
 
+__device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(FULL, v, src); }
+__device__ __forceinline__ double shfl_t(double v, int src) { return __shfl_sync(FULL, v, src); }
+__device__ __forceinline__ df64 shfl_t(df64 v, int src) {
+    return df64(__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src));
+}
+
 template <class S>
 struct PState {
     S x, y, z, m;
 };
+
+// Leaves above 32 particles (only at the deepest level): one side at a time, lane = target
+// particle, sources in increasing order.
+template <class T, bool POT>
+__device__ __forceinline__ void p2p_generic(int lane, bool self, int fA, int nA, int fB, int nB, long long o,
+                                            typename Prec<T>::S rx, typename Prec<T>::S ry,
+                                            typename Prec<T>::S rz,
+                                            const PState<typename Prec<T>::S>* __restrict__ pos,
+                                            Quad<T>* __restrict__ part) {
+    using S = typename Prec<T>::S;
+    for (int side = 0; side < (self ? 1 : 2); side++) {
+        int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
+        long long oT = side ? o + nA : o;
+        S sx = side ? -rx : rx, sy = side ? -ry : ry, sz = side ? -rz : rz;
+        for (int t = lane; t < nT; t += 32) {
+            PState<S> pt = pos[fT + t];
+            pt = PState<S>{sx + pt.x, sy + pt.y, sz + pt.z, pt.m};
+            T ax = T(0), ay = T(0), az = T(0), ph = T(0);
+            for (int u = 0; u < nS; u++) {
+                if (self && u == t) continue;
+                PState<S> ps = pos[fS + u];
+                T dx = Prec<T>::sep(pt.x, ps.x), dy = Prec<T>::sep(pt.y, ps.y);
+                T dz = Prec<T>::sep(pt.z, ps.z);
+                T r2 = dx * dx + dy * dy + dz * dz;
+                if (!is_zero(r2)) {
+                    T ir = rsqrt_t(r2);
+                    T fb = Prec<T>::mass(ps.m) * (ir * ir * ir);
+                    ax = fma_t(-fb, dx, ax);
+                    ay = fma_t(-fb, dy, ay);
+                    az = fma_t(-fb, dz, az);
+                    ph = fma_t(-Prec<T>::mass(ps.m), ir, ph);
+                }
+            }
+            part[oT + t] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
+                                   POT ? Prec<T>::fin(ph) : T(0)};
+        }
+    }
+}
 
 // The pair kernel in arithmetic T over positions stored as S = Prec<T>::S.
 template <class T, bool POT>
@@ -146,35 +193,94 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
             }
             __syncwarp();
         } else {
-            // ---- leaves above 32 particles (only at the deepest level): one side at a time
-            for (int side = 0; side < (self ? 1 : 2); side++) {
-                int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
-                long long oT = side ? o + nA : o;
-                S sx = side ? -rx : rx, sy = side ? -ry : ry, sz = side ? -rz : rz;
-                for (int t = lane; t < nT; t += 32) {
-                    PState<S> pt = pos[fT + t];
-                    pt = PState<S>{sx + pt.x, sy + pt.y, sz + pt.z, pt.m};
-                    T ax = T(0), ay = T(0), az = T(0), ph = T(0);
-                    for (int u = 0; u < nS; u++) {
-                        if (self && u == t) continue;
-                        PState<S> ps = pos[fS + u];
-                        T dx = Prec<T>::sep(pt.x, ps.x), dy = Prec<T>::sep(pt.y, ps.y);
-                        T dz = Prec<T>::sep(pt.z, ps.z);
-                        T r2 = dx * dx + dy * dy + dz * dz;
-                        if (!is_zero(r2)) {
-                            T ir = rsqrt_t(r2);
-                            T fb = Prec<T>::mass(ps.m) * (ir * ir * ir);
-                            ax = fma_t(-fb, dx, ax);
-                            ay = fma_t(-fb, dy, ay);
-                            az = fma_t(-fb, dz, az);
-                            ph = fma_t(-Prec<T>::mass(ps.m), ir, ph);
-                        }
+            p2p_generic<T, POT>(lane, self, fA, nA, fB, nB, o, rx, ry, rz, pos, part);
+        }
+    }
+}
+
+// The ring form of the same pair kernel (one warp per leaf pair, both leaves <= 32):
+// lane i holds particle a_i of A (shifted by R = Z_A - Z_B) in registers and B's particles
+// sit in shared memory.  In step k lane i meets b_j, j = (i + k) mod L, L = max(nA, nB):
+// over L steps every (a_i, b_j) meets exactly once.  The pair force is formed once and
+// applied to both partners: a_i's sum stays in lane i, b_j's sum travels with the ring (one
+// shuffle to lane i - 1 per step) and is back in lane j after L steps.  A self pair is
+// evaluated from both ends (L = nA, steps 1 .. L-1, no travelling sum), which costs twice
+// the pair arithmetic for 1/L of the work and needs no reduction.  Every sum runs in a
+// fixed order, independent of scheduling.
+template <class T, bool POT>
+__global__ void __launch_bounds__(PB) p2p_ring_k(int64_t npairs, const int2* __restrict__ pairs,
+                                                 const long long* __restrict__ off, const int* __restrict__ nfirst,
+                                                 const int* __restrict__ ncount,
+                                                 const PState<typename Prec<T>::S>* __restrict__ pos,
+                                                 const typename Prec<T>::S* __restrict__ sep,
+                                                 Quad<T>* __restrict__ part) {
+    using S = typename Prec<T>::S;
+    __shared__ PState<S> sB[PW][32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
+    for (int64_t k = gw; k < npairs; k += nw) {
+        int2 pr = pairs[k];
+        int A = pr.x, B = pr.y;
+        int nA = ncount[A], nB = ncount[B], fA = nfirst[A], fB = nfirst[B];
+        long long o = off[k];
+        bool self = A == B;
+        S rx = sep[3 * k], ry = sep[3 * k + 1], rz = sep[3 * k + 2];
+        if (nA > 32 || nB > 32) {
+            p2p_generic<T, POT>(lane, self, fA, nA, fB, nB, o, rx, ry, rz, pos, part);
+            continue;
+        }
+        PState<S> pa = PState<S>{S(0), S(0), S(0), S(0)};
+        if (lane < nA) {
+            PState<S> q = pos[fA + lane];
+            pa = PState<S>{rx + q.x, ry + q.y, rz + q.z, q.m};
+        }
+        __syncwarp();
+        if (lane < nB) sB[w][lane] = pos[fB + lane];
+        __syncwarp();
+        T ma = Prec<T>::mass(pa.m);
+        T ax = T(0), ay = T(0), az = T(0), ap = T(0);
+        T bx = T(0), by = T(0), bz = T(0), bp = T(0);
+        int L = self ? nA : max(nA, nB);
+        int nxt = lane + 1 < L ? lane + 1 : 0;
+        bool mine = lane < nA;
+        for (int kk = self ? 1 : 0; kk < L; kk++) {
+            int j = lane + kk;
+            if (j >= L) j -= L;
+            if (mine && j < nB) {
+                const PState<S>& pb = sB[w][j];
+                T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
+                T r2 = dx * dx + dy * dy + dz * dz;
+                if (!is_zero(r2)) {
+                    T ir = rsqrt_t(r2);
+                    T ir3 = ir * ir * ir;
+                    T mb = Prec<T>::mass(pb.m);
+                    T sa = mb * ir3;
+                    ax = fma_t(-sa, dx, ax);
+                    ay = fma_t(-sa, dy, ay);
+                    az = fma_t(-sa, dz, az);
+                    if (POT) ap = fma_t(-mb, ir, ap);
+                    if (!self) {
+                        T sb = ma * ir3;
+                        bx = fma_t(sb, dx, bx);
+                        by = fma_t(sb, dy, by);
+                        bz = fma_t(sb, dz, bz);
+                        if (POT) bp = fma_t(-ma, ir, bp);
                     }
-                    part[oT + t] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
-                                           POT ? Prec<T>::fin(ph) : T(0)};
                 }
             }
+            if (!self) {
+                bx = shfl_t(bx, nxt);
+                by = shfl_t(by, nxt);
+                bz = shfl_t(bz, nxt);
+                if (POT) bp = shfl_t(bp, nxt);
+            }
         }
+        if (mine) part[o + lane] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
+                                           POT ? Prec<T>::fin(ap) : T(0)};
+        if (!self && lane < nB)
+            part[o + nA + lane] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
+                                          POT ? Prec<T>::fin(bp) : T(0)};
+        __syncwarp();
     }
 }
 
@@ -208,6 +314,12 @@ __global__ void pack_pos_k(int n, const int* __restrict__ leaf_of, const double*
     }
 }
 
+// which pair kernel each arithmetic runs (ring: binary32; panel: binary64 and double-float)
+template <class T>
+struct P2PRing {
+    static constexpr bool value = RING_ALL || sizeof(T) == 4;
+};
+
 template <class T>
 static void p2p_launch(fmm_ctx* c, bool want_pot) {
     using S = typename Prec<T>::S;
@@ -236,14 +348,22 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
                                                      c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
     GB_LAUNCH("p2p_sep_k");
-    size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
-    auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;
-    GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     stage_begin(c, ST_P2P);
-    kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
-                                           c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
-                                           c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
-    GB_LAUNCH("p2p_k");
+    if (P2PRing<T>::value) {
+        auto kern = want_pot ? p2p_ring_k<T, true> : p2p_ring_k<T, false>;
+        kern<<<(unsigned)blocks, PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
+                                             c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
+                                             c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
+        GB_LAUNCH("p2p_ring_k");
+    } else {
+        size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
+        auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;
+        GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
+                                               c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
+                                               c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
+        GB_LAUNCH("p2p_k");
+    }
     stage_end(c, ST_P2P);
 }
 

@@ -294,9 +294,25 @@ __global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const doub
     }
 }
 
-__global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, double* __restrict__ rmax) {
+// r_max, plus every node's centre as double-float words with r_max rounded up to binary32
+// (zh = (hi(Z), r_max up), zl = (lo(Z), 0)): the walk's binary32 acceptance prefilter and
+// the binary32 M2L separations read these
+__global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, const double* __restrict__ Zx,
+                       const double* __restrict__ Zy, const double* __restrict__ Zz, double* __restrict__ rmax,
+                       float4* __restrict__ zh, float4* __restrict__ zl) {
     int nd = blockIdx.x * TB + threadIdx.x;
-    if (nd < nn) rmax[nd] = __dsqrt_rn(__longlong_as_double((long long)r2bits[nd]));
+    if (nd >= nn) return;
+    double r = __dsqrt_rn(__longlong_as_double((long long)r2bits[nd]));
+    rmax[nd] = r;
+    double z[3] = {Zx[nd], Zy[nd], Zz[nd]};
+    float h[3], l[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        h[i] = (float)z[i];
+        l[i] = (float)(z[i] - (double)h[i]);
+    }
+    zh[nd] = make_float4(h[0], h[1], h[2], __double2float_ru(r));
+    zl[nd] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
 // ------------------------------------------------------------------ batches of systems
@@ -558,7 +574,10 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
                                            c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
                                            c->nZz.as<double>(), c->nr2.as<unsigned long long>());
     GB_LAUNCH("rmax2_k");
-    rmax_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nr2.as<unsigned long long>(), c->nrmax.as<double>());
+    ensure(c->zhl, sizeof(float4) * 2 * (size_t)nn);
+    rmax_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nr2.as<unsigned long long>(), c->nZx.as<double>(),
+                                           c->nZy.as<double>(), c->nZz.as<double>(), c->nrmax.as<double>(),
+                                           c->zhl.as<float4>(), c->zhl.as<float4>() + nn);
     GB_LAUNCH("rmax_k");
     return FMM_OK;
 }

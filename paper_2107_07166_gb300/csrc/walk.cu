@@ -34,6 +34,28 @@ __device__ __forceinline__ bool mac_accept(const NodeView& nv, int A, int B, dou
     return R > 0.0 && __dadd_rn(nv.rmax[A], nv.rmax[B]) <= __dmul_rn(theta, R);
 }
 
+// binary32 prefilter of mac_accept: 1 accept, 0 reject, -1 too close to call.  The
+// separation comes from the double-float centre words ((hi - hi) + (lo - lo): exact high
+// difference when the centres are close, else within 2^-23), r_max is rounded up, and the
+// squared test (r_A + r_B)^2 vs theta^2 R^2 carries a relative error below 2^-18 while
+// max|Z| / R <= 2^20 and nothing under- or overflows; a 2^-12 margin on either side is
+// therefore decided exactly as the binary64 test decides it, and the rest (ties within
+// the margin, extreme ranges) falls through to that test.
+__device__ __forceinline__ int mac_fast(const NodeView& nv, int A, int B, float th2) {
+    float4 ah = nv.zh[A], bh = nv.zh[B], al = nv.zl[A], bl = nv.zl[B];
+    float dx = __fadd_rn(__fsub_rn(ah.x, bh.x), __fsub_rn(al.x, bl.x));
+    float dy = __fadd_rn(__fsub_rn(ah.y, bh.y), __fsub_rn(al.y, bl.y));
+    float dz = __fadd_rn(__fsub_rn(ah.z, bh.z), __fsub_rn(al.z, bl.z));
+    float R2 = dx * dx + dy * dy + dz * dz;
+    float z2 = fmaxf(ah.x * ah.x + ah.y * ah.y + ah.z * ah.z, bh.x * bh.x + bh.y * bh.y + bh.z * bh.z);
+    if (!(R2 >= 0x1p-100f && R2 <= 0x1p100f) || R2 < 0x1p-40f * z2 || !(ah.w + bh.w <= 0x1p50f)) return -1;
+    float rs = ah.w + bh.w;
+    float lhs = rs * rs, rhs = th2 * R2;
+    if (lhs <= rhs * (1.f - 0x1p-12f)) return 1;
+    if (lhs >= rhs * (1.f + 0x1p-12f)) return 0;
+    return -1;
+}
+
 // true: split A; false: split B (neither is a leaf here)
 __device__ __forceinline__ bool split_a(const NodeView& nv, int A, int B) {
     double ra = nv.rmax[A], rb = nv.rmax[B];
@@ -44,7 +66,7 @@ __device__ __forceinline__ bool split_a(const NodeView& nv, int A, int B) {
 }
 
 // decision: 0 = split, 1 = M2L, 2 = P2P; *split_node / *nnew for splits
-__device__ __forceinline__ int decide(const NodeView& nv, int2 it, double theta, int* nnew, bool* sa) {
+__device__ __forceinline__ int decide(const NodeView& nv, int2 it, double theta, float th2, int* nnew, bool* sa) {
     int A = it.x, B = it.y;
     if (A == B) {
         int nc = nv.nchild[A];
@@ -52,7 +74,8 @@ __device__ __forceinline__ int decide(const NodeView& nv, int2 it, double theta,
         *nnew = nc * (nc + 1) / 2;
         return 0;
     }
-    if (mac_accept(nv, A, B, theta)) return 1;
+    int f = mac_fast(nv, A, B, th2);
+    if (f == 1 || (f < 0 && mac_accept(nv, A, B, theta))) return 1;
     bool la = nv.nchild[A] == 0, lb = nv.nchild[B] == 0;
     if (la && lb) return 2;
     bool s = lb ? true : (la ? false : split_a(nv, A, B));
@@ -83,7 +106,7 @@ __device__ __forceinline__ int warp_claim(int* counter, int want, unsigned lane_
 }
 
 __global__ void walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out, WalkCounters* __restrict__ cnt,
-                            int par, NodeView nv, double theta, int2* __restrict__ m2l, int cap_m2l,
+                            int par, NodeView nv, double theta, float th2, int2* __restrict__ m2l, int cap_m2l,
                             int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
     int nf = min(cnt->nf[par], cap_fr);  // a frontier beyond the buffer was not stored (retried)
     int lane = threadIdx.x & 31;
@@ -96,7 +119,7 @@ __global__ void walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ f
         bool sa = false;
         if (i < nf) {
             it = fr_in[i];
-            d = decide(nv, it, theta, &nnew, &sa);
+            d = decide(nv, it, theta, th2, &nnew, &sa);
         }
         int om = warp_claim(&cnt->n_m2l, d == 1 ? 1 : 0, 0);
         int op = warp_claim(&cnt->n_p2p, d == 2 ? 1 : 0, 0);
@@ -249,6 +272,7 @@ void run_walk(fmm_ctx* c, double theta) {
     int64_t nn = c->n_nodes;
     // fixed number of steps, no host round trip between them; one retry if a buffer overflowed
     int steps = 2 * c->n_levels + 2;
+    float th2 = (float)theta * (float)theta;  // prefilter only; relative error far inside its margin
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int grid = dev_sms * 8;
@@ -268,7 +292,7 @@ void run_walk(fmm_ctx* c, double theta) {
             int par = k & 1;
             int2* fin = par ? c->fr1.as<int2>() : c->fr0.as<int2>();
             int2* fout = par ? c->fr0.as<int2>() : c->fr1.as<int2>();
-            walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, nv, theta, c->m2l_pairs.as<int2>(), (int)cap_m2l,
+            walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, nv, theta, th2, c->m2l_pairs.as<int2>(), (int)cap_m2l,
                                             c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr);
             GB_LAUNCH("walk_step_k");
             walk_advance_k<<<1, 1, 0, s>>>(cnt, par, max_fr);
