@@ -129,6 +129,9 @@ struct fmm_ctx {
     gbfmm::DevBuf lf_x, lf_v, lf_m, lf_a, lf_diag;  // leapfrog state (input order)
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     gbfmm::DevBuf p2p_sep;                     // centre separation of every P2P pair, storage type
+    gbfmm::DevBuf p2p_cls, p2p_list;           // ring-kernel size classes: flags/ranks, pair lists
+    int64_t p2p_ncls[4] = {0, 0, 0, 0};        // pairs per size class
+    int64_t walk_gen = 0, p2p_cls_gen = -1;    // walks run so far; walk the classes belong to
     bool pos_valid = false;
     gbfmm::DevBuf momT;                        // raw moments in the pair-kernel type (range-scaled, padded)
     gbfmm::DevBuf nk;                          // per-node moment unit exponent (scaled modes)

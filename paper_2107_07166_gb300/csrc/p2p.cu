@@ -198,56 +198,70 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
     }
 }
 
-// The ring form of the same pair kernel (one warp per leaf pair, both leaves <= 32):
-// lane i holds particle a_i of A (shifted by R = Z_A - Z_B) in registers and B's particles
-// sit in shared memory.  In step k lane i meets b_j, j = (i + k) mod L, L = max(nA, nB):
-// over L steps every (a_i, b_j) meets exactly once.  The pair force is formed once and
-// applied to both partners: a_i's sum stays in lane i, b_j's sum travels with the ring (one
-// shuffle to lane i - 1 per step) and is back in lane j after L steps.  A self pair is
-// evaluated from both ends (L = nA, steps 1 .. L-1, no travelling sum), which costs twice
-// the pair arithmetic for 1/L of the work and needs no reduction.  Every sum runs in a
-// fixed order, independent of scheduling.
-template <class T, bool POT>
-__global__ void __launch_bounds__(PB) p2p_ring_k(int64_t npairs, const int2* __restrict__ pairs,
-                                                 const long long* __restrict__ off, const int* __restrict__ nfirst,
-                                                 const int* __restrict__ ncount,
+// The ring form of the same pair kernel, for leaves of at most 32 particles: a segment of
+// SEG lanes takes one leaf pair (32 / SEG pairs per warp, pairs taken from a list of one
+// size class).  Lane i of the segment holds particle a_i of A (shifted by R = Z_A - Z_B) in
+// registers and B's particles sit in shared memory.  In step k lane i meets b_j,
+// j = (i + k) mod L, L = max(nA, nB): over L steps every (a_i, b_j) meets exactly once.  The
+// pair force is formed once and applied to both partners: a_i's sum stays in lane i, b_j's
+// sum travels with the ring (one shuffle from lane i + 1 per step) and is back in lane j
+// after L steps; segments with a shorter ring hold still for the remaining steps.  A self
+// pair is evaluated from both ends (L = nA, no travelling sum), which costs twice the pair
+// arithmetic for 1/L of the work and needs no reduction.  Every sum runs in a fixed order.
+template <class T, bool POT, int SEG>
+__global__ void __launch_bounds__(PB) p2p_ring_k(int64_t nlist, const int* __restrict__ list,
+                                                 const int2* __restrict__ pairs, const long long* __restrict__ off,
+                                                 const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                  const PState<typename Prec<T>::S>* __restrict__ pos,
                                                  const typename Prec<T>::S* __restrict__ sep,
                                                  Quad<T>* __restrict__ part) {
     using S = typename Prec<T>::S;
+    constexpr int PPW = 32 / SEG;
     __shared__ PState<S> sB[PW][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i = lane % SEG, base = lane - i;
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
-    for (int64_t k = gw; k < npairs; k += nw) {
-        int2 pr = pairs[k];
-        int A = pr.x, B = pr.y;
-        int nA = ncount[A], nB = ncount[B], fA = nfirst[A], fB = nfirst[B];
-        long long o = off[k];
-        bool self = A == B;
-        S rx = sep[3 * k], ry = sep[3 * k + 1], rz = sep[3 * k + 2];
-        if (nA > 32 || nB > 32) {
-            p2p_generic<T, POT>(lane, self, fA, nA, fB, nB, o, rx, ry, rz, pos, part);
-            continue;
+    for (int64_t q = gw; q * PPW < nlist; q += nw) {
+        int64_t li = q * PPW + lane / SEG;
+        int A = 0, B = 0, nA = 0, nB = 0, fA = 0, fB = 0;
+        long long o = 0;
+        S rx = S(0), ry = S(0), rz = S(0);
+        if (li < nlist) {
+            int k = list[li];
+            int2 pr = pairs[k];
+            A = pr.x;
+            B = pr.y;
+            nA = ncount[A];
+            nB = ncount[B];
+            fA = nfirst[A];
+            fB = nfirst[B];
+            o = off[k];
+            rx = sep[3 * k];
+            ry = sep[3 * k + 1];
+            rz = sep[3 * k + 2];
         }
+        bool self = A == B;
         PState<S> pa = PState<S>{S(0), S(0), S(0), S(0)};
-        if (lane < nA) {
-            PState<S> q = pos[fA + lane];
-            pa = PState<S>{rx + q.x, ry + q.y, rz + q.z, q.m};
+        if (i < nA) {
+            PState<S> qa = pos[fA + i];
+            pa = PState<S>{rx + qa.x, ry + qa.y, rz + qa.z, qa.m};
         }
         __syncwarp();
-        if (lane < nB) sB[w][lane] = pos[fB + lane];
+        if (i < nB) sB[w][lane] = pos[fB + i];
         __syncwarp();
         T ma = Prec<T>::mass(pa.m);
         T ax = T(0), ay = T(0), az = T(0), ap = T(0);
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);
         int L = self ? nA : max(nA, nB);
-        int nxt = lane + 1 < L ? lane + 1 : 0;
-        bool mine = lane < nA;
-        for (int kk = self ? 1 : 0; kk < L; kk++) {
-            int j = lane + kk;
+        int Lmax = __reduce_max_sync(FULL, L);
+        int nxt = base + (i + 1 < L ? i + 1 : 0);
+        bool mine = i < nA;
+        for (int kk = 0; kk < Lmax; kk++) {
+            bool act = kk < L;
+            int j = i + kk;
             if (j >= L) j -= L;
-            if (mine && j < nB) {
-                const PState<S>& pb = sB[w][j];
+            if (act && mine && j < nB && !(self && j == i)) {
+                const PState<S>& pb = sB[w][base + j];
                 T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
                 T r2 = dx * dx + dy * dy + dz * dz;
                 if (!is_zero(r2)) {
@@ -268,20 +282,72 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(int64_t npairs, const int2* __r
                     }
                 }
             }
-            if (!self) {
-                bx = shfl_t(bx, nxt);
-                by = shfl_t(by, nxt);
-                bz = shfl_t(bz, nxt);
-                if (POT) bp = shfl_t(bp, nxt);
-            }
+            int src = (act && !self) ? nxt : lane;
+            bx = shfl_t(bx, src);
+            by = shfl_t(by, src);
+            bz = shfl_t(bz, src);
+            if (POT) bp = shfl_t(bp, src);
         }
-        if (mine) part[o + lane] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
-                                           POT ? Prec<T>::fin(ap) : T(0)};
-        if (!self && lane < nB)
-            part[o + nA + lane] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
-                                          POT ? Prec<T>::fin(bp) : T(0)};
+        if (mine) part[o + i] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
+                                        POT ? Prec<T>::fin(ap) : T(0)};
+        if (!self && i < nB)
+            part[o + nA + i] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
+                                       POT ? Prec<T>::fin(bp) : T(0)};
         __syncwarp();
     }
+}
+
+// pairs with a leaf above 32 particles (only at the deepest level), from the list
+template <class T, bool POT>
+__global__ void __launch_bounds__(PB) p2p_big_k(int64_t nlist, const int* __restrict__ list,
+                                                const int2* __restrict__ pairs, const long long* __restrict__ off,
+                                                const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                                                const PState<typename Prec<T>::S>* __restrict__ pos,
+                                                const typename Prec<T>::S* __restrict__ sep,
+                                                Quad<T>* __restrict__ part) {
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
+    for (int64_t li = gw; li < nlist; li += nw) {
+        int k = list[li];
+        int2 pr = pairs[k];
+        p2p_generic<T, POT>(lane, pr.x == pr.y, nfirst[pr.x], ncount[pr.x], nfirst[pr.y], ncount[pr.y], off[k],
+                            sep[3 * k], sep[3 * k + 1], sep[3 * k + 2], pos, part);
+    }
+}
+
+// size classes of the ring kernel: L = nA (self) or max(nA, nB); class 0: L <= 8, 1: <= 16,
+// 2: <= 32, 3: above.  flags[k] marks classes 0..2; the exclusive scan of the flags gives
+// each pair its rank in its class, and p2p_fill_k writes the class lists back to back in
+// pair order (a stable partition, so the lists do not depend on scheduling)
+__device__ __forceinline__ int ring_class(int2 p, const int* __restrict__ ncount) {
+    int L = p.x == p.y ? ncount[p.x] : max(ncount[p.x], ncount[p.y]);
+    return L <= 8 ? 0 : (L <= 16 ? 1 : (L <= 32 ? 2 : 3));
+}
+
+__global__ void p2p_class_k(int64_t n, const int2* __restrict__ pairs, const int* __restrict__ ncount,
+                            Cnt3* __restrict__ flags) {
+    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (k >= n) return;
+    int c = ring_class(pairs[k], ncount);
+    flags[k] = Cnt3{c == 0, c == 1, c == 2};
+}
+
+__global__ void p2p_fill_k(int64_t n, const int2* __restrict__ pairs, const int* __restrict__ ncount,
+                           const Cnt3* __restrict__ rank, int* __restrict__ lists) {
+    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (k >= n) return;
+    Cnt3 r = rank[k], t = rank[n];
+    int c = ring_class(pairs[k], ncount);
+    int64_t at;
+    if (c == 0)
+        at = r.a;
+    else if (c == 1)
+        at = (int64_t)t.a + r.b;
+    else if (c == 2)
+        at = (int64_t)t.a + t.b + r.c;
+    else
+        at = (int64_t)t.a + t.b + t.c + (k - r.a - r.b - r.c);
+    lists[at] = (int)k;
 }
 
 // centre separation Z_A - Z_B of every P2P pair, formed in binary64 once per pair and
@@ -348,13 +414,52 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
                                                      c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
     GB_LAUNCH("p2p_sep_k");
+    int64_t* ncls = c->p2p_ncls;
+    if (c->p2p_cls_gen != c->walk_gen) {
+        // size classes of the leaf pairs: list bookkeeping, once per walk
+        int64_t np = c->n_p2p;
+        ensure(c->p2p_cls, sizeof(Cnt3) * 2 * (size_t)(np + 1));
+        ensure(c->p2p_list, sizeof(int) * (size_t)(np > 0 ? np : 1));
+        Cnt3* flags = c->p2p_cls.as<Cnt3>();
+        Cnt3* rank = flags + np + 1;
+        p2p_class_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_pairs.as<int2>(), c->ncount.as<int>(), flags);
+        GB_LAUNCH("p2p_class_k");
+        scan_cnt3(c, flags, np, rank);
+        p2p_fill_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_pairs.as<int2>(), c->ncount.as<int>(), rank,
+                                                  c->p2p_list.as<int>());
+        GB_LAUNCH("p2p_fill_k");
+        Cnt3 t;
+        GB_CUDA(cudaMemcpyAsync(&t, rank + np, sizeof(Cnt3), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        ncls[0] = t.a;
+        ncls[1] = t.b;
+        ncls[2] = t.c;
+        ncls[3] = np - t.a - t.b - t.c;
+        c->p2p_cls_gen = c->walk_gen;
+    }
     stage_begin(c, ST_P2P);
-    if (P2PRing<T>::value) {
-        auto kern = want_pot ? p2p_ring_k<T, true> : p2p_ring_k<T, false>;
-        kern<<<(unsigned)blocks, PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
+    if constexpr (P2PRing<T>::value) {
+        const int* lst = c->p2p_list.as<int>();
+        auto args = [&](auto kern, int64_t nl, const int* l, int per_warp) {
+            if (nl <= 0) return;
+            int64_t bl = (nl + per_warp * PW - 1) / (per_warp * PW);
+            if (bl > cap) bl = cap;
+            kern<<<(unsigned)bl, PB, 0, s>>>(nl, l, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
                                              c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
                                              c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
-        GB_LAUNCH("p2p_ring_k");
+            GB_LAUNCH("p2p_ring_k");
+        };
+        if (want_pot) {
+            args(p2p_ring_k<T, true, 8>, ncls[0], lst, 4);
+            args(p2p_ring_k<T, true, 16>, ncls[1], lst + ncls[0], 2);
+            args(p2p_ring_k<T, true, 32>, ncls[2], lst + ncls[0] + ncls[1], 1);
+            args(p2p_big_k<T, true>, ncls[3], lst + ncls[0] + ncls[1] + ncls[2], 1);
+        } else {
+            args(p2p_ring_k<T, false, 8>, ncls[0], lst, 4);
+            args(p2p_ring_k<T, false, 16>, ncls[1], lst + ncls[0], 2);
+            args(p2p_ring_k<T, false, 32>, ncls[2], lst + ncls[0] + ncls[1], 1);
+            args(p2p_big_k<T, false>, ncls[3], lst + ncls[0] + ncls[1] + ncls[2], 1);
+        }
     } else {
         size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
         auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;

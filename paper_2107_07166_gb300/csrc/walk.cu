@@ -356,6 +356,7 @@ void run_walk(fmm_ctx* c, double theta) {
     build_items(c, c->m2l_seg.as<long long>(), (int)nn, M2L_CHUNK, c->m2l_items);
     build_items(c, c->p2p_seg.as<long long>(), (int)nn, P2P_CHUNK, c->p2p_items);
     c->list_theta = theta;
+    c->walk_gen++;
 }
 
 }  // namespace gbfmm
