@@ -205,9 +205,9 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
 // j = (i + k) mod L, L = max(nA, nB): over L steps every (a_i, b_j) meets exactly once.  The
 // pair force is formed once and applied to both partners: a_i's sum stays in lane i, b_j's
 // sum travels with the ring (one shuffle from lane i + 1 per step) and is back in lane j
-// after L steps; segments with a shorter ring hold still for the remaining steps.  A self
-// pair is evaluated from both ends (L = nA, no travelling sum), which costs twice the pair
-// arithmetic for 1/L of the work and needs no reduction.  Every sum runs in a fixed order.
+// after a full turn.  A self pair is evaluated from both ends (its travelling sums are
+// dropped), which costs twice the pair arithmetic for 1/L of the work and needs no
+// reduction.  Every sum runs in a fixed order.
 template <class T, bool POT, int SEG>
 __global__ void __launch_bounds__(PB) p2p_ring_k(int64_t nlist, const int* __restrict__ list,
                                                  const int2* __restrict__ pairs, const long long* __restrict__ off,
@@ -252,15 +252,17 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(int64_t nlist, const int* __res
         T ma = Prec<T>::mass(pa.m);
         T ax = T(0), ay = T(0), az = T(0), ap = T(0);
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);
+        // one ring length for the whole warp (the longest of its segments): a segment with
+        // a shorter ring meets empty slots, and a self pair meets each particle itself at
+        // zero separation, which the r = 0 rule skips; the travelling sums of a self pair
+        // are formed but not stored
         int L = self ? nA : max(nA, nB);
-        int Lmax = __reduce_max_sync(FULL, L);
-        int nxt = base + (i + 1 < L ? i + 1 : 0);
+        int Lr = __reduce_max_sync(FULL, L);
+        int nxt = base + (i + 1 < Lr ? i + 1 : 0);
         bool mine = i < nA;
-        for (int kk = 0; kk < Lmax; kk++) {
-            bool act = kk < L;
-            int j = i + kk;
-            if (j >= L) j -= L;
-            if (act && mine && j < nB && !(self && j == i)) {
+        int j = i;
+        for (int kk = 0; kk < Lr; kk++) {
+            if (mine && j < nB) {
                 const PState<S>& pb = sB[w][base + j];
                 T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
                 T r2 = dx * dx + dy * dy + dz * dz;
@@ -273,20 +275,18 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(int64_t nlist, const int* __res
                     ay = fma_t(-sa, dy, ay);
                     az = fma_t(-sa, dz, az);
                     if (POT) ap = fma_t(-mb, ir, ap);
-                    if (!self) {
-                        T sb = ma * ir3;
-                        bx = fma_t(sb, dx, bx);
-                        by = fma_t(sb, dy, by);
-                        bz = fma_t(sb, dz, bz);
-                        if (POT) bp = fma_t(-ma, ir, bp);
-                    }
+                    T sb = ma * ir3;
+                    bx = fma_t(sb, dx, bx);
+                    by = fma_t(sb, dy, by);
+                    bz = fma_t(sb, dz, bz);
+                    if (POT) bp = fma_t(-ma, ir, bp);
                 }
             }
-            int src = (act && !self) ? nxt : lane;
-            bx = shfl_t(bx, src);
-            by = shfl_t(by, src);
-            bz = shfl_t(bz, src);
-            if (POT) bp = shfl_t(bp, src);
+            bx = shfl_t(bx, nxt);
+            by = shfl_t(by, nxt);
+            bz = shfl_t(bz, nxt);
+            if (POT) bp = shfl_t(bp, nxt);
+            j = (j + 1 == Lr) ? 0 : j + 1;
         }
         if (mine) part[o + i] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
                                         POT ? Prec<T>::fin(ap) : T(0)};
