@@ -532,6 +532,64 @@ def run_reference(args):
     return line
 
 
+def run_two_shapes(args):
+    """Synthetic stand-in for the paper's two-shape test (Fig. 2): two irregular clusters of
+    4000 particles at COM distance d, each alone in one child of the root (leaf size 4000,
+    theta = 0.999), so that the walk emits exactly one mutual M2L between them and evaluates
+    each cluster's own forces directly.  The deviation from the full direct sum is then the
+    error of the approximated inter-shape force, reported relative to that force (L2 over
+    all particles), with the net force and torque of the result."""
+    import torch
+    from paper_2107_07166_gb300 import fmm, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n_each, seed = 4000, 7
+    forms = [("order0-standard", 1, fmm.STANDARD), ("order0-realigned", 1, fmm.CONSERVING),
+             ("order0-realigned-literal", 1, fmm.CONSERVING_PAPER0), ("order1-standard", 2, fmm.STANDARD),
+             ("order1-realigned", 2, fmm.CONSERVING)]
+    prec = {"fp64": fmm.FP64, "df64": fmm.DF64, "mixed": fmm.MIXED}[args.precision]
+    f = fmm.FMM(0, prec, torch.cuda.current_stream())
+    rows = []
+    for d in (4.0, 8.0, 16.0, 32.0, 64.0):
+        x, m = synth.clusters_pair(n_each, seed, d)
+        N = x.shape[0]
+        X = torch.from_numpy(x).to(dev)
+        M = torch.from_numpy(m).to(dev)
+        side = torch.cat([torch.zeros(n_each, dtype=torch.bool), torch.ones(n_each, dtype=torch.bool)]).to(dev)
+        full = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+        inter = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+        for i0 in range(0, N, 512):
+            dd = X[i0:i0 + 512, None, :] - X[None, :, :]
+            r2 = (dd * dd).sum(-1)
+            inv3 = torch.where(r2 > 0, r2.rsqrt() ** 3, torch.zeros_like(r2))
+            w = M[None, :] * inv3
+            full[i0:i0 + 512] = -(w[..., None] * dd).sum(1)
+            other = (side[i0:i0 + 512, None] != side[None, :]).to(torch.float64)
+            inter[i0:i0 + 512] = -((w * other)[..., None] * dd).sum(1)
+        xm = (M[:, None] * X)
+        fs = float((M * inter.norm(dim=1)).sum())
+        ts = float((M * X.norm(dim=1) * inter.norm(dim=1)).sum())
+        row = {"d": d}
+        for name, p, variant in forms:
+            acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
+            f.build(X, M, n_each)
+            f.forces(p, 0.999, variant, acc, None)
+            cnt = f.counts()
+            F = (M[:, None] * acc).sum(0)
+            T = torch.cross(X, acc, dim=1).mul(M[:, None]).sum(0)
+            row[name] = {"err": float((acc - full).norm() / inter.norm()),
+                         "net_force_rel": float(F.norm()) / fs, "net_torque_rel": float(T.norm()) / ts,
+                         "n_m2l": int(cnt["n_m2l"])}
+        del xm
+        rows.append(row)
+    f.close()
+    line = {"study": "two-shapes", "n_each": n_each, "seed": seed, "theta": 0.999, "leaf_size": n_each,
+            "precision": args.precision, "rows": rows,
+            "note": "error of the approximated inter-shape force relative to that force, L2 over both shapes"}
+    print(json.dumps(line))
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,6 +606,8 @@ def main():
     ap.add_argument("--leapfrog", type=int, default=100, help="KDK steps of the momentum-drift run (0: skip)")
     ap.add_argument("--no-modes", dest="modes", action="store_false",
                     help="skip timing the other arithmetic modes on the same input")
+    ap.add_argument("--study", default=None, choices=["two-shapes"],
+                    help="run a study instead of the benchmark (one JSON line)")
     args = ap.parse_args()
     args.variant_set = args.variant is not None
     args.precision_set = args.precision is not None
@@ -555,6 +615,9 @@ def main():
     args.precision = args.precision or "fp64"
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.study == "two-shapes":
+        run_two_shapes(args)
         return
     if args.warmup < 3:
         args.warmup = 3

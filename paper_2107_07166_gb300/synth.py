@@ -126,8 +126,9 @@ def binary(n_each: int, seed_a: int, seed_b: int, separation: float = 10.0):
 
 
 def clusters_pair(n_each: int, seed: int, distance: float):
-    """Two irregular clusters (unions of random blobs, unit size) with centres
-    `distance` apart along a random direction: a stand-in for the two-shape test."""
+    """Two irregular clusters (unions of five Gaussian blobs, unit size), each shifted to its
+    own mean, with centres `distance` apart along x: a stand-in for the two-shape test.
+    Every particle has mass 1 / (2 n_each)."""
     rng = _rng(seed)
     out = []
     for s in (-0.5, 0.5):

@@ -542,3 +542,28 @@ def test_power_of_two_rescaling_is_exact(fmm, torch_cuda, precision):
         assert rel(b["acc"] * s * s, a["acc"]) < 1e-13, (variant, rel(b["acc"] * s * s, a["acc"]))
         a["f"].close()
         b["f"].close()
+
+
+# ------------------------------------------------------------- two-shape study configuration
+
+def test_two_shape_configuration(fmm, torch_cuda, orc):
+    """The two-shape study (the paper's Fig. 2 setup): two 4000-particle clusters, each one
+    leaf under the root, meet in exactly one mutual M2L.  Every form matches the oracle; the
+    realigned forms have no net torque, the standard first-order form has one."""
+    x, m = synth.clusters_pair(4000, 7, 8.0)
+    for p, variant in ((1, 0), (1, 1), (1, 2), (2, 0), (2, 1)):
+        r = orc.run(x, m, 4000, p, 0.999, variant, want_pot=False)
+        assert r.m2l.tolist() == [[1, 2]]
+        g = run_gpu(fmm, torch_cuda, x, m, 4000, p, 0.999, variant, want_pot=False)
+        assert g["f"].counts()["n_m2l"] == 1
+        assert rel(g["acc"], r.acc) < TOL, (p, variant)
+        F, T = g["f"].diagnostics()
+        a = g["acc"]
+        fs = (m * np.linalg.norm(a, axis=1)).sum()
+        ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum()
+        assert np.linalg.norm(F) < 1e-14 * fs
+        if variant != 0 or p == 1:
+            assert np.linalg.norm(T) < 1e-14 * ts, (p, variant)
+        else:
+            assert np.linalg.norm(T) > 1e-8 * ts
+        g["f"].close()
