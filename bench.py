@@ -39,7 +39,7 @@ WORKLOADS = {
     "binary4m": dict(workload="binary-2x2m", N=1 << 22, seed=3, p=6, theta=0.7, leaf=32, variant="conserving",
                      precision="mixed", gen="binary"),
     "batch512": dict(workload="batch-512-systems", N=None, seed=1000, p=4, theta=0.6, leaf=32,
-                     variant="conserving", precision="mixed", gen="batch", n_sys=512),
+                     variant="conserving", precision="mixed", gen="batch", n_sys=512, autotune=True),
     "disk16m": dict(workload="disk-bulge-16m", N=1 << 24, seed=5, p=5, theta=0.7, leaf=32, variant="conserving",
                     precision="mixed", gen="disk", leapfrog=20),
 }
@@ -192,6 +192,18 @@ def run_gbfmm(args):
     f = fmm.FMM(local, prec, stream)
     variant = fmm.CONSERVING if args.variant == "conserving" else fmm.STANDARD
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    # leaf size and M2L tile length chosen by the library's autotuner (untimed)
+    tune = None
+    if W.get("autotune"):
+        leaves, chunks = (16, 24, 32, 48, 64), (16, 32, 64)
+        with torch.cuda.stream(stream):
+            bl, bc, tms = f.autotune(xd, md, W["p"], W["theta"], variant, leaf_sizes=leaves, m2l_chunks=chunks,
+                                     offsets=offsets, reps=2)
+        stream.synchronize()
+        W["leaf"] = bl
+        tune = {"leaf_sizes": list(leaves), "m2l_chunks": list(chunks), "best_leaf": bl, "best_m2l_chunk": bc,
+                "best_ms": tms}
 
     def step():
         if offsets is not None:
@@ -430,6 +442,7 @@ def run_gbfmm(args):
         "config": {"workload": W["workload"], "N": N, "n_systems": (len(offsets) - 1 if offsets is not None else 1),
                    "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
                    "variant": W["variant"], "precision": W["precision"], "parallelism": f"replicas{world}",
+                   "autotune": tune,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
         "work": {"n_m2l_pairs": work["n_m2l"], "n_p2p_particle_pairs": work["n_pp"],

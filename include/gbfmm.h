@@ -165,6 +165,24 @@ GBFMM_API int fmm_get_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p);
  * again with larger buffers (see fmm_walk_retries); the results do not depend on the
  * sizes.  Invalidates cached lists. */
 GBFMM_API int fmm_set_walk_capacity(fmm_ctx *c, int64_t frontier, int64_t m2l, int64_t p2p);
+/* Tile shapes: directed M2L entries per M2L work item (default 32) and directed P2P
+ * entries per reduction item (default 64), each in [1, 4096].  Results change only in
+ * summation order.  Invalidates cached lists. */
+GBFMM_API int fmm_set_tiles(fmm_ctx *c, int m2l_chunk, int p2p_chunk);
+
+/* Autotuner: times build + forces (p, theta, variant, no potentials) on the given input
+ * for every leaf size in leaf_sizes[n_leaf] and M2L chunk length in m2l_chunks[n_chunk]
+ * (one untimed evaluation, then reps timed ones, CUDA events on the context's stream) and
+ * returns the fastest pair in *best_leaf, *best_chunk with its time per evaluation in
+ * *best_ms.  x, m (N particles) and offsets (n_sys + 1 entries, or NULL for one system,
+ * as in fmm_build_batch) may be host or device memory.  The context is left built with
+ * the winning leaf size and tiles.  Errors of the trial builds or evaluations are
+ * returned as they occur. */
+GBFMM_API int fmm_autotune(fmm_ctx *c, const double *x, const double *m, int64_t N, const int64_t *offsets,
+                           int n_sys, int p, double theta, int variant, const int *leaf_sizes, int n_leaf,
+                           const int *m2l_chunks, int n_chunk, int reps, int *best_leaf, int *best_chunk,
+                           double *best_ms);
+
 /* Number of walks this context has re-run after a buffer overflow. */
 GBFMM_API int fmm_walk_retries(fmm_ctx *c, int64_t *retries);
 

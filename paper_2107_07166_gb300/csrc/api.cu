@@ -131,7 +131,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
                           &c->momT, &c->nk, &c->zhl, &c->m2l_kpart, &c->p2p_sep, &c->p2p_cls, &c->p2p_list, &c->m2m_tmp,
                           &c->lf_x, &c->lf_v,
-                          &c->lf_m, &c->lf_a, &c->lf_diag, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
+                          &c->lf_m, &c->lf_a, &c->lf_diag, &c->tune_acc, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -447,6 +447,82 @@ int fmm_set_walk_capacity(fmm_ctx* c, int64_t frontier, int64_t m2l, int64_t p2p
     c->cap_p2p = p2p;
     c->caps_user = true;
     c->list_theta = -1.0;
+    return FMM_OK;
+}
+
+int fmm_set_tiles(fmm_ctx* c, int m2l_chunk, int p2p_chunk) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_tiles: NULL context");
+    if (m2l_chunk < 1 || m2l_chunk > 4096 || p2p_chunk < 1 || p2p_chunk > 4096)
+        return fail(FMM_ERR_INVALID, "fmm_set_tiles: chunk lengths must be in [1, 4096]");
+    if (c->m2l_chunk != m2l_chunk || c->p2p_chunk != p2p_chunk) c->list_theta = -1.0;
+    c->m2l_chunk = m2l_chunk;
+    c->p2p_chunk = p2p_chunk;
+    return FMM_OK;
+}
+
+int fmm_autotune(fmm_ctx* c, const double* x, const double* m, int64_t N, const int64_t* offsets, int n_sys,
+                 int p, double theta, int variant, const int* leaf_sizes, int n_leaf, const int* m2l_chunks,
+                 int n_chunk, int reps, int* best_leaf, int* best_chunk, double* best_ms) {
+    if (!c || !x || !m || !leaf_sizes || !m2l_chunks || !best_leaf || !best_chunk || !best_ms)
+        return fail(FMM_ERR_INVALID, "fmm_autotune: NULL argument");
+    if (n_leaf < 1 || n_chunk < 1 || reps < 1 || N < 1) return fail(FMM_ERR_INVALID, "fmm_autotune: empty search");
+    for (int i = 0; i < n_leaf; i++)
+        if (leaf_sizes[i] < 1) return fail(FMM_ERR_INVALID, "fmm_autotune: leaf sizes must be >= 1");
+    int keep_p2p = c->p2p_chunk;
+    double best = -1.0;
+    int bl = leaf_sizes[0], bc = m2l_chunks[0];
+    auto build = [&](int leaf) {
+        return offsets ? fmm_build_batch(c, x, m, offsets, n_sys, leaf) : fmm_build(c, x, m, N, leaf);
+    };
+    for (int a = 0; a < n_leaf; a++) {
+        for (int b = 0; b < n_chunk; b++) {
+            int rc = fmm_set_tiles(c, m2l_chunks[b], keep_p2p);
+            if (rc != FMM_OK) return rc;
+            double* acc = nullptr;
+            rc = guarded(c, [&]() -> int {
+                ensure(c->tune_acc, sizeof(double) * 3 * (size_t)N);
+                acc = c->tune_acc.as<double>();
+                return FMM_OK;
+            });
+            if (rc != FMM_OK) return rc;
+            // one untimed evaluation sizes every buffer, then reps timed ones
+            rc = build(leaf_sizes[a]);
+            if (rc == FMM_OK) rc = fmm_forces(c, p, theta, variant, acc, nullptr);
+            if (rc != FMM_OK) return rc;
+            float ms = 0.f;
+            rc = guarded(c, [&]() -> int {
+                cudaEvent_t e0, e1;
+                GB_CUDA(cudaEventCreate(&e0));
+                GB_CUDA(cudaEventCreate(&e1));
+                GB_CUDA(cudaEventRecord(e0, c->stream));
+                int r = FMM_OK;
+                for (int k = 0; k < reps && r == FMM_OK; k++) {
+                    r = build(leaf_sizes[a]);
+                    if (r == FMM_OK) r = fmm_forces(c, p, theta, variant, acc, nullptr);
+                }
+                GB_CUDA(cudaEventRecord(e1, c->stream));
+                GB_CUDA(cudaEventSynchronize(e1));
+                GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r;
+            });
+            if (rc != FMM_OK) return rc;
+            double t = (double)ms / reps;
+            if (best < 0.0 || t < best) {
+                best = t;
+                bl = leaf_sizes[a];
+                bc = m2l_chunks[b];
+            }
+        }
+    }
+    // leave the context built with the winner
+    int rc = fmm_set_tiles(c, bc, keep_p2p);
+    if (rc == FMM_OK) rc = build(bl);
+    if (rc != FMM_OK) return rc;
+    *best_leaf = bl;
+    *best_chunk = bc;
+    *best_ms = best;
     return FMM_OK;
 }
 

@@ -111,6 +111,8 @@ struct fmm_ctx {
     gbfmm::DevBuf fr0, fr1, cnt, cnt_off;      // walk frontier and counters
     int64_t cap_fr = 1 << 16, cap_m2l = 1 << 16, cap_p2p = 1 << 16;   // walk buffer sizes (grow only)
     bool caps_user = false;                    // sizes set by fmm_set_walk_capacity
+    int m2l_chunk = gbfmm::M2L_CHUNK;          // directed M2L entries per work item (fmm_set_tiles)
+    int p2p_chunk = gbfmm::P2P_CHUNK;          // directed P2P entries per reduction item
     int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
     gbfmm::DevBuf m2l_dir;                     // uint64 directed keys (tgt << b | src), sorted
@@ -127,6 +129,7 @@ struct fmm_ctx {
     gbfmm::DevBuf cmom;                        // conserving source moments, n_nodes x 4 nmi(p-1)
     gbfmm::DevBuf m2m_tmp;                     // shifted child moments of one level
     gbfmm::DevBuf lf_x, lf_v, lf_m, lf_a, lf_diag;  // leapfrog state (input order)
+    gbfmm::DevBuf tune_acc;                    // output of the autotuner's trial evaluations
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     gbfmm::DevBuf p2p_sep;                     // centre separation of every P2P pair, storage type
     gbfmm::DevBuf p2p_cls, p2p_list;           // ring-kernel size classes: flags/ranks, pair lists

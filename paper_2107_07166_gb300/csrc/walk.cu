@@ -352,9 +352,9 @@ void run_walk(fmm_ctx* c, double theta) {
     seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->p2p_dir.as<uint64_t>(), np, bits, (int)nn,
                                                     c->p2p_seg.as<long long>());
     GB_LAUNCH("seg_bounds_k");
-    // work items: 32 M2L sources per chunk, 64 P2P entries per chunk
-    build_items(c, c->m2l_seg.as<long long>(), (int)nn, M2L_CHUNK, c->m2l_items);
-    build_items(c, c->p2p_seg.as<long long>(), (int)nn, P2P_CHUNK, c->p2p_items);
+    // work items: m2l_chunk M2L sources (default 32) and p2p_chunk P2P entries (64) per chunk
+    build_items(c, c->m2l_seg.as<long long>(), (int)nn, c->m2l_chunk, c->m2l_items);
+    build_items(c, c->p2p_seg.as<long long>(), (int)nn, c->p2p_chunk, c->p2p_items);
     c->list_theta = theta;
     c->walk_gen++;
 }

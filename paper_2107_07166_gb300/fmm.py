@@ -30,7 +30,8 @@ STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_build_batch", "fmm_forces",
            "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
-           "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
+           "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
             "fmm_get_lists": (i32, [P, P, P]),
             "fmm_stage_times": (i32, [P, P, i32]),
             "fmm_set_walk_capacity": (i32, [P, i64, i64, i64]),
+            "fmm_set_tiles": (i32, [P, i32, i32]),
+            "fmm_autotune": (i32, [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, P, i32, i32, P, P, P]),
             "fmm_leapfrog": (i32, [P, P, P, P, i64, i32, i32, dbl, i32, dbl, i32, P]),
             "fmm_walk_retries": (i32, [P, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
@@ -242,6 +245,28 @@ class FMM:
 
     def set_walk_capacity(self, frontier: int, m2l: int, p2p: int):
         _check(self.lib.fmm_set_walk_capacity(self.h, int(frontier), int(m2l), int(p2p)), "fmm_set_walk_capacity")
+
+    def set_tiles(self, m2l_chunk: int, p2p_chunk: int = 64):
+        _check(self.lib.fmm_set_tiles(self.h, int(m2l_chunk), int(p2p_chunk)), "fmm_set_tiles")
+
+    def autotune(self, x, m, p: int, theta: float, variant: int, leaf_sizes=(16, 24, 32, 48, 64),
+                 m2l_chunks=(16, 32, 64), offsets=None, reps: int = 3):
+        """Fastest (leaf size, M2L chunk) for build + forces on this input; the context is
+        left built with it.  Returns (leaf_size, m2l_chunk, ms per evaluation)."""
+        n = int(x.shape[0])
+        leaves = np.ascontiguousarray(leaf_sizes, dtype=np.int32)
+        chunks = np.ascontiguousarray(m2l_chunks, dtype=np.int32)
+        off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
+        bl, bc = np.zeros(1, np.int32), np.zeros(1, np.int32)
+        ms = np.zeros(1)
+        _check(self.lib.fmm_autotune(self.h, _ptr(x, np.float64), _ptr(m, np.float64), n, _ptr(off, np.int64),
+                                     0 if off is None else int(off.shape[0]) - 1, int(p), float(theta), int(variant),
+                                     _ptr(leaves), int(leaves.shape[0]), _ptr(chunks), int(chunks.shape[0]),
+                                     int(reps), _ptr(bl), _ptr(bc), _ptr(ms)), "fmm_autotune")
+        self.N = n
+        if off is not None:
+            self.n_sys = int(off.shape[0]) - 1
+        return int(bl[0]), int(bc[0]), float(ms[0])
 
     def walk_retries(self) -> int:
         r = np.zeros(1, np.int64)

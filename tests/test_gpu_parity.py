@@ -567,3 +567,44 @@ def test_two_shape_configuration(fmm, torch_cuda, orc):
         else:
             assert np.linalg.norm(T) > 1e-8 * ts
         g["f"].close()
+
+
+# ------------------------------------------------------------- tiles and autotuner
+
+def test_tiles_change_only_summation_order(fmm, torch_cuda, orc):
+    x, m = synth.hernquist(6000, 31)
+    r = orc.run(x, m, 16, 4, 0.6, 1, want_pot=False)
+    ref = None
+    for chunk in (1, 7, 32, 300):
+        f = new_ctx(fmm, torch_cuda)
+        f.set_tiles(chunk, 64 if chunk != 7 else 5)
+        f.build(x, m, 16)
+        a = np.empty((6000, 3))
+        f.forces(4, 0.6, 1, a, None)
+        m2l, p2p = f.get_lists()
+        assert np.array_equal(m2l, r.m2l) and np.array_equal(p2p, r.p2p)
+        assert rel(a, r.acc) < TOL, chunk
+        ref = a if ref is None else ref
+        assert rel(a, ref) < 1e-14
+        f.close()
+    f = new_ctx(fmm, torch_cuda)
+    for bad in ((0, 64), (32, 0), (5000, 64)):
+        with pytest.raises(fmm.FMMError) as e:
+            f.set_tiles(*bad)
+        assert e.value.status == -1
+    f.close()
+
+
+def test_autotune_picks_a_candidate_and_leaves_the_context_built(fmm, torch_cuda, orc):
+    x, m, off = synth.batch(6, 77, 500, 4000)
+    f = new_ctx(fmm, torch_cuda, 1)
+    leaf, chunk, ms = f.autotune(x, m, 4, 0.6, 1, leaf_sizes=(8, 32), m2l_chunks=(16, 64), offsets=off, reps=1)
+    assert leaf in (8, 32) and chunk in (16, 64) and ms > 0
+    a = np.empty_like(x)
+    f.forces(4, 0.6, 1, a, None)
+    # the same as an ordinary build with the winning leaf size, system by system
+    for s in range(6):
+        lo, hi = int(off[s]), int(off[s + 1])
+        r = orc.run(x[lo:hi], m[lo:hi], leaf, 4, 0.6, 1, want_pot=False, want_internals=False)
+        assert rel(a[lo:hi], r.acc) < MODE_TOL[1], s
+    f.close()
