@@ -40,7 +40,9 @@ namespace gbfmm {
 
 constexpr int EB = 128;
 
-// a5 P2M: moments of every leaf from its particles (y = X - Z)
+// a5 P2M: moments of every leaf from its particles (y = X - Z), one thread per leaf.  (A warp
+// per leaf with a butterfly reduction was 4x slower: every lane then runs the reduction's
+// binary64 adds, and binary64 warp instructions cost the same with idle lanes.)
 template <int P>
 __global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                             const int* __restrict__ nnchild, const double* __restrict__ xs,
@@ -60,7 +62,6 @@ __global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfir
 #pragma unroll
     for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = M[k];
 }
-
 
 // ---- range scaling helpers (binary32 and double-float kernels)
 

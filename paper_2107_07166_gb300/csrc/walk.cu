@@ -13,7 +13,7 @@
 // partners in increasing id order, which is also the canonical (min id, max id) order,
 // and every later sum runs in that order.  The order in which a frontier step emits its
 // outputs therefore cannot change any result, so one kernel per step claims output
-// slots with warp-aggregated integer atomics, and the host launches a fixed number of
+// slots with block-aggregated integer atomics, and the host launches a fixed number of
 // steps (2 x levels + 2 bounds the recursion depth) without waiting between them.  The
 // counters keep counting past the buffers' capacity; one read at the end detects an
 // overflow and the walk is run again with buffers of the reported sizes.
@@ -89,59 +89,73 @@ struct WalkCounters {
     int n_m2l, n_p2p;
 };
 
-__device__ __forceinline__ int warp_claim(int* counter, int want, unsigned lane_lt) {
-    // exclusive prefix of `want` over the warp and one atomic per warp
-    int incl = want;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int o = __shfl_up_sync(FULL, incl, d);
-        if ((int)(threadIdx.x & 31) >= d) incl += o;
-    }
-    int total = __shfl_sync(FULL, incl, 31);
-    int base = 0;
-    if ((threadIdx.x & 31) == 31 && total > 0) base = atomicAdd(counter, total);
-    base = __shfl_sync(FULL, base, 31);
-    (void)lane_lt;
-    return base + incl - want;
-}
+// One frontier step.  A block takes WB * WIPT frontier items per round (WIPT per thread),
+// decides them, forms every thread's output offsets with one block scan and claims the
+// block's output ranges with one atomic per counter, then writes.  Claiming per warp put
+// three same-address atomics on every 32 items and made the step contention-bound.
+constexpr int WIPT = 4;
 
-__global__ void walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out, WalkCounters* __restrict__ cnt,
-                            int par, NodeView nv, double theta, float th2, int2* __restrict__ m2l, int cap_m2l,
-                            int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
+__global__ void __launch_bounds__(WB) walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out,
+                                                  WalkCounters* __restrict__ cnt, int par, NodeView nv, double theta,
+                                                  float th2, int2* __restrict__ m2l, int cap_m2l,
+                                                  int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
+    __shared__ int sbase[3];
     int nf = min(cnt->nf[par], cap_fr);  // a frontier beyond the buffer was not stored (retried)
-    int lane = threadIdx.x & 31;
-    int64_t warp0 = ((int64_t)blockIdx.x * WB + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * WB) >> 5;
-    for (int64_t base = warp0 * 32; base < nf; base += nwarps * 32) {
-        int64_t i = base + lane;
-        int2 it = make_int2(0, 0);
-        int d = -1, nnew = 0;
-        bool sa = false;
-        if (i < nf) {
-            it = fr_in[i];
-            d = decide(nv, it, theta, th2, &nnew, &sa);
+    for (int64_t base = (int64_t)blockIdx.x * WB * WIPT; base < nf; base += (int64_t)gridDim.x * WB * WIPT) {
+        int2 it[WIPT];
+        int d[WIPT], nnew[WIPT];
+        bool sa[WIPT];
+        Cnt3 mine{0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < WIPT; j++) {
+            int64_t i = base + (int64_t)j * WB + threadIdx.x;
+            d[j] = -1;
+            nnew[j] = 0;
+            sa[j] = false;
+            it[j] = make_int2(0, 0);
+            if (i < nf) {
+                it[j] = fr_in[i];
+                d[j] = decide(nv, it[j], theta, th2, &nnew[j], &sa[j]);
+            }
+            mine.a += d[j] == 1;
+            mine.b += d[j] == 2;
+            mine.c += d[j] == 0 ? nnew[j] : 0;
         }
-        int om = warp_claim(&cnt->n_m2l, d == 1 ? 1 : 0, 0);
-        int op = warp_claim(&cnt->n_p2p, d == 2 ? 1 : 0, 0);
-        int of = warp_claim(&cnt->nf[par ^ 1], d == 0 ? nnew : 0, 0);
-        if (d == 1) {
-            if (om < cap_m2l) m2l[om] = it;
-        } else if (d == 2) {
-            if (op < cap_p2p) p2p[op] = it;
-        } else if (d == 0) {
-            if (it.x == it.y) {
-                int c0 = nv.child_first[it.x], nc = nv.nchild[it.x];
-                int k = of;
-                for (int a = 0; a < nc; a++)
-                    for (int b = a; b < nc; b++, k++)
-                        if (k < cap_fr) fr_out[k] = make_int2(c0 + a, c0 + b);
-            } else {
-                int S = sa ? it.x : it.y;
-                int c0 = nv.child_first[S], nc = nv.nchild[S];
-                for (int a = 0; a < nc; a++)
-                    if (of + a < cap_fr) fr_out[of + a] = sa ? make_int2(c0 + a, it.y) : make_int2(it.x, c0 + a);
+        Cnt3 tot;
+        Cnt3 off = block_exclusive_scan(mine, &tot);
+        if (threadIdx.x == 0) {
+            sbase[0] = tot.a ? atomicAdd(&cnt->n_m2l, tot.a) : 0;
+            sbase[1] = tot.b ? atomicAdd(&cnt->n_p2p, tot.b) : 0;
+            sbase[2] = tot.c ? atomicAdd(&cnt->nf[par ^ 1], tot.c) : 0;
+        }
+        __syncthreads();
+        int om = sbase[0] + off.a, op = sbase[1] + off.b, of = sbase[2] + off.c;
+#pragma unroll
+        for (int j = 0; j < WIPT; j++) {
+            if (d[j] == 1) {
+                if (om < cap_m2l) m2l[om] = it[j];
+                om++;
+            } else if (d[j] == 2) {
+                if (op < cap_p2p) p2p[op] = it[j];
+                op++;
+            } else if (d[j] == 0) {
+                if (it[j].x == it[j].y) {
+                    int c0 = nv.child_first[it[j].x], nc = nv.nchild[it[j].x];
+                    int k = of;
+                    for (int a = 0; a < nc; a++)
+                        for (int b = a; b < nc; b++, k++)
+                            if (k < cap_fr) fr_out[k] = make_int2(c0 + a, c0 + b);
+                } else {
+                    int S = sa[j] ? it[j].x : it[j].y;
+                    int c0 = nv.child_first[S], nc = nv.nchild[S];
+                    for (int a = 0; a < nc; a++)
+                        if (of + a < cap_fr)
+                            fr_out[of + a] = sa[j] ? make_int2(c0 + a, it[j].y) : make_int2(it[j].x, c0 + a);
+                }
+                of += nnew[j];
             }
         }
+        __syncthreads();  // sbase is reused by the next round
     }
 }
 
