@@ -125,7 +125,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nrmax, &c->mom, &c->loc, &c->locp, &c->fr0,
                           &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
-                          &c->p2p_dir, &c->p2p_dval, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
+                          &c->p2p_dval, &c->p2p_psize, &c->big_off, &c->big_k, &c->big_v, &c->big_k2, &c->big_v2, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
@@ -400,39 +400,46 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_get_lists: NULL context");
     if (c->list_theta < 0) return fail(FMM_ERR_STATE, "fmm_get_lists: call fmm_forces first");
     return guarded(c, [&]() -> int {
-        int b = c->id_bits;
-        uint64_t mask = (1ull << b) - 1ull;
-        // the directed entries with target < source, in sorted order, are the canonical list
+        size_t nn = (size_t)c->n_nodes;
+        // every target's segment lists its partners in increasing id: the entries with
+        // target < partner (<= for P2P, whose self pairs have one entry) in segment order
+        // are the canonical list
         if (m2l && c->n_m2l > 0) {
-            std::vector<uint64_t> k(2 * (size_t)c->n_m2l);
-            copy_out(c, k.data(), c->m2l_dir.p, sizeof(uint64_t) * k.size());
+            std::vector<long long> seg(nn + 1);
+            std::vector<uint32_t> src(2 * (size_t)c->n_m2l);
+            copy_out(c, seg.data(), c->m2l_seg.p, sizeof(long long) * seg.size());
+            copy_out(c, src.data(), c->m2l_dir.p, sizeof(uint32_t) * src.size());
             GB_CUDA(cudaStreamSynchronize(c->stream));
             std::vector<int32_t> out;
             out.reserve(2 * (size_t)c->n_m2l);
-            for (uint64_t e : k) {
-                int32_t t = (int32_t)(e >> b), s = (int32_t)(e & mask);
-                if (t < s) {
-                    out.push_back(t);
-                    out.push_back(s);
-                }
-            }
+            for (size_t t = 0; t < nn; t++)
+                for (long long e = seg[t]; e < seg[t + 1]; e++)
+                    if ((int64_t)src[e] > (int64_t)t) {
+                        out.push_back((int32_t)t);
+                        out.push_back((int32_t)src[e]);
+                    }
             GB_CUDA(cudaMemcpy(m2l, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
         }
         if (p2p && c->n_p2p > 0) {
-            std::vector<uint64_t> k(2 * (size_t)c->n_p2p);
-            copy_out(c, k.data(), c->p2p_dir.p, sizeof(uint64_t) * k.size());
+            std::vector<long long> seg(nn + 1);
+            std::vector<int2> pairs((size_t)c->n_p2p);
+            copy_out(c, seg.data(), c->p2p_seg.p, sizeof(long long) * seg.size());
+            GB_CUDA(cudaStreamSynchronize(c->stream));
+            std::vector<uint32_t> val((size_t)seg[nn]);
+            copy_out(c, val.data(), c->p2p_dval.p, sizeof(uint32_t) * val.size());
+            copy_out(c, pairs.data(), c->p2p_pairs.p, sizeof(int2) * pairs.size());
             GB_CUDA(cudaStreamSynchronize(c->stream));
             std::vector<int32_t> out;
             out.reserve(2 * (size_t)c->n_p2p);
-            uint64_t invalid = (1ull << (2 * b)) - 1ull;
-            for (uint64_t e : k) {
-                if (e == invalid) continue;
-                int32_t t = (int32_t)(e >> b), s = (int32_t)(e & mask);
-                if (t <= s) {
-                    out.push_back(t);
-                    out.push_back(s);
+            for (size_t t = 0; t < nn; t++)
+                for (long long e = seg[t]; e < seg[t + 1]; e++) {
+                    int2 pr = pairs[val[e] >> 1];
+                    int32_t partner = (val[e] & 1u) ? pr.x : pr.y;
+                    if ((int64_t)partner >= (int64_t)t) {
+                        out.push_back((int32_t)t);
+                        out.push_back(partner);
+                    }
                 }
-            }
             GB_CUDA(cudaMemcpy(p2p, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
         }
         return FMM_OK;

@@ -6,7 +6,7 @@
 //   mom[n * NM + k]     raw moments M_alpha about Z_n, alpha in generated order
 //   loc[n * NM + k]     standard locals L_gamma                       (variant 0)
 //   loc[n * NSU + k]    conserving locals [S | Ux | Uy | Uz]          (variants 1 and 2)
-//   m2l_dir[e]          directed entry tgt << bits | src, sorted; m2l_seg[n] = first entry of n
+//   m2l_dir[e]          source id of entry e; m2l_seg[n] = first entry of target n (sources increase)
 //
 // Range scaling of the binary32 and double-float M2L (their exponent range is binary32's).
 // A tensor of order n at separation R grows like R^-(n+1) (R^-(n+3) for the conserving
@@ -86,12 +86,12 @@ __device__ __forceinline__ float dsep(float ah, float al, float bh, float bl) {
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // the item unit exponent: min over the item's sources of floor(log2 |R|_inf)
-__device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint64_t* __restrict__ dir, uint64_t mask,
+__device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint32_t* __restrict__ dir,
                                         const float4* __restrict__ zh, const float4* __restrict__ zl) {
     float4 ah = zh[tgt], al = zl[tgt];
     int k = 100;
     for (int e = e0; e < e1; e++) {
-        int src = (int)(dir[e] & mask);
+        int src = (int)dir[e];
         float4 bh = zh[src], bl = zl[src];
         k = min(k, sep_exp(dsep(ah.x, al.x, bh.x, bl.x), dsep(ah.y, al.y, bh.y, bl.y), dsep(ah.z, al.z, bh.z, bl.z)));
     }
@@ -203,7 +203,7 @@ struct M2LGeom {
 // exponent to kpart[item] in the scaled modes); m2l_reduce_k sums a cell's items in order.
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __restrict__ items,
-                                                const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                                const uint32_t* __restrict__ dir, M2LGeom g,
                                                 const T* __restrict__ mom, T* __restrict__ part,
                                                 int* __restrict__ kpart) {
     using E = Exp<P>;
@@ -214,14 +214,13 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
     T L[E::NM];
 #pragma unroll
     for (int k = 0; k < E::NM; k++) L[k] = T(0);
-    uint64_t mask = (1ull << bits) - 1ull;
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
         kpart[it] = kI;
     }
     for (int e = w.y; e < w.z; e++) {
-        int src = (int)(dir[e] & mask);
+        int src = (int)dir[e];
         T rx, ry, rz;
         SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
         T D[E::NM];
@@ -257,7 +256,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
 // and form the conserving ones on load
 template <int P, class T>
 __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __restrict__ items,
-                                                const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                                const uint32_t* __restrict__ dir, M2LGeom g,
                                                 const T* __restrict__ cmom, T* __restrict__ part,
                                                 int* __restrict__ kpart) {
     using E = Exp<P>;
@@ -268,14 +267,13 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     T SU[E::NSU];
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) SU[k] = T(0);
-    uint64_t mask = (1ull << bits) - 1ull;
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
         kpart[it] = kI;
     }
     for (int e = w.y; e < w.z; e++) {
-        int src = (int)(dir[e] & mask);
+        int src = (int)dir[e];
         T rx, ry, rz;
         SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
         T H[E::NQ];
@@ -323,7 +321,7 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
 // Moment order (10 entries): 1 | x y z | xx xy xz yy yz zz; locals [S | Ux | Uy | Uz], 4 each.
 template <class T>
 __global__ void __launch_bounds__(EB) m2l_p0_k(int64_t nitems, const int4* __restrict__ items,
-                                               const uint64_t* __restrict__ dir, int bits, M2LGeom g,
+                                               const uint32_t* __restrict__ dir, M2LGeom g,
                                                const T* __restrict__ mom, T* __restrict__ part,
                                                int* __restrict__ kpart) {
     constexpr bool SC = !std::is_same<T, double>::value;
@@ -334,14 +332,13 @@ __global__ void __launch_bounds__(EB) m2l_p0_k(int64_t nitems, const int4* __res
     T SU[NSU];
 #pragma unroll
     for (int k = 0; k < NSU; k++) SU[k] = T(0);
-    uint64_t mask = (1ull << bits) - 1ull;
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, mask, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
         kpart[it] = kI;
     }
     for (int e = w.y; e < w.z; e++) {
-        int src = (int)(dir[e] & mask);
+        int src = (int)dir[e];
         T r[3];
         SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, r[0], r[1], r[2]);
         // scaled modes: the terms are formed in entry units (|R'| ~ 1) and moved to item
@@ -654,7 +651,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     using E = Exp<P>;
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
-    const uint64_t* dir = c->m2l_dir.as<uint64_t>();
+    const uint32_t* dir = c->m2l_dir.as<uint32_t>();
     const ItemSet& it = c->m2l_items;
     int64_t ni = it.n_items;
     bool native = c->precision == FMM_FP64;
@@ -681,7 +678,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         if constexpr (P == 2) {
             ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
             if (ni > 0) {
-                m2l_p0_k<T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, mom, part,
+                m2l_p0_k<T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,
                                                             kpart);
                 GB_LAUNCH("m2l_p0_k");
             }
@@ -691,7 +688,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
-            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, cmom, part,
+            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, cmom, part,
                                                             kpart);
             GB_LAUNCH("m2l_con_k");
         }
@@ -701,7 +698,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
         if (ni > 0) {
-            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, c->id_bits, g, mom, part,
+            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,
                                                             kpart);
             GB_LAUNCH("m2l_std_k");
         }

@@ -18,6 +18,7 @@
 // counters keep counting past the buffers' capacity; one read at the end detects an
 // overflow and the walk is run again with buffers of the reported sizes.
 #include <algorithm>
+#include <vector>
 
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
@@ -180,50 +181,261 @@ __global__ void walk_init_k(WalkCounters* cnt, int2* fr0, int* max_fr, int nsys)
     }
 }
 
-// directed M2L entries: (A -> B) and (B -> A) for every mutual pair
-__global__ void m2l_dir_k(const int2* __restrict__ pairs, int64_t n, int bits, uint64_t* __restrict__ keys) {
+// ---- per-target segments of the directed lists
+// Every mutual pair (A, B) gives a directed entry for target A (partner B) and, unless
+// A == B, one for target B (partner A).  Entries are counted per target (integer atomics),
+// the counts scanned into segment starts, the entries scattered into their target's
+// segment in any order, and every segment then sorted by its key, which starts with the
+// partner id: each cell sees its partners in increasing id, the canonical order, whatever
+// order the walk and the scatter produced.  The key is the partner (M2L) or
+// partner << 32 | (pair << 1 | side) (P2P); the low 32 bits are kept.
+
+__global__ void seg_count_k(const int2* __restrict__ pairs, int64_t n, int* __restrict__ cnt) {
     int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
     if (k >= n) return;
     int2 p = pairs[k];
-    keys[2 * k] = ((uint64_t)p.x << bits) | (uint64_t)p.y;
-    keys[2 * k + 1] = ((uint64_t)p.y << bits) | (uint64_t)p.x;
+    atomicAdd(&cnt[p.x], 1);
+    if (p.x != p.y) atomicAdd(&cnt[p.y], 1);
 }
 
-// directed P2P entries carry (pair << 1 | side); a self pair has one entry, its second
-// slot holds the all-ones key, which sorts after every real entry
-__global__ void p2p_dir_k(const int2* __restrict__ pairs, int64_t n, int bits, uint64_t* __restrict__ keys,
-                          uint32_t* __restrict__ vals, const int* __restrict__ count, long long* __restrict__ psize) {
+__global__ void seg_scatter_k(const int2* __restrict__ pairs, int64_t n, bool payload,
+                              const long long* __restrict__ seg, int* __restrict__ cur,
+                              uint64_t* __restrict__ keys) {
     int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
     if (k >= n) return;
     int2 p = pairs[k];
-    keys[2 * k] = ((uint64_t)p.x << bits) | (uint64_t)p.y;
-    vals[2 * k] = (uint32_t)(2 * k);
+    uint64_t ka = payload ? ((uint64_t)(uint32_t)p.y << 32) | (uint64_t)(uint32_t)(2 * k) : (uint64_t)(uint32_t)p.y;
+    keys[seg[p.x] + atomicAdd(&cur[p.x], 1)] = ka;
     if (p.x != p.y) {
-        keys[2 * k + 1] = ((uint64_t)p.y << bits) | (uint64_t)p.x;
-        vals[2 * k + 1] = (uint32_t)(2 * k + 1);
-        psize[k] = (long long)count[p.x] + count[p.y];
-    } else {
-        keys[2 * k + 1] = (1ull << (2 * bits)) - 1ull;
-        vals[2 * k + 1] = 0xffffffffu;
-        psize[k] = count[p.x];
+        uint64_t kb = payload ? ((uint64_t)(uint32_t)p.x << 32) | (uint64_t)(uint32_t)(2 * k + 1)
+                              : (uint64_t)(uint32_t)p.x;
+        keys[seg[p.y] + atomicAdd(&cur[p.y], 1)] = kb;
     }
 }
 
-// seg[x] = first sorted entry whose target is >= x (binary search), x in [0, nn]
-__global__ void seg_bounds_k(const uint64_t* __restrict__ keys, int64_t n, int bits, int nn,
-                             long long* __restrict__ seg) {
-    int x = blockIdx.x * WB + threadIdx.x;
-    if (x > nn) return;
-    uint64_t key = (uint64_t)x << bits;
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (keys[mid] < key)
-            lo = mid + 1;
-        else
-            hi = mid;
+// partial slots of every P2P pair: nA + nB (a self pair: nA)
+__global__ void p2p_psize_k(const int2* __restrict__ pairs, int64_t n, const int* __restrict__ count,
+                            long long* __restrict__ psize) {
+    int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
+    if (k >= n) return;
+    int2 p = pairs[k];
+    psize[k] = p.x != p.y ? (long long)count[p.x] + count[p.y] : (long long)count[p.x];
+}
+
+// Segments of at most 256 entries (most): one warp per segment, a bitonic network on
+// NR = 1, 2, 4 or 8 registers per lane (wider register networks measured slower than the
+// shared-memory sort below).  Element e = r * 32 + lane sits in register r of
+// the lane; a compare-exchange at distance j < 32 is a shuffle, at j >= 32 a register swap.
+// Padding is the largest key, so it sorts to the end.
+template <int NR>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[NR], int lane) {
+    constexpr int P2 = 32 * NR;
+#pragma unroll
+    for (int k = 2; k <= P2; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    int q = r ^ jr;
+                    if (q > r) {
+                        int e = r * 32 + lane;
+                        bool up = (e & k) == 0;
+                        uint64_t a = v[r], b = v[q];
+                        bool sw = (a > b) == up;
+                        v[r] = sw ? b : a;
+                        v[q] = sw ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    int e = r * 32 + lane;
+                    uint64_t o = __shfl_xor_sync(FULL, v[r], j);
+                    bool lower = (lane & j) == 0;  // this lane holds the lower index of the pair
+                    bool up = (e & k) == 0;
+                    // the lower index keeps the min when ascending, the max when descending
+                    bool keep_min = lower == up;
+                    v[r] = keep_min ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
+                }
+            }
+        }
     }
-    seg[x] = lo;
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_sort_segment(const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
+                                                  long long s0, int L, int lane) {
+    uint64_t v[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        int e = r * 32 + lane;
+        v[r] = e < L ? keys[s0 + e] : ~0ull;
+    }
+    warp_bitonic<NR>(v, lane);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        int e = r * 32 + lane;
+        if (e < L) out[s0 + e] = (uint32_t)v[r];
+    }
+}
+
+constexpr int SS_WARP_MAX = 256, SS_MAX = 4096, SSB = 256;
+
+__global__ void __launch_bounds__(SSB) seg_sort_warp_k(const long long* __restrict__ seg, int nn,
+                                                       const uint64_t* __restrict__ keys, uint32_t* __restrict__ out) {
+    int lane = threadIdx.x & 31;
+    int64_t w0 = ((int64_t)blockIdx.x * SSB + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * SSB) >> 5;
+    for (int64_t x = w0; x < nn; x += nw) {
+        long long s0 = seg[x];
+        int L = (int)(seg[x + 1] - s0);  // uniform over the warp
+        if (L <= 1) {
+            if (L == 1 && lane == 0) out[s0] = (uint32_t)keys[s0];
+        } else if (L <= 32) {
+            warp_sort_segment<1>(keys, out, s0, L, lane);
+        } else if (L <= 64) {
+            warp_sort_segment<2>(keys, out, s0, L, lane);
+        } else if (L <= 128) {
+            warp_sort_segment<4>(keys, out, s0, L, lane);
+        } else if (L <= SS_WARP_MAX) {
+            warp_sort_segment<8>(keys, out, s0, L, lane);
+        }
+    }
+}
+
+// Segments of 257 .. SS_MAX entries: one block per segment, bitonic sort in shared
+// memory.  Longer segments are listed in big[] for the fallback below.
+__global__ void __launch_bounds__(SSB) seg_sort_small_k(const long long* __restrict__ seg, int nn,
+                                                        const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
+                                                        int* __restrict__ big, int* __restrict__ nbig) {
+    __shared__ uint64_t sk[SS_MAX];
+    for (int x = blockIdx.x; x < nn; x += gridDim.x) {
+        long long s0 = seg[x];
+        int L = (int)(seg[x + 1] - s0);
+        if (L <= SS_WARP_MAX) continue;  // sorted by seg_sort_warp_k; uniform over the block
+        if (L > SS_MAX) {
+            if (threadIdx.x == 0) big[atomicAdd(nbig, 1)] = x;
+            continue;
+        }
+        int P2 = 2;
+        while (P2 < L) P2 <<= 1;
+        for (int i = threadIdx.x; i < P2; i += SSB) sk[i] = i < L ? keys[s0 + i] : ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= P2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P2; i += SSB) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        uint64_t a = sk[i], b = sk[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            sk[i] = b;
+                            sk[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < L; i += SSB) out[s0 + i] = (uint32_t)sk[i];
+        __syncthreads();
+    }
+}
+
+// fallback for the rare long segments (sparse halo cells with thousands of partners):
+// their entries are copied with the key (rank of the segment << bits | partner), radix
+// sorted together, and the payloads written back
+__global__ void big_gather_k(const int* __restrict__ big, const long long* __restrict__ boff,
+                             const long long* __restrict__ seg, const uint64_t* __restrict__ keys, int bits,
+                             bool payload, uint64_t* __restrict__ bkeys, uint32_t* __restrict__ bvals) {
+    int b = blockIdx.x;
+    int x = big[b];
+    long long s0 = seg[x], L = seg[x + 1] - s0, o = boff[b];
+    for (long long i = threadIdx.x; i < L; i += SSB) {
+        uint64_t k = keys[s0 + i];
+        uint64_t partner = payload ? (k >> 32) : k;
+        bkeys[o + i] = ((uint64_t)b << bits) | partner;
+        bvals[o + i] = (uint32_t)k;
+    }
+}
+
+__global__ void big_scatter_k(const int* __restrict__ big, const long long* __restrict__ boff,
+                              const long long* __restrict__ seg, const uint32_t* __restrict__ bvals,
+                              uint32_t* __restrict__ out) {
+    int b = blockIdx.x;
+    int x = big[b];
+    long long s0 = seg[x], L = seg[x + 1] - s0, o = boff[b];
+    for (long long i = threadIdx.x; i < L; i += SSB) out[s0 + i] = bvals[o + i];
+}
+
+// builds seg[0..nn] and the sorted per-target lists out[] of the pairs[0..n)
+static void build_segments(fmm_ctx* c, const int2* pairs, int64_t n, int nn, bool payload, DevBuf& seg_buf,
+                           DevBuf& out_buf) {
+    cudaStream_t s = c->stream;
+    int bits = c->id_bits;
+    ensure(seg_buf, sizeof(long long) * (size_t)(nn + 1));
+    ensure(c->seg_cnt, sizeof(int) * (size_t)(2 * nn + 2));
+    int* cnt = c->seg_cnt.as<int>();
+    int* cur = cnt + nn + 1;
+    GB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(2 * nn + 2), s));
+    if (n > 0) {
+        seg_count_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, cnt);
+        GB_LAUNCH("seg_count_k");
+    }
+    long long* seg = seg_buf.as<long long>();
+    scan_i64(c, cnt, nn, seg);
+    int64_t ne = 0;
+    GB_CUDA(cudaMemcpyAsync(&ne, seg + nn, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    ensure(c->keys1, sizeof(uint64_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
+    ensure(out_buf, sizeof(uint32_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
+    ensure(c->cnt_off, sizeof(int) * 2);
+    int* nbig_d = c->cnt_off.as<int>();
+    GB_CUDA(cudaMemsetAsync(nbig_d, 0, sizeof(int), s));
+    uint64_t* keys = c->keys1.as<uint64_t>();
+    if (n > 0) {
+        seg_scatter_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, payload, seg, cur, keys);
+        GB_LAUNCH("seg_scatter_k");
+    }
+    ensure(c->flags, sizeof(int) * (size_t)(nn > 0 ? nn : 1));
+    int* big = c->flags.as<int>();
+    int dev_sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int g = std::min<int64_t>(nn, (int64_t)dev_sms * 8);
+    if (g > 0) {
+        seg_sort_warp_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>());
+        GB_LAUNCH("seg_sort_warp_k");
+        seg_sort_small_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>(), big, nbig_d);
+        GB_LAUNCH("seg_sort_small_k");
+    }
+    int nbig = 0;
+    GB_CUDA(cudaMemcpyAsync(&nbig, nbig_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (nbig == 0) return;
+    // the long segments, in a fixed order (by cell id), sorted together
+    std::vector<int> bh(nbig);
+    GB_CUDA(cudaMemcpy(bh.data(), big, sizeof(int) * nbig, cudaMemcpyDeviceToHost));
+    std::sort(bh.begin(), bh.end());
+    std::vector<long long> sh(2 * (size_t)nbig);
+    for (int b = 0; b < nbig; b++) {
+        GB_CUDA(cudaMemcpy(&sh[2 * b], seg + bh[b], sizeof(long long) * 2, cudaMemcpyDeviceToHost));
+    }
+    std::vector<long long> boff(nbig + 1, 0);
+    for (int b = 0; b < nbig; b++) boff[b + 1] = boff[b] + (sh[2 * b + 1] - sh[2 * b]);
+    int64_t tot = boff[nbig];
+    GB_CUDA(cudaMemcpyAsync(big, bh.data(), sizeof(int) * nbig, cudaMemcpyHostToDevice, s));
+    ensure(c->big_off, sizeof(long long) * (size_t)(nbig + 1));
+    GB_CUDA(cudaMemcpyAsync(c->big_off.p, boff.data(), sizeof(long long) * (nbig + 1), cudaMemcpyHostToDevice, s));
+    ensure(c->big_k, sizeof(uint64_t) * (size_t)tot);
+    ensure(c->big_v, sizeof(uint32_t) * (size_t)tot);
+    big_gather_k<<<nbig, SSB, 0, s>>>(big, c->big_off.as<long long>(), seg, keys, bits, payload,
+                                      c->big_k.as<uint64_t>(), c->big_v.as<uint32_t>());
+    GB_LAUNCH("big_gather_k");
+    int bb = 1;
+    while (((int64_t)1 << bb) <= nbig) bb++;
+    radix_sort(c, c->big_k, c->big_k2, &c->big_v, &c->big_v2, tot, bits + bb);
+    big_scatter_k<<<nbig, SSB, 0, s>>>(big, c->big_off.as<long long>(), seg, c->big_v.as<uint32_t>(),
+                                       out_buf.as<uint32_t>());
+    GB_LAUNCH("big_scatter_k");
+    GB_CUDA(cudaStreamSynchronize(s));
 }
 
 // Work items over segments seg[0..n]: every segment is cut into chunks of CH entries.
@@ -338,34 +550,19 @@ void run_walk(fmm_ctx* c, double theta) {
     c->n_p2p = n_p2p;
     int bits = bits_for(nn);
     c->id_bits = bits;
-    // M2L: directed entries sorted by (target, source)
-    int64_t nd = 2 * n_m2l;
-    ensure(c->m2l_dir, sizeof(uint64_t) * (size_t)(nd > 0 ? nd : 1));
-    ensure(c->m2l_seg, sizeof(long long) * (size_t)(nn + 1));
-    if (n_m2l > 0) {
-        m2l_dir_k<<<grid_for(n_m2l, WB), WB, 0, s>>>(c->m2l_pairs.as<int2>(), n_m2l, bits, c->m2l_dir.as<uint64_t>());
-        GB_LAUNCH("m2l_dir_k");
-        radix_sort(c, c->m2l_dir, c->keys1, nullptr, nullptr, nd, 2 * bits);
-    }
-    seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->m2l_dir.as<uint64_t>(), nd, bits, (int)nn,
-                                                    c->m2l_seg.as<long long>());
-    GB_LAUNCH("seg_bounds_k");
-    // P2P: directed entries with payload (pair << 1 | side), plus partial offsets
-    int64_t np = 2 * n_p2p;
-    ensure(c->p2p_dir, sizeof(uint64_t) * (size_t)np);
-    ensure(c->p2p_dval, sizeof(uint32_t) * (size_t)np);
+    // M2L: per-target segments of source ids in increasing order
+    build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, false, c->m2l_seg, c->m2l_dir);
+    // P2P: per-target segments of (pair << 1 | side) in increasing partner order, plus the
+    // partial offsets of every pair
     ensure(c->p2p_off, sizeof(long long) * (size_t)(n_p2p + 1));
-    ensure(c->p2p_seg, sizeof(long long) * (size_t)(nn + 1));
-    ensure(c->flags, sizeof(long long) * (size_t)(n_p2p + 1));  // per-pair partial sizes
-    p2p_dir_k<<<grid_for(n_p2p, WB), WB, 0, s>>>(c->p2p_pairs.as<int2>(), n_p2p, bits, c->p2p_dir.as<uint64_t>(),
-                                                 c->p2p_dval.as<uint32_t>(), c->ncount.as<int>(),
-                                                 c->flags.as<long long>());
-    GB_LAUNCH("p2p_dir_k");
-    scan_i64_from_i64(c, c->flags.as<long long>(), n_p2p, c->p2p_off.as<long long>());
-    radix_sort(c, c->p2p_dir, c->keys1, &c->p2p_dval, &c->vals1, np, 2 * bits);
-    seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->p2p_dir.as<uint64_t>(), np, bits, (int)nn,
-                                                    c->p2p_seg.as<long long>());
-    GB_LAUNCH("seg_bounds_k");
+    ensure(c->p2p_psize, sizeof(long long) * (size_t)(n_p2p + 1));
+    if (n_p2p > 0) {
+        p2p_psize_k<<<grid_for(n_p2p, WB), WB, 0, s>>>(c->p2p_pairs.as<int2>(), n_p2p, c->ncount.as<int>(),
+                                                      c->p2p_psize.as<long long>());
+        GB_LAUNCH("p2p_psize_k");
+    }
+    scan_i64_from_i64(c, c->p2p_psize.as<long long>(), n_p2p, c->p2p_off.as<long long>());
+    build_segments(c, c->p2p_pairs.as<int2>(), n_p2p, (int)nn, true, c->p2p_seg, c->p2p_dval);
     // work items: m2l_chunk M2L sources (default 32) and p2p_chunk P2P entries (64) per chunk
     build_items(c, c->m2l_seg.as<long long>(), (int)nn, c->m2l_chunk, c->m2l_items);
     build_items(c, c->p2p_seg.as<long long>(), (int)nn, c->p2p_chunk, c->p2p_items);
