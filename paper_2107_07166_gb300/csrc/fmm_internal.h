@@ -137,6 +137,9 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_cls, p2p_list;           // ring-kernel size classes: flags/ranks, pair lists
     int64_t p2p_ncls[4] = {0, 0, 0, 0};        // pairs per size class
     int64_t walk_gen = 0, p2p_cls_gen = -1;    // walks run so far; walk the classes belong to
+    int64_t gather_gen = -1;                   // walk the P2P item slots and entry bases belong to
+    long long p2p_nslots = 0;                  // particle slots over all P2P reduction items
+    gbfmm::DevBuf p2p_pbase;                   // int64 first partial slot of every directed P2P entry
     bool pos_valid = false;
     gbfmm::DevBuf momT;                        // raw moments in the pair-kernel type (range-scaled, padded)
     gbfmm::DevBuf nk;                          // per-node moment unit exponent (scaled modes)

@@ -486,14 +486,22 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
 // item's entries (increasing partner id) into ipart[islot[item] + slot].
 //   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
 //   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
-__device__ __forceinline__ double to_acc(double v, double) { return v; }
-__device__ __forceinline__ df64 to_acc(df64 v, df64) { return v; }
-__device__ __forceinline__ df64 to_acc(float v, df64) { return df64(v, 0.f); }
+// acc + v for the item sums: binary64 and double-float partials add as usual; a binary32
+// partial is added to the double-float sum by TwoSum on the high word with the rounding
+// error gathered in the low word (left unnormalised until the end: a few dozen terms keep
+// it far inside the high word's last bits)
+__device__ __forceinline__ double acc_add(double acc, double v) { return acc + v; }
+__device__ __forceinline__ df64 acc_add(df64 acc, df64 v) { return acc + v; }
+__device__ __forceinline__ df64 acc_add(df64 acc, float v) {
+    df64 t = two_sum(acc.hi, v);
+    return df64(t.hi, __fadd_rn(acc.lo, t.lo));
+}
+__device__ __forceinline__ double acc_fin(double a) { return a; }
+__device__ __forceinline__ df64 acc_fin(df64 a) { return fast_two_sum(a.hi, a.lo); }
 
 template <class G, class PT>
 __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
-                                                   const int* __restrict__ ncount, const uint32_t* __restrict__ pdval,
-                                                   const int2* __restrict__ pairs, const long long* __restrict__ poff,
+                                                   const int* __restrict__ ncount, const long long* __restrict__ pbase,
                                                    const Quad<PT>* __restrict__ part,
                                                    const long long* __restrict__ islot, Quad<G>* __restrict__ ipart) {
     int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;
@@ -503,18 +511,41 @@ __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* _
     int cnt = ncount[w.x];
     for (int slot = lane; slot < cnt; slot += 32) {
         Quad<G> acc{G(0), G(0), G(0), G(0)};
-        for (int e = w.y; e < w.z; e++) {
-            uint32_t v = pdval[e];
-            uint32_t k = v >> 1;
-            long long o = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll) + slot;
-            Quad<PT> q = part[o];
-            acc.x = acc.x + to_acc(q.x, G());
-            acc.y = acc.y + to_acc(q.y, G());
-            acc.z = acc.z + to_acc(q.z, G());
-            acc.w = acc.w + to_acc(q.w, G());
+        int e = w.y;
+        // four partials in flight at a time; the sum still runs in entry order
+        for (; e + 4 <= w.z; e += 4) {
+            Quad<PT> q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = part[pbase[e + u] + slot];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                acc.x = acc_add(acc.x, q[u].x);
+                acc.y = acc_add(acc.y, q[u].y);
+                acc.z = acc_add(acc.z, q[u].z);
+                acc.w = acc_add(acc.w, q[u].w);
+            }
         }
-        ipart[islot[it] + slot] = acc;
+        for (; e < w.z; e++) {
+            Quad<PT> q = part[pbase[e] + slot];
+            acc.x = acc_add(acc.x, q.x);
+            acc.y = acc_add(acc.y, q.y);
+            acc.z = acc_add(acc.z, q.z);
+            acc.w = acc_add(acc.w, q.w);
+        }
+        ipart[islot[it] + slot] = Quad<G>{acc_fin(acc.x), acc_fin(acc.y), acc_fin(acc.z), acc_fin(acc.w)};
     }
+}
+
+// first partial slot of every directed P2P entry: its pair's block, then (for side 1) past
+// the first leaf's slots
+__global__ void p2p_pbase_k(int64_t ne, const uint32_t* __restrict__ pdval, const int2* __restrict__ pairs,
+                            const long long* __restrict__ poff, const int* __restrict__ ncount,
+                            long long* __restrict__ pbase) {
+    int64_t e = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (e >= ne) return;
+    uint32_t v = pdval[e];
+    uint32_t k = v >> 1;
+    pbase[e] = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll);
 }
 
 // slot offsets of the P2P items: islot[i] = sum of the leaf sizes of items before i
@@ -524,8 +555,9 @@ __global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, con
     if (i < nitems) sizes[i] = ncount[items[i].x];
 }
 
-template <class G, class PT>
-static void gather_launch(fmm_ctx* c) {
+// item slots and entry bases depend only on the lists: formed once per walk
+static void gather_setup(fmm_ctx* c) {
+    if (c->gather_gen == c->walk_gen) return;
     cudaStream_t s = c->stream;
     const ItemSet& it = c->p2p_items;
     int64_t ni = it.n_items;
@@ -534,15 +566,38 @@ static void gather_launch(fmm_ctx* c) {
     item_slots_k<<<grid_for(ni, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(), c->flags.as<long long>());
     GB_LAUNCH("item_slots_k");
     scan_i64_from_i64(c, c->flags.as<long long>(), ni, c->p2p_islot.as<long long>());
-    long long nslots = 0;
-    GB_CUDA(cudaMemcpyAsync(&nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    long long ne = 0;
+    GB_CUDA(cudaMemcpyAsync(&c->p2p_nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long),
+                            cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&ne, c->p2p_seg.as<long long>() + c->n_nodes, sizeof(long long), cudaMemcpyDeviceToHost,
+                            s));
     GB_CUDA(cudaStreamSynchronize(s));
+    ensure(c->p2p_pbase, sizeof(long long) * (size_t)(ne > 0 ? ne : 1));
+    if (ne > 0) {
+        p2p_pbase_k<<<grid_for(ne, PB), PB, 0, s>>>(ne, c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
+                                                    c->p2p_off.as<long long>(), c->ncount.as<int>(),
+                                                    c->p2p_pbase.as<long long>());
+        GB_LAUNCH("p2p_pbase_k");
+    }
+    c->gather_gen = c->walk_gen;
+}
+
+template <class G, class PT>
+static void gather_launch(fmm_ctx* c) {
+    cudaStream_t s = c->stream;
+    gather_setup(c);
+    const ItemSet& it = c->p2p_items;
+    int64_t ni = it.n_items;
+    long long nslots = c->p2p_nslots;
     ensure(c->p2p_ipart, sizeof(Quad<G>) * (size_t)(nslots > 0 ? nslots : 1));
-    p2p_gather_k<G, PT><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
-                                                              c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
-                                                              c->p2p_off.as<long long>(), c->p2p_part.as<Quad<PT>>(),
-                                                              c->p2p_islot.as<long long>(), c->p2p_ipart.as<Quad<G>>());
-    GB_LAUNCH("p2p_gather_k");
+    if (ni > 0) {
+        p2p_gather_k<G, PT><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
+                                                                  c->p2p_pbase.as<long long>(),
+                                                                  c->p2p_part.as<Quad<PT>>(),
+                                                                  c->p2p_islot.as<long long>(),
+                                                                  c->p2p_ipart.as<Quad<G>>());
+        GB_LAUNCH("p2p_gather_k");
+    }
 }
 
 void run_p2p_gather(fmm_ctx* c) {
