@@ -44,8 +44,10 @@ typedef struct fmm_ctx fmm_ctx;
 #define GBFMM_API
 #endif
 
-/* highest multipole order compiled into the library, and into its FMM_DF64 mode */
-#define FMM_P_MAX 6
+/* highest multipole order compiled into the library (binary64), and into its FMM_MIXED
+ * and FMM_DF64 modes */
+#define FMM_P_MAX 8
+#define FMM_MIXED_P_MAX 6
 #define FMM_DF64_P_MAX 5
 
 /* variants */

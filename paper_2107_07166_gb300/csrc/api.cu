@@ -240,6 +240,8 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
     if (!(theta >= 0.0 && theta < 1.0)) return fail(FMM_ERR_INVALID, "fmm_forces: theta must be in [0, 1)");
     if (c->precision == FMM_DF64 && p > FMM_DF64_P_MAX)
         return fail(FMM_ERR_INVALID, "fmm_forces: FMM_DF64 supports p <= FMM_DF64_P_MAX");
+    if (c->precision == FMM_MIXED && p > FMM_MIXED_P_MAX)
+        return fail(FMM_ERR_INVALID, "fmm_forces: FMM_MIXED supports p <= FMM_MIXED_P_MAX");
     if (variant != FMM_STANDARD && variant != FMM_CONSERVING && variant != FMM_CONSERVING_PAPER0)
         return fail(FMM_ERR_INVALID, "fmm_forces: unknown variant");
     if (variant == FMM_CONSERVING_PAPER0 && p != 1)

@@ -18,6 +18,8 @@ void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc, double* p
         case 4: call(4); break;                                         \
         case 5: call(5); break;                                         \
         case 6: call(6); break;                                         \
+        case 7: call(7); break;                                         \
+        case 8: call(8); break;                                         \
         default: throw FmmError{FMM_ERR_INVALID, "order p out of range"}; \
     }
 

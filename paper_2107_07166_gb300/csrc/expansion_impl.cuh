@@ -688,9 +688,13 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
-            m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, cmom, part,
-                                                            kpart);
-            GB_LAUNCH("m2l_con_k");
+            if constexpr (P >= 7) {
+                m2l_generic_launch(c, P, 1, reinterpret_cast<double*>(part));
+            } else {
+                m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, cmom, part,
+                                                                kpart);
+                GB_LAUNCH("m2l_con_k");
+            }
         }
         reduce(m2l_reduce_k<E::NSU, E::NQ, 1, T>, E::NSU, c->loc.as<double>());
     }
@@ -698,9 +702,13 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;
         ensure(L, sizeof(double) * (size_t)nn * E::NM);
         if (ni > 0) {
-            m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,
-                                                            kpart);
-            GB_LAUNCH("m2l_std_k");
+            if constexpr (P >= 7) {
+                m2l_generic_launch(c, P, 0, reinterpret_cast<double*>(part));
+            } else {
+                m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,
+                                                                kpart);
+                GB_LAUNCH("m2l_std_k");
+            }
         }
         reduce(m2l_reduce_k<E::NM, E::NQ, 0, T>, E::NM, L.as<double>());
     }
@@ -715,24 +723,31 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
         m2l_launch<P, double>(c, variant, std_locals);
     else if (c->precision == FMM_DF64) {
         if constexpr (P <= FMM_DF64_P_MAX) m2l_launch<P, df64>(c, variant, std_locals);
-    } else
-        m2l_launch<P, float>(c, variant, std_locals);
+    } else {
+        if constexpr (P <= FMM_MIXED_P_MAX) m2l_launch<P, float>(c, variant, std_locals);
+    }
     stage_end(c, ST_M2L);
     stage_begin(c, ST_L2L);
     for (int l = 1; l < c->n_levels; l++) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];
-        if (variant != 0) {
-            l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
-                                                              c->nZy.as<double>(), c->nZz.as<double>(),
-                                                              c->loc.as<double>());
-            GB_LAUNCH("l2l_con_k");
-        }
-        if (std_locals) {
-            DevBuf& L = variant == 0 ? c->loc : c->locp;
-            l2l_std_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
-                                                              c->nZy.as<double>(), c->nZz.as<double>(),
-                                                              L.as<double>());
-            GB_LAUNCH("l2l_std_k");
+        if constexpr (P >= 7) {
+            // table-driven at the high orders (straight-line shifts take minutes to compile)
+            if (variant != 0) l2l_generic_launch(c, P, 1, lo, hi, c->loc.as<double>());
+            if (std_locals) l2l_generic_launch(c, P, 0, lo, hi, (variant == 0 ? c->loc : c->locp).as<double>());
+        } else {
+            if (variant != 0) {
+                l2l_con_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(), c->nZx.as<double>(),
+                                                                  c->nZy.as<double>(), c->nZz.as<double>(),
+                                                                  c->loc.as<double>());
+                GB_LAUNCH("l2l_con_k");
+            }
+            if (std_locals) {
+                DevBuf& L = variant == 0 ? c->loc : c->locp;
+                l2l_std_k<P><<<grid_for(hi - lo, EB), EB, 0, s>>>(lo, hi, c->nparent.as<int>(),
+                                                                  c->nZx.as<double>(), c->nZy.as<double>(),
+                                                                  c->nZz.as<double>(), L.as<double>());
+                GB_LAUNCH("l2l_std_k");
+            }
         }
     }
     stage_end(c, ST_L2L);

@@ -186,6 +186,11 @@ void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
 // particle-particle + final reduction (p2p.cu)
 void run_p2p(fmm_ctx* c, bool want_pot);
 void run_p2p_gather(fmm_ctx* c);
+
+// high-order (p = 7, 8) binary64 M2L into the item partials and L2L of one level
+// (high_order.cu)
+void m2l_generic_launch(fmm_ctx* c, int p, int variant, double* part);
+void l2l_generic_launch(fmm_ctx* c, int p, int variant, int lo, int hi, double* loc);
 void run_gather_out(fmm_ctx* c, int p, int variant, bool want_pot, double* acc_out, double* pot_out);
 void run_diagnostics(fmm_ctx* c, double* out6_host);
 void run_diagnostics_sys(fmm_ctx* c, double* out_dev);

@@ -32,7 +32,8 @@ import os
 import sys
 from fractions import Fraction
 
-PMAX = 6  # orders compiled into the library
+PMAX = 8  # orders compiled into the library (M2L of p = 7, 8: the table-driven m2l_generic.cu)
+MIXED_PMAX = 6  # highest order of the binary32 M2L (p = 7, 8 run in binary64 only)
 DF64_PMAX = 5  # highest order of the double-float M2L (p = 6 takes minutes to compile)
 
 
@@ -407,7 +408,7 @@ def main(outdir):
                f"// generated: expansion stages of order p = {p}\n" + inc +
                f"namespace gbfmm {{\nGBFMM_INSTANTIATE({p})\n}}\n")
         for tname, t in (("f64", "double"), ("f32", "float"), ("df64", "df64")):
-            if t == "df64" and p > DF64_PMAX:
+            if (t == "df64" and p > DF64_PMAX) or (t == "float" and p > MIXED_PMAX):
                 continue
             _write(os.path.join(outdir, f"expansion_p{p}_{tname}.cu"),
                    f"// generated: M2L of order p = {p} in {t}\n" + inc +

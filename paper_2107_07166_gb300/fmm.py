@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(HERE, "libgbfmm.so")
 
 STANDARD, CONSERVING, CONSERVING_PAPER0 = 0, 1, 2
 FP64, MIXED, DF64 = 0, 1, 2
-P_MAX = 6
+P_MAX = 8
+MIXED_P_MAX = 6
 DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_build_batch", "fmm_forces",

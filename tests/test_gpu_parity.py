@@ -98,7 +98,7 @@ def test_parity_against_oracle(fmm, torch_cuda, orc, case, variant):
     g["f"].close()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_order(fmm, torch_cuda, orc, p):
     x, m = synth.plummer(2048, 10 + p)
     for variant in (0, 1):
@@ -607,4 +607,17 @@ def test_autotune_picks_a_candidate_and_leaves_the_context_built(fmm, torch_cuda
         lo, hi = int(off[s]), int(off[s + 1])
         r = orc.run(x[lo:hi], m[lo:hi], leaf, 4, 0.6, 1, want_pot=False, want_internals=False)
         assert rel(a[lo:hi], r.acc) < MODE_TOL[1], s
+    f.close()
+
+
+def test_binary32_order_limit(fmm, torch_cuda):
+    """Orders 7 and 8 run in binary64 only: the binary32 mode refuses them."""
+    x, m = synth.plummer(1000, 3)
+    f = new_ctx(fmm, torch_cuda, 1)
+    f.build(x, m, 16)
+    acc = np.full((1000, 3), 7.0)
+    with pytest.raises(fmm.FMMError) as e:
+        f.forces(fmm.MIXED_P_MAX + 1, 0.5, 1, acc, None)
+    assert e.value.status == -1
+    assert np.all(acc == 7.0)
     f.close()
