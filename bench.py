@@ -136,10 +136,10 @@ def algorithmic_flops(counts, tree_counts, p, variant):
             "per_m2l_pair": per_m2l}
 
 
-# DRAM bytes (read + write) per unit of the dominant kernels, from one ncu --set full
-# capture of the current kernels at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md),
-# scaled here by the units of the timed launch: per mutual M2L pair, per particle pair.
-NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 68.3, ("p2p_k", "fp64"): 5.25}
+# DRAM bytes (read + write) per unit of the dominant binary64 kernels, from an ncu capture
+# of their DRAM counters at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md), scaled
+# here by the units of the timed launch: per mutual M2L pair, per particle pair.
+NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 58.7, ("p2p_k", "fp64"): 5.19}
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
