@@ -125,7 +125,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nrmax, &c->mom, &c->loc, &c->locp, &c->fr0,
                           &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
-                          &c->p2p_dval, &c->p2p_psize, &c->p2p_pbase, &c->big_off, &c->big_k, &c->big_v, &c->big_k2, &c->big_v2, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
+                          &c->p2p_dval, &c->p2p_psize, &c->p2p_pbase, &c->big_off, &c->big_k, &c->big_v, &c->big_k2, &c->big_v2, &c->seg_mid, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,

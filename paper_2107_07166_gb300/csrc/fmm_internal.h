@@ -121,6 +121,7 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]
     gbfmm::DevBuf p2p_psize;                   // int64 partial slots per P2P pair
     gbfmm::DevBuf big_off, big_k, big_v, big_k2, big_v2;  // long-segment fallback of the list sort
+    gbfmm::DevBuf seg_mid;                     // list segments for the shared-memory sort
     gbfmm::DevBuf p2p_off;                     // int64 [n_p2p + 1] partial offsets
     gbfmm::DevBuf p2p_part;                    // double4 partials
     gbfmm::DevBuf seg_cnt;

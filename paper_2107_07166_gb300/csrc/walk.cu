@@ -284,7 +284,9 @@ __device__ __forceinline__ void warp_sort_segment(const uint64_t* __restrict__ k
 constexpr int SS_WARP_MAX = 256, SS_MAX = 4096, SSB = 256;
 
 __global__ void __launch_bounds__(SSB) seg_sort_warp_k(const long long* __restrict__ seg, int nn,
-                                                       const uint64_t* __restrict__ keys, uint32_t* __restrict__ out) {
+                                                       const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
+                                                       int* __restrict__ mid, int* __restrict__ cnt2,
+                                                       int* __restrict__ big) {
     int lane = threadIdx.x & 31;
     int64_t w0 = ((int64_t)blockIdx.x * SSB + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * SSB) >> 5;
     for (int64_t x = w0; x < nn; x += nw) {
@@ -300,43 +302,46 @@ __global__ void __launch_bounds__(SSB) seg_sort_warp_k(const long long* __restri
             warp_sort_segment<4>(keys, out, s0, L, lane);
         } else if (L <= SS_WARP_MAX) {
             warp_sort_segment<8>(keys, out, s0, L, lane);
+        } else if (lane == 0) {
+            // longer segments are listed for the block sort or the long-segment fallback
+            if (L <= SS_MAX)
+                mid[atomicAdd(&cnt2[0], 1)] = (int)x;
+            else
+                big[atomicAdd(&cnt2[1], 1)] = (int)x;
         }
     }
 }
 
-// Segments of 257 .. SS_MAX entries: one block per segment, bitonic sort in shared
-// memory.  Longer segments are listed in big[] for the fallback below.
-__global__ void __launch_bounds__(SSB) seg_sort_small_k(const long long* __restrict__ seg, int nn,
+// Segments of 257 .. SS_MAX entries, from the list seg_sort_warp_k made: one block per
+// segment, bitonic sort in shared memory.
+__global__ void __launch_bounds__(SSB) seg_sort_small_k(const long long* __restrict__ seg,
                                                         const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
-                                                        int* __restrict__ big, int* __restrict__ nbig) {
+                                                        const int* __restrict__ mid, const int* __restrict__ cnt2) {
     __shared__ uint64_t sk[SS_MAX];
-    for (int x = blockIdx.x; x < nn; x += gridDim.x) {
+    int nmid = cnt2[0];
+    for (int i = blockIdx.x; i < nmid; i += gridDim.x) {
+        int x = mid[i];
         long long s0 = seg[x];
         int L = (int)(seg[x + 1] - s0);
-        if (L <= SS_WARP_MAX) continue;  // sorted by seg_sort_warp_k; uniform over the block
-        if (L > SS_MAX) {
-            if (threadIdx.x == 0) big[atomicAdd(nbig, 1)] = x;
-            continue;
-        }
         int P2 = 2;
         while (P2 < L) P2 <<= 1;
-        for (int i = threadIdx.x; i < P2; i += SSB) sk[i] = i < L ? keys[s0 + i] : ~0ull;
+        for (int j = threadIdx.x; j < P2; j += SSB) sk[j] = j < L ? keys[s0 + j] : ~0ull;
         __syncthreads();
         for (int k = 2; k <= P2; k <<= 1)
             for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < P2; i += SSB) {
-                    int ixj = i ^ j;
-                    if (ixj > i) {
-                        uint64_t a = sk[i], b = sk[ixj];
-                        if ((a > b) == ((i & k) == 0)) {
-                            sk[i] = b;
-                            sk[ixj] = a;
+                for (int a = threadIdx.x; a < P2; a += SSB) {
+                    int ixj = a ^ j;
+                    if (ixj > a) {
+                        uint64_t u = sk[a], v = sk[ixj];
+                        if ((u > v) == ((a & k) == 0)) {
+                            sk[a] = v;
+                            sk[ixj] = u;
                         }
                     }
                 }
                 __syncthreads();
             }
-        for (int i = threadIdx.x; i < L; i += SSB) out[s0 + i] = (uint32_t)sk[i];
+        for (int j = threadIdx.x; j < L; j += SSB) out[s0 + j] = (uint32_t)sk[j];
         __syncthreads();
     }
 }
@@ -388,8 +393,9 @@ static void build_segments(fmm_ctx* c, const int2* pairs, int64_t n, int nn, boo
     ensure(c->keys1, sizeof(uint64_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
     ensure(out_buf, sizeof(uint32_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
     ensure(c->cnt_off, sizeof(int) * 2);
-    int* nbig_d = c->cnt_off.as<int>();
-    GB_CUDA(cudaMemsetAsync(nbig_d, 0, sizeof(int), s));
+    int* cnt2 = c->cnt_off.as<int>();  // [segments for the block sort, long segments]
+    int* nbig_d = cnt2 + 1;
+    GB_CUDA(cudaMemsetAsync(cnt2, 0, sizeof(int) * 2, s));
     uint64_t* keys = c->keys1.as<uint64_t>();
     if (n > 0) {
         seg_scatter_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, payload, seg, cur, keys);
@@ -397,13 +403,15 @@ static void build_segments(fmm_ctx* c, const int2* pairs, int64_t n, int nn, boo
     }
     ensure(c->flags, sizeof(int) * (size_t)(nn > 0 ? nn : 1));
     int* big = c->flags.as<int>();
+    ensure(c->seg_mid, sizeof(int) * (size_t)(nn > 0 ? nn : 1));
+    int* mid = c->seg_mid.as<int>();
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int g = std::min<int64_t>(nn, (int64_t)dev_sms * 8);
     if (g > 0) {
-        seg_sort_warp_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>());
+        seg_sort_warp_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>(), mid, cnt2, big);
         GB_LAUNCH("seg_sort_warp_k");
-        seg_sort_small_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>(), big, nbig_d);
+        seg_sort_small_k<<<g, SSB, 0, s>>>(seg, keys, out_buf.as<uint32_t>(), mid, cnt2);
         GB_LAUNCH("seg_sort_small_k");
     }
     int nbig = 0;

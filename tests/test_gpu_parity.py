@@ -621,3 +621,16 @@ def test_binary32_order_limit(fmm, torch_cuda):
     assert e.value.status == -1
     assert np.all(acc == 7.0)
     f.close()
+
+
+def test_long_list_segments(fmm, torch_cuda, orc):
+    """theta = 0 with one particle per leaf: every leaf has about N - 1 P2P partners, so the
+    per-target list segments exceed the shared-memory sort (4096 entries) and take the
+    long-segment path; lists and forces must still match the oracle and the direct sum."""
+    x, m = synth.plummer(5000, 29)
+    r = orc.run(x, m, 1, 2, 0.0, 0, want_pot=False)
+    g = run_gpu(fmm, torch_cuda, x, m, 1, 2, 0.0, 0, want_pot=False)
+    m2l, p2p = g["f"].get_lists()
+    assert np.array_equal(p2p, r.p2p) and np.array_equal(m2l, r.m2l)
+    assert rel(g["acc"], r.acc) < 1e-13
+    g["f"].close()
