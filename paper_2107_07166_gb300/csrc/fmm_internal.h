@@ -135,8 +135,9 @@ struct fmm_ctx {
     gbfmm::DevBuf tune_acc;                    // output of the autotuner's trial evaluations
     gbfmm::DevBuf pos4;                        // packed (x, y, z, m) per sorted particle, storage type
     gbfmm::DevBuf p2p_sep;                     // centre separation of every P2P pair, storage type
-    gbfmm::DevBuf p2p_cls, p2p_list;           // ring-kernel size classes: flags/ranks, pair lists
-    int64_t p2p_ncls[4] = {0, 0, 0, 0};        // pairs per size class
+    gbfmm::DevBuf p2p_cls, p2p_cls2;           // ring-kernel class keys of the P2P pairs (+ sort scratch)
+    gbfmm::DevBuf p2p_list, p2p_list2;         // P2P pair ids in class order (+ sort scratch)
+    gbfmm::DevBuf p2p_tab;                     // ring class table: start, count, warp prefix per width
     int64_t walk_gen = 0, p2p_cls_gen = -1;    // walks run so far; walk the classes belong to
     int64_t gather_gen = -1;                   // walk the P2P item slots and entry bases belong to
     long long p2p_nslots = 0;                  // particle slots over all P2P reduction items
@@ -169,7 +170,6 @@ void release(DevBuf& b);
 void scan_int(fmm_ctx* c, const int* in, int64_t n, int* out);
 void scan_i64(fmm_ctx* c, const int* in, int64_t n, long long* out);
 void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* out);
-void scan_cnt3(fmm_ctx* c, const Cnt3* in, int64_t n, Cnt3* out);
 // radix sort of keys [+ values] on bits [0, bits); result in place
 void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
 

@@ -70,7 +70,6 @@ void scan_i64(fmm_ctx* c, const int* in, int64_t n, long long* out) { scan_impl<
 void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* out) {
     scan_impl<long long, long long>(c, in, n, out);
 }
-void scan_cnt3(fmm_ctx* c, const Cnt3* in, int64_t n, Cnt3* out) { scan_impl<Cnt3, Cnt3>(c, in, n, out); }
 
 // ------------------------------------------------------------------ radix sort
 

@@ -198,108 +198,193 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
     }
 }
 
-// The ring form of the same pair kernel, for leaves of at most 32 particles: a segment of
-// SEG lanes takes one leaf pair (32 / SEG pairs per warp, pairs taken from a list of one
-// size class).  Lane i of the segment holds particle a_i of A (shifted by R = Z_A - Z_B) in
-// registers and B's particles sit in shared memory.  In step k lane i meets b_j,
-// j = (i + k) mod L, L = max(nA, nB): over L steps every (a_i, b_j) meets exactly once.  The
-// pair force is formed once and applied to both partners: a_i's sum stays in lane i, b_j's
-// sum travels with the ring (one shuffle from lane i + 1 per step) and is back in lane j
-// after a full turn.  A self pair is evaluated from both ends (its travelling sums are
-// dropped), which costs twice the pair arithmetic for 1/L of the work and needs no
-// reduction.  Every sum runs in a fixed order.
-template <class T, bool POT, int SEG>
-__global__ void __launch_bounds__(PB) p2p_ring_k(int64_t nlist, const int* __restrict__ list,
+// Ring classes.  A leaf pair with both leaves of at most 32 particles runs as a ring over
+// its smaller leaf: w = min(nA, nB) slots (a self pair: w = nA), while the larger leaf
+// passes through the ring in m = ceil(max(nA, nB) / w) chunks of at most w particles.  The
+// pairs are ordered by the key (w - 1) * 32 + (m - 1) (pairs with a larger leaf take
+// RING_BIG), stably, so the order is fixed by the list; a warp then carries 32 / w
+// segments of one width with similar chunk counts.  A ring over the larger leaf would
+// leave nA nB / max(nA, nB)^2 of its lane steps busy, about half for Plummer leaves.
+constexpr int RING_BIG = 32 * 32;
+constexpr int RING_KEY_BITS = 11;
+
+struct RingTab {
+    int start[34];  // first list index of width w = 1..32; [33]: pairs with a leaf above 32
+    int count[34];  // pairs of width w
+    int wpre[34];   // ring warps before width w; wpre[33]: all ring warps
+};
+
+__device__ __forceinline__ unsigned ring_key(int2 p, const int* __restrict__ ncount) {
+    int nA = ncount[p.x], nB = ncount[p.y];
+    if (nA > 32 || nB > 32) return RING_BIG;
+    if (p.x == p.y) return (unsigned)(nA - 1) * 32u;
+    int w = min(nA, nB), g = max(nA, nB);
+    return (unsigned)(w - 1) * 32u + (unsigned)((g + w - 1) / w - 1);
+}
+
+// class of a key: the width w (1..32), or 33 for RING_BIG
+__device__ __forceinline__ int ring_cls(uint64_t key) { return (int)(key >> 5) + 1; }
+
+__global__ void p2p_ring_key_k(int64_t n, const int2* __restrict__ pairs, const int* __restrict__ ncount,
+                               uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (k >= n) return;
+    keys[k] = ring_key(pairs[k], ncount);
+    vals[k] = (uint32_t)k;
+}
+
+// first index and one-past-last index of every class present in the sorted keys (the
+// table was set to -1 before)
+__global__ void p2p_ring_bounds_k(int64_t n, const uint64_t* __restrict__ keys, RingTab* __restrict__ tab) {
+    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (k >= n) return;
+    int c = ring_cls(keys[k]);
+    if (k == 0 || ring_cls(keys[k - 1]) != c) tab->start[c] = (int)k;
+    if (k == n - 1 || ring_cls(keys[k + 1]) != c) tab->count[c] = (int)(k + 1);
+}
+
+__global__ void p2p_ring_tab_k(RingTab* __restrict__ tab) {
+    int wp = 0;
+    for (int c = 1; c <= 33; c++) {
+        int st = tab->start[c];
+        int cnt = st < 0 ? 0 : tab->count[c] - st;
+        tab->start[c] = st < 0 ? 0 : st;
+        tab->count[c] = cnt;
+        tab->wpre[c] = wp;
+        if (c <= 32) {
+            int per = 32 / c;
+            wp += (cnt + per - 1) / per;
+        }
+    }
+    tab->start[0] = tab->count[0] = tab->wpre[0] = 0;
+}
+
+// The ring pair kernel for leaves of at most 32 particles.  A warp takes 32 / w segments of
+// w lanes, one leaf pair each.  Lane i of a segment holds particle g = c w + i of the
+// larger ("lane") leaf in chunk c, shifted by that leaf's side of R = Z_A - Z_B; the
+// smaller ("ring") leaf sits in shared memory.  In step k lane i meets ring particle
+// j = (i + k) mod w: over w steps every (g, j) of the chunk meets exactly once.  The pair
+// force is formed once and applied to both partners: g's sum stays in lane i and is stored
+// after its chunk, j's sum travels with the ring (one shuffle from lane i + 1 per step), is
+// back in lane j after every full turn and collects all chunks before it is stored.  A
+// self pair runs one chunk over itself from both ends (each pair twice, 1/w of the work,
+// no reduction) and drops the travelling sums.  Every sum runs in a fixed order.
+template <class T, bool POT>
+__global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
                                                  const int2* __restrict__ pairs, const long long* __restrict__ off,
                                                  const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                  const PState<typename Prec<T>::S>* __restrict__ pos,
                                                  const typename Prec<T>::S* __restrict__ sep,
                                                  Quad<T>* __restrict__ part) {
     using S = typename Prec<T>::S;
-    constexpr int PPW = 32 / SEG;
     __shared__ PState<S> sB[PW][32];
+    __shared__ int ts[34], tc[34], tw[34];
+    for (int t = threadIdx.x; t < 34; t += PB) {
+        ts[t] = tab->start[t];
+        tc[t] = tab->count[t];
+        tw[t] = tab->wpre[t];
+    }
+    __syncthreads();
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int i = lane % SEG, base = lane - i;
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
-    for (int64_t q = gw; q * PPW < nlist; q += nw) {
-        int64_t li = q * PPW + lane / SEG;
-        int A = 0, B = 0, nA = 0, nB = 0, fA = 0, fB = 0;
+    int64_t total = tw[33];
+    for (int64_t q = gw; q < total; q += nw) {
+        // the width of this warp: the largest W with tw[W] <= q (tw is nondecreasing)
+        int W = 1;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (W + step <= 32 && tw[W + step] <= q) W += step;
+        int per = 32 / W;
+        int sg = lane / W;
+        bool live = sg < per;
+        int i = live ? lane - sg * W : 0, base = live ? sg * W : lane;
+        int64_t li = (q - tw[W]) * per + sg;
+        bool ok = live && li < tc[W];
+        int nA = 0, nB = 0, fA = 0, fB = 0;
         long long o = 0;
+        bool self = false;
         S rx = S(0), ry = S(0), rz = S(0);
-        if (li < nlist) {
-            int k = list[li];
+        if (ok) {
+            int k = (int)list[ts[W] + li];
             int2 pr = pairs[k];
-            A = pr.x;
-            B = pr.y;
-            nA = ncount[A];
-            nB = ncount[B];
-            fA = nfirst[A];
-            fB = nfirst[B];
+            self = pr.x == pr.y;
+            nA = ncount[pr.x];
+            nB = ncount[pr.y];
+            fA = nfirst[pr.x];
+            fB = nfirst[pr.y];
             o = off[k];
             rx = sep[3 * k];
             ry = sep[3 * k + 1];
             rz = sep[3 * k + 2];
         }
-        bool self = A == B;
-        PState<S> pa = PState<S>{S(0), S(0), S(0), S(0)};
-        if (i < nA) {
-            PState<S> qa = pos[fA + i];
-            pa = PState<S>{rx + qa.x, ry + qa.y, rz + qa.z, qa.m};
+        // lane leaf: A unless B is the larger; its particles are shifted by its side of R
+        bool laneA = nA >= nB;
+        int fL = laneA ? fA : fB, nL = laneA ? nA : nB, fR = laneA ? fB : fA;
+        long long oL = laneA ? o : o + nA, oR = laneA ? o + nA : o;
+        if (!laneA) {
+            rx = -rx;
+            ry = -ry;
+            rz = -rz;
         }
         __syncwarp();
-        if (i < nB) sB[w][lane] = pos[fB + i];
+        if (ok) sB[w][lane] = pos[fR + i];  // i < W = the ring leaf's count
         __syncwarp();
-        T ma = Prec<T>::mass(pa.m);
-        T ax = T(0), ay = T(0), az = T(0), ap = T(0);
+        int m = ok ? (self ? 1 : (nL + W - 1) / W) : 0;
+        int mmax = __reduce_max_sync(FULL, m);
+        int nxt = live ? base + (i + 1 < W ? i + 1 : 0) : lane;
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);
-        // one ring length for the whole warp (the longest of its segments): a segment with
-        // a shorter ring meets empty slots, and a self pair meets each particle itself at
-        // zero separation, which the r = 0 rule skips; the travelling sums of a self pair
-        // are formed but not stored
-        int L = self ? nA : max(nA, nB);
-        int Lr = __reduce_max_sync(FULL, L);
-        int nxt = base + (i + 1 < Lr ? i + 1 : 0);
-        bool mine = i < nA;
-        int j = i;
-        for (int kk = 0; kk < Lr; kk++) {
-            if (mine && j < nB) {
-                const PState<S>& pb = sB[w][base + j];
-                T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
-                T r2 = dx * dx + dy * dy + dz * dz;
-                if (!is_zero(r2)) {
-                    T ir = rsqrt_t(r2);
-                    T ir3 = ir * ir * ir;
-                    T mb = Prec<T>::mass(pb.m);
-                    T sa = mb * ir3;
-                    ax = fma_t(-sa, dx, ax);
-                    ay = fma_t(-sa, dy, ay);
-                    az = fma_t(-sa, dz, az);
-                    if (POT) ap = fma_t(-mb, ir, ap);
-                    T sb = ma * ir3;
-                    bx = fma_t(sb, dx, bx);
-                    by = fma_t(sb, dy, by);
-                    bz = fma_t(sb, dz, bz);
-                    if (POT) bp = fma_t(-ma, ir, bp);
-                }
+        for (int ch = 0; ch < mmax; ch++) {
+            int g = ch * W + i;
+            bool mine = ok && ch < m && g < nL;
+            PState<S> pa = PState<S>{S(0), S(0), S(0), S(0)};
+            if (mine) {
+                PState<S> qa = pos[fL + g];
+                pa = PState<S>{rx + qa.x, ry + qa.y, rz + qa.z, qa.m};
             }
-            bx = shfl_t(bx, nxt);
-            by = shfl_t(by, nxt);
-            bz = shfl_t(bz, nxt);
-            if (POT) bp = shfl_t(bp, nxt);
-            j = (j + 1 == Lr) ? 0 : j + 1;
+            T ma = Prec<T>::mass(pa.m);
+            T ax = T(0), ay = T(0), az = T(0), ap = T(0);
+            int j = i;
+            for (int kk = 0; kk < W; kk++) {
+                if (mine) {
+                    const PState<S>& pb = sB[w][base + j];
+                    T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
+                    T r2 = dx * dx + dy * dy + dz * dz;
+                    if (!is_zero(r2)) {
+                        T ir = rsqrt_t(r2);
+                        T ir3 = ir * ir * ir;
+                        T mb = Prec<T>::mass(pb.m);
+                        T sa = mb * ir3;
+                        ax = fma_t(-sa, dx, ax);
+                        ay = fma_t(-sa, dy, ay);
+                        az = fma_t(-sa, dz, az);
+                        if (POT) ap = fma_t(-mb, ir, ap);
+                        T sb = ma * ir3;
+                        bx = fma_t(sb, dx, bx);
+                        by = fma_t(sb, dy, by);
+                        bz = fma_t(sb, dz, bz);
+                        if (POT) bp = fma_t(-ma, ir, bp);
+                    }
+                }
+                bx = shfl_t(bx, nxt);
+                by = shfl_t(by, nxt);
+                bz = shfl_t(bz, nxt);
+                if (POT) bp = shfl_t(bp, nxt);
+                j = (j + 1 == W) ? 0 : j + 1;
+            }
+            if (mine) part[oL + g] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
+                                             POT ? Prec<T>::fin(ap) : T(0)};
         }
-        if (mine) part[o + i] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
-                                        POT ? Prec<T>::fin(ap) : T(0)};
-        if (!self && i < nB)
-            part[o + nA + i] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
-                                       POT ? Prec<T>::fin(bp) : T(0)};
+        if (ok && !self)
+            part[oR + i] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
+                                   POT ? Prec<T>::fin(bp) : T(0)};
         __syncwarp();
     }
 }
 
-// pairs with a leaf above 32 particles (only at the deepest level), from the list
+// pairs with a leaf above 32 particles (only at the deepest level), from the end of the
+// sorted list
 template <class T, bool POT>
-__global__ void __launch_bounds__(PB) p2p_big_k(int64_t nlist, const int* __restrict__ list,
+__global__ void __launch_bounds__(PB) p2p_big_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
                                                 const int2* __restrict__ pairs, const long long* __restrict__ off,
                                                 const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                 const PState<typename Prec<T>::S>* __restrict__ pos,
@@ -307,47 +392,13 @@ __global__ void __launch_bounds__(PB) p2p_big_k(int64_t nlist, const int* __rest
                                                 Quad<T>* __restrict__ part) {
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
+    int64_t first = tab->start[33], nlist = tab->count[33];
     for (int64_t li = gw; li < nlist; li += nw) {
-        int k = list[li];
+        int k = (int)list[first + li];
         int2 pr = pairs[k];
         p2p_generic<T, POT>(lane, pr.x == pr.y, nfirst[pr.x], ncount[pr.x], nfirst[pr.y], ncount[pr.y], off[k],
                             sep[3 * k], sep[3 * k + 1], sep[3 * k + 2], pos, part);
     }
-}
-
-// size classes of the ring kernel: L = nA (self) or max(nA, nB); class 0: L <= 8, 1: <= 16,
-// 2: <= 32, 3: above.  flags[k] marks classes 0..2; the exclusive scan of the flags gives
-// each pair its rank in its class, and p2p_fill_k writes the class lists back to back in
-// pair order (a stable partition, so the lists do not depend on scheduling)
-__device__ __forceinline__ int ring_class(int2 p, const int* __restrict__ ncount) {
-    int L = p.x == p.y ? ncount[p.x] : max(ncount[p.x], ncount[p.y]);
-    return L <= 8 ? 0 : (L <= 16 ? 1 : (L <= 32 ? 2 : 3));
-}
-
-__global__ void p2p_class_k(int64_t n, const int2* __restrict__ pairs, const int* __restrict__ ncount,
-                            Cnt3* __restrict__ flags) {
-    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
-    if (k >= n) return;
-    int c = ring_class(pairs[k], ncount);
-    flags[k] = Cnt3{c == 0, c == 1, c == 2};
-}
-
-__global__ void p2p_fill_k(int64_t n, const int2* __restrict__ pairs, const int* __restrict__ ncount,
-                           const Cnt3* __restrict__ rank, int* __restrict__ lists) {
-    int64_t k = (int64_t)blockIdx.x * PB + threadIdx.x;
-    if (k >= n) return;
-    Cnt3 r = rank[k], t = rank[n];
-    int c = ring_class(pairs[k], ncount);
-    int64_t at;
-    if (c == 0)
-        at = r.a;
-    else if (c == 1)
-        at = (int64_t)t.a + r.b;
-    else if (c == 2)
-        at = (int64_t)t.a + t.b + r.c;
-    else
-        at = (int64_t)t.a + t.b + t.c + (k - r.a - r.b - r.c);
-    lists[at] = (int)k;
 }
 
 // centre separation Z_A - Z_B of every P2P pair, formed in binary64 once per pair and
@@ -414,51 +465,51 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
                                                      c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
     GB_LAUNCH("p2p_sep_k");
-    int64_t* ncls = c->p2p_ncls;
-    if (c->p2p_cls_gen != c->walk_gen) {
-        // size classes of the leaf pairs: list bookkeeping, once per walk
+    if constexpr (P2PRing<T>::value) {
         int64_t np = c->n_p2p;
-        ensure(c->p2p_cls, sizeof(Cnt3) * 2 * (size_t)(np + 1));
-        ensure(c->p2p_list, sizeof(int) * (size_t)(np > 0 ? np : 1));
-        Cnt3* flags = c->p2p_cls.as<Cnt3>();
-        Cnt3* rank = flags + np + 1;
-        p2p_class_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_pairs.as<int2>(), c->ncount.as<int>(), flags);
-        GB_LAUNCH("p2p_class_k");
-        scan_cnt3(c, flags, np, rank);
-        p2p_fill_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_pairs.as<int2>(), c->ncount.as<int>(), rank,
-                                                  c->p2p_list.as<int>());
-        GB_LAUNCH("p2p_fill_k");
-        Cnt3 t;
-        GB_CUDA(cudaMemcpyAsync(&t, rank + np, sizeof(Cnt3), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaStreamSynchronize(s));
-        ncls[0] = t.a;
-        ncls[1] = t.b;
-        ncls[2] = t.c;
-        ncls[3] = np - t.a - t.b - t.c;
-        c->p2p_cls_gen = c->walk_gen;
+        if (c->p2p_cls_gen != c->walk_gen && np > 0) {
+            // ring classes of the leaf pairs: list bookkeeping, once per walk
+            ensure(c->p2p_cls, sizeof(uint64_t) * (size_t)np);
+            ensure(c->p2p_list, sizeof(uint32_t) * (size_t)np);
+            ensure(c->p2p_tab, sizeof(RingTab));
+            p2p_ring_key_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_pairs.as<int2>(), c->ncount.as<int>(),
+                                                          c->p2p_cls.as<uint64_t>(), c->p2p_list.as<uint32_t>());
+            GB_LAUNCH("p2p_ring_key_k");
+            radix_sort(c, c->p2p_cls, c->p2p_cls2, &c->p2p_list, &c->p2p_list2, np, RING_KEY_BITS);
+            RingTab* tab = c->p2p_tab.as<RingTab>();
+            GB_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(RingTab), s));
+            p2p_ring_bounds_k<<<grid_for(np, PB), PB, 0, s>>>(np, c->p2p_cls.as<uint64_t>(), tab);
+            GB_LAUNCH("p2p_ring_bounds_k");
+            p2p_ring_tab_k<<<1, 1, 0, s>>>(tab);
+            GB_LAUNCH("p2p_ring_tab_k");
+            c->p2p_cls_gen = c->walk_gen;
+        }
     }
     stage_begin(c, ST_P2P);
     if constexpr (P2PRing<T>::value) {
-        const int* lst = c->p2p_list.as<int>();
-        auto args = [&](auto kern, int64_t nl, const int* l, int per_warp) {
-            if (nl <= 0) return;
-            int64_t bl = (nl + per_warp * PW - 1) / (per_warp * PW);
-            if (bl > cap) bl = cap;
-            kern<<<(unsigned)bl, PB, 0, s>>>(nl, l, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
-                                             c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
-                                             c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
-            GB_LAUNCH("p2p_ring_k");
-        };
-        if (want_pot) {
-            args(p2p_ring_k<T, true, 8>, ncls[0], lst, 4);
-            args(p2p_ring_k<T, true, 16>, ncls[1], lst + ncls[0], 2);
-            args(p2p_ring_k<T, true, 32>, ncls[2], lst + ncls[0] + ncls[1], 1);
-            args(p2p_big_k<T, true>, ncls[3], lst + ncls[0] + ncls[1] + ncls[2], 1);
-        } else {
-            args(p2p_ring_k<T, false, 8>, ncls[0], lst, 4);
-            args(p2p_ring_k<T, false, 16>, ncls[1], lst + ncls[0], 2);
-            args(p2p_ring_k<T, false, 32>, ncls[2], lst + ncls[0] + ncls[1], 1);
-            args(p2p_big_k<T, false>, ncls[3], lst + ncls[0] + ncls[1] + ncls[2], 1);
+        int64_t np = c->n_p2p;
+        if (np > 0) {
+            const RingTab* tab = c->p2p_tab.as<RingTab>();
+            const uint32_t* lst = c->p2p_list.as<uint32_t>();
+            auto run = [&](auto kern, int64_t bl) {
+                kern<<<(unsigned)bl, PB, 0, s>>>(tab, lst, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
+                                                 c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
+                                                 c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
+            };
+            // the warp counts live on the device: persistent grids, warps stride over the work
+            int64_t ring_bl = (np + PW - 1) / PW;
+            if (ring_bl > cap) ring_bl = cap;
+            if (want_pot) {
+                run(p2p_ring_k<T, true>, ring_bl);
+                GB_LAUNCH("p2p_ring_k");
+                run(p2p_big_k<T, true>, dev_sms);
+                GB_LAUNCH("p2p_big_k");
+            } else {
+                run(p2p_ring_k<T, false>, ring_bl);
+                GB_LAUNCH("p2p_ring_k");
+                run(p2p_big_k<T, false>, dev_sms);
+                GB_LAUNCH("p2p_big_k");
+            }
         }
     } else {
         size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
