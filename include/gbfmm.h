@@ -78,7 +78,7 @@ enum {
     FMM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
     FMM_ERR_OOM = -4,      /* device allocation failed */
     FMM_ERR_CAPACITY = -5, /* an internal size limit was exceeded (N >= 2^31, > 2^31 list entries) */
-    FMM_ERR_TIMEOUT = -6   /* reserved for bounded device waits */
+    FMM_ERR_TIMEOUT = -6   /* a bounded device wait ran out (the walk's ordered output claims) */
 };
 
 /* Create a context on CUDA device `device` with arithmetic `precision` (FMM_FP64,

@@ -125,7 +125,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nrmax, &c->mom, &c->loc, &c->locp, &c->fr0,
                           &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
-                          &c->p2p_dval, &c->p2p_psize, &c->p2p_pbase, &c->big_off, &c->big_k, &c->big_v, &c->big_k2, &c->big_v2, &c->seg_mid, &c->p2p_seg, &c->p2p_off, &c->p2p_part, &c->seg_cnt,
+                          &c->p2p_dval, &c->p2p_psize, &c->p2p_pbase, &c->seg_k, &c->seg_k2, &c->seg_v2, &c->walk_status, &c->seg_cnt, &c->p2p_seg, &c->p2p_off, &c->p2p_part,
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
@@ -403,9 +403,8 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
     if (c->list_theta < 0) return fail(FMM_ERR_STATE, "fmm_get_lists: call fmm_forces first");
     return guarded(c, [&]() -> int {
         size_t nn = (size_t)c->n_nodes;
-        // every target's segment lists its partners in increasing id: the entries with
-        // target < partner (<= for P2P, whose self pairs have one entry) in segment order
-        // are the canonical list
+        // the canonical list: for every target in increasing id, its partners above it
+        // (at or above it for P2P, whose self pairs have one entry) in increasing id
         if (m2l && c->n_m2l > 0) {
             std::vector<long long> seg(nn + 1);
             std::vector<uint32_t> src(2 * (size_t)c->n_m2l);
@@ -414,12 +413,17 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
             GB_CUDA(cudaStreamSynchronize(c->stream));
             std::vector<int32_t> out;
             out.reserve(2 * (size_t)c->n_m2l);
-            for (size_t t = 0; t < nn; t++)
+            std::vector<int32_t> part;
+            for (size_t t = 0; t < nn; t++) {
+                part.clear();
                 for (long long e = seg[t]; e < seg[t + 1]; e++)
-                    if ((int64_t)src[e] > (int64_t)t) {
-                        out.push_back((int32_t)t);
-                        out.push_back((int32_t)src[e]);
-                    }
+                    if ((int64_t)src[e] > (int64_t)t) part.push_back((int32_t)src[e]);
+                std::sort(part.begin(), part.end());
+                for (int32_t q : part) {
+                    out.push_back((int32_t)t);
+                    out.push_back(q);
+                }
+            }
             GB_CUDA(cudaMemcpy(m2l, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
         }
         if (p2p && c->n_p2p > 0) {
@@ -433,15 +437,20 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
             GB_CUDA(cudaStreamSynchronize(c->stream));
             std::vector<int32_t> out;
             out.reserve(2 * (size_t)c->n_p2p);
-            for (size_t t = 0; t < nn; t++)
+            std::vector<int32_t> part;
+            for (size_t t = 0; t < nn; t++) {
+                part.clear();
                 for (long long e = seg[t]; e < seg[t + 1]; e++) {
                     int2 pr = pairs[val[e] >> 1];
                     int32_t partner = (val[e] & 1u) ? pr.x : pr.y;
-                    if ((int64_t)partner >= (int64_t)t) {
-                        out.push_back((int32_t)t);
-                        out.push_back(partner);
-                    }
+                    if ((int64_t)partner >= (int64_t)t) part.push_back(partner);
                 }
+                std::sort(part.begin(), part.end());
+                for (int32_t q : part) {
+                    out.push_back((int32_t)t);
+                    out.push_back(q);
+                }
+            }
             GB_CUDA(cudaMemcpy(p2p, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
         }
         return FMM_OK;

@@ -120,11 +120,11 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_dval;                    // uint32 (pair << 1 | side), per-target segments by partner id
     gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]
     gbfmm::DevBuf p2p_psize;                   // int64 partial slots per P2P pair
-    gbfmm::DevBuf big_off, big_k, big_v, big_k2, big_v2;  // long-segment fallback of the list sort
-    gbfmm::DevBuf seg_mid;                     // list segments for the shared-memory sort
+    gbfmm::DevBuf seg_k, seg_k2, seg_v2;       // directed-entry keys of the list sort (+ scratch)
+    gbfmm::DevBuf walk_status;                 // per-tile look-back words of the walk steps
+    gbfmm::DevBuf seg_cnt;                     // per-segment chunk counts of the work items
     gbfmm::DevBuf p2p_off;                     // int64 [n_p2p + 1] partial offsets
     gbfmm::DevBuf p2p_part;                    // double4 partials
-    gbfmm::DevBuf seg_cnt;
     gbfmm::ItemSet m2l_items, p2p_items;
     gbfmm::DevBuf m2l_part;                    // M2L partial locals per item
     gbfmm::DevBuf p2p_islot;                   // long long [items + 1]: slot offsets of P2P items
@@ -172,6 +172,8 @@ void scan_i64(fmm_ctx* c, const int* in, int64_t n, long long* out);
 void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* out);
 // radix sort of keys [+ values] on bits [0, bits); result in place
 void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
+// the same on 32-bit keys
+void radix_sort32(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
 
 // tree (tree.cu)
 int build_tree(fmm_ctx* c, const double* x_dev, const double* m_dev);

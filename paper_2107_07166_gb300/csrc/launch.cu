@@ -73,7 +73,8 @@ void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* ou
 
 // ------------------------------------------------------------------ radix sort
 
-__global__ void rs_hist_k(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+template <class K>
+__global__ void rs_hist_k(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
                           int ntiles) {
     __shared__ uint32_t sh[RS_BINS];
     for (int i = threadIdx.x; i < RS_BINS; i += RS_BLOCK) sh[i] = 0;
@@ -91,10 +92,10 @@ __global__ void rs_hist_k(const uint64_t* __restrict__ keys, int64_t n, int shif
     for (int d = threadIdx.x; d < RS_BINS; d += RS_BLOCK) hist[(int64_t)d * ntiles + blockIdx.x] = sh[d];
 }
 
-template <bool V>
-__global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restrict__ kin,
+template <class K, bool V>
+__global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const K* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin,
-                                                         uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          int64_t n, int shift, const uint32_t* __restrict__ offs,
                                                          int ntiles) {
     __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_BLOCK) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
-    uint64_t k[RS_ITEMS];
+    K k[RS_ITEMS];
     uint32_t v[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
     unsigned lt = (1u << lane) - 1u;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const uint64_t* __restr
     for (int j = 0; j < RS_ITEMS; j++) {
         int64_t i = base + j * 32 + lane;
         bool ok = i < n;
-        k[j] = ok ? kin[i] : 0ull;
+        k[j] = ok ? kin[i] : K(0);
         if (V) v[j] = ok ? vin[i] : 0u;
         unsigned d = ok ? (unsigned)((k[j] >> shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
         unsigned peers = __match_any_sync(FULL, d);
@@ -153,40 +154,42 @@ void rs_pass_raw(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint3
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     int64_t nh = (int64_t)RS_BINS * ntiles;
     int nst = (int)((nh + SCAN_TILE - 1) / SCAN_TILE);
-    rs_hist_k<<<ntiles, RS_BLOCK, 0, s>>>(kin, n, shift, hist, ntiles);
+    rs_hist_k<uint64_t><<<ntiles, RS_BLOCK, 0, s>>>(kin, n, shift, hist, ntiles);
     scan_tiles_k<int, int><<<nst, SCAN_BLOCK, 0, s>>>(reinterpret_cast<const int*>(hist), nh, sums);
     scan_sums_k<int><<<1, SCAN_BLOCK, 0, s>>>(sums, nst);
     scan_apply_k<int, int><<<nst, SCAN_BLOCK, 0, s>>>(reinterpret_cast<const int*>(hist), nh, sums, offs);
-    rs_scatter_k<true><<<ntiles, RS_BLOCK, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                   reinterpret_cast<const uint32_t*>(offs), ntiles);
+    rs_scatter_k<uint64_t, true><<<ntiles, RS_BLOCK, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                             reinterpret_cast<const uint32_t*>(offs), ntiles);
 }
 
-void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits) {
+template <class K>
+static void radix_sort_t(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n,
+                         int bits) {
     if (n <= 1 || bits <= 0) return;
     if (n >= (int64_t)1 << 31) throw FmmError{FMM_ERR_CAPACITY, "radix sort: more than 2^31 keys"};
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
-    ensure(keys_tmp, sizeof(uint64_t) * (size_t)n);
+    ensure(keys_tmp, sizeof(K) * (size_t)n);
     if (vals) ensure(*vals_tmp, sizeof(uint32_t) * (size_t)n);
     ensure(c->rs_hist, sizeof(uint32_t) * (size_t)(RS_BINS * ntiles + 1));
     ensure(c->rs_offs, sizeof(int) * (size_t)(RS_BINS * ntiles + 1));
-    uint64_t* ka = keys.as<uint64_t>();
-    uint64_t* kb = keys_tmp.as<uint64_t>();
+    K* ka = keys.as<K>();
+    K* kb = keys_tmp.as<K>();
     uint32_t* va = vals ? vals->as<uint32_t>() : nullptr;
     uint32_t* vb = vals ? vals_tmp->as<uint32_t>() : nullptr;
     int passes = (bits + RS_BITS - 1) / RS_BITS;
     for (int ps = 0; ps < passes; ps++) {
         int shift = RS_BITS * ps;
         uint32_t* hist = c->rs_hist.as<uint32_t>();
-        rs_hist_k<<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, n, shift, hist, ntiles);
+        rs_hist_k<K><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, n, shift, hist, ntiles);
         GB_LAUNCH("rs_hist_k");
         scan_int(c, reinterpret_cast<const int*>(hist), (int64_t)RS_BINS * ntiles, c->rs_offs.as<int>());
         const uint32_t* offs = reinterpret_cast<const uint32_t*>(c->rs_offs.as<int>());
         if (vals)
-            rs_scatter_k<true><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+            rs_scatter_k<K, true><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, offs, ntiles);
         else
-            rs_scatter_k<false><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, nullptr, kb, nullptr, n, shift, offs, ntiles);
+            rs_scatter_k<K, false><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, nullptr, kb, nullptr, n, shift, offs, ntiles);
         GB_LAUNCH("rs_scatter_k");
-        uint64_t* tk = ka;
+        K* tk = ka;
         ka = kb;
         kb = tk;
         uint32_t* tv = va;
@@ -203,6 +206,14 @@ void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf
             *vals_tmp = u;
         }
     }
+}
+
+void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits) {
+    radix_sort_t<uint64_t>(c, keys, keys_tmp, vals, vals_tmp, n, bits);
+}
+
+void radix_sort32(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits) {
+    radix_sort_t<uint32_t>(c, keys, keys_tmp, vals, vals_tmp, n, bits);
 }
 
 // ------------------------------------------------------------------ stage timers

@@ -8,12 +8,11 @@
 //               otherwise split A or B into its children: a leaf is never split; between
 //               two inner nodes the larger r_max is split, ties -> larger count, then
 //               lower id.
-// The rule is symmetric in (A, B), so the emitted pair set is unique.  The lists are then
-// expanded into directed entries (target, source) and radix-sorted: every cell sees its
-// partners in increasing id order, which is also the canonical (min id, max id) order,
-// and every later sum runs in that order.  The order in which a frontier step emits its
-// outputs therefore cannot change any result, so one kernel per step claims output
-// slots with block-aggregated integer atomics, and the host launches a fixed number of
+// The rule is symmetric in (A, B), so the emitted pair set is unique.  One kernel per
+// frontier step decides its items and places the outputs in frontier order (ordered
+// claims by look-back over tiles), so the pair lists come out in a fixed order; they are
+// then expanded into directed entries (target, partner) and stably radix-sorted by
+// target, and every later sum runs in that order.  The host launches a fixed number of
 // steps (2 x levels + 2 bounds the recursion depth) without waiting between them.  The
 // counters keep counting past the buffers' capacity; one read at the end detects an
 // overflow and the walk is run again with buffers of the reported sizes.
@@ -86,48 +85,112 @@ __device__ __forceinline__ int decide(const NodeView& nv, int2 it, double theta,
 }
 
 struct WalkCounters {
-    int nf[2];       // frontier sizes (read by the step of that parity, appended by the other)
-    int n_m2l, n_p2p;
+    int nf[2];                  // frontier sizes (read by the step of that parity)
+    int n_m2l, n_p2p;           // pairs emitted by the finished steps
+    int ticket;                 // next tile of the running step
+    int step_tot[3];            // M2L pairs, P2P pairs and new items of the running step
+    int err;                    // a wait for a preceding tile ran out (never expected)
 };
 
-// One frontier step.  A block takes WB * WIPT frontier items per round (WIPT per thread),
-// decides them, forms every thread's output offsets with one block scan and claims the
-// block's output ranges with one atomic per counter, then writes.  Claiming per warp put
-// three same-address atomics on every 32 items and made the step contention-bound.
-constexpr int WIPT = 4;
+// One frontier step.  Blocks take tiles of WTILE consecutive frontier items in the order of
+// a ticket counter, decide them (WIPT consecutive items per thread) and form the output
+// offsets inside the tile with one block scan.  The tile's place in the outputs comes
+// from a decoupled look-back over the tiles before it: each tile publishes its counts,
+// then its inclusive prefix, as one 64-bit word (tag << 32 | value) per counter; a
+// waiting tile adds published counts backwards until it meets a prefix.  Tickets are
+// handed out in tile order to running blocks, so every tile waited on has started and
+// publishes its counts without waiting itself.  The outputs therefore keep the frontier
+// order: every list the walk emits is a fixed function of the tree.  The tags carry the
+// step index, so the status words are cleared once per walk.
+constexpr int WIPT = 4, WTILE = WB * WIPT;
+constexpr long long WALK_SPIN_LIMIT = 1ll << 22;  // polls of one status word (~0.1-1 s)
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned tag, int value) {
+    unsigned long long v = ((unsigned long long)tag << 32) | (unsigned)value;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __global__ void __launch_bounds__(WB) walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out,
-                                                  WalkCounters* __restrict__ cnt, int par, NodeView nv, double theta,
-                                                  float th2, int2* __restrict__ m2l, int cap_m2l,
+                                                  WalkCounters* __restrict__ cnt, int par, int step,
+                                                  unsigned long long* __restrict__ status, NodeView nv,
+                                                  double theta, float th2, int2* __restrict__ m2l, int cap_m2l,
                                                   int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
+    __shared__ int s_tile;
     __shared__ int sbase[3];
     int nf = min(cnt->nf[par], cap_fr);  // a frontier beyond the buffer was not stored (retried)
-    for (int64_t base = (int64_t)blockIdx.x * WB * WIPT; base < nf; base += (int64_t)gridDim.x * WB * WIPT) {
+    int bm = cnt->n_m2l, bp = cnt->n_p2p;
+    int ntiles = (nf + WTILE - 1) / WTILE;
+    const unsigned tag_agg = 2u * (unsigned)step + 1u, tag_pre = 2u * (unsigned)step + 2u;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&cnt->ticket, 1);
+        __syncthreads();
+        int tile = s_tile;
+        if (tile >= ntiles) break;
+        int64_t i0 = (int64_t)tile * WTILE + (int64_t)threadIdx.x * WIPT;
         int2 it[WIPT];
         int d[WIPT], nnew[WIPT];
         bool sa[WIPT];
+        if (i0 + WIPT <= nf) {
+            const int4* f4 = reinterpret_cast<const int4*>(fr_in + i0);
+            int4 u = f4[0], v = f4[1];
+            it[0] = make_int2(u.x, u.y);
+            it[1] = make_int2(u.z, u.w);
+            it[2] = make_int2(v.x, v.y);
+            it[3] = make_int2(v.z, v.w);
+        } else {
+#pragma unroll
+            for (int j = 0; j < WIPT; j++) it[j] = i0 + j < nf ? fr_in[i0 + j] : make_int2(0, 0);
+        }
         Cnt3 mine{0, 0, 0};
 #pragma unroll
         for (int j = 0; j < WIPT; j++) {
-            int64_t i = base + (int64_t)j * WB + threadIdx.x;
             d[j] = -1;
             nnew[j] = 0;
             sa[j] = false;
-            it[j] = make_int2(0, 0);
-            if (i < nf) {
-                it[j] = fr_in[i];
-                d[j] = decide(nv, it[j], theta, th2, &nnew[j], &sa[j]);
-            }
+            if (i0 + j < nf) d[j] = decide(nv, it[j], theta, th2, &nnew[j], &sa[j]);
             mine.a += d[j] == 1;
             mine.b += d[j] == 2;
             mine.c += d[j] == 0 ? nnew[j] : 0;
         }
         Cnt3 tot;
         Cnt3 off = block_exclusive_scan(mine, &tot);
-        if (threadIdx.x == 0) {
-            sbase[0] = tot.a ? atomicAdd(&cnt->n_m2l, tot.a) : 0;
-            sbase[1] = tot.b ? atomicAdd(&cnt->n_p2p, tot.b) : 0;
-            sbase[2] = tot.c ? atomicAdd(&cnt->nf[par ^ 1], tot.c) : 0;
+        if (threadIdx.x < 3) {
+            // thread q claims counter q: publish, look back, publish the prefix
+            int q = threadIdx.x;
+            int v = q == 0 ? tot.a : (q == 1 ? tot.b : tot.c);
+            unsigned long long* my = status + 3 * (int64_t)tile + q;
+            int ex = 0;
+            if (tile > 0) {
+                st_status(my, tag_agg, v);
+                int t = tile - 1;
+                long long spins = 0;
+                while (t >= 0) {
+                    unsigned long long w = ld_status(status + 3 * (int64_t)t + q);
+                    unsigned tag = (unsigned)(w >> 32);
+                    if (tag == tag_pre) {
+                        ex += (int)(unsigned)w;
+                        break;
+                    }
+                    if (tag == tag_agg) {
+                        ex += (int)(unsigned)w;
+                        t--;
+                        continue;
+                    }
+                    if (++spins > WALK_SPIN_LIMIT) {  // a tile before this one never published
+                        atomicExch(&cnt->err, 1);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            st_status(my, tag_pre, ex + v);
+            if (tile == ntiles - 1) cnt->step_tot[q] = ex + v;
+            sbase[q] = ex + (q == 0 ? bm : (q == 1 ? bp : 0));
         }
         __syncthreads();
         int om = sbase[0] + off.a, op = sbase[1] + off.b, of = sbase[2] + off.c;
@@ -156,16 +219,22 @@ __global__ void __launch_bounds__(WB) walk_step_k(const int2* __restrict__ fr_in
                 of += nnew[j];
             }
         }
-        __syncthreads();  // sbase is reused by the next round
+        __syncthreads();  // s_tile and sbase are reused by the next tile
     }
 }
 
-// prepares the next step: its input count is this step's output, its output starts at 0;
-// frontier overflow is recorded in *over (the largest frontier seen)
+// closes a step: its totals move into the running counts, its output becomes the next
+// step's input, and the tickets start again; frontier overflow is recorded in *max_fr (the
+// largest frontier seen)
 __global__ void walk_advance_k(WalkCounters* cnt, int par, int* max_fr) {
-    int nxt = cnt->nf[par ^ 1];
+    int nxt = cnt->step_tot[2];
     if (nxt > *max_fr) *max_fr = nxt;
+    cnt->n_m2l += cnt->step_tot[0];
+    cnt->n_p2p += cnt->step_tot[1];
+    cnt->nf[par ^ 1] = nxt;
     cnt->nf[par] = 0;
+    cnt->step_tot[0] = cnt->step_tot[1] = cnt->step_tot[2] = 0;
+    cnt->ticket = 0;
 }
 
 // the walk starts with Self(root) of every system of the batch (roots are nodes 0..nsys-1)
@@ -177,40 +246,45 @@ __global__ void walk_init_k(WalkCounters* cnt, int2* fr0, int* max_fr, int nsys)
         cnt->nf[1] = 0;
         cnt->n_m2l = 0;
         cnt->n_p2p = 0;
+        cnt->ticket = 0;
+        cnt->step_tot[0] = cnt->step_tot[1] = cnt->step_tot[2] = 0;
+        cnt->err = 0;
         *max_fr = nsys;
     }
 }
 
 // ---- per-target segments of the directed lists
-// Every mutual pair (A, B) gives a directed entry for target A (partner B) and, unless
-// A == B, one for target B (partner A).  Entries are counted per target (integer atomics),
-// the counts scanned into segment starts, the entries scattered into their target's
-// segment in any order, and every segment then sorted by its key, which starts with the
-// partner id: each cell sees its partners in increasing id, the canonical order, whatever
-// order the walk and the scatter produced.  The key is the partner (M2L) or
-// partner << 32 | (pair << 1 | side) (P2P); the low 32 bits are kept.
+// Every mutual pair k = (A, B) gives a directed entry for target A (partner B) and, unless
+// A == B, one for target B (partner A).  The entries are laid out in pair order (2k for A,
+// 2k + 1 for B) and stably radix-sorted by target, so every target's segment lists its
+// partners in the order the walk emitted the pairs, which is fixed by the tree.  The value
+// kept is the partner (M2L) or pair << 1 | side (P2P).  A self pair's second entry takes
+// the key 2^bits - 1, above every node id, and sorts past the last segment.
 
-__global__ void seg_count_k(const int2* __restrict__ pairs, int64_t n, int* __restrict__ cnt) {
+__global__ void seg_expand_k(const int2* __restrict__ pairs, int64_t n, bool payload, uint32_t none,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
     if (k >= n) return;
     int2 p = pairs[k];
-    atomicAdd(&cnt[p.x], 1);
-    if (p.x != p.y) atomicAdd(&cnt[p.y], 1);
+    keys[2 * k] = (uint32_t)p.x;
+    keys[2 * k + 1] = p.x != p.y ? (uint32_t)p.y : none;
+    vals[2 * k] = payload ? (uint32_t)(2 * k) : (uint32_t)p.y;
+    vals[2 * k + 1] = payload ? (uint32_t)(2 * k + 1) : (uint32_t)p.x;
 }
 
-__global__ void seg_scatter_k(const int2* __restrict__ pairs, int64_t n, bool payload,
-                              const long long* __restrict__ seg, int* __restrict__ cur,
-                              uint64_t* __restrict__ keys) {
-    int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
-    if (k >= n) return;
-    int2 p = pairs[k];
-    uint64_t ka = payload ? ((uint64_t)(uint32_t)p.y << 32) | (uint64_t)(uint32_t)(2 * k) : (uint64_t)(uint32_t)p.y;
-    keys[seg[p.x] + atomicAdd(&cur[p.x], 1)] = ka;
-    if (p.x != p.y) {
-        uint64_t kb = payload ? ((uint64_t)(uint32_t)p.x << 32) | (uint64_t)(uint32_t)(2 * k + 1)
-                              : (uint64_t)(uint32_t)p.x;
-        keys[seg[p.y] + atomicAdd(&cur[p.y], 1)] = kb;
+// seg[t] = the first sorted entry whose target is >= t, t = 0..nn
+__global__ void seg_bounds_k(const uint32_t* __restrict__ keys, int64_t ne, int nn, long long* __restrict__ seg) {
+    int t = blockIdx.x * WB + threadIdx.x;
+    if (t > nn) return;
+    int64_t lo = 0, hi = ne;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < (uint32_t)t)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
+    seg[t] = lo;
 }
 
 // partial slots of every P2P pair: nA + nB (a self pair: nA)
@@ -222,228 +296,23 @@ __global__ void p2p_psize_k(const int2* __restrict__ pairs, int64_t n, const int
     psize[k] = p.x != p.y ? (long long)count[p.x] + count[p.y] : (long long)count[p.x];
 }
 
-// Segments of at most 256 entries (most): one warp per segment, a bitonic network on
-// NR = 1, 2, 4 or 8 registers per lane (wider register networks measured slower than the
-// shared-memory sort below).  Element e = r * 32 + lane sits in register r of
-// the lane; a compare-exchange at distance j < 32 is a shuffle, at j >= 32 a register swap.
-// Padding is the largest key, so it sorts to the end.
-template <int NR>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[NR], int lane) {
-    constexpr int P2 = 32 * NR;
-#pragma unroll
-    for (int k = 2; k <= P2; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                int jr = j >> 5;
-#pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    int q = r ^ jr;
-                    if (q > r) {
-                        int e = r * 32 + lane;
-                        bool up = (e & k) == 0;
-                        uint64_t a = v[r], b = v[q];
-                        bool sw = (a > b) == up;
-                        v[r] = sw ? b : a;
-                        v[q] = sw ? a : b;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    int e = r * 32 + lane;
-                    uint64_t o = __shfl_xor_sync(FULL, v[r], j);
-                    bool lower = (lane & j) == 0;  // this lane holds the lower index of the pair
-                    bool up = (e & k) == 0;
-                    // the lower index keeps the min when ascending, the max when descending
-                    bool keep_min = lower == up;
-                    v[r] = keep_min ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
-                }
-            }
-        }
-    }
-}
-
-template <int NR>
-__device__ __forceinline__ void warp_sort_segment(const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
-                                                  long long s0, int L, int lane) {
-    uint64_t v[NR];
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-        int e = r * 32 + lane;
-        v[r] = e < L ? keys[s0 + e] : ~0ull;
-    }
-    warp_bitonic<NR>(v, lane);
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-        int e = r * 32 + lane;
-        if (e < L) out[s0 + e] = (uint32_t)v[r];
-    }
-}
-
-constexpr int SS_WARP_MAX = 256, SS_MAX = 4096, SSB = 256;
-
-__global__ void __launch_bounds__(SSB) seg_sort_warp_k(const long long* __restrict__ seg, int nn,
-                                                       const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
-                                                       int* __restrict__ mid, int* __restrict__ cnt2,
-                                                       int* __restrict__ big) {
-    int lane = threadIdx.x & 31;
-    int64_t w0 = ((int64_t)blockIdx.x * SSB + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * SSB) >> 5;
-    for (int64_t x = w0; x < nn; x += nw) {
-        long long s0 = seg[x];
-        int L = (int)(seg[x + 1] - s0);  // uniform over the warp
-        if (L <= 1) {
-            if (L == 1 && lane == 0) out[s0] = (uint32_t)keys[s0];
-        } else if (L <= 32) {
-            warp_sort_segment<1>(keys, out, s0, L, lane);
-        } else if (L <= 64) {
-            warp_sort_segment<2>(keys, out, s0, L, lane);
-        } else if (L <= 128) {
-            warp_sort_segment<4>(keys, out, s0, L, lane);
-        } else if (L <= SS_WARP_MAX) {
-            warp_sort_segment<8>(keys, out, s0, L, lane);
-        } else if (lane == 0) {
-            // longer segments are listed for the block sort or the long-segment fallback
-            if (L <= SS_MAX)
-                mid[atomicAdd(&cnt2[0], 1)] = (int)x;
-            else
-                big[atomicAdd(&cnt2[1], 1)] = (int)x;
-        }
-    }
-}
-
-// Segments of 257 .. SS_MAX entries, from the list seg_sort_warp_k made: one block per
-// segment, bitonic sort in shared memory.
-__global__ void __launch_bounds__(SSB) seg_sort_small_k(const long long* __restrict__ seg,
-                                                        const uint64_t* __restrict__ keys, uint32_t* __restrict__ out,
-                                                        const int* __restrict__ mid, const int* __restrict__ cnt2) {
-    __shared__ uint64_t sk[SS_MAX];
-    int nmid = cnt2[0];
-    for (int i = blockIdx.x; i < nmid; i += gridDim.x) {
-        int x = mid[i];
-        long long s0 = seg[x];
-        int L = (int)(seg[x + 1] - s0);
-        int P2 = 2;
-        while (P2 < L) P2 <<= 1;
-        for (int j = threadIdx.x; j < P2; j += SSB) sk[j] = j < L ? keys[s0 + j] : ~0ull;
-        __syncthreads();
-        for (int k = 2; k <= P2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int a = threadIdx.x; a < P2; a += SSB) {
-                    int ixj = a ^ j;
-                    if (ixj > a) {
-                        uint64_t u = sk[a], v = sk[ixj];
-                        if ((u > v) == ((a & k) == 0)) {
-                            sk[a] = v;
-                            sk[ixj] = u;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        for (int j = threadIdx.x; j < L; j += SSB) out[s0 + j] = (uint32_t)sk[j];
-        __syncthreads();
-    }
-}
-
-// fallback for the rare long segments (sparse halo cells with thousands of partners):
-// their entries are copied with the key (rank of the segment << bits | partner), radix
-// sorted together, and the payloads written back
-__global__ void big_gather_k(const int* __restrict__ big, const long long* __restrict__ boff,
-                             const long long* __restrict__ seg, const uint64_t* __restrict__ keys, int bits,
-                             bool payload, uint64_t* __restrict__ bkeys, uint32_t* __restrict__ bvals) {
-    int b = blockIdx.x;
-    int x = big[b];
-    long long s0 = seg[x], L = seg[x + 1] - s0, o = boff[b];
-    for (long long i = threadIdx.x; i < L; i += SSB) {
-        uint64_t k = keys[s0 + i];
-        uint64_t partner = payload ? (k >> 32) : k;
-        bkeys[o + i] = ((uint64_t)b << bits) | partner;
-        bvals[o + i] = (uint32_t)k;
-    }
-}
-
-__global__ void big_scatter_k(const int* __restrict__ big, const long long* __restrict__ boff,
-                              const long long* __restrict__ seg, const uint32_t* __restrict__ bvals,
-                              uint32_t* __restrict__ out) {
-    int b = blockIdx.x;
-    int x = big[b];
-    long long s0 = seg[x], L = seg[x + 1] - s0, o = boff[b];
-    for (long long i = threadIdx.x; i < L; i += SSB) out[s0 + i] = bvals[o + i];
-}
-
-// builds seg[0..nn] and the sorted per-target lists out[] of the pairs[0..n)
+// builds seg[0..nn] and the per-target lists out[] of the pairs[0..n)
 static void build_segments(fmm_ctx* c, const int2* pairs, int64_t n, int nn, bool payload, DevBuf& seg_buf,
                            DevBuf& out_buf) {
     cudaStream_t s = c->stream;
     int bits = c->id_bits;
+    int64_t ne = 2 * n;
     ensure(seg_buf, sizeof(long long) * (size_t)(nn + 1));
-    ensure(c->seg_cnt, sizeof(int) * (size_t)(2 * nn + 2));
-    int* cnt = c->seg_cnt.as<int>();
-    int* cur = cnt + nn + 1;
-    GB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(2 * nn + 2), s));
+    ensure(c->seg_k, sizeof(uint32_t) * (size_t)(ne > 0 ? ne : 1));
+    ensure(out_buf, sizeof(uint32_t) * (size_t)(ne > 0 ? ne : 1));
     if (n > 0) {
-        seg_count_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, cnt);
-        GB_LAUNCH("seg_count_k");
+        seg_expand_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, payload, (uint32_t)((1ll << bits) - 1),
+                                                  c->seg_k.as<uint32_t>(), out_buf.as<uint32_t>());
+        GB_LAUNCH("seg_expand_k");
+        radix_sort32(c, c->seg_k, c->seg_k2, &out_buf, &c->seg_v2, ne, bits);
     }
-    long long* seg = seg_buf.as<long long>();
-    scan_i64(c, cnt, nn, seg);
-    int64_t ne = 0;
-    GB_CUDA(cudaMemcpyAsync(&ne, seg + nn, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    ensure(c->keys1, sizeof(uint64_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
-    ensure(out_buf, sizeof(uint32_t) * (size_t)(2 * n > 0 ? 2 * n : 1));
-    ensure(c->cnt_off, sizeof(int) * 2);
-    int* cnt2 = c->cnt_off.as<int>();  // [segments for the block sort, long segments]
-    int* nbig_d = cnt2 + 1;
-    GB_CUDA(cudaMemsetAsync(cnt2, 0, sizeof(int) * 2, s));
-    uint64_t* keys = c->keys1.as<uint64_t>();
-    if (n > 0) {
-        seg_scatter_k<<<grid_for(n, WB), WB, 0, s>>>(pairs, n, payload, seg, cur, keys);
-        GB_LAUNCH("seg_scatter_k");
-    }
-    ensure(c->flags, sizeof(int) * (size_t)(nn > 0 ? nn : 1));
-    int* big = c->flags.as<int>();
-    ensure(c->seg_mid, sizeof(int) * (size_t)(nn > 0 ? nn : 1));
-    int* mid = c->seg_mid.as<int>();
-    int dev_sms = 0;
-    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
-    int g = std::min<int64_t>(nn, (int64_t)dev_sms * 8);
-    if (g > 0) {
-        seg_sort_warp_k<<<g, SSB, 0, s>>>(seg, nn, keys, out_buf.as<uint32_t>(), mid, cnt2, big);
-        GB_LAUNCH("seg_sort_warp_k");
-        seg_sort_small_k<<<g, SSB, 0, s>>>(seg, keys, out_buf.as<uint32_t>(), mid, cnt2);
-        GB_LAUNCH("seg_sort_small_k");
-    }
-    int nbig = 0;
-    GB_CUDA(cudaMemcpyAsync(&nbig, nbig_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    if (nbig == 0) return;
-    // the long segments, in a fixed order (by cell id), sorted together
-    std::vector<int> bh(nbig);
-    GB_CUDA(cudaMemcpy(bh.data(), big, sizeof(int) * nbig, cudaMemcpyDeviceToHost));
-    std::sort(bh.begin(), bh.end());
-    std::vector<long long> sh(2 * (size_t)nbig);
-    for (int b = 0; b < nbig; b++) {
-        GB_CUDA(cudaMemcpy(&sh[2 * b], seg + bh[b], sizeof(long long) * 2, cudaMemcpyDeviceToHost));
-    }
-    std::vector<long long> boff(nbig + 1, 0);
-    for (int b = 0; b < nbig; b++) boff[b + 1] = boff[b] + (sh[2 * b + 1] - sh[2 * b]);
-    int64_t tot = boff[nbig];
-    GB_CUDA(cudaMemcpyAsync(big, bh.data(), sizeof(int) * nbig, cudaMemcpyHostToDevice, s));
-    ensure(c->big_off, sizeof(long long) * (size_t)(nbig + 1));
-    GB_CUDA(cudaMemcpyAsync(c->big_off.p, boff.data(), sizeof(long long) * (nbig + 1), cudaMemcpyHostToDevice, s));
-    ensure(c->big_k, sizeof(uint64_t) * (size_t)tot);
-    ensure(c->big_v, sizeof(uint32_t) * (size_t)tot);
-    big_gather_k<<<nbig, SSB, 0, s>>>(big, c->big_off.as<long long>(), seg, keys, bits, payload,
-                                      c->big_k.as<uint64_t>(), c->big_v.as<uint32_t>());
-    GB_LAUNCH("big_gather_k");
-    int bb = 1;
-    while (((int64_t)1 << bb) <= nbig) bb++;
-    radix_sort(c, c->big_k, c->big_k2, &c->big_v, &c->big_v2, tot, bits + bb);
-    big_scatter_k<<<nbig, SSB, 0, s>>>(big, c->big_off.as<long long>(), seg, c->big_v.as<uint32_t>(),
-                                       out_buf.as<uint32_t>());
-    GB_LAUNCH("big_scatter_k");
-    GB_CUDA(cudaStreamSynchronize(s));
+    seg_bounds_k<<<grid_for(nn + 1, WB), WB, 0, s>>>(c->seg_k.as<uint32_t>(), ne, nn, seg_buf.as<long long>());
+    GB_LAUNCH("seg_bounds_k");
 }
 
 // Work items over segments seg[0..n]: every segment is cut into chunks of CH entries.
@@ -520,14 +389,18 @@ void run_walk(fmm_ctx* c, double theta) {
         ensure(c->cnt, sizeof(WalkCounters) + 16);
         WalkCounters* cnt = reinterpret_cast<WalkCounters*>(c->cnt.p);
         int* max_fr = reinterpret_cast<int*>(cnt + 1);
+        size_t nstat = 3 * (size_t)(cap_fr / WTILE + 1);
+        ensure(c->walk_status, sizeof(unsigned long long) * nstat);
+        unsigned long long* status = c->walk_status.as<unsigned long long>();
+        GB_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * nstat, s));
         walk_init_k<<<grid_for(c->n_sys, WB), WB, 0, s>>>(cnt, c->fr0.as<int2>(), max_fr, c->n_sys);
         GB_LAUNCH("walk_init_k");
         for (int k = 0; k < steps; k++) {
             int par = k & 1;
             int2* fin = par ? c->fr1.as<int2>() : c->fr0.as<int2>();
             int2* fout = par ? c->fr0.as<int2>() : c->fr1.as<int2>();
-            walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, nv, theta, th2, c->m2l_pairs.as<int2>(), (int)cap_m2l,
-                                            c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr);
+            walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, k, status, nv, theta, th2, c->m2l_pairs.as<int2>(),
+                                            (int)cap_m2l, c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr);
             GB_LAUNCH("walk_step_k");
             walk_advance_k<<<1, 1, 0, s>>>(cnt, par, max_fr);
             GB_LAUNCH("walk_advance_k");
@@ -537,6 +410,7 @@ void run_walk(fmm_ctx* c, double theta) {
         GB_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(WalkCounters), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaMemcpyAsync(&hmax, max_fr, sizeof(int), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
+        if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "walk: a frontier tile waited too long for the tiles before it"};
         if (h.nf[0] != 0 || h.nf[1] != 0) throw FmmError{FMM_ERR_CAPACITY, "walk did not finish in 2 x levels + 2 steps"};
         bool over = h.n_m2l > cap_m2l || h.n_p2p > cap_p2p || hmax > cap_fr;
         if (h.n_m2l < 0 || h.n_p2p < 0 || hmax < 0) throw FmmError{FMM_ERR_CAPACITY, "walk counters above 2^31"};
