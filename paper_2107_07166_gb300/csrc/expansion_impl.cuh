@@ -90,10 +90,22 @@ __device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint32_t*
                                         const float4* __restrict__ zh, const float4* __restrict__ zl) {
     float4 ah = zh[tgt], al = zl[tgt];
     int k = 100;
-    for (int e = e0; e < e1; e++) {
-        int src = (int)dir[e];
-        float4 bh = zh[src], bl = zl[src];
-        k = min(k, sep_exp(dsep(ah.x, al.x, bh.x, bl.x), dsep(ah.y, al.y, bh.y, bl.y), dsep(ah.z, al.z, bh.z, bl.z)));
+    // four entries per round with all loads first: the id -> centre chains overlap (an index
+    // past the end repeats the last entry, which leaves the minimum unchanged)
+    for (int e = e0; e < e1; e += 4) {
+        int s[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) s[j] = (int)dir[min(e + j, e1 - 1)];
+        float4 bh[4], bl[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            bh[j] = zh[s[j]];
+            bl[j] = zl[s[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            k = min(k, sep_exp(dsep(ah.x, al.x, bh[j].x, bl[j].x), dsep(ah.y, al.y, bh[j].y, bl[j].y),
+                               dsep(ah.z, al.z, bh[j].z, bl[j].z)));
     }
     return k;
 }
@@ -197,8 +209,62 @@ struct M2LGeom {
     const int* nk;               // per-node moment unit exponent (scaled modes)
 };
 
+// An M2L entry's source geometry (centre, and moment unit in the scaled modes), fetched one
+// entry ahead of its use so that the id -> centre load chain of the next entry overlaps
+// this entry's arithmetic; the target's is loaded once per item.
+template <class T>
+struct SrcGeo {  // binary64 and double-float: binary64 centres
+    double x, y, z;
+    int nk;
+    __device__ void load(const M2LGeom& g, int s) {
+        x = g.Zx[s];
+        y = g.Zy[s];
+        z = g.Zz[s];
+        nk = std::is_same<T, double>::value ? 0 : g.nk[s];
+    }
+};
+template <>
+struct SrcGeo<float> {
+    float4 h, l;
+    int nk;
+    __device__ void load(const M2LGeom& g, int s) {
+        h = g.zh[s];
+        l = g.zl[s];
+        nk = g.nk[s];
+    }
+};
+template <class T>
+struct TgtGeo {
+    double x, y, z;
+    __device__ void load(const M2LGeom& g, int t) {
+        x = g.Zx[t];
+        y = g.Zy[t];
+        z = g.Zz[t];
+    }
+    // R = Z_tgt - Z_src, formed in binary64 and rounded to T
+    __device__ void sep(const SrcGeo<T>& s, T& rx, T& ry, T& rz) const {
+        rx = to_kernel(x - s.x, T());
+        ry = to_kernel(y - s.y, T());
+        rz = to_kernel(z - s.z, T());
+    }
+};
+template <>
+struct TgtGeo<float> {
+    float4 h, l;
+    __device__ void load(const M2LGeom& g, int t) {
+        h = g.zh[t];
+        l = g.zl[t];
+    }
+    // R from the double-float centre words: (hi - hi) + (lo - lo)
+    __device__ void sep(const SrcGeo<float>& s, float& rx, float& ry, float& rz) const {
+        rx = dsep(h.x, l.x, s.h.x, s.l.x);
+        ry = dsep(h.y, l.y, s.h.y, s.l.y);
+        rz = dsep(h.z, l.z, s.h.z, s.l.z);
+    }
+};
+
 // a8 M2L, standard, one work item = up to M2L_CHUNK directed entries of one target cell
-// (sources in increasing id): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src),
+// (sources in list order): L_gamma += sum_beta M_beta D_{beta+gamma}(Z_tgt - Z_src),
 // in the pair-kernel type T.  The item's partial local goes to part[item] (and its unit
 // exponent to kpart[item] in the scaled modes); m2l_reduce_k sums a cell's items in order.
 template <int P, class T>
@@ -219,10 +285,15 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
         kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
         kpart[it] = kI;
     }
+    TgtGeo<T> tg;
+    tg.load(g, w.x);
+    int src = (int)dir[w.y];  // an item holds at least one entry
+    SrcGeo<T> sg;
+    sg.load(g, src);
     for (int e = w.y; e < w.z; e++) {
-        int src = (int)dir[e];
+        int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
         T rx, ry, rz;
-        SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
+        tg.sep(sg, rx, ry, rz);
         T D[E::NM];
         if constexpr (SC) {
             T ux, uy, uz;
@@ -234,7 +305,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
 #pragma unroll
             for (int k = 0; k < E::NM; k++) D[k] = scale_t(D[k], vp[mi_deg(k) + 1]);
             float f[P + 1];
-            moment_factors<P + 1>(g.nk[src] - kI, f);
+            moment_factors<P + 1>(sg.nk - kI, f);
             if constexpr (sizeof(T) == 4) {
                 T Ms[E::NMP];
                 load_f4<E::NMP>(mom + (int64_t)src * E::NMP, Ms);
@@ -246,6 +317,8 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
             E::dtensor(rx, ry, rz, D);
             E::m2l_std(mom + (int64_t)src * E::NM, D, L);
         }
+        src = nsrc;
+        sg.load(g, src);
     }
 #pragma unroll
     for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = Prec<T>::fin(L[k]);
@@ -272,10 +345,15 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
         kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
         kpart[it] = kI;
     }
+    TgtGeo<T> tg;
+    tg.load(g, w.x);
+    int src = (int)dir[w.y];  // an item holds at least one entry
+    SrcGeo<T> sg;
+    sg.load(g, src);
     for (int e = w.y; e < w.z; e++) {
-        int src = (int)dir[e];
+        int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
         T rx, ry, rz;
-        SepOf<T>::get(g.Zx, g.Zy, g.Zz, g.zh, g.zl, w.x, src, rx, ry, rz);
+        tg.sep(sg, rx, ry, rz);
         T H[E::NQ];
         if constexpr (SC) {
             T ux, uy, uz;
@@ -298,15 +376,17 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
             T Ms[E::NMP];
             load_f4<E::NMP>(cmom + (int64_t)src * E::NMP, Ms);
             float f[P + 1];
-            moment_factors<P + 1>(g.nk[src] - kI, f);
+            moment_factors<P + 1>(sg.nk - kI, f);
             E::m2l_con_m(Ms, f, H, rx, ry, rz, SU);
         } else if constexpr (SC) {
             float f[P + 1];
-            moment_factors<P + 1>(g.nk[src] - kI, f);
+            moment_factors<P + 1>(sg.nk - kI, f);
             E::m2l_con_m(cmom + (int64_t)src * E::NMP, f, H, rx, ry, rz, SU);
         } else {
             E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
         }
+        src = nsrc;
+        sg.load(g, src);
     }
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::fin(SU[k]);

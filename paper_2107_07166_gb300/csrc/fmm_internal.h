@@ -115,9 +115,9 @@ struct fmm_ctx {
     int p2p_chunk = gbfmm::P2P_CHUNK;          // directed P2P entries per reduction item
     int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
-    gbfmm::DevBuf m2l_dir;                     // uint32 source ids, per-target segments in increasing id
+    gbfmm::DevBuf m2l_dir;                     // uint32 source ids, per-target segments in list order
     gbfmm::DevBuf m2l_seg;                     // int64 [n_nodes + 1] segment starts per target
-    gbfmm::DevBuf p2p_dval;                    // uint32 (pair << 1 | side), per-target segments by partner id
+    gbfmm::DevBuf p2p_dval;                    // uint32 (pair << 1 | side), per-target segments in list order
     gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]
     gbfmm::DevBuf p2p_psize;                   // int64 partial slots per P2P pair
     gbfmm::DevBuf seg_k, seg_k2, seg_v2;       // directed-entry keys of the list sort (+ scratch)

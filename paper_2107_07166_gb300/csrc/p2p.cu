@@ -9,7 +9,7 @@
 // columns give a_b = +sum_a m_a d r^-3 (phi_b = -sum_a m_a r^-1).  Each pair force is
 // formed once and applied to both partners (action = reaction).  A self pair keeps a < b.
 // Results go to a per-(pair, side, slot) partial buffer that the final per-particle
-// kernels sum in increasing partner id: no floating-point atomics, run-to-run identical.
+// kernels sum in list order: no floating-point atomics, run-to-run identical.
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
@@ -534,7 +534,7 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
 
 // a12/a13 first level: one warp per P2P work item (up to P2P_CHUNK directed entries of
 // one leaf); lane = particle slot of the leaf.  Sums the per-pair partials of the
-// item's entries (increasing partner id) into ipart[islot[item] + slot].
+// item's entries (in list order) into ipart[islot[item] + slot].
 //   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
 //   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
 // acc + v for the item sums: binary64 and double-float partials add as usual; a binary32

@@ -434,7 +434,7 @@ void run_walk(fmm_ctx* c, double theta) {
     c->id_bits = bits;
     // M2L: per-target segments of source ids in increasing order
     build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, false, c->m2l_seg, c->m2l_dir);
-    // P2P: per-target segments of (pair << 1 | side) in increasing partner order, plus the
+    // P2P: per-target segments of (pair << 1 | side) in list order, plus the
     // partial offsets of every pair
     ensure(c->p2p_off, sizeof(long long) * (size_t)(n_p2p + 1));
     ensure(c->p2p_psize, sizeof(long long) * (size_t)(n_p2p + 1));

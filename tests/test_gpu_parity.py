@@ -328,6 +328,42 @@ def test_precision_modes(fmm, torch_cuda, orc, case, precision):
         g["f"].close()
 
 
+@pytest.mark.parametrize("precision", [2, 1], ids=["df64", "mixed"])
+def test_precision_modes_coincident(fmm, torch_cuda, orc, precision):
+    """Leaves above leaf_size at the deepest level (duplicated positions) take the pair
+    kernel's general path in every arithmetic; zero masses and r = 0 pairs add nothing."""
+    rng = np.random.default_rng(14)
+    base = rng.normal(size=(400, 3))
+    x = np.concatenate([base, np.repeat(base[:2], 70, axis=0), np.repeat(base[5:8], 35, axis=0)])
+    m = rng.random(x.shape[0])
+    m[::9] = 0.0
+    for variant in (0, 1):
+        r = orc.run(x, m, 8, 3, 0.5, variant, want_pot=True)
+        assert r.tree["count"][r.tree["nchild"] == 0].max() > 32
+        g = run_gpu(fmm, torch_cuda, x, m, 8, 3, 0.5, variant, precision=precision)
+        check_structure(g["f"], r, x.shape[0])
+        assert rel(g["acc"], r.acc) < MODE_TOL[precision]
+        assert rel(g["pot"], r.pot) < MODE_TOL[precision]
+        g["f"].close()
+
+
+@pytest.mark.parametrize("precision", [2, 1], ids=["df64", "mixed"])
+def test_precision_modes_theta_zero(fmm, torch_cuda, orc, precision):
+    """theta = 0 turns every leaf pair into a P2P pair: leaf sizes 1..32 meet in every
+    combination (ring widths 1..32, up to 32 chunks of the larger leaf), and the result is
+    the direct sum in the mode's arithmetic."""
+    x, m = synth.plummer(6000, 17)
+    a, ph = orc.direct(x, m)
+    g = run_gpu(fmm, torch_cuda, x, m, 32, 2, 0.0, 1, precision=precision)
+    tol = TOL if precision == 2 else 2e-6
+    assert rel(g["acc"], a) < tol
+    assert rel(g["pot"], ph) < tol
+    F, _ = g["f"].diagnostics()
+    fs = (m * np.linalg.norm(g["acc"], axis=1)).sum()
+    assert np.linalg.norm(F) < (1e-14 if precision == 2 else 1e-6) * fs
+    g["f"].close()
+
+
 def test_df64_every_order_and_full_size_sample(fmm, torch_cuda, orc):
     for p in range(1, fmm.DF64_P_MAX + 1):
         x, m = synth.plummer(2048, 40 + p)
