@@ -10,6 +10,8 @@
 // formed once and applied to both partners (action = reaction).  A self pair keeps a < b.
 // Results go to a per-(pair, side, slot) partial buffer that the final per-particle
 // kernels sum in list order: no floating-point atomics, run-to-run identical.
+#include <type_traits>
+
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
@@ -18,9 +20,6 @@
 namespace gbfmm {
 
 constexpr int PB = 128;                 // 4 warps
-#ifndef RING_ALL
-#define RING_ALL 0
-#endif
 constexpr int PW = PB / 32;
 // panel columns: 8-byte types use 8 columns so that four warps of panels leave room for
 // four blocks per SM; 4-byte types use 16
@@ -31,11 +30,6 @@ struct Panel {
     static constexpr int SIZE = 32 * ROW;     // elements per warp panel
 };
 
-__device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(FULL, v, src); }
-__device__ __forceinline__ double shfl_t(double v, int src) { return __shfl_sync(FULL, v, src); }
-__device__ __forceinline__ df64 shfl_t(df64 v, int src) {
-    return df64(__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src));
-}
 
 template <class S>
 struct PState {
@@ -259,25 +253,57 @@ __global__ void p2p_ring_tab_k(RingTab* __restrict__ tab) {
     tab->start[0] = tab->count[0] = tab->wpre[0] = 0;
 }
 
-// The ring pair kernel for leaves of at most 32 particles.  A warp takes 32 / w segments of
-// w lanes, one leaf pair each.  Lane i of a segment holds particle g = c w + i of the
-// larger ("lane") leaf in chunk c, shifted by that leaf's side of R = Z_A - Z_B; the
-// smaller ("ring") leaf sits in shared memory.  In step k lane i meets ring particle
-// j = (i + k) mod w: over w steps every (g, j) of the chunk meets exactly once.  The pair
-// force is formed once and applied to both partners: g's sum stays in lane i and is stored
-// after its chunk, j's sum travels with the ring (one shuffle from lane i + 1 per step), is
-// back in lane j after every full turn and collects all chunks before it is stored.  A
-// self pair runs one chunk over itself from both ends (each pair twice, 1/w of the work,
-// no reduction) and drops the travelling sums.  Every sum runs in a fixed order.
-template <class T, bool POT>
+// one ring step of a lane particle a with ring particle b, positions as double-float words
+// (hi, lo) in binary32 arithmetic: the pair force is formed once, -m_b d r^-3 goes to a's
+// sum and +m_a d r^-3 to b's travelling sum (potentials -m r^-1); r = 0 adds nothing.
+// The separation is (hi - hi) + (lo - lo), exact in its high difference for close pairs.
+template <bool POT>
+__device__ __forceinline__ void ring_pair(const float4& ah, const float4& al, float ma, const float4& bh,
+                                          const float4& bl, float4& a, float& bx, float& by, float& bz, float& bp) {
+    float dx = __fadd_rn(__fsub_rn(ah.x, bh.x), __fsub_rn(al.x, bl.x));
+    float dy = __fadd_rn(__fsub_rn(ah.y, bh.y), __fsub_rn(al.y, bl.y));
+    float dz = __fadd_rn(__fsub_rn(ah.z, bh.z), __fsub_rn(al.z, bl.z));
+    float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 != 0.f) {
+        float ir = rsqrtf(r2);
+        float ir3 = ir * ir * ir;
+        float mb = bh.w;
+        float sa = mb * ir3;
+        a.x = fmaf(-sa, dx, a.x);
+        a.y = fmaf(-sa, dy, a.y);
+        a.z = fmaf(-sa, dz, a.z);
+        if (POT) a.w = fmaf(-mb, ir, a.w);
+        float sb = ma * ir3;
+        bx = fmaf(sb, dx, bx);
+        by = fmaf(sb, dy, by);
+        bz = fmaf(sb, dz, bz);
+        if (POT) bp = fmaf(-ma, ir, bp);
+    }
+}
+
+// lane particles held at once by a ring lane (chunks of the lane leaf per pass)
+constexpr int RING_CHUNKS = 2;
+
+// The binary32 ring pair kernel for leaves of at most 32 particles.  A warp takes 32 / w
+// segments of w lanes, one leaf pair each.  Lane i of a segment holds particle
+// g = c w + i of the larger ("lane") leaf in chunk c, shifted by that leaf's side of
+// R = Z_A - Z_B; the smaller ("ring") leaf sits in shared memory as two float4 arrays
+// (high words and mass, low words), so that a quarter-warp's 16-byte reads are
+// contiguous.  A lane holds RING_CHUNKS chunks at a time: every ring particle read meets
+// all of them.  In step k lane i meets ring particle j = (i + k) mod w: over w steps
+// every (g, j) of the chunks meets exactly once.  The pair force is formed once and
+// applied to both partners: g's sum stays in lane i and is stored after its chunk, j's
+// sum travels with the ring (one shuffle from lane i + 1 per step), is back in lane j
+// after every full turn and collects all chunks before it is stored.  A self pair runs
+// one chunk over itself from both ends (each pair twice, 1/w of the work, no reduction)
+// and drops the travelling sums.  Every sum runs in a fixed order.
+template <bool POT>
 __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
                                                  const int2* __restrict__ pairs, const long long* __restrict__ off,
                                                  const int* __restrict__ nfirst, const int* __restrict__ ncount,
-                                                 const PState<typename Prec<T>::S>* __restrict__ pos,
-                                                 const typename Prec<T>::S* __restrict__ sep,
-                                                 Quad<T>* __restrict__ part) {
-    using S = typename Prec<T>::S;
-    __shared__ PState<S> sB[PW][32];
+                                                 const PState<df64>* __restrict__ pos, const df64* __restrict__ sep,
+                                                 Quad<float>* __restrict__ part) {
+    __shared__ float4 sH[PW][32], sL[PW][32];
     __shared__ int ts[34], tc[34], tw[34];
     for (int t = threadIdx.x; t < 34; t += PB) {
         ts[t] = tab->start[t];
@@ -297,13 +323,14 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
         int per = 32 / W;
         int sg = lane / W;
         bool live = sg < per;
-        int i = live ? lane - sg * W : 0, base = live ? sg * W : lane;
+        // a lane past the last segment reads slot j of segment 0 (in bounds, unused)
+        int i = live ? lane - sg * W : 0, base = live ? sg * W : 0;
         int64_t li = (q - tw[W]) * per + sg;
         bool ok = live && li < tc[W];
         int nA = 0, nB = 0, fA = 0, fB = 0;
         long long o = 0;
         bool self = false;
-        S rx = S(0), ry = S(0), rz = S(0);
+        df64 rx = df64(0.f), ry = df64(0.f), rz = df64(0.f);
         if (ok) {
             int k = (int)list[ts[W] + li];
             int2 pr = pairs[k];
@@ -327,56 +354,51 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
             rz = -rz;
         }
         __syncwarp();
-        if (ok) sB[w][lane] = pos[fR + i];  // i < W = the ring leaf's count
+        if (ok) {  // i < W = the ring leaf's count
+            PState<df64> b = pos[fR + i];
+            sH[w][lane] = make_float4(b.x.hi, b.y.hi, b.z.hi, b.m.hi);
+            sL[w][lane] = make_float4(b.x.lo, b.y.lo, b.z.lo, 0.f);
+        }
         __syncwarp();
         int m = ok ? (self ? 1 : (nL + W - 1) / W) : 0;
         int mmax = __reduce_max_sync(FULL, m);
         int nxt = live ? base + (i + 1 < W ? i + 1 : 0) : lane;
-        T bx = T(0), by = T(0), bz = T(0), bp = T(0);
-        for (int ch = 0; ch < mmax; ch++) {
-            int g = ch * W + i;
-            bool mine = ok && ch < m && g < nL;
-            PState<S> pa = PState<S>{S(0), S(0), S(0), S(0)};
-            if (mine) {
-                PState<S> qa = pos[fL + g];
-                pa = PState<S>{rx + qa.x, ry + qa.y, rz + qa.z, qa.m};
+        float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+        for (int ch = 0; ch < mmax; ch += RING_CHUNKS) {
+            float4 ah[RING_CHUNKS], al[RING_CHUNKS], acc[RING_CHUNKS];
+            float ma[RING_CHUNKS];
+            bool mine[RING_CHUNKS];
+#pragma unroll
+            for (int r = 0; r < RING_CHUNKS; r++) {
+                int g = (ch + r) * W + i;
+                mine[r] = ok && ch + r < m && g < nL;
+                ah[r] = al[r] = acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ma[r] = 0.f;
+                if (mine[r]) {
+                    PState<df64> qa = pos[fL + g];
+                    df64 x = rx + qa.x, y = ry + qa.y, z = rz + qa.z;
+                    ah[r] = make_float4(x.hi, y.hi, z.hi, 0.f);
+                    al[r] = make_float4(x.lo, y.lo, z.lo, 0.f);
+                    ma[r] = qa.m.hi;
+                }
             }
-            T ma = Prec<T>::mass(pa.m);
-            T ax = T(0), ay = T(0), az = T(0), ap = T(0);
             int j = i;
             for (int kk = 0; kk < W; kk++) {
-                if (mine) {
-                    const PState<S>& pb = sB[w][base + j];
-                    T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y), dz = Prec<T>::sep(pa.z, pb.z);
-                    T r2 = dx * dx + dy * dy + dz * dz;
-                    if (!is_zero(r2)) {
-                        T ir = rsqrt_t(r2);
-                        T ir3 = ir * ir * ir;
-                        T mb = Prec<T>::mass(pb.m);
-                        T sa = mb * ir3;
-                        ax = fma_t(-sa, dx, ax);
-                        ay = fma_t(-sa, dy, ay);
-                        az = fma_t(-sa, dz, az);
-                        if (POT) ap = fma_t(-mb, ir, ap);
-                        T sb = ma * ir3;
-                        bx = fma_t(sb, dx, bx);
-                        by = fma_t(sb, dy, by);
-                        bz = fma_t(sb, dz, bz);
-                        if (POT) bp = fma_t(-ma, ir, bp);
-                    }
-                }
-                bx = shfl_t(bx, nxt);
-                by = shfl_t(by, nxt);
-                bz = shfl_t(bz, nxt);
-                if (POT) bp = shfl_t(bp, nxt);
+                float4 bh = sH[w][base + j], bl = sL[w][base + j];
+#pragma unroll
+                for (int r = 0; r < RING_CHUNKS; r++)
+                    if (mine[r]) ring_pair<POT>(ah[r], al[r], ma[r], bh, bl, acc[r], bx, by, bz, bp);
+                bx = __shfl_sync(FULL, bx, nxt);
+                by = __shfl_sync(FULL, by, nxt);
+                bz = __shfl_sync(FULL, bz, nxt);
+                if (POT) bp = __shfl_sync(FULL, bp, nxt);
                 j = (j + 1 == W) ? 0 : j + 1;
             }
-            if (mine) part[oL + g] = Quad<T>{Prec<T>::fin(ax), Prec<T>::fin(ay), Prec<T>::fin(az),
-                                             POT ? Prec<T>::fin(ap) : T(0)};
+#pragma unroll
+            for (int r = 0; r < RING_CHUNKS; r++)
+                if (mine[r]) part[oL + (ch + r) * W + i] = Quad<float>{acc[r].x, acc[r].y, acc[r].z, POT ? acc[r].w : 0.f};
         }
-        if (ok && !self)
-            part[oR + i] = Quad<T>{Prec<T>::fin(bx), Prec<T>::fin(by), Prec<T>::fin(bz),
-                                   POT ? Prec<T>::fin(bp) : T(0)};
+        if (ok && !self) part[oR + i] = Quad<float>{bx, by, bz, POT ? bp : 0.f};
         __syncwarp();
     }
 }
@@ -434,7 +456,7 @@ __global__ void pack_pos_k(int n, const int* __restrict__ leaf_of, const double*
 // which pair kernel each arithmetic runs (ring: binary32; panel: binary64 and double-float)
 template <class T>
 struct P2PRing {
-    static constexpr bool value = RING_ALL || sizeof(T) == 4;
+    static constexpr bool value = std::is_same<T, float>::value;
 };
 
 template <class T>
@@ -500,12 +522,12 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
             int64_t ring_bl = (np + PW - 1) / PW;
             if (ring_bl > cap) ring_bl = cap;
             if (want_pot) {
-                run(p2p_ring_k<T, true>, ring_bl);
+                run(p2p_ring_k<true>, ring_bl);
                 GB_LAUNCH("p2p_ring_k");
                 run(p2p_big_k<T, true>, dev_sms);
                 GB_LAUNCH("p2p_big_k");
             } else {
-                run(p2p_ring_k<T, false>, ring_bl);
+                run(p2p_ring_k<false>, ring_bl);
                 GB_LAUNCH("p2p_ring_k");
                 run(p2p_big_k<T, false>, dev_sms);
                 GB_LAUNCH("p2p_big_k");

@@ -97,7 +97,8 @@ struct WalkCounters {
 // offsets inside the tile with one block scan.  The tile's place in the outputs comes
 // from a decoupled look-back over the tiles before it: each tile publishes its counts,
 // then its inclusive prefix, as one 64-bit word (tag << 32 | value) per counter; a
-// waiting tile adds published counts backwards until it meets a prefix.  Tickets are
+// waiting tile adds published counts backwards, 32 tiles per warp read, until it meets a
+// prefix.  Tickets are
 // handed out in tile order to running blocks, so every tile waited on has started and
 // publishes its counts without waiting itself.  The outputs therefore keep the frontier
 // order: every list the walk emits is a fixed function of the tree.  The tags carry the
@@ -159,38 +160,48 @@ __global__ void __launch_bounds__(WB) walk_step_k(const int2* __restrict__ fr_in
         }
         Cnt3 tot;
         Cnt3 off = block_exclusive_scan(mine, &tot);
-        if (threadIdx.x < 3) {
-            // thread q claims counter q: publish, look back, publish the prefix
-            int q = threadIdx.x;
+        if (threadIdx.x < 96) {
+            // warp q claims counter q: publish the tile's count, look back over the tiles
+            // before it 32 at a time (lane l reads tile t - l) until one has published its
+            // prefix, then publish this tile's prefix
+            int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
             int v = q == 0 ? tot.a : (q == 1 ? tot.b : tot.c);
-            unsigned long long* my = status + 3 * (int64_t)tile + q;
+            unsigned long long* word = status + q;  // counter q of tile t: word[3 t]
             int ex = 0;
             if (tile > 0) {
-                st_status(my, tag_agg, v);
+                if (lane == 0) st_status(word + 3 * (int64_t)tile, tag_agg, v);
                 int t = tile - 1;
                 long long spins = 0;
-                while (t >= 0) {
-                    unsigned long long w = ld_status(status + 3 * (int64_t)t + q);
+                for (;;) {
+                    int u = t - lane;
+                    // before tile 0 every counter starts at 0: a published prefix of 0
+                    unsigned long long w = u >= 0 ? ld_status(word + 3 * (int64_t)u) : (unsigned long long)tag_pre << 32;
                     unsigned tag = (unsigned)(w >> 32);
-                    if (tag == tag_pre) {
-                        ex += (int)(unsigned)w;
-                        break;
-                    }
-                    if (tag == tag_agg) {
-                        ex += (int)(unsigned)w;
-                        t--;
+                    unsigned pre = __ballot_sync(FULL, tag == tag_pre);
+                    unsigned wait = __ballot_sync(FULL, tag != tag_pre && tag != tag_agg);
+                    int first = pre ? __ffs(pre) - 1 : 32;  // nearest tile with a prefix
+                    unsigned need = first >= 31 ? FULL : ((2u << first) - 1u);
+                    if (wait & need) {  // a tile in the window has not published yet
+                        if (++spins > WALK_SPIN_LIMIT) {
+                            if (lane == 0) atomicExch(&cnt->err, 1);
+                            break;
+                        }
+                        __nanosleep(32);
                         continue;
                     }
-                    if (++spins > WALK_SPIN_LIMIT) {  // a tile before this one never published
-                        atomicExch(&cnt->err, 1);
-                        break;
-                    }
-                    __nanosleep(32);
+                    int val = lane <= first ? (int)(unsigned)w : 0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(FULL, val, o);
+                    ex += val;
+                    if (first < 32) break;
+                    t -= 32;
                 }
             }
-            st_status(my, tag_pre, ex + v);
-            if (tile == ntiles - 1) cnt->step_tot[q] = ex + v;
-            sbase[q] = ex + (q == 0 ? bm : (q == 1 ? bp : 0));
+            if (lane == 0) {
+                st_status(word + 3 * (int64_t)tile, tag_pre, ex + v);
+                if (tile == ntiles - 1) cnt->step_tot[q] = ex + v;
+                sbase[q] = ex + (q == 0 ? bm : (q == 1 ? bp : 0));
+            }
         }
         __syncthreads();
         int om = sbase[0] + off.a, op = sbase[1] + off.b, of = sbase[2] + off.c;
