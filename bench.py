@@ -139,7 +139,7 @@ def algorithmic_flops(counts, tree_counts, p, variant):
 # DRAM bytes (read + write) per unit of the dominant binary64 kernels, from an ncu capture
 # of their DRAM counters at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md), scaled
 # here by the units of the timed launch: per mutual M2L pair, per particle pair.
-NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 58.7, ("p2p_k", "fp64"): 5.19}
+NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 58.9, ("p2p_k", "fp64"): 5.12}
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:

@@ -466,6 +466,25 @@ def test_batch_matches_each_system_alone(fmm, torch_cuda, orc):
         f.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+def test_batch_bitwise_equals_each_system_alone(fmm, torch_cuda, precision):
+    """The walk keeps every system's pairs in the order the system alone produces, so a
+    system's forces inside a batch are bit-identical to the same system run by itself."""
+    x, m, off = synth.batch(5, 500, 300, 4000)
+    f = new_ctx(fmm, torch_cuda, precision)
+    f.build_batch(x, m, off, 16)
+    acc = np.empty_like(x)
+    pot = np.empty(x.shape[0])
+    f.forces_batch(4, 0.6, 1, acc, pot)
+    f.close()
+    for s in range(len(off) - 1):
+        a, b = off[s], off[s + 1]
+        g = run_gpu(fmm, torch_cuda, x[a:b], m[a:b], 16, 4, 0.6, 1, precision=precision)
+        assert np.array_equal(acc[a:b], g["acc"]), s
+        assert np.array_equal(pot[a:b], g["pot"]), s
+        g["f"].close()
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_workload_shape(fmm, torch_cuda, orc, precision):
     """64 systems with N log-uniform in [1k, 8k] (the batch workload's recipe at reduced
