@@ -40,19 +40,23 @@ namespace gbfmm {
 
 constexpr int EB = 128;
 
-// a5 P2M: moments of every leaf from its particles (y = X - Z), one thread per leaf.  (A warp
+// a5 P2M: moments of every leaf from its particles (y = X - Z), one thread per leaf, leaves
+// taken in order of size so that a warp's lanes finish together.  (A warp
 // per leaf with a butterfly reduction was 4x slower: every lane then runs the reduction's
 // binary64 adds, and binary64 warp instructions cost the same with idle lanes.)
 template <int P>
-__global__ void __launch_bounds__(EB) p2m_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
+__global__ void __launch_bounds__(EB) p2m_k(int nn, const uint32_t* __restrict__ order,
+                                            const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                             const int* __restrict__ nnchild, const double* __restrict__ xs,
                                             const double* __restrict__ ys, const double* __restrict__ zs,
                                             const double* __restrict__ ms, const double* __restrict__ Zx,
                                             const double* __restrict__ Zy, const double* __restrict__ Zz,
                                             double* __restrict__ mom) {
     using E = Exp<P>;
-    int nd = blockIdx.x * EB + threadIdx.x;
-    if (nd >= nn || nnchild[nd] != 0) return;
+    int t = blockIdx.x * EB + threadIdx.x;
+    if (t >= nn) return;
+    int nd = (int)order[t];  // nodes by leaf size: a warp's leaves hold equal counts
+    if (nnchild[nd] != 0) return;
     double M[E::NM];
 #pragma unroll
     for (int k = 0; k < E::NM; k++) M[k] = 0.0;
@@ -684,7 +688,8 @@ void run_moments_p(fmm_ctx* c) {
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
     ensure(c->mom, sizeof(double) * (size_t)nn * E::NM);
-    p2m_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->nfirst.as<int>(), c->ncount.as<int>(), c->nnchild.as<int>(),
+    p2m_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->leaf_order.as<uint32_t>(), c->nfirst.as<int>(),
+                                             c->ncount.as<int>(), c->nnchild.as<int>(),
                                              c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
                                              c->ms.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
                                              c->nZz.as<double>(), c->mom.as<double>());

@@ -424,6 +424,17 @@ __global__ void cur_init_k(const long long* __restrict__ off, int nsys, int64_t 
 
 // ------------------------------------------------------------------ host driver
 
+// Per-leaf work (P2M) runs one thread per leaf, so a warp lasts as long as its largest
+// leaf.  Nodes ordered by this key (leaf size, capped at 510; inner nodes 511, last) give
+// warps leaves of equal size.
+__global__ void leaf_key_k(int nn, const int* __restrict__ ncount, const int* __restrict__ nnchild,
+                           uint32_t* __restrict__ key, uint32_t* __restrict__ order) {
+    int nd = blockIdx.x * TB + threadIdx.x;
+    if (nd >= nn) return;
+    key[nd] = nnchild[nd] != 0 ? 511u : (uint32_t)min(ncount[nd], 510);
+    order[nd] = (uint32_t)nd;
+}
+
 static void ensure_nodes(fmm_ctx* c, int64_t need) {
     if (need <= c->cap_nodes) return;
     int64_t cap = need + need / 2 + 1024;
@@ -579,6 +590,13 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
                                            c->nZy.as<double>(), c->nZz.as<double>(), c->nrmax.as<double>(),
                                            c->zhl.as<float4>(), c->zhl.as<float4>() + nn);
     GB_LAUNCH("rmax_k");
+    // nodes by leaf size for the per-leaf kernels (one stable 9-bit radix pass)
+    ensure(c->leaf_key, sizeof(uint32_t) * (size_t)nn);
+    ensure(c->leaf_order, sizeof(uint32_t) * (size_t)nn);
+    leaf_key_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->ncount.as<int>(), c->nnchild.as<int>(),
+                                               c->leaf_key.as<uint32_t>(), c->leaf_order.as<uint32_t>());
+    GB_LAUNCH("leaf_key_k");
+    radix_sort32(c, c->leaf_key, c->leaf_key2, &c->leaf_order, &c->leaf_order2, nn, 9);
     return FMM_OK;
 }
 
