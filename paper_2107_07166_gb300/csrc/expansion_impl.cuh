@@ -620,33 +620,100 @@ __global__ void __launch_bounds__(EB) l2l_con_k(int lo, int hi, const int* __res
     }
 }
 
+// a11 in the scaled modes: the L2P runs in the pair-kernel type X on every leaf's locals
+// expressed in the leaf's unit 2^k (k = nk, the moments' unit exponent, so |x| 2^-k < 2 for
+// its particles): with u = x 2^-k, a standard coefficient L_g becomes L_g 2^(k|g|) (the
+// acceleration then carries 2^-k), a conserving S_g becomes S_g 2^(k(|g|+1)) and U_g
+// becomes U_g 2^(k|g|), so that a = u S''(u) + U'(u) needs no factor.  Every factor is a
+// power of two applied in binary64.  The acceptance test bounds a leaf's coefficients of
+// degree d by about (M/R) theta^d in these units, so no term leaves binary32's range.  A
+// leaf with r_max = 0 has no such bound (single particles can meet in M2L at any
+// separation), but all its particles sit at its centre: the L2P there keeps only the
+// degree-0 terms, read in binary64 (finish_k), and the leaf is skipped here.  One thread
+// per (node, coefficient).
+template <int P, int V, class X>
+__global__ void scale_locals_k(int nn, const int* __restrict__ nnchild, const double* __restrict__ rmax,
+                               const int* __restrict__ nk, const double* __restrict__ loc,
+                               const double* __restrict__ locp, X* __restrict__ locT, X* __restrict__ locpT) {
+    using E = Exp<P>;
+    constexpr int NL = V == 0 ? E::NM : E::NSU, NQ = E::NSU / 4;
+    int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (t >= (int64_t)nn * NL) return;
+    int n = (int)(t / NL), k = (int)(t - (int64_t)n * NL);
+    if (nnchild[n] != 0 || rmax[n] == 0.0) return;
+    int kn = nk[n];
+    int e = V == 0 ? kn * mi_deg(k) : (k < NQ ? kn * (mi_deg(k) + 1) : kn * mi_deg(k % NQ));
+    locT[t] = to_kernel(loc[t] * pow2d(e), X());
+    if (V != 0 && locp && k < E::NM)
+        locpT[(int64_t)n * E::NM + k] = to_kernel(locp[(int64_t)n * E::NM + k] * pow2d(kn * mi_deg(k)), X());
+}
+
 // a11 + a13: far field at every particle from its leaf's locals, plus the leaf's P2P item
-// sums (full chunks in order, then the partial one), written in input order.
-template <int P, int V, class G>
+// sums (full chunks in order, then the partial one), written in input order.  X is the
+// L2P arithmetic: binary64, or the pair-kernel type on the scaled locals above.
+template <int P, int V, class G, class X>
 __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ leaf_of, const int* __restrict__ nfirst,
                                                const double* __restrict__ xs, const double* __restrict__ ys,
                                                const double* __restrict__ zs, const double* __restrict__ Zx,
                                                const double* __restrict__ Zy, const double* __restrict__ Zz,
-                                               const double* __restrict__ loc, const double* __restrict__ locp,
-                                               const long long* __restrict__ fo, const long long* __restrict__ po,
-                                               long long nfull, const long long* __restrict__ islot,
-                                               const Quad<G>* __restrict__ ipart, const uint32_t* __restrict__ perm,
-                                               double* __restrict__ acc_s, double* __restrict__ pot_s,
-                                               double* __restrict__ acc_out, double* __restrict__ pot_out) {
+                                               const double* __restrict__ rmax, const int* __restrict__ nk,
+                                               const double* __restrict__ loc64, const double* __restrict__ locp64,
+                                               const X* __restrict__ loc, const X* __restrict__ locp,
+                                               const long long* __restrict__ fo,
+                                               const long long* __restrict__ po, long long nfull,
+                                               const long long* __restrict__ islot, const Quad<G>* __restrict__ ipart,
+                                               const uint32_t* __restrict__ perm, double* __restrict__ acc_s,
+                                               double* __restrict__ pot_s, double* __restrict__ acc_out,
+                                               double* __restrict__ pot_out) {
     using E = Exp<P>;
+    constexpr bool SC = !std::is_same<X, double>::value;
     int i = blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
     int lf = leaf_of[i];
     int slot = i - nfirst[lf];
     double x = xs[i] - Zx[lf], y = ys[i] - Zy[lf], z = zs[i] - Zz[lf];
+    double sc = 1.0;  // 2^-k in the scaled modes
+    if constexpr (SC) {
+        sc = pow2d(-nk[lf]);
+        x *= sc;
+        y *= sc;
+        z *= sc;
+    }
+    X ux = to_kernel(x, X()), uy = to_kernel(y, X()), uz = to_kernel(z, X());
+    X bx, by, bz, bp = X(0);
     double ax, ay, az, ph = 0.0;
-    if (V == 0) {
-        E::l2p_std(loc + (int64_t)lf * E::NM, x, y, z, ax, ay, az, ph);
+    if (SC && rmax[lf] == 0.0) {
+        // every particle of the leaf is at its centre (x = 0): the degree-0 terms, in binary64
+        // (multi-index order 1 | x y z | ...; conserving rows [S | Ux | Uy | Uz])
+        if (V == 0) {
+            const double* L = loc64 + (int64_t)lf * E::NM;
+            ax = -L[1];
+            ay = -L[2];
+            az = -L[3];
+            ph = L[0];
+        } else {
+            const double* SU = loc64 + (int64_t)lf * E::NSU;
+            constexpr int NQ = E::NSU / 4;
+            ax = SU[NQ];
+            ay = SU[2 * NQ];
+            az = SU[3 * NQ];
+            if (locp64) ph = locp64[(int64_t)lf * E::NM];
+        }
+    } else if (V == 0) {
+        E::l2p_std(loc + (int64_t)lf * E::NM, ux, uy, uz, bx, by, bz, bp);
+        ax = as_double(bx) * sc;
+        ay = as_double(by) * sc;
+        az = as_double(bz) * sc;
+        ph = as_double(bp);
     } else {
-        E::l2p_con(loc + (int64_t)lf * E::NSU, x, y, z, ax, ay, az);
+        E::l2p_con(loc + (int64_t)lf * E::NSU, ux, uy, uz, bx, by, bz);
+        ax = as_double(bx);
+        ay = as_double(by);
+        az = as_double(bz);
         if (locp) {
-            double bx, by, bz;
-            E::l2p_std(locp + (int64_t)lf * E::NM, x, y, z, bx, by, bz, ph);
+            X cx, cy, cz;
+            E::l2p_std(locp + (int64_t)lf * E::NM, ux, uy, uz, cx, cy, cz, bp);
+            ph = as_double(bp);
         }
     }
     double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
@@ -838,33 +905,69 @@ void run_far_field_p(fmm_ctx* c, int variant, bool want_pot) {
     stage_end(c, ST_L2L);
 }
 
-template <int P, class G>
+template <int P, class G, class X>
 static void finish_launch(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
+    using E = Exp<P>;
     cudaStream_t s = c->stream;
     int n = (int)c->N;
+    int nn = (int)c->n_nodes;
     const ItemSet& it = c->p2p_items;
-    const double* locp = (variant != 0 && want_pot) ? c->locp.as<double>() : nullptr;
+    bool pot_con = variant != 0 && want_pot;  // potentials of the realigned forms: standard locals
+    const X* locX = nullptr;
+    const X* locpX = nullptr;
+    if constexpr (std::is_same<X, double>::value) {
+        locX = c->loc.as<double>();
+        locpX = pot_con ? c->locp.as<double>() : nullptr;
+    } else {
+        int NL = variant == 0 ? E::NM : E::NSU;
+        ensure(c->locT, sizeof(X) * (size_t)nn * NL);
+        if (pot_con) ensure(c->locpT, sizeof(X) * (size_t)nn * E::NM);
+        auto sl = [&](auto kern) {
+            kern<<<grid_for((int64_t)nn * NL, EB), EB, 0, s>>>(
+                nn, c->nnchild.as<int>(), c->nrmax.as<double>(), c->nk.as<int>(), c->loc.as<double>(),
+                pot_con ? c->locp.as<double>() : nullptr, c->locT.as<X>(), pot_con ? c->locpT.as<X>() : nullptr);
+        };
+        if (variant == 0)
+            sl(scale_locals_k<P, 0, X>);
+        else
+            sl(scale_locals_k<P, 1, X>);
+        GB_LAUNCH("scale_locals_k");
+        locX = c->locT.as<X>();
+        locpX = pot_con ? c->locpT.as<X>() : nullptr;
+    }
     auto args = [&](auto kern) {
         kern<<<grid_for(n, EB), EB, 0, s>>>(
             n, c->leaf_of.as<int>(), c->nfirst.as<int>(), c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
-            c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->loc.as<double>(), locp,
+            c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->nrmax.as<double>(), c->nk.as<int>(),
+            c->loc.as<double>(), pot_con ? c->locp.as<double>() : nullptr, locX, locpX,
             it.fo.as<long long>(), it.po.as<long long>(), it.n_full, c->p2p_islot.as<long long>(),
             c->p2p_ipart.as<Quad<G>>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
             want_pot ? pot_out : nullptr);
     };
     if (variant == 0)
-        args(finish_k<P, 0, G>);
+        args(finish_k<P, 0, G, X>);
     else
-        args(finish_k<P, 1, G>);
+        args(finish_k<P, 1, G, X>);
     GB_LAUNCH("finish_k");
 }
 
+// the L2P arithmetic follows the pair kernels': binary64, or double-float / binary32 on
+// leaf-scaled locals (the modes' order limits are checked at the API)
 template <int P>
 void run_finish_p(fmm_ctx* c, int variant, bool want_pot, double* acc_out, double* pot_out) {
-    if (c->precision == FMM_FP64)
-        finish_launch<P, double>(c, variant, want_pot, acc_out, pot_out);
-    else
-        finish_launch<P, df64>(c, variant, want_pot, acc_out, pot_out);
+    if (c->precision == FMM_FP64) {
+        finish_launch<P, double, double>(c, variant, want_pot, acc_out, pot_out);
+    } else if (c->precision == FMM_DF64) {
+        if constexpr (P <= FMM_DF64_P_MAX)
+            finish_launch<P, df64, df64>(c, variant, want_pot, acc_out, pot_out);
+        else
+            throw FmmError{FMM_ERR_INVALID, "double-float mode: order above FMM_DF64_P_MAX"};
+    } else {
+        if constexpr (P <= FMM_MIXED_P_MAX)
+            finish_launch<P, df64, float>(c, variant, want_pot, acc_out, pot_out);
+        else
+            throw FmmError{FMM_ERR_INVALID, "mixed mode: order above FMM_MIXED_P_MAX"};
+    }
 }
 
 // One translation unit per order instantiates the order's stages; the M2L launches of

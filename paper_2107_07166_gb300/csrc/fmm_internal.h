@@ -106,6 +106,7 @@ struct fmm_ctx {
     gbfmm::DevBuf mom;   // n_nodes x nmi(p)
     gbfmm::DevBuf loc;   // n_nodes x (nmi(p) | 4 nmi(p-1))
     gbfmm::DevBuf locp;  // standard locals for potentials of the conserving form
+    gbfmm::DevBuf locT, locpT;  // leaf locals in leaf units, pair-kernel type (scaled-mode L2P)
     // lists
     double list_theta = -1.0;
     int64_t n_m2l = 0, n_p2p = 0;
