@@ -167,9 +167,9 @@ GBFMM_API int fmm_get_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p);
  * again with larger buffers (see fmm_walk_retries); the results do not depend on the
  * sizes.  Invalidates cached lists. */
 GBFMM_API int fmm_set_walk_capacity(fmm_ctx *c, int64_t frontier, int64_t m2l, int64_t p2p);
-/* Tile shapes: directed M2L entries per M2L work item (default 32) and directed P2P
- * entries per reduction item (default 64), each in [1, 4096].  Results change only in
- * summation order.  Invalidates cached lists. */
+/* Tile shapes: directed M2L entries per M2L work item (default 32; 64 in FMM_MIXED) and
+ * directed P2P entries per reduction item (default 64), each in [1, 4096].  Results change
+ * only in summation order.  Invalidates cached lists. */
 GBFMM_API int fmm_set_tiles(fmm_ctx *c, int m2l_chunk, int p2p_chunk);
 
 /* Autotuner: times build + forces (p, theta, variant, no potentials) on the given input

@@ -97,6 +97,10 @@ int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
     if (!c) return fail(FMM_ERR_OOM, "fmm_create: host allocation failed");
     c->device = device;
     c->precision = precision;
+    // the binary32 M2L is cheap next to the binary64 reduction of its item partials, so its
+    // work items are longer (measured at N = 2^20: 32 entries is best in binary64, 64 in
+    // binary32; double-float is indifferent)
+    if (precision == FMM_MIXED) c->m2l_chunk = gbfmm::M2L_CHUNK_MIXED;
     int rc = guarded(c, [&]() -> int {
         if (cuda_stream) {
             c->stream = static_cast<cudaStream_t>(cuda_stream);

@@ -207,6 +207,39 @@ __device__ __forceinline__ void load_f4(const float* __restrict__ src, float* ds
 }
 
 // geometry of the M2L kernels
+// a5 in the double-float and binary32 modes: y = X - Z in binary64, in units of the leaf
+// 2^k (k = floor(log2 r_max), so |y| 2^-k < 2 and no monomial leaves binary32's range), then
+// the monomials and their sums in double-float (about 2^-44 relative) on the binary32
+// units; moment alpha is stored in binary64 times 2^(k |alpha|) (exact) for the binary64
+// M2M.  Leaves in order of size, as above.
+template <int P>
+__global__ void __launch_bounds__(EB) p2m_df_k(int nn, const uint32_t* __restrict__ order,
+                                               const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                                               const int* __restrict__ nnchild, const double* __restrict__ rmax,
+                                               const double* __restrict__ xs,
+                                               const double* __restrict__ ys, const double* __restrict__ zs,
+                                               const double* __restrict__ ms, const double* __restrict__ Zx,
+                                               const double* __restrict__ Zy, const double* __restrict__ Zz,
+                                               double* __restrict__ mom) {
+    using E = Exp<P>;
+    int t = blockIdx.x * EB + threadIdx.x;
+    if (t >= nn) return;
+    int nd = (int)order[t];
+    if (nnchild[nd] != 0) return;
+    df64 M[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) M[k] = df64();
+    double r = rmax[nd];
+    int kn = r > 0.0 ? max(-120, min(120, ilogb(r))) : 0;
+    double sc = pow2d(-kn);
+    double zx = Zx[nd], zy = Zy[nd], zz = Zz[nd];
+    int f = nfirst[nd], e = f + ncount[nd];
+    for (int i = f; i < e; i++)
+        E::p2m(to_df(ms[i]), to_df((xs[i] - zx) * sc), to_df((ys[i] - zy) * sc), to_df((zs[i] - zz) * sc), M);
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) mom[(int64_t)nd * E::NM + k] = to_double(M[k]) * pow2d(kn * mi_deg(k));
+}
+
 struct M2LGeom {
     const double *Zx, *Zy, *Zz;  // binary64 centres
     const float4 *zh, *zl;       // double-float centres (scaled modes)
@@ -755,11 +788,25 @@ void run_moments_p(fmm_ctx* c) {
     cudaStream_t s = c->stream;
     int nn = (int)c->n_nodes;
     ensure(c->mom, sizeof(double) * (size_t)nn * E::NM);
-    p2m_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->leaf_order.as<uint32_t>(), c->nfirst.as<int>(),
-                                             c->ncount.as<int>(), c->nnchild.as<int>(),
-                                             c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
-                                             c->ms.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
-                                             c->nZz.as<double>(), c->mom.as<double>());
+    auto p2m64 = [&]() {
+        p2m_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->leaf_order.as<uint32_t>(), c->nfirst.as<int>(),
+                                                 c->ncount.as<int>(), c->nnchild.as<int>(), c->xs.as<double>(),
+                                                 c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>(),
+                                                 c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                                                 c->mom.as<double>());
+    };
+    if constexpr (P > FMM_MIXED_P_MAX) {  // binary64 only at these orders
+        p2m64();
+    } else {
+        if (c->precision == FMM_FP64)
+            p2m64();
+        else
+            p2m_df_k<P><<<grid_for(nn, EB), EB, 0, s>>>(
+                nn, c->leaf_order.as<uint32_t>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->nnchild.as<int>(),
+                c->nrmax.as<double>(), c->xs.as<double>(), c->ys.as<double>(), c->zs.as<double>(),
+                c->ms.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                c->mom.as<double>());
+    }
     GB_LAUNCH("p2m_k");
     for (int l = c->n_levels - 2; l >= 0; l--) {
         int lo = c->level_start[l], hi = c->level_start[l + 1];

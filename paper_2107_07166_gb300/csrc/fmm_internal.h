@@ -58,6 +58,7 @@ struct ItemSet {
 };
 
 constexpr int M2L_CHUNK = 32;
+constexpr int M2L_CHUNK_MIXED = 64;  // default in FMM_MIXED
 constexpr int P2P_CHUNK = 64;
 
 enum Stage {
