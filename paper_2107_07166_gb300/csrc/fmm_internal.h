@@ -101,6 +101,7 @@ struct fmm_ctx {
     std::vector<int> level_start;              // size n_levels + 1
     gbfmm::DevBuf nfirst, ncount, nlevel, nparent, nchildf, nnchild;
     gbfmm::DevBuf nM, nSx, nSy, nSz, nZx, nZy, nZz, nr2, nrmax;
+    gbfmm::DevBuf nr2f;                        // binary32 estimate of r_max^2 (prefilter)
     gbfmm::DevBuf leaf_key, leaf_key2, leaf_order, leaf_order2;  // nodes by leaf size (per-leaf kernels)
     // expansions
     int mom_p = -1;

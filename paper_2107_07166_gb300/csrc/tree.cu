@@ -260,27 +260,107 @@ __global__ void com_inner_k(int lo, int hi, const int* __restrict__ nfirst, cons
 
 // ------------------------------------------------------------------ r_max
 
-// For every level, each particle computes its squared distance to the COM of its node at
-// that level; equal nodes are contiguous in sorted order, so a segmented warp maximum
-// leaves one integer atomicMax (on the bit pattern of a non-negative double, which
-// orders like the value) per node and warp.  Max is order independent: bit exact.
+// Every node's centre as double-float words: zh = (hi(Z), 0), zl = (lo(Z), 0); rmax_k fills
+// zh.w with r_max rounded up.  The walk's binary32 acceptance prefilter, the binary32 M2L
+// separations and the r_max prefilter below read these.
+__global__ void centre_words_k(int nn, const double* __restrict__ Zx, const double* __restrict__ Zy,
+                               const double* __restrict__ Zz, float4* __restrict__ zh, float4* __restrict__ zl) {
+    int nd = blockIdx.x * TB + threadIdx.x;
+    if (nd >= nn) return;
+    double z[3] = {Zx[nd], Zy[nd], Zz[nd]};
+    float h[3], l[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        h[i] = (float)z[i];
+        l[i] = (float)(z[i] - (double)h[i]);
+    }
+    zh[nd] = make_float4(h[0], h[1], h[2], 0.f);
+    zl[nd] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// r_max^2 = max over the node's particles of |X - Z|^2 for every node, exact in binary64
+// (A11), in two passes over (particle, level).  Equal nodes are contiguous in sorted order,
+// so a segmented warp maximum leaves one integer atomicMax per node and warp (on the bit
+// pattern of a non-negative number, which orders like the value); max is order
+// independent, so the result is bit exact.
+//  * Pass 1 (binary32): |X - Z|^2 from the double-float words of X and Z, (hi - hi) +
+//    (lo - lo) per axis; its relative error is below 2^-20 while r_max >= 2^-20 |Z| and
+//    nothing under- or overflows.  The node's maximum m goes to r2f.
+//  * Pass 2: a particle whose binary32 estimate is within 2^-16 of m, or of a node outside
+//    that range, forms |X - Z|^2 in binary64 (the formula of the oracle) for the exact max.
+//    The binary64 work falls from every (particle, level) to the few near the maximum.
+__device__ __forceinline__ void split_df(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+__device__ __forceinline__ float d2_words(float xh, float xl, float yh, float yl, float zh_, float zl_, float4 ch,
+                                          float4 cl) {
+    float dx = __fadd_rn(__fsub_rn(xh, ch.x), __fsub_rn(xl, cl.x));
+    float dy = __fadd_rn(__fsub_rn(yh, ch.y), __fsub_rn(yl, cl.y));
+    float dz = __fadd_rn(__fsub_rn(zh_, ch.z), __fsub_rn(zl_, cl.z));
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__global__ void rmax2f_k(int n, int nlev, const int* __restrict__ nal, const double* __restrict__ xs,
+                         const double* __restrict__ ys, const double* __restrict__ zs, const float4* __restrict__ zh,
+                         const float4* __restrict__ zl, unsigned* __restrict__ r2f) {
+    int i = blockIdx.x * TB + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    bool in = i < n;
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh_ = 0.f, zl_ = 0.f;
+    if (in) {
+        split_df(xs[i], xh, xl);
+        split_df(ys[i], yh, yl);
+        split_df(zs[i], zh_, zl_);
+    }
+    for (int l = 0; l < nlev; l++) {
+        int nd = in ? nal[(int64_t)l * n + i] : -1;
+        unsigned v = 0u;
+        if (nd >= 0) v = __float_as_uint(d2_words(xh, xl, yh, yl, zh_, zl_, zh[nd], zl[nd]));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            unsigned u = __shfl_down_sync(FULL, v, off);
+            int no = __shfl_down_sync(FULL, nd, off);
+            if (lane + off < 32 && no == nd && u > v) v = u;
+        }
+        int prev = __shfl_up_sync(FULL, nd, 1);
+        bool head = (lane == 0) || (prev != nd);
+        if (head && nd >= 0 && v != 0u) atomicMax(&r2f[nd], v);
+    }
+}
+
 __global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const double* __restrict__ xs,
                         const double* __restrict__ ys, const double* __restrict__ zs,
                         const double* __restrict__ Zx, const double* __restrict__ Zy,
-                        const double* __restrict__ Zz, unsigned long long* __restrict__ r2bits) {
+                        const double* __restrict__ Zz, const float4* __restrict__ zh, const float4* __restrict__ zl,
+                        const unsigned* __restrict__ r2f, unsigned long long* __restrict__ r2bits) {
     int i = blockIdx.x * TB + threadIdx.x;
     int lane = threadIdx.x & 31;
     bool in = i < n;
     double px = in ? xs[i] : 0.0, py = in ? ys[i] : 0.0, pz = in ? zs[i] : 0.0;
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh_ = 0.f, zl_ = 0.f;
+    if (in) {
+        split_df(px, xh, xl);
+        split_df(py, yh, yl);
+        split_df(pz, zh_, zl_);
+    }
     for (int l = 0; l < nlev; l++) {
         int nd = in ? nal[(int64_t)l * n + i] : -1;
         unsigned long long v = 0ull;
         if (nd >= 0) {
-            double dx = __dsub_rn(px, Zx[nd]);
-            double dy = __dsub_rn(py, Zy[nd]);
-            double dz = __dsub_rn(pz, Zz[nd]);
-            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            v = (unsigned long long)__double_as_longlong(d2);
+            float4 ch = zh[nd], cl = zl[nd];
+            float m = __uint_as_float(r2f[nd]);
+            float z2 = ch.x * ch.x + ch.y * ch.y + ch.z * ch.z;
+            bool ranged = m >= 0x1p-100f && m <= 0x1p100f && m >= 0x1p-40f * z2;
+            bool cand = !ranged || d2_words(xh, xl, yh, yl, zh_, zl_, ch, cl) >= m * (1.f - 0x1p-16f);
+            if (cand) {
+                double dx = __dsub_rn(px, Zx[nd]);
+                double dy = __dsub_rn(py, Zy[nd]);
+                double dz = __dsub_rn(pz, Zz[nd]);
+                double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                v = (unsigned long long)__double_as_longlong(d2);
+            }
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -290,29 +370,18 @@ __global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const doub
         }
         int prev = __shfl_up_sync(FULL, nd, 1);
         bool head = (lane == 0) || (prev != nd);
-        if (head && nd >= 0) atomicMax(&r2bits[nd], v);
+        if (head && nd >= 0 && v != 0ull) atomicMax(&r2bits[nd], v);
     }
 }
 
-// r_max, plus every node's centre as double-float words with r_max rounded up to binary32
-// (zh = (hi(Z), r_max up), zl = (lo(Z), 0)): the walk's binary32 acceptance prefilter and
-// the binary32 M2L separations read these
-__global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, const double* __restrict__ Zx,
-                       const double* __restrict__ Zy, const double* __restrict__ Zz, double* __restrict__ rmax,
-                       float4* __restrict__ zh, float4* __restrict__ zl) {
+// r_max from its square; zh.w = r_max rounded up to binary32 (the centre words are set)
+__global__ void rmax_k(int nn, const unsigned long long* __restrict__ r2bits, double* __restrict__ rmax,
+                       float4* __restrict__ zh) {
     int nd = blockIdx.x * TB + threadIdx.x;
     if (nd >= nn) return;
     double r = __dsqrt_rn(__longlong_as_double((long long)r2bits[nd]));
     rmax[nd] = r;
-    double z[3] = {Zx[nd], Zy[nd], Zz[nd]};
-    float h[3], l[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        h[i] = (float)z[i];
-        l[i] = (float)(z[i] - (double)h[i]);
-    }
-    zh[nd] = make_float4(h[0], h[1], h[2], __double2float_ru(r));
-    zl[nd] = make_float4(l[0], l[1], l[2], 0.f);
+    zh[nd].w = __double2float_ru(r);
 }
 
 // ------------------------------------------------------------------ batches of systems
@@ -579,16 +648,25 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
                                                          c->nZy.as<double>(), c->nZz.as<double>());
         GB_LAUNCH("com_inner_k");
     }
-    // r_max
+    // r_max: binary32 prefilter, then binary64 for the particles near each node's maximum
+    ensure(c->zhl, sizeof(float4) * 2 * (size_t)nn);
+    float4* zh = c->zhl.as<float4>();
+    float4* zl = zh + nn;
+    centre_words_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                                                   zh, zl);
+    GB_LAUNCH("centre_words_k");
+    ensure(c->nr2f, sizeof(unsigned) * (size_t)nn);
+    GB_CUDA(cudaMemsetAsync(c->nr2f.p, 0, sizeof(unsigned) * (size_t)nn, s));
     GB_CUDA(cudaMemsetAsync(c->nr2.p, 0, sizeof(unsigned long long) * (size_t)nn, s));
+    rmax2f_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->nal.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+                                            c->zs.as<double>(), zh, zl, c->nr2f.as<unsigned>());
+    GB_LAUNCH("rmax2f_k");
     rmax2_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->nal.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
                                            c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
-                                           c->nZz.as<double>(), c->nr2.as<unsigned long long>());
+                                           c->nZz.as<double>(), zh, zl, c->nr2f.as<unsigned>(),
+                                           c->nr2.as<unsigned long long>());
     GB_LAUNCH("rmax2_k");
-    ensure(c->zhl, sizeof(float4) * 2 * (size_t)nn);
-    rmax_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nr2.as<unsigned long long>(), c->nZx.as<double>(),
-                                           c->nZy.as<double>(), c->nZz.as<double>(), c->nrmax.as<double>(),
-                                           c->zhl.as<float4>(), c->zhl.as<float4>() + nn);
+    rmax_k<<<grid_for(nn, TB), TB, 0, s>>>(nn, c->nr2.as<unsigned long long>(), c->nrmax.as<double>(), zh);
     GB_LAUNCH("rmax_k");
     // nodes by leaf size for the per-leaf kernels (one stable 9-bit radix pass)
     ensure(c->leaf_key, sizeof(uint32_t) * (size_t)nn);
