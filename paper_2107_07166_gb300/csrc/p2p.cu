@@ -555,8 +555,13 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
 }
 
 // a12/a13 first level: one warp per P2P work item (up to P2P_CHUNK directed entries of
-// one leaf); lane = particle slot of the leaf.  Sums the per-pair partials of the
-// item's entries (in list order) into ipart[islot[item] + slot].
+// one leaf).  Sums the per-pair partials of the item's entries into
+// ipart[islot[item] + slot].  A leaf of cnt <= 32 particles uses 32 / cnt lane groups of
+// cnt lanes (lane = particle slot): group g sums entries g, g + groups, ... in list order,
+// and the group sums are added in group order, so the sum runs in one fixed order while
+// most lanes work (leaves hold ~9 particles; one lane per slot left two thirds of the
+// warp idle, and idle lanes cost full binary64 issue).  Larger leaves take one entry
+// stream per slot.
 //   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
 //   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
 // acc + v for the item sums: binary64 and double-float partials add as usual; a binary32
@@ -572,41 +577,67 @@ __device__ __forceinline__ df64 acc_add(df64 acc, float v) {
 __device__ __forceinline__ double acc_fin(double a) { return a; }
 __device__ __forceinline__ df64 acc_fin(df64 a) { return fast_two_sum(a.hi, a.lo); }
 
+__device__ __forceinline__ double shfl_g(double v, int src) { return __shfl_sync(FULL, v, src); }
+__device__ __forceinline__ df64 shfl_g(df64 v, int src) {
+    return df64(__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src));
+}
+
+// sum of the partials of entries e0, e0 + step, ... < e1 for one slot, four in flight
+template <class G, class PT>
+__device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, int slot,
+                                              const long long* __restrict__ pbase,
+                                              const Quad<PT>* __restrict__ part) {
+    Quad<G> acc{G(0), G(0), G(0), G(0)};
+    int e = e0;
+    for (; e + 3 * step < e1; e += 4 * step) {
+        Quad<PT> q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = part[pbase[e + u * step] + slot];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            acc.x = acc_add(acc.x, q[u].x);
+            acc.y = acc_add(acc.y, q[u].y);
+            acc.z = acc_add(acc.z, q[u].z);
+            acc.w = acc_add(acc.w, q[u].w);
+        }
+    }
+    for (; e < e1; e += step) {
+        Quad<PT> q = part[pbase[e] + slot];
+        acc.x = acc_add(acc.x, q.x);
+        acc.y = acc_add(acc.y, q.y);
+        acc.z = acc_add(acc.z, q.z);
+        acc.w = acc_add(acc.w, q.w);
+    }
+    return Quad<G>{acc_fin(acc.x), acc_fin(acc.y), acc_fin(acc.z), acc_fin(acc.w)};
+}
+
 template <class G, class PT>
 __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
                                                    const int* __restrict__ ncount, const long long* __restrict__ pbase,
                                                    const Quad<PT>* __restrict__ part,
                                                    const long long* __restrict__ islot, Quad<G>* __restrict__ ipart) {
-    int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;
+    int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;  // one item per warp
     int lane = threadIdx.x & 31;
     if (it >= nitems) return;
     int4 w = items[it];
     int cnt = ncount[w.x];
-    for (int slot = lane; slot < cnt; slot += 32) {
-        Quad<G> acc{G(0), G(0), G(0), G(0)};
-        int e = w.y;
-        // four partials in flight at a time; the sum still runs in entry order
-        for (; e + 4 <= w.z; e += 4) {
-            Quad<PT> q[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) q[u] = part[pbase[e + u] + slot];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                acc.x = acc_add(acc.x, q[u].x);
-                acc.y = acc_add(acc.y, q[u].y);
-                acc.z = acc_add(acc.z, q[u].z);
-                acc.w = acc_add(acc.w, q[u].w);
-            }
-        }
-        for (; e < w.z; e++) {
-            Quad<PT> q = part[pbase[e] + slot];
-            acc.x = acc_add(acc.x, q.x);
-            acc.y = acc_add(acc.y, q.y);
-            acc.z = acc_add(acc.z, q.z);
-            acc.w = acc_add(acc.w, q.w);
-        }
-        ipart[islot[it] + slot] = Quad<G>{acc_fin(acc.x), acc_fin(acc.y), acc_fin(acc.z), acc_fin(acc.w)};
+    if (cnt > 32) {
+        for (int slot = lane; slot < cnt; slot += 32)
+            ipart[islot[it] + slot] = gather_run<G, PT>(w.y, w.z, 1, slot, pbase, part);
+        return;
     }
+    int groups = 32 / cnt, grp = lane / cnt, slot = lane - grp * cnt;
+    Quad<G> own{G(0), G(0), G(0), G(0)};
+    if (grp < groups) own = gather_run<G, PT>(w.y + grp, w.z, groups, slot, pbase, part);
+    // group 0's lanes add the other groups' sums (read from the unchanged own values) in
+    // group order
+    Quad<G> acc = own;
+    for (int g = 1; g < groups; g++) {
+        int src = lane + g * cnt;  // < 32 for group 0's lanes
+        Quad<G> o{shfl_g(own.x, src), shfl_g(own.y, src), shfl_g(own.z, src), shfl_g(own.w, src)};
+        acc = Quad<G>{acc.x + o.x, acc.y + o.y, acc.z + o.z, acc.w + o.w};
+    }
+    if (grp == 0) ipart[islot[it] + slot] = acc;
 }
 
 // first partial slot of every directed P2P entry: its pair's block, then (for side 1) past
