@@ -289,7 +289,7 @@ constexpr int RING_CHUNKS = 2;
 // g = c w + i of the larger ("lane") leaf in chunk c, shifted by that leaf's side of
 // R = Z_A - Z_B; the smaller ("ring") leaf sits in shared memory as two float4 arrays
 // (high words and mass, low words), so that a quarter-warp's 16-byte reads are
-// contiguous.  A lane holds RING_CHUNKS chunks at a time: every ring particle read meets
+// contiguous, each stored twice in a row so that the ring index never wraps.  A lane holds RING_CHUNKS chunks at a time: every ring particle read meets
 // all of them.  In step k lane i meets ring particle j = (i + k) mod w: over w steps
 // every (g, j) of the chunks meets exactly once.  The pair force is formed once and
 // applied to both partners: g's sum stays in lane i and is stored after its chunk, j's
@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
                                                  const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                  const PState<df64>* __restrict__ pos, const df64* __restrict__ sep,
                                                  Quad<float>* __restrict__ part) {
-    __shared__ float4 sH[PW][32], sL[PW][32];
+    // the ring leaf twice in a row per segment (slots 0..w-1, 0..w-1): lane i reads slot
+    // i + k without wrapping, at a fixed stride from one pointer
+    __shared__ float4 sH[PW][64], sL[PW][64];
     __shared__ int ts[34], tc[34], tw[34];
     for (int t = threadIdx.x; t < 34; t += PB) {
         ts[t] = tab->start[t];
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
         int per = 32 / W;
         int sg = lane / W;
         bool live = sg < per;
-        // a lane past the last segment reads slot j of segment 0 (in bounds, unused)
+        // a lane past the last segment reads segment 0's rows (in bounds, unused)
         int i = live ? lane - sg * W : 0, base = live ? sg * W : 0;
         int64_t li = (q - tw[W]) * per + sg;
         bool ok = live && li < tc[W];
@@ -354,10 +356,13 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
             rz = -rz;
         }
         __syncwarp();
-        if (ok) {  // i < W = the ring leaf's count
+        if (ok) {  // i < W = the ring leaf's count; the segment's rows are [2 base, 2 base + 2 W)
             PState<df64> b = pos[fR + i];
-            sH[w][lane] = make_float4(b.x.hi, b.y.hi, b.z.hi, b.m.hi);
-            sL[w][lane] = make_float4(b.x.lo, b.y.lo, b.z.lo, 0.f);
+            float4 h = make_float4(b.x.hi, b.y.hi, b.z.hi, b.m.hi), lo = make_float4(b.x.lo, b.y.lo, b.z.lo, 0.f);
+            sH[w][2 * base + i] = h;
+            sH[w][2 * base + W + i] = h;
+            sL[w][2 * base + i] = lo;
+            sL[w][2 * base + W + i] = lo;
         }
         __syncwarp();
         int m = ok ? (self ? 1 : (nL + W - 1) / W) : 0;
@@ -382,9 +387,11 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
                     ma[r] = qa.m.hi;
                 }
             }
-            int j = i;
+            const float4* rh = &sH[w][2 * base + i];  // slot i + kk for kk < W: row < 2 base + 2 W <= 64
+            const float4* rl = &sL[w][2 * base + i];
+#pragma unroll 4
             for (int kk = 0; kk < W; kk++) {
-                float4 bh = sH[w][base + j], bl = sL[w][base + j];
+                float4 bh = rh[kk], bl = rl[kk];
 #pragma unroll
                 for (int r = 0; r < RING_CHUNKS; r++)
                     if (mine[r]) ring_pair<POT>(ah[r], al[r], ma[r], bh, bl, acc[r], bx, by, bz, bp);
@@ -392,7 +399,6 @@ __global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab
                 by = __shfl_sync(FULL, by, nxt);
                 bz = __shfl_sync(FULL, bz, nxt);
                 if (POT) bp = __shfl_sync(FULL, bp, nxt);
-                j = (j + 1 == W) ? 0 : j + 1;
             }
 #pragma unroll
             for (int r = 0; r < RING_CHUNKS; r++)
