@@ -297,8 +297,10 @@ constexpr int RING_CHUNKS = 2;
 // after every full turn and collects all chunks before it is stored.  A self pair runs
 // one chunk over itself from both ends (each pair twice, 1/w of the work, no reduction)
 // and drops the travelling sums.  Every sum runs in a fixed order.
+// Eight blocks per SM (64 registers): 28 -> 32 warps per SM took 10% off the binary32
+// P2P; 48 registers spilled into the ring loop and lost it again.
 template <bool POT>
-__global__ void __launch_bounds__(PB) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
+__global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
                                                  const int2* __restrict__ pairs, const long long* __restrict__ off,
                                                  const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                  const PState<df64>* __restrict__ pos, const df64* __restrict__ sep,
