@@ -93,7 +93,7 @@ __global__ void rs_hist_k(const K* __restrict__ keys, int64_t n, int shift, uint
 }
 
 template <class K, bool V>
-__global__ void __launch_bounds__(RS_BLOCK) rs_scatter_k(const K* __restrict__ kin,
+__global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 4 : 2) rs_scatter_k(const K* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin,
                                                          K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          int64_t n, int shift, const uint32_t* __restrict__ offs,
