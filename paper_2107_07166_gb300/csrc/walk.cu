@@ -116,7 +116,7 @@ __device__ __forceinline__ void st_status(unsigned long long* p, unsigned tag, i
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(WB) walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out,
+__global__ void __launch_bounds__(WB, 6) walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out,
                                                   WalkCounters* __restrict__ cnt, int par, int step,
                                                   unsigned long long* __restrict__ status, NodeView nv,
                                                   double theta, float th2, int2* __restrict__ m2l, int cap_m2l,
