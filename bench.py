@@ -139,7 +139,9 @@ def algorithmic_flops(counts, tree_counts, p, variant):
 # DRAM bytes (read + write) per unit of the dominant binary64 kernels, from an ncu capture
 # of their DRAM counters at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md), scaled
 # here by the units of the timed launch: per mutual M2L pair, per particle pair.
-NCU_TRAFFIC_PER_UNIT = {("m2l_con_k", "fp64"): 58.9, ("p2p_k", "fp64"): 5.12}
+# DRAM bytes per unit from ncu at N = 2^19 (profiles/): the binary64 M2L stage is the pair-tensor
+# kernel plus m2l_con_t_k (per mutual pair), the binary64 P2P is p2p_k (per particle pair)
+NCU_TRAFFIC_PER_UNIT = {("m2l_con_t_k", "fp64"): 659.0, ("p2p_k", "fp64"): 5.13}
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
@@ -420,13 +422,19 @@ def run_gbfmm(args):
                  + ("; the double-float kernels run on the binary32 units and are rated against the binary64 "
                     "peak they replace" if args.precision == "df64" else ""))
     achieved = work[dom] / (stage_avg[dom] / 1e3) / 1e12
-    kname = ("m2l_con_k" if variant == 1 else "m2l_std_k") if dom == "m2l" else "p2p_k"
+    if dom == "m2l":
+        shared = args.precision == "fp64" and W["p"] <= 6  # binary64 M2L on shared pair tensors
+        kname = ("m2l_con" if variant == 1 else "m2l_std") + ("_t_k" if shared else "_k")
+    else:
+        kname = "p2p_k" if args.precision != "mixed" else "p2p_ring_k"
     per_unit = NCU_TRAFFIC_PER_UNIT.get((kname, args.precision)) if W["p"] == 4 else None
     units = work["n_m2l"] if dom == "m2l" else work["n_pp"]
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": (round(per_unit * units) if per_unit else None),
-                "traffic_basis": ("ncu dram bytes per unit at N=2^19, scaled to this launch" if per_unit else None),
+                "traffic_basis": (("ncu dram bytes per unit at N=2^19 (m2l_ptensor_k + m2l_con_t_k, the M2L stage), "
+                                   "scaled to this launch") if per_unit and dom == "m2l" else
+                                  ("ncu dram bytes per unit at N=2^19, scaled to this launch" if per_unit else None)),
                 "kernel": kname,
                 "peak_basis": basis, "sm_mhz_median": sm_mhz}
     cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n and args.workload == "plummer1m") else None

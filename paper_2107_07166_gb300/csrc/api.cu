@@ -128,7 +128,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->rs_hist, &c->rs_offs, &c->cur, &c->nal, &c->leaf_of, &c->nfirst, &c->ncount,
                           &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nr2f, &c->nrmax, &c->leaf_key, &c->leaf_key2, &c->leaf_order, &c->leaf_order2, &c->mom, &c->loc, &c->locp, &c->locT, &c->locpT, &c->fr0,
-                          &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_seg,
+                          &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_dirp, &c->m2l_pth, &c->m2l_ptd, &c->m2l_seg,
                           &c->p2p_dval, &c->p2p_psize, &c->p2p_pbase, &c->seg_k, &c->seg_k2, &c->seg_v2, &c->walk_status, &c->seg_cnt, &c->p2p_seg, &c->p2p_off, &c->p2p_part,
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,

@@ -429,6 +429,98 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::fin(SU[k]);
 }
 
+// Binary64 M2L with shared pair tensors.  The tensor of R = Z_A - Z_B (D for the standard
+// form, h for the conserving one) is formed once per mutual pair; the entry of cell A
+// (side 0) uses it as it is, the entry of cell B (side 1) sees R' = -R, whose tensor is the
+// same with the odd degrees negated.  That is exact: every term of a component of degree n
+// carries n factors of R, and binary64 rounding is symmetric, so the result is the one
+// the per-entry tensor gives.  It halves the tensor work of the binary64-bound M2L; the
+// tensors come from memory, whose latency the binary64 pipe hides.
+template <int P, int V>
+__global__ void __launch_bounds__(EB) m2l_ptensor_k(int64_t npairs, const int2* __restrict__ pairs,
+                                                    const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                    const double* __restrict__ Zz, double* __restrict__ T) {
+    using E = Exp<P>;
+    constexpr int NT = V == 0 ? E::NM : E::NQ;
+    int64_t k = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (k >= npairs) return;
+    int2 pr = pairs[k];
+    double rx = Zx[pr.x] - Zx[pr.y], ry = Zy[pr.x] - Zy[pr.y], rz = Zz[pr.x] - Zz[pr.y];
+    double H[NT];
+    if constexpr (V == 0)
+        E::dtensor(rx, ry, rz, H);
+    else
+        E::htensor(rx, ry, rz, H);
+#pragma unroll
+    for (int j = 0; j < NT; j++) T[k * NT + j] = H[j];
+}
+
+// the pair tensor of entry v = pair << 1 | side, as seen from the entry's target
+template <int NT>
+__device__ __forceinline__ void load_pair_tensor(const double* __restrict__ T, uint32_t v, double* __restrict__ H) {
+    const double* Tp = T + (int64_t)(v >> 1) * NT;
+    unsigned long long flip = (v & 1u) ? 0x8000000000000000ull : 0ull;
+#pragma unroll
+    for (int j = 0; j < NT; j++) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(Tp[j]);
+        if (mi_deg(j) & 1) b ^= flip;
+        H[j] = __longlong_as_double((long long)b);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(EB) m2l_std_t_k(int64_t nitems, const int4* __restrict__ items,
+                                                  const uint32_t* __restrict__ dir, const uint32_t* __restrict__ dirp,
+                                                  const double* __restrict__ T, const double* __restrict__ mom,
+                                                  double* __restrict__ part) {
+    using E = Exp<P>;
+    int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
+    double L[E::NM];
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) L[k] = 0.0;
+    for (int e = w.y; e < w.z; e++) {
+        int src = (int)dir[e];
+        double D[E::NM];
+        load_pair_tensor<E::NM>(T, dirp[e], D);
+        E::m2l_std(mom + (int64_t)src * E::NM, D, L);
+    }
+#pragma unroll
+    for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = L[k];
+}
+
+template <int P>
+__global__ void __launch_bounds__(EB) m2l_con_t_k(int64_t nitems, const int4* __restrict__ items,
+                                                  const uint32_t* __restrict__ dir, const uint32_t* __restrict__ dirp,
+                                                  M2LGeom g, const double* __restrict__ T,
+                                                  const double* __restrict__ cmom, double* __restrict__ part) {
+    using E = Exp<P>;
+    int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
+    double SU[E::NSU];
+#pragma unroll
+    for (int k = 0; k < E::NSU; k++) SU[k] = 0.0;
+    TgtGeo<double> tg;
+    tg.load(g, w.x);
+    int src = (int)dir[w.y];  // an item holds at least one entry
+    SrcGeo<double> sg;
+    sg.load(g, src);
+    for (int e = w.y; e < w.z; e++) {
+        int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
+        double rx, ry, rz;
+        tg.sep(sg, rx, ry, rz);
+        double H[E::NQ];
+        load_pair_tensor<E::NQ>(T, dirp[e], H);
+        E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
+        src = nsrc;
+        sg.load(g, src);
+    }
+#pragma unroll
+    for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = SU[k];
+}
+
 // a8'' M2L, literal order-0 realigned form (eq. aaB0), run at expansion order 2: from the
 // raw moments of the source (M = M_0, Qbar_ii = 2 M_{2e_i}, Qbar_ij = M_{e_i+e_j}) the
 // degree-1 conserving locals of
@@ -845,6 +937,27 @@ void run_moments_p(fmm_ctx* c) {
     GB_LAUNCH("scale_moments_k");
 }
 
+// the binary64 pair tensors of the current lists at order P (V = 0: D, V = 1: h), formed
+// once per walk and order
+template <int P, int V>
+static const double* pair_tensors(fmm_ctx* c, DevBuf& buf, int64_t& gen, int& order) {
+    using E = Exp<P>;
+    constexpr int NT = V == 0 ? E::NM : E::NQ;
+    int64_t np = c->n_m2l;
+    if (gen != c->walk_gen || order != P) {
+        ensure(buf, sizeof(double) * (size_t)NT * (size_t)(np > 0 ? np : 1));
+        if (np > 0) {
+            m2l_ptensor_k<P, V><<<grid_for(np, EB), EB, 0, c->stream>>>(
+                np, c->m2l_pairs.as<int2>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                buf.as<double>());
+            GB_LAUNCH("m2l_ptensor_k");
+        }
+        gen = c->walk_gen;
+        order = P;
+    }
+    return buf.as<double>();
+}
+
 template <int P, class T>
 void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     using E = Exp<P>;
@@ -889,6 +1002,11 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         if (ni > 0) {
             if constexpr (P >= 7) {
                 m2l_generic_launch(c, P, 1, reinterpret_cast<double*>(part));
+            } else if constexpr (std::is_same<T, double>::value) {
+                const double* pt = pair_tensors<P, 1>(c, c->m2l_pth, c->pth_gen, c->pth_p);
+                m2l_con_t_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir,
+                                                               c->m2l_dirp.as<uint32_t>(), g, pt, cmom, part);
+                GB_LAUNCH("m2l_con_t_k");
             } else {
                 m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, cmom, part,
                                                                 kpart);
@@ -903,6 +1021,11 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
         if (ni > 0) {
             if constexpr (P >= 7) {
                 m2l_generic_launch(c, P, 0, reinterpret_cast<double*>(part));
+            } else if constexpr (std::is_same<T, double>::value) {
+                const double* pt = pair_tensors<P, 0>(c, c->m2l_ptd, c->ptd_gen, c->ptd_p);
+                m2l_std_t_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir,
+                                                               c->m2l_dirp.as<uint32_t>(), pt, mom, part);
+                GB_LAUNCH("m2l_std_t_k");
             } else {
                 m2l_std_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,
                                                                 kpart);

@@ -120,6 +120,10 @@ struct fmm_ctx {
     int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
     gbfmm::DevBuf m2l_dir;                     // uint32 source ids, per-target segments in list order
+    gbfmm::DevBuf m2l_dirp;                    // uint32 (pair << 1 | side) of the same entries
+    gbfmm::DevBuf m2l_pth, m2l_ptd;            // binary64 h and D tensors of every M2L pair
+    int64_t pth_gen = -1, ptd_gen = -1;        // walk the pair tensors belong to ...
+    int pth_p = -1, ptd_p = -1;                // ... and their order
     gbfmm::DevBuf m2l_seg;                     // int64 [n_nodes + 1] segment starts per target
     gbfmm::DevBuf p2p_dval;                    // uint32 (pair << 1 | side), per-target segments in list order
     gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]

@@ -298,6 +298,18 @@ __global__ void seg_bounds_k(const uint32_t* __restrict__ keys, int64_t ne, int 
     seg[t] = lo;
 }
 
+// source id of every directed M2L entry (pair << 1 | side): side 0 is the entry of the
+// pair's first cell, whose partner is the second (M2L pairs are never self pairs, so all
+// 2n entries lie inside the segments)
+__global__ void m2l_src_k(int64_t ne, const uint32_t* __restrict__ dirp, const int2* __restrict__ pairs,
+                          uint32_t* __restrict__ dir) {
+    int64_t e = (int64_t)blockIdx.x * WB + threadIdx.x;
+    if (e >= ne) return;
+    uint32_t v = dirp[e];
+    int2 pr = pairs[v >> 1];
+    dir[e] = (uint32_t)((v & 1u) ? pr.x : pr.y);
+}
+
 // partial slots of every P2P pair: nA + nB (a self pair: nA)
 __global__ void p2p_psize_k(const int2* __restrict__ pairs, int64_t n, const int* __restrict__ count,
                             long long* __restrict__ psize) {
@@ -443,8 +455,19 @@ void run_walk(fmm_ctx* c, double theta) {
     c->n_p2p = n_p2p;
     int bits = bits_for(nn);
     c->id_bits = bits;
-    // M2L: per-target segments of source ids in increasing order
-    build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, false, c->m2l_seg, c->m2l_dir);
+    // M2L: per-target segments of source ids; binary64 also keeps every entry's
+    // (pair << 1 | side) for the shared pair tensors of its M2L
+    if (c->precision == FMM_FP64) {
+        build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, true, c->m2l_seg, c->m2l_dirp);
+        ensure(c->m2l_dir, sizeof(uint32_t) * (size_t)(n_m2l > 0 ? 2 * n_m2l : 1));
+        if (n_m2l > 0) {
+            m2l_src_k<<<grid_for(2 * n_m2l, WB), WB, 0, s>>>(2 * n_m2l, c->m2l_dirp.as<uint32_t>(),
+                                                            c->m2l_pairs.as<int2>(), c->m2l_dir.as<uint32_t>());
+            GB_LAUNCH("m2l_src_k");
+        }
+    } else {
+        build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, false, c->m2l_seg, c->m2l_dir);
+    }
     // P2P: per-target segments of (pair << 1 | side) in list order, plus the
     // partial offsets of every pair
     ensure(c->p2p_off, sizeof(long long) * (size_t)(n_p2p + 1));
