@@ -421,22 +421,30 @@ def run_gbfmm(args):
         basis = ("binary64 FMA rate derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz"
                  + ("; the double-float kernels run on the binary32 units and are rated against the binary64 "
                     "peak they replace" if args.precision == "df64" else ""))
-    achieved = work[dom] / (stage_avg[dom] / 1e3) / 1e12
-    if dom == "m2l":
-        shared = args.precision == "fp64" and W["p"] <= 6  # binary64 M2L on shared pair tensors
-        kname = ("m2l_con" if variant == 1 else "m2l_std") + ("_t_k" if shared else "_k")
-    else:
-        kname = "p2p_k" if args.precision != "mixed" else "p2p_ring_k"
-    per_unit = NCU_TRAFFIC_PER_UNIT.get((kname, args.precision)) if W["p"] == 4 else None
-    units = work["n_m2l"] if dom == "m2l" else work["n_pp"]
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+    def stage_roofline(st):
+        """roofline of one pair stage: algorithmic flops over its event time, ncu traffic"""
+        achieved = work[st] / (stage_avg[st] / 1e3) / 1e12
+        if st == "m2l":
+            shared = args.precision == "fp64" and W["p"] <= 6  # binary64 M2L on shared pair tensors
+            kname = ("m2l_con" if variant == 1 else "m2l_std") + ("_t_k" if shared else "_k")
+        else:
+            kname = "p2p_k" if args.precision != "mixed" else "p2p_ring_k"
+        per_unit = NCU_TRAFFIC_PER_UNIT.get((kname, args.precision)) if W["p"] == 4 else None
+        units = work["n_m2l"] if st == "m2l" else work["n_pp"]
+        return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": (round(per_unit * units) if per_unit else None),
                 "traffic_basis": (("ncu dram bytes per unit at N=2^19 (m2l_ptensor_k + m2l_con_t_k, the M2L stage), "
-                                   "scaled to this launch") if per_unit and dom == "m2l" else
+                                   "scaled to this launch") if per_unit and st == "m2l" else
                                   ("ncu dram bytes per unit at N=2^19, scaled to this launch" if per_unit else None)),
                 "kernel": kname,
                 "peak_basis": basis, "sm_mhz_median": sm_mhz}
+
+    roofline = stage_roofline(dom)
+    # both pair stages, since their times are close: the algorithmic count of a particle pair
+    # (26 flops, the reciprocal square root counted as one) is far below the binary64
+    # instructions it takes, so the P2P line reads low while its binary64 pipe is busy
+    roofline_stages = {st: stage_roofline(st) for st in ("m2l", "p2p") if stage_avg[st]}
     cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n and args.workload == "plummer1m") else None
     rng = np.random.default_rng(0)
     line = {
@@ -458,6 +466,7 @@ def run_gbfmm(args):
         "force_err_rel_l2": err,
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
+        "roofline_stages": roofline_stages,
         "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,
