@@ -6,9 +6,12 @@ binary64 -- particles per second.
 
 One step = fmm_build + fmm_forces on device-resident inputs.  Each timed step is
 bracketed by CUDA events on the library's stream; between steps a 512 MiB buffer is
-rewritten to flush the 129 MB L2.  Under torchrun every rank runs the same workload on
-its own GPU (independent replicas, weak scaling, no collective on the data path); rank 0
-prints one JSON line with the whole-job throughput.  `--impl reference` times the CPU
+rewritten to flush the 129 MB L2.  Under torchrun every rank works on its own GPU with no
+collective on the data path (weak scaling): a single system runs as independent replicas,
+and the batch workload is sharded -- a batch of n_sys x WORLD_SIZE systems split across the
+ranks by a longest-processing-time partition, so each rank carries about one n_sys batch of
+work.  Rank 0 prints one JSON line with the whole-job throughput (all ranks' particles over
+the max-over-ranks time).  `--impl reference` times the CPU
 oracle (the FP64 C reference this library is checked against) on a bounded sample.
 """
 from __future__ import annotations
@@ -156,7 +159,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 def run_gbfmm(args):
     import torch
-    from paper_2107_07166_gb300 import fmm, synth
+    from paper_2107_07166_gb300 import fmm, shard, synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -181,7 +184,15 @@ def run_gbfmm(args):
     elif gen == "disk":
         x, m = synth.disk_bulge(W["N"], W["seed"])
     elif gen == "batch":
-        x, m, offsets = synth.batch(W["n_sys"], W["seed"])
+        if world > 1:
+            # the units are systems: rank r takes its part of a batch of n_sys x world
+            n_glob = W["n_sys"] * world
+            sizes, _ = synth.batch_sizes(n_glob, W["seed"])
+            mine = shard.lpt_partition(sizes, world)[rank]
+            x, m, offsets = synth.batch_subset(n_glob, W["seed"], mine)
+            W["n_sys_total"] = n_glob
+        else:
+            x, m, offsets = synth.batch(W["n_sys"], W["seed"])
         W["N"] = int(offsets[-1])
     else:
         x, m = synth.plummer(W["N"], W["seed"])
@@ -259,7 +270,13 @@ def run_gbfmm(args):
         t = torch.tensor([t_step], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_step = float(t.item())
-    value = world * N / t_step
+    n_total = N * world  # replicas
+    if world > 1 and W.get("n_sys_total"):
+        import torch.distributed as dist
+        tn = torch.tensor([float(N)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+        n_total = int(tn.item())
+    value = n_total / t_step
 
     # end to end through the public API with host buffers (pinned), copies inside
     xh = torch.from_numpy(x).pin_memory()
@@ -277,6 +294,11 @@ def run_gbfmm(args):
         torch.cuda.synchronize(dev)
         e2e_t.append(time.perf_counter() - t0)
     e2e_step = statistics.median(e2e_t)
+    if world > 1:
+        import torch.distributed as dist
+        te = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_step = float(te.item())
 
     # accuracy and conservation of the timed configuration
     Fsum, Tsum = f.diagnostics()
@@ -455,9 +477,10 @@ def run_gbfmm(args):
                  "binary": "synthetic (seeded binary of two Plummer spheres, 10 apart)",
                  "disk": "synthetic (seeded exponential disk + Hernquist bulge)",
                  "batch": "synthetic (seeded batch of Plummer/Hernquist systems, log-uniform sizes)"}[gen],
-        "config": {"workload": W["workload"], "N": N, "n_systems": (len(offsets) - 1 if offsets is not None else 1),
+        "config": {"workload": W["workload"], "N": n_total if W.get("n_sys_total") else N,
+                   "n_systems": W.get("n_sys_total") or (len(offsets) - 1 if offsets is not None else 1),
                    "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
-                   "variant": W["variant"], "precision": W["precision"], "parallelism": f"replicas{world}",
+                   "variant": W["variant"], "precision": W["precision"], "parallelism": (f"lpt-shard{world}" if W.get("n_sys_total") else f"replicas{world}"),
                    "autotune": tune,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
@@ -470,7 +493,7 @@ def run_gbfmm(args):
         "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,
-        "e2e": {"value": world * N / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
+        "e2e": {"value": n_total / e2e_step, "unit": "particles/s", "h2d_bytes_per_step": int(32 * N),
                 "d2h_bytes_per_step": int(24 * N)},
         "gpu_launches": int(launches),
         "clocks": clocks,

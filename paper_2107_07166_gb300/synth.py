@@ -144,18 +144,34 @@ def clusters_pair(n_each: int, seed: int, distance: float):
     return x, m
 
 
+def batch_sizes(n_sys: int, seed: int, n_min: int = 1024, n_max: int = 65536):
+    """Particle counts and profiles (True: Plummer) of the systems of batch(n_sys, seed)."""
+    rng = _rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_sys))).astype(np.int64)
+    kinds = rng.random(n_sys) < 0.5
+    return sizes, kinds
+
+
+def batch_subset(n_sys: int, seed: int, idx, n_min: int = 1024, n_max: int = 65536):
+    """The systems idx (increasing) of batch(n_sys, seed, n_min, n_max), concatenated:
+    the same particles as the matching slices of the full batch.
+    Returns (x[N, 3], m[N], offsets[len(idx) + 1])."""
+    sizes, kinds = batch_sizes(n_sys, seed, n_min, n_max)
+    idx = np.asarray(idx, dtype=np.int64)
+    xs, ms = [], []
+    for i in idx:
+        gen = plummer if kinds[i] else hernquist
+        x, m = gen(int(sizes[i]), seed + 1 + int(i))
+        xs.append(x)
+        ms.append(m)
+    off = np.concatenate([[0], np.cumsum(sizes[idx])]).astype(np.int64)
+    if not xs:
+        return np.zeros((0, 3)), np.zeros(0), off
+    return np.concatenate(xs), np.concatenate(ms), off
+
+
 def batch(n_sys: int, seed: int, n_min: int = 1024, n_max: int = 65536):
     """Independent systems concatenated: system i has N_i = floor(exp U(ln n_min, ln n_max))
     particles, a Plummer or a Hernquist (a = 1) profile by a coin flip, seed seed + i.
     Returns (x[N, 3], m[N], offsets[n_sys + 1])."""
-    rng = _rng(seed)
-    sizes = np.floor(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_sys))).astype(np.int64)
-    kinds = rng.random(n_sys) < 0.5
-    xs, ms = [], []
-    for i in range(n_sys):
-        gen = plummer if kinds[i] else hernquist
-        x, m = gen(int(sizes[i]), seed + 1 + i)
-        xs.append(x)
-        ms.append(m)
-    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    return np.concatenate(xs), np.concatenate(ms), off
+    return batch_subset(n_sys, seed, np.arange(n_sys), n_min, n_max)
