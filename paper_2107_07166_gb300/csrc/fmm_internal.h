@@ -94,7 +94,7 @@ struct fmm_ctx {
     gbfmm::DevBuf perm;                        // sorted position -> input index (uint32)
     gbfmm::DevBuf flags, scan_out, scan_tmp, geom, errflag;
     gbfmm::DevBuf rs_hist, rs_offs;            // radix sort histograms and offsets
-    gbfmm::DevBuf cur, nal, leaf_of;           // build state, node at level, leaf of particle
+    gbfmm::DevBuf leaf_of;                     // leaf of every sorted particle
     // nodes
     int64_t n_nodes = 0, cap_nodes = 0;
     int n_levels = 0;                          // levels 0 .. n_levels-1

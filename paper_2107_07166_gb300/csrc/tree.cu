@@ -141,66 +141,88 @@ __global__ void gather_k(const double* __restrict__ x, const double* __restrict_
 
 // ------------------------------------------------------------------ octree, level by level
 
-// Boundary flags of the children of every splittable node at `level`: a particle starts
-// a child when it is the first of its node or its level+1 octant differs from the
-// previous particle's.  Also records the node of every particle at this level.
-__global__ void tree_mark_k(const uint64_t* __restrict__ keys, int n, int level, int leaf,
-                            const int* __restrict__ cur, const int* __restrict__ nfirst,
-                            const int* __restrict__ ncount, int* __restrict__ flag, int* __restrict__ nal_l) {
-    int i = blockIdx.x * TB + threadIdx.x;
-    if (i >= n) return;
-    int c = cur[i];
-    nal_l[i] = c;
-    int f = 0;
-    if (c >= 0 && ncount[c] > leaf && level < MAX_LEVEL) {
-        int shift = 60 - 3 * level;
-        f = (i == nfirst[c]) || ((keys[i] >> shift) != (keys[i - 1] >> shift));
+// A node at `level` splits when it holds more than `leaf` particles and level < MAX_LEVEL.
+// Its particles' keys are sorted and share the node's prefix, so the level+1 octant
+// digit never decreases over [f, e): child o starts at the first particle whose digit is
+// at least o, and octants with no particle are omitted.  One thread per (node, octant)
+// finds that bound by binary search (lanes 8t .. 8t + 7 of a warp hold node t's octants),
+// so a level costs one search depth of latency and work proportional to its nodes.
+struct Octant {
+    int b, next;  // octant range [b, next)
+    bool split;   // the node splits
+    unsigned grp; // non-empty octants of the node, bit o
+};
+
+__device__ __forceinline__ Octant octant_of(const uint64_t* __restrict__ keys, bool in, int f, int cn, int level,
+                                            int leaf, int o) {
+    Octant r;
+    r.split = in && cn > leaf && level < MAX_LEVEL;
+    int e = f + cn, lo = f;
+    if (r.split && o > 0) {
+        int hi = e, shift = 60 - 3 * level;
+        while (lo < hi) {
+            int mid = lo + ((hi - lo) >> 1);
+            if ((int)((keys[mid] >> shift) & 7ull) < o)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
     }
-    flag[i] = f;
+    r.b = lo;
+    int nb = __shfl_down_sync(FULL, lo, 1, 8);
+    r.next = o == 7 ? e : nb;
+    unsigned bal = __ballot_sync(FULL, r.split && r.next > r.b);
+    r.grp = (bal >> (threadIdx.x & 24)) & 0xffu;
+    return r;
 }
 
-__global__ void tree_emit_k(int n, int level, int leaf, int new_base, const int* __restrict__ flag,
-                            const int* __restrict__ pos, int* __restrict__ cur, int* __restrict__ nfirst,
-                            const int* __restrict__ ncount, int* __restrict__ nlevel, int* __restrict__ nparent,
-                            int* __restrict__ nchildf, int* __restrict__ nnchild, int* __restrict__ leaf_of) {
-    int i = blockIdx.x * TB + threadIdx.x;
-    if (i >= n) return;
-    int c = cur[i];
-    if (c < 0) return;
-    if (!(ncount[c] > leaf && level < MAX_LEVEL)) {  // c is a leaf
-        leaf_of[i] = c;
-        cur[i] = -1;
-        return;
+// number of children of the m nodes lo .. lo + m - 1 of `level`
+__global__ void split_count_k(const uint64_t* __restrict__ keys, int lo, int m, int level, int leaf,
+                              const int* __restrict__ nfirst, const int* __restrict__ ncount, int* __restrict__ nch) {
+    int64_t g = (int64_t)blockIdx.x * TB + threadIdx.x;
+    int t = (int)(g >> 3), o = (int)(g & 7);
+    bool in = t < m;  // groups of 8 are whole: all in or all out
+    int f = in ? nfirst[lo + t] : 0, cn = in ? ncount[lo + t] : 0;
+    Octant q = octant_of(keys, in, f, cn, level, leaf, o);
+    if (in && o == 0) nch[t] = __popc(q.grp);
+}
+
+// children of the level's nodes get breadth-first ids new_base + pos[t] + (rank among the
+// node's non-empty octants); pos is the exclusive scan of nch
+__global__ void split_emit_k(const uint64_t* __restrict__ keys, int lo, int m, int level, int leaf, int new_base,
+                             const int* __restrict__ pos, int* __restrict__ nfirst, int* __restrict__ ncount,
+                             int* __restrict__ nlevel, int* __restrict__ nparent, int* __restrict__ nchildf,
+                             int* __restrict__ nnchild) {
+    int64_t g = (int64_t)blockIdx.x * TB + threadIdx.x;
+    int t = (int)(g >> 3), o = (int)(g & 7);
+    bool in = t < m;
+    int nd = lo + t;
+    int f = in ? nfirst[nd] : 0, cn = in ? ncount[nd] : 0;
+    Octant q = octant_of(keys, in, f, cn, level, leaf, o);
+    if (!in || q.grp == 0u) return;  // a leaf keeps nchildf = -1, nnchild = 0 from its creation
+    int base = new_base + pos[t];
+    if (o == 0) {
+        nchildf[nd] = base;
+        nnchild[nd] = __popc(q.grp);
     }
-    int id = new_base + pos[i] + flag[i] - 1;
-    if (flag[i]) {
-        nfirst[id] = i;
+    if ((q.grp >> o) & 1u) {
+        int id = base + __popc(q.grp & ((1u << o) - 1u));
+        nfirst[id] = q.b;
+        ncount[id] = q.next - q.b;
         nlevel[id] = level + 1;
-        nparent[id] = c;
+        nparent[id] = nd;
         nchildf[id] = -1;
         nnchild[id] = 0;
-        if (i == nfirst[c]) nchildf[c] = id;
     }
-    cur[i] = id;
 }
 
-__global__ void tree_count_k(int new_base, int total, const int* __restrict__ nfirst, int* __restrict__ ncount,
-                             const int* __restrict__ nparent, const int* __restrict__ nchildf,
-                             int* __restrict__ nnchild) {
-    int t = blockIdx.x * TB + threadIdx.x;
-    if (t >= total) return;
-    int k = new_base + t;
-    int par = nparent[k];
-    bool last = (t + 1 == total) || (nparent[k + 1] != par);
-    int next = last ? nfirst[par] + ncount[par] : nfirst[k + 1];
-    ncount[k] = next - nfirst[k];
-    if (last) nnchild[par] = k - nchildf[par] + 1;
-}
-
-__global__ void tree_finish_k(int n, const int* __restrict__ cur, int* __restrict__ leaf_of) {
-    int i = blockIdx.x * TB + threadIdx.x;
-    if (i >= n) return;
-    if (cur[i] >= 0) leaf_of[i] = cur[i];
+// leaf of every particle
+__global__ void leaf_of_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                          const int* __restrict__ nnchild, int* __restrict__ leaf_of) {
+    int nd = blockIdx.x * TB + threadIdx.x;
+    if (nd >= nn || nnchild[nd] != 0) return;
+    int f = nfirst[nd], e = f + ncount[nd];
+    for (int i = f; i < e; i++) leaf_of[i] = nd;
 }
 
 // ------------------------------------------------------------------ centres of mass
@@ -279,7 +301,8 @@ __global__ void centre_words_k(int nn, const double* __restrict__ Zx, const doub
 }
 
 // r_max^2 = max over the node's particles of |X - Z|^2 for every node, exact in binary64
-// (A11), in two passes over (particle, level).  Equal nodes are contiguous in sorted order,
+// (A11), in two passes over (particle, level); a particle's node at each level comes from
+// the parent chain of its leaf, deepest level first.  Equal nodes are contiguous in sorted order,
 // so a segmented warp maximum leaves one integer atomicMax per node and warp (on the bit
 // pattern of a non-negative number, which orders like the value); max is order
 // independent, so the result is bit exact.
@@ -302,20 +325,25 @@ __device__ __forceinline__ float d2_words(float xh, float xl, float yh, float yl
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-__global__ void rmax2f_k(int n, int nlev, const int* __restrict__ nal, const double* __restrict__ xs,
+__global__ void rmax2f_k(int n, int nlev, const int* __restrict__ leaf_of, const int* __restrict__ nlevel,
+                         const int* __restrict__ nparent, const double* __restrict__ xs,
                          const double* __restrict__ ys, const double* __restrict__ zs, const float4* __restrict__ zh,
                          const float4* __restrict__ zl, unsigned* __restrict__ r2f) {
     int i = blockIdx.x * TB + threadIdx.x;
     int lane = threadIdx.x & 31;
     bool in = i < n;
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh_ = 0.f, zl_ = 0.f;
+    int up = -1, dl = -1;  // the particle's ancestor at the current level, and its leaf's level
     if (in) {
         split_df(xs[i], xh, xl);
         split_df(ys[i], yh, yl);
         split_df(zs[i], zh_, zl_);
+        up = leaf_of[i];
+        dl = nlevel[up];
     }
-    for (int l = 0; l < nlev; l++) {
-        int nd = in ? nal[(int64_t)l * n + i] : -1;
+    for (int l = nlev - 1; l >= 0; l--) {
+        int nd = l <= dl ? up : -1;
+        if (nd >= 0 && l > 0) up = nparent[nd];
         unsigned v = 0u;
         if (nd >= 0) v = __float_as_uint(d2_words(xh, xl, yh, yl, zh_, zl_, zh[nd], zl[nd]));
 #pragma unroll
@@ -330,7 +358,8 @@ __global__ void rmax2f_k(int n, int nlev, const int* __restrict__ nal, const dou
     }
 }
 
-__global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const double* __restrict__ xs,
+__global__ void rmax2_k(int n, int nlev, const int* __restrict__ leaf_of, const int* __restrict__ nlevel,
+                        const int* __restrict__ nparent, const double* __restrict__ xs,
                         const double* __restrict__ ys, const double* __restrict__ zs,
                         const double* __restrict__ Zx, const double* __restrict__ Zy,
                         const double* __restrict__ Zz, const float4* __restrict__ zh, const float4* __restrict__ zl,
@@ -340,13 +369,17 @@ __global__ void rmax2_k(int n, int nlev, const int* __restrict__ nal, const doub
     bool in = i < n;
     double px = in ? xs[i] : 0.0, py = in ? ys[i] : 0.0, pz = in ? zs[i] : 0.0;
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh_ = 0.f, zl_ = 0.f;
+    int up = -1, dl = -1;
     if (in) {
         split_df(px, xh, xl);
         split_df(py, yh, yl);
         split_df(pz, zh_, zl_);
+        up = leaf_of[i];
+        dl = nlevel[up];
     }
-    for (int l = 0; l < nlev; l++) {
-        int nd = in ? nal[(int64_t)l * n + i] : -1;
+    for (int l = nlev - 1; l >= 0; l--) {
+        int nd = l <= dl ? up : -1;
+        if (nd >= 0 && l > 0) up = nparent[nd];
         unsigned long long v = 0ull;
         if (nd >= 0) {
             float4 ch = zh[nd], cl = zl[nd];
@@ -486,11 +519,6 @@ __global__ void roots_k(const long long* __restrict__ off, int nsys, int* nfirst
     nnchild[sys] = 0;
 }
 
-__global__ void cur_init_k(const long long* __restrict__ off, int nsys, int64_t n, int* __restrict__ cur) {
-    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i < n) cur[i] = system_of(off, nsys, i);
-}
-
 // ------------------------------------------------------------------ host driver
 
 // Per-leaf work (P2M) runs one thread per leaf, so a warp lasts as long as its largest
@@ -582,49 +610,42 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     // a4: octree, level by level (breadth-first ids)
     const uint64_t* keys = c->keys0.as<uint64_t>();
     ensure_nodes(c, (int64_t)n / 4 + 64);
-    ensure(c->cur, sizeof(int) * (size_t)n);
-    ensure(c->flags, sizeof(int) * (size_t)n);
-    ensure(c->scan_out, sizeof(int) * (size_t)(n + 1));
+    size_t lev_max = (size_t)(n > nsys ? n : nsys);  // nodes of one level: the roots, or at most n
+    ensure(c->flags, sizeof(int) * lev_max);
+    ensure(c->scan_out, sizeof(int) * (lev_max + 1));
     ensure(c->leaf_of, sizeof(int) * (size_t)n);
-    ensure(c->nal, sizeof(int) * (size_t)n * (MAX_LEVEL + 1));
     ensure_nodes(c, (int64_t)nsys + 64);
     roots_k<<<grid_for(nsys, TB), TB, 0, s>>>(off, nsys, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
                                               c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
     GB_LAUNCH("roots_k");
-    cur_init_k<<<grid_for(n, TB), TB, 0, s>>>(off, nsys, n, c->cur.as<int>());
-    GB_LAUNCH("cur_init_k");
     c->level_start.assign(1, 0);
     c->level_start.push_back(nsys);
     int64_t n_nodes = nsys;
-    int level = 0;
-    for (;; level++) {
-        int* nal_l = c->nal.as<int>() + (int64_t)level * n;
-        tree_mark_k<<<grid_for(n, TB), TB, 0, s>>>(keys, n, level, c->leaf, c->cur.as<int>(), c->nfirst.as<int>(),
-                                                   c->ncount.as<int>(), c->flags.as<int>(), nal_l);
-        GB_LAUNCH("tree_mark_k");
-        if (level >= MAX_LEVEL) break;
-        scan_int(c, c->flags.as<int>(), n, c->scan_out.as<int>());
+    // below the roots the nodes of a level are disjoint and non-empty: at most n of them
+    for (int level = 0; level < MAX_LEVEL; level++) {
+        int lo = c->level_start[level];
+        int m = c->level_start[level + 1] - lo;
+        split_count_k<<<grid_for(8 * (int64_t)m, TB), TB, 0, s>>>(keys, lo, m, level, c->leaf, c->nfirst.as<int>(),
+                                                     c->ncount.as<int>(), c->flags.as<int>());
+        GB_LAUNCH("split_count_k");
+        scan_int(c, c->flags.as<int>(), m, c->scan_out.as<int>());
         int total = 0;
-        GB_CUDA(cudaMemcpyAsync(&total, c->scan_out.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&total, c->scan_out.as<int>() + m, sizeof(int), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
         if (total == 0) break;
         ensure_nodes(c, n_nodes + total);
-        tree_emit_k<<<grid_for(n, TB), TB, 0, s>>>(n, level, c->leaf, (int)n_nodes, c->flags.as<int>(),
-                                                   c->scan_out.as<int>(), c->cur.as<int>(), c->nfirst.as<int>(),
-                                                   c->ncount.as<int>(), c->nlevel.as<int>(), c->nparent.as<int>(),
-                                                   c->nchildf.as<int>(), c->nnchild.as<int>(),
-                                                   c->leaf_of.as<int>());
-        GB_LAUNCH("tree_emit_k");
-        tree_count_k<<<grid_for(total, TB), TB, 0, s>>>((int)n_nodes, total, c->nfirst.as<int>(),
-                                                        c->ncount.as<int>(), c->nparent.as<int>(),
-                                                        c->nchildf.as<int>(), c->nnchild.as<int>());
-        GB_LAUNCH("tree_count_k");
+        split_emit_k<<<grid_for(8 * (int64_t)m, TB), TB, 0, s>>>(keys, lo, m, level, c->leaf, (int)n_nodes,
+                                                                 c->scan_out.as<int>(),
+                                                    c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
+                                                    c->nparent.as<int>(), c->nchildf.as<int>(),
+                                                    c->nnchild.as<int>());
+        GB_LAUNCH("split_emit_k");
         n_nodes += total;
         c->level_start.push_back((int)n_nodes);
     }
-    // particles still holding a node sit in leaves of the deepest level
-    tree_finish_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->cur.as<int>(), c->leaf_of.as<int>());
-    GB_LAUNCH("tree_finish_k");
+    leaf_of_k<<<grid_for(n_nodes, TB), TB, 0, s>>>((int)n_nodes, c->nfirst.as<int>(), c->ncount.as<int>(),
+                                                   c->nnchild.as<int>(), c->leaf_of.as<int>());
+    GB_LAUNCH("leaf_of_k");
     c->n_levels = (int)c->level_start.size() - 1;
     c->n_nodes = n_nodes;
     // centres of mass, bottom-up
@@ -658,10 +679,12 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     ensure(c->nr2f, sizeof(unsigned) * (size_t)nn);
     GB_CUDA(cudaMemsetAsync(c->nr2f.p, 0, sizeof(unsigned) * (size_t)nn, s));
     GB_CUDA(cudaMemsetAsync(c->nr2.p, 0, sizeof(unsigned long long) * (size_t)nn, s));
-    rmax2f_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->nal.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+    rmax2f_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->leaf_of.as<int>(), c->nlevel.as<int>(),
+                                            c->nparent.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
                                             c->zs.as<double>(), zh, zl, c->nr2f.as<unsigned>());
     GB_LAUNCH("rmax2f_k");
-    rmax2_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->nal.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
+    rmax2_k<<<grid_for(n, TB), TB, 0, s>>>(n, c->n_levels, c->leaf_of.as<int>(), c->nlevel.as<int>(),
+                                           c->nparent.as<int>(), c->xs.as<double>(), c->ys.as<double>(),
                                            c->zs.as<double>(), c->nZx.as<double>(), c->nZy.as<double>(),
                                            c->nZz.as<double>(), zh, zl, c->nr2f.as<unsigned>(),
                                            c->nr2.as<unsigned long long>());
