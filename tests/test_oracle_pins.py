@@ -331,7 +331,42 @@ def check_tree(r, N, leaf):
             assert np.all(t["level"][ch] == t["level"][n] + 1)
     leaves = t["nchild"] == 0
     assert t["count"][leaves].sum() == N
-    assert np.all(np.diff(r.keys.astype(np.float64)) >= 0)
+    k = r.keys
+    assert np.all(k[1:] >= k[:-1])
+    # a node at level l is a key prefix of 3 l bits: its particles share it, and its
+    # children are its non-empty octants at level l + 1, in increasing octant order
+    for n in range(nn):
+        f, c, lv = t["first"][n], t["count"][n], t["level"][n]
+        assert c >= 1
+        if lv > 0:
+            s = np.uint64(63 - 3 * lv)
+            assert k[f] >> s == k[f + c - 1] >> s
+        if t["nchild"][n] > 0:
+            ch = np.arange(t["child_first"][n], t["child_first"][n] + t["nchild"][n])
+            dig = (k[t["first"][ch]] >> np.uint64(60 - 3 * lv)) & np.uint64(7)
+            assert np.all(dig[1:] > dig[:-1])
+
+
+@pytest.mark.parametrize("case", ["plummer", "coincident", "leaf1"])
+def test_tree_is_the_octree_of_the_keys(orc, case):
+    """The tree is the octree of the sorted keys: breadth-first, children the non-empty
+    octants in Morton order, split while count > leaf below level 21."""
+    rng = np.random.default_rng(8)
+    if case == "plummer":
+        x, m = synth.plummer(4000, 9)
+        leaf = 16
+    elif case == "coincident":
+        x = np.concatenate([rng.normal(size=(400, 3)), np.repeat(rng.normal(size=(2, 3)), 30, axis=0)])
+        m = rng.random(x.shape[0])
+        leaf = 8
+    else:
+        x, m = synth.hernquist(600, 10)
+        leaf = 1
+    r = orc.run(x, m, leaf, 1, 0.5, 0, want_pot=False)
+    check_tree(r, x.shape[0], leaf)
+    if case == "coincident":
+        deep = (r.tree["level"] == 21) & (r.tree["nchild"] == 0)
+        assert np.any(r.tree["count"][deep] > leaf)
 
 
 @pytest.mark.parametrize("variant", [0, 1])
