@@ -52,7 +52,7 @@ def _load():
         lib.orc_run.restype = P
         lib.orc_run.argtypes = [P, P, i64, i32, i32, dbl, i32, i32]
         lib.orc_free.argtypes = [P]
-        for f in ("orc_n_nodes", "orc_n_m2l", "orc_n_p2p"):
+        for f in ("orc_n_nodes", "orc_n_m2l", "orc_n_p2p", "orc_n_trace"):
             getattr(lib, f).restype = i64
             getattr(lib, f).argtypes = [P]
         lib.orc_get_keys.argtypes = [P, P, P, P, P]
@@ -62,6 +62,8 @@ def _load():
         lib.orc_get_locals.argtypes = [P, P, P]
         lib.orc_get_locals.restype = i32
         lib.orc_get_lists.argtypes = [P, P, P]
+        lib.orc_set_trace.argtypes = [i32]
+        lib.orc_get_trace.argtypes = [P, P]
         lib.orc_get_result.argtypes = [P, P, P]
         lib.orc_nmi.argtypes = [i32]
         lib.orc_nmi.restype = i32
@@ -220,14 +222,24 @@ class Result:
         self.__dict__.update(kw)
 
 
-def run(x, m, leaf_size, p, theta, variant=STANDARD, want_pot=True, want_internals=True) -> Result:
+# decisions of the walk trace
+WALK_SELF_SPLIT, WALK_M2L, WALK_P2P, WALK_SPLIT_A, WALK_SPLIT_B = 0, 1, 2, 3, 4
+
+
+def run(x, m, leaf_size, p, theta, variant=STANDARD, want_pot=True, want_internals=True,
+        want_trace=False) -> Result:
     """One full FMM evaluation (steps a1..a13): returns accelerations and potentials in
-    input order plus, if requested, keys, permutation, tree, geometry, moments, lists and locals."""
+    input order plus, if requested, keys, permutation, tree, geometry, moments, lists and locals.
+    want_trace adds ``trace``: every pair the walk visited, in visiting order, as rows
+    (A, B, decision) with the WALK_* decisions above."""
     lib = _load()
     x = _f64(x, (-1, 3))
     m = _f64(m)
     N = x.shape[0]
-    h = lib.orc_run(_p(x), _p(m), N, int(leaf_size), int(p), float(theta), int(variant), int(bool(want_pot)))
+    with _lock:
+        lib.orc_set_trace(int(bool(want_trace)))
+        h = lib.orc_run(_p(x), _p(m), N, int(leaf_size), int(p), float(theta), int(variant), int(bool(want_pot)))
+        lib.orc_set_trace(0)
     if not h:
         raise ValueError("oracle rejected the arguments")
     try:
@@ -236,6 +248,10 @@ def run(x, m, leaf_size, p, theta, variant=STANDARD, want_pot=True, want_interna
         pot = np.zeros(N) if want_pot else None
         lib.orc_get_result(h, _p(acc), _p(pot))
         r = Result(acc=acc, pot=pot, n_nodes=nn, n_m2l=nm2l, n_p2p=np2p)
+        if want_trace:
+            tr = np.zeros((lib.orc_n_trace(h), 3), dtype=np.int32)
+            lib.orc_get_trace(h, _p(tr))
+            r.trace = tr
         if want_internals:
             keys_s = np.zeros(N, dtype=np.uint64)
             perm = np.zeros(N, dtype=np.int64)

@@ -263,6 +263,9 @@ typedef struct {
     /* interaction lists (canonical: (min id, max id) lexicographic) */
     int64_t n_m2l, cap_m2l, n_p2p, cap_p2p;
     int32_t *m2l, *p2p;
+    /* optional record of the walk: every visited pair (A, B) with its decision */
+    int64_t n_trace, cap_trace;
+    int32_t *trace; /* triples (A, B, decision), see WALK_* */
     /* results (input order) */
     double *acc, *pot;
     double *acc_s, *pot_s; /* sorted order */
@@ -383,13 +386,34 @@ static void node_geometry(orc_t *o) {
 
 /* ---------------- dual-tree walk (mutual) ---------------- */
 
+/* decisions recorded by the walk trace (a debug export for the tests) */
+enum { WALK_SELF_SPLIT = 0, WALK_M2L = 1, WALK_P2P = 2, WALK_SPLIT_A = 3, WALK_SPLIT_B = 4 };
+static int g_trace_on = 0;
+
+/* switch the walk trace of later orc_run calls on (1) or off (0) */
+void orc_set_trace(int on) { g_trace_on = on; }
+
+static void trace(orc_t *o, int32_t A, int32_t B, int32_t decision) {
+    if (!g_trace_on) return;
+    if (o->n_trace == o->cap_trace) {
+        o->cap_trace = o->cap_trace ? 2 * o->cap_trace : 1024;
+        o->trace = (int32_t *)realloc(o->trace, sizeof(int32_t) * 3 * (size_t)o->cap_trace);
+    }
+    o->trace[3 * o->n_trace] = A;
+    o->trace[3 * o->n_trace + 1] = B;
+    o->trace[3 * o->n_trace + 2] = decision;
+    o->n_trace++;
+}
+
 static void walk_pair(orc_t *o, int32_t A, int32_t B);
 
 static void walk_self(orc_t *o, int32_t A) {
     if (is_leaf(o, A)) {
+        trace(o, A, A, WALK_P2P);
         push_pair(&o->p2p, &o->n_p2p, &o->cap_p2p, A, A);
         return;
     }
+    trace(o, A, A, WALK_SELF_SPLIT);
     int32_t c0 = o->child_first[A], nc = o->nchild[A];
     for (int32_t i = 0; i < nc; i++)
         for (int32_t j = i; j < nc; j++) {
@@ -418,15 +442,18 @@ static int split_first(const orc_t *o, int32_t A, int32_t B) {
 
 static void walk_pair(orc_t *o, int32_t A, int32_t B) {
     if (mac_accept(o, A, B)) {
+        trace(o, A, B, WALK_M2L);
         push_pair(&o->m2l, &o->n_m2l, &o->cap_m2l, A, B);
         return;
     }
     int la = is_leaf(o, A), lb = is_leaf(o, B);
     if (la && lb) {
+        trace(o, A, B, WALK_P2P);
         push_pair(&o->p2p, &o->n_p2p, &o->cap_p2p, A, B);
         return;
     }
     int splitA = lb ? 1 : (la ? 0 : split_first(o, A, B));
+    trace(o, A, B, splitA ? WALK_SPLIT_A : WALK_SPLIT_B);
     if (splitA) {
         for (int32_t c = o->child_first[A]; c < o->child_first[A] + o->nchild[A]; c++) walk_pair(o, c, B);
     } else {
@@ -742,7 +769,7 @@ void orc_free(orc_t *o) {
     if (!o) return;
     void *ptrs[] = {o->keys, o->perm, o->X, o->m, o->first, o->count, o->level, o->parent, o->child_first,
                     o->nchild, o->M, o->S, o->Z, o->rmax, o->leaf_of, o->mom, o->L, o->SU, o->m2l, o->p2p,
-                    o->acc, o->pot, o->acc_s, o->pot_s};
+                    o->acc, o->pot, o->acc_s, o->pot_s, o->trace};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
     free(o);
 }
@@ -750,6 +777,11 @@ void orc_free(orc_t *o) {
 /* ---------------- accessors ---------------- */
 
 int64_t orc_n_nodes(const orc_t *o) { return o->n_nodes; }
+int64_t orc_n_trace(const orc_t *o) { return o->n_trace; }
+/* the walk trace (orc_set_trace): n_trace x 3 int32, in visiting order */
+void orc_get_trace(const orc_t *o, int32_t *out) {
+    if (o->n_trace) memcpy(out, o->trace, sizeof(int32_t) * 3 * (size_t)o->n_trace);
+}
 int64_t orc_n_m2l(const orc_t *o) { return o->n_m2l; }
 int64_t orc_n_p2p(const orc_t *o) { return o->n_p2p; }
 

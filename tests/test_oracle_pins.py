@@ -284,22 +284,74 @@ def test_conserving_pair_force_is_central(orc):
 
 # ---------------------------------------------------------------- keys, sort, tree, walk
 
+def _exact_quantised(x, lo, side):
+    """q = min(floor((x - lo) 2^21 / side), 2^21 - 1) in exact rational arithmetic, and the
+    distance of the exact t from the nearest integer (where the binary64 rounding of t
+    may decide the floor, the pin does not apply)."""
+    q = np.zeros(x.shape, dtype=np.int64)
+    near = np.zeros(x.shape, dtype=bool)
+    S = Fraction(side)
+    for i in range(x.shape[0]):
+        for d in range(3):
+            t = (Fraction(float(x[i, d])) - Fraction(float(lo[d]))) * (1 << 21) / S
+            f = math.floor(t)
+            # t = 0 (the minimum, exact in binary64 too) and t near 2^21 (the largest
+            # extent, clamped to the last cell either way) decide nothing
+            near[i, d] = (min(t - f, f + 1 - t) < Fraction(1, 10 ** 8) and t != 0
+                          and abs(t - (1 << 21)) > Fraction(1, 10 ** 8))
+            q[i, d] = min(f, (1 << 21) - 1)
+    return q, near
+
+
+def _deinterleave(k):
+    """(qx, qy, qz) of 63-bit keys: bit 3b + 2 = x bit b, 3b + 1 = y bit b, 3b = z bit b"""
+    q = np.zeros((k.shape[0], 3), dtype=np.int64)
+    ki = k.astype(np.int64)
+    for b in range(21):
+        for d in range(3):
+            q[:, d] |= ((ki >> (3 * b + 2 - d)) & 1) << b
+    return q
+
+
 def test_keys_quantise_positions(orc):
+    """Morton quantisation of the tree's cube (reading A12): the cube is the per-axis
+    minimum and the largest extent, and every coordinate maps to exactly
+    min(floor((x - lo) 2^21 / side), 2^21 - 1) -- the floor of the exact rational, not a
+    rounding of it -- except within 1e-8 of a cell boundary, where binary64 rounding of t
+    may decide (none of the drawn points lies there)."""
     rng = np.random.default_rng(1)
-    x = rng.normal(size=(300, 3))
+    x = np.concatenate([rng.normal(size=(300, 3)), rng.uniform(-3, 5, size=(200, 3))])
     lo, side = orc.bbox(x)
-    assert np.allclose(lo, x.min(0), rtol=0, atol=0)
+    assert np.array_equal(lo, x.min(0))
     assert side == (x.max(0) - x.min(0)).max()
     k = orc.keys(x, lo, side)
-    q = np.zeros((300, 3), dtype=np.int64)
-    for b in range(21):                 # de-interleave
-        for d in range(3):
-            q[:, d] |= ((k.astype(np.int64) >> (3 * b + 2 - d)) & 1) << b
-    cell = side / 2 ** 21
-    t = (x - lo) / cell
-    assert np.all(q >= 0) and np.all(q <= 2 ** 21 - 1)
-    assert np.all(np.abs(q - np.minimum(np.floor(t), 2 ** 21 - 1)) <= 1)
     assert np.all(k < 2 ** 63)
+    q = _deinterleave(k)
+    want, near = _exact_quantised(x, lo, side)
+    assert near.sum() == 0
+    assert np.array_equal(q, want)
+    # the extreme points: the minimum maps to cell 0, the maximum of the longest axis to
+    # the last cell (the clamp), and about half of all coordinates sit in the upper half
+    # of their cell, where rounding instead of the floor would move them up by one
+    ax = int(np.argmax(x.max(0) - x.min(0)))
+    assert q[np.argmax(x[:, ax]), ax] == 2 ** 21 - 1
+    assert np.all(q[np.argmin(x, axis=0), np.arange(3)] == 0)
+
+
+def test_keys_quantise_cell_boundaries(orc):
+    """Points placed exactly on and just inside cell boundaries of a dyadic cube (side 8,
+    lo 0: one cell is 2^-18) quantise to the cell that starts there."""
+    cell = 8.0 / 2 ** 21
+    base = np.array([0.0, 1.0, 3.5, 7.25, 4.0 - cell, 8.0])
+    x = np.stack([base, base[::-1], np.full(6, 2.0)], axis=1)
+    x[0, 2] = 0.0
+    x[1, 2] = 8.0
+    lo, side = orc.bbox(x)
+    assert np.array_equal(lo, [0.0, 0.0, 0.0]) and side == 8.0
+    q = _deinterleave(orc.keys(x, lo, side))
+    want = np.minimum(np.floor(x / cell).astype(np.int64), 2 ** 21 - 1)
+    assert np.array_equal(q, want)
+    assert q[4, 0] == 2 ** 20 - 1 and q[5, 0] == 2 ** 21 - 1 and q[2, 0] == 7 * 2 ** 17
 
 
 def test_sort_is_stable(orc):
@@ -407,6 +459,133 @@ def test_walk_covers_every_pair_once(orc, variant):
     d = Z[m2l[:, 0]] - Z[m2l[:, 1]]
     R = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
     assert np.all(rm[m2l[:, 0]] + rm[m2l[:, 1]] <= 0.5 * R)
+    # and every P2P pair between two leaves fails it (a pair that passes is never
+    # evaluated directly)
+    q = p2p[p2p[:, 0] != p2p[:, 1]]
+    d = Z[q[:, 0]] - Z[q[:, 1]]
+    R = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
+    assert not np.any((R > 0) & (rm[q[:, 0]] + rm[q[:, 1]] <= 0.5 * R))
+
+
+def _read_walk_cases():
+    cases, cur = [], None
+    with open(os.path.join(GOLD, "walk_hand.txt")) as f:
+        for line in f:
+            w = line.split()
+            if not w or w[0].startswith("#"):
+                continue
+            if w[0] == "case":
+                cur = {"name": w[1], "tree": [], "m2l": [], "p2p": []}
+            elif w[0] == "x":
+                cur["x"] = np.array([float(v) for v in w[1:]])
+            elif w[0] == "tree":
+                cur["tree"].append([int(v) for v in w[1:]])
+            elif w[0] in ("m2l", "p2p"):
+                cur[w[0]].append([int(w[1]), int(w[2])])
+            elif w[0] == "end":
+                cases.append(cur)
+    return cases
+
+
+WALK_CASES = _read_walk_cases()
+
+
+@pytest.mark.parametrize("case", WALK_CASES, ids=[c["name"] for c in WALK_CASES])
+def test_walk_hand_worked_lists(orc, case):
+    """Trees and lists worked out by hand (tests/golden/walk_hand.txt) for collinear unit
+    masses with exact dyadic geometry: the split of the larger r_max, the tie-breaks by
+    count and then by id, and the "<=" of eq. mac_criterion on a pair that sits exactly
+    on r_A + r_B = theta R."""
+    n = case["x"].shape[0]
+    x = np.zeros((n, 3))
+    x[:, 0] = case["x"]
+    r = orc.run(x, np.ones(n), 2, 2, 0.5, 1, want_pot=False)
+    t = np.array(case["tree"], dtype=np.int32)
+    names = ("first", "count", "level", "parent", "child_first", "nchild")
+    assert r.n_nodes == t.shape[0]
+    for j, k in enumerate(names):
+        assert np.array_equal(r.tree[k], t[:, j]), k
+    assert np.array_equal(r.m2l, np.array(case["m2l"], dtype=np.int32).reshape(-1, 2))
+    assert np.array_equal(r.p2p, np.array(case["p2p"], dtype=np.int32).reshape(-1, 2))
+
+
+def test_walk_hand_worked_boundary_needs_le(orc):
+    """The tie_by_id case with theta just below 1/2: the pair (4,5), which sits exactly on
+    r_A + r_B = theta R at theta = 1/2, is no longer accepted and becomes P2P."""
+    case = WALK_CASES[0]
+    n = case["x"].shape[0]
+    x = np.zeros((n, 3))
+    x[:, 0] = case["x"]
+    r = orc.run(x, np.ones(n), 2, 2, 0.5 - 2 ** -40, 1, want_pot=False)
+    assert [4, 5] not in r.m2l.tolist() and [4, 5] in r.p2p.tolist()
+
+
+def _check_trace(r, theta):
+    """Every pair the walk visited was decided by eq. mac_criterion and reading A10, and
+    the visited pairs are exactly Self(roots) plus the children of every split."""
+    t = r.tree
+    leaf = t["nchild"] == 0
+    Z, rm, cnt = r.Z, r.rmax, t["count"]
+    tr = r.trace
+    A, B, dec = tr[:, 0].astype(np.int64), tr[:, 1].astype(np.int64), tr[:, 2]
+    selfv = A == B
+    assert np.all(dec[selfv & leaf[A]] == 2)                 # Self(leaf) -> P2P
+    assert np.all(dec[selfv & ~leaf[A]] == 0)                # Self(inner) -> children
+    d = Z[A] - Z[B]
+    R = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
+    acc = (R > 0) & (rm[A] + rm[B] <= theta * R)
+    pr = ~selfv
+    assert np.all(dec[pr & acc] == 1)                        # accepted -> M2L
+    assert np.all(acc[pr & (dec == 1)])
+    both = leaf[A] & leaf[B]
+    assert np.all(dec[pr & ~acc & both] == 2)                # rejected leaves -> P2P
+    spl = pr & ~acc & ~both
+    assert np.all((dec[spl] == 3) | (dec[spl] == 4))
+    sa = dec == 3
+    sb = dec == 4
+    assert not np.any(sa & leaf[A]) and not np.any(sb & leaf[B])   # a leaf is never split
+    inner = spl & ~leaf[A] & ~leaf[B]
+    # the larger r_max is split; ties: the larger count, then the lower id
+    want_a = np.where(rm[A] != rm[B], rm[A] > rm[B], np.where(cnt[A] != cnt[B], cnt[A] > cnt[B], A < B))
+    assert np.array_equal(sa[inner], want_a[inner])
+    # completeness: every visited pair is Self(root) or a child of exactly one split
+    expect = [(0, 0)]
+    for a, b, dd in zip(A.tolist(), B.tolist(), dec.tolist()):
+        if dd == 0:
+            c0, nc = t["child_first"][a], t["nchild"][a]
+            for i in range(nc):
+                for j in range(i, nc):
+                    expect.append((c0 + i, c0 + j))
+        elif dd in (3, 4):
+            s = a if dd == 3 else b
+            for c in range(t["child_first"][s], t["child_first"][s] + t["nchild"][s]):
+                expect.append((c, b) if dd == 3 else (a, c))
+    assert sorted(expect) == sorted(zip(A.tolist(), B.tolist()))
+    # the lists are the M2L and P2P decisions, nothing else
+    m2l = sorted((min(a, b), max(a, b)) for a, b, dd in zip(A.tolist(), B.tolist(), dec.tolist()) if dd == 1)
+    p2p = sorted((min(a, b), max(a, b)) for a, b, dd in zip(A.tolist(), B.tolist(), dec.tolist()) if dd == 2)
+    assert m2l == [tuple(v) for v in r.m2l.tolist()]
+    assert p2p == [tuple(v) for v in r.p2p.tolist()]
+
+
+@pytest.mark.parametrize("case", ["plummer", "hernquist-leaf1", "coincident"])
+def test_walk_decisions_follow_the_rule(orc, case):
+    """The oracle's walk trace, checked pair by pair: P2P only for leaf pairs that fail
+    the acceptance test, splits only of pairs that fail it, the split node chosen by
+    reading A10, and no pair visited that the recursion does not produce."""
+    rng = np.random.default_rng(4)
+    if case == "plummer":
+        x, m = synth.plummer(3000, 4)
+        leaf, theta = 8, 0.5
+    elif case == "hernquist-leaf1":
+        x, m = synth.hernquist(700, 10)
+        leaf, theta = 1, 0.6
+    else:
+        x = np.concatenate([rng.normal(size=(300, 3)), np.repeat(rng.normal(size=(2, 3)), 20, axis=0)])
+        m = rng.random(x.shape[0])
+        leaf, theta = 4, 0.7
+    r = orc.run(x, m, leaf, 2, theta, 0, want_pot=False, want_trace=True)
+    _check_trace(r, theta)
 
 
 def test_geometry_matches_definition(orc):
