@@ -188,6 +188,17 @@ GBFMM_API int fmm_autotune(fmm_ctx *c, const double *x, const double *m, int64_t
 /* Number of walks this context has re-run after a buffer overflow. */
 GBFMM_API int fmm_walk_retries(fmm_ctx *c, int64_t *retries);
 
+/* Limit of the walk's only device-side wait, for tests of its failure path.  Each walk
+ * step places its outputs after those of the tiles before it (eq. mac_criterion decides
+ * the pairs; the order of the lists is fixed by the tree), so a tile polls a status word
+ * of its predecessors; after `polls` polls (0: the default, about 4 million, far beyond
+ * any correct run) it gives up, the remaining steps do nothing, and fmm_forces returns
+ * FMM_ERR_TIMEOUT with no output written.  never_satisfied != 0 makes every such wait
+ * look for a status that no tile publishes, so the limit is reached whenever a step has
+ * more than one tile of 1024 frontier pairs.  The context stays usable; the next
+ * fmm_forces walks again.  Invalidates cached lists. */
+GBFMM_API int fmm_set_wait_limit(fmm_ctx *c, int64_t polls, int never_satisfied);
+
 /* Device time in milliseconds of each stage of the last build/forces call, measured
  * with CUDA events on the context's stream: [build, moments, walk, m2l, l2l, p2p, l2p].
  * A stage that did not run in that call reports -1. */
@@ -199,21 +210,24 @@ GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
 /* Bounding cube, Morton keys and stable sort of fmm_build, for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a service entry point.
  *
- * Who needs it: code that must not call cudaMalloc/cudaFree -- they can synchronise the
- * whole device and are not allowed while a stream is being captured -- and hosts that
- * hand out all device memory from their own pool or budget it up front.  The call
- * allocates nothing: its scratch is one fixed array of about 2.2 MiB in the library's
- * device image, which every GPU that loads the library holds until the process exits.
+ * Who needs it: hosts that hand out all device memory from their own pool or budget it
+ * up front, and code that must not call cudaMalloc/cudaFree because those calls can
+ * synchronise the whole device.  The call allocates nothing: its scratch is one fixed
+ * array of about 2.2 MiB in the library's device image, which every GPU that loads the
+ * library holds until the process exits.
  *
- *   x: N x 3 row-major positions, device memory; 1 <= N <= FMM_NOALLOC_MAX_N.
+ *   x: N x 3 row-major positions, device memory of the current device (or managed
+ *   memory); 1 <= N <= FMM_NOALLOC_MAX_N.
  *   keys_sorted[N] (device): the 63-bit Morton keys in stable sorted order.
  *   perm[N] (device): input index of each sorted particle.
  *   lo[3], side[1] (device, either may be NULL): the bounding cube.
- *   cuda_stream: stream to queue the work on (NULL: the legacy default stream); the call
- *   returns after that stream has finished it.
+ *   cuda_stream: stream to queue the work on (NULL: the legacy default stream).
+ * The call synchronises that stream before it returns: it reads back a flag that says
+ * whether every coordinate was finite.  Only that stream is waited for, not the device.
  * Results equal those of fmm_build followed by fmm_get_keys on the same positions.
- * Returns FMM_ERR_CAPACITY for N above the maximum, FMM_ERR_INVALID for NULL or host
- * arrays, N < 1, or a non-finite coordinate (outputs are then unspecified).
+ * Returns FMM_ERR_CAPACITY for N above the maximum; FMM_ERR_INVALID for NULL arrays,
+ * host arrays, arrays of another device, N < 1, or a non-finite coordinate (outputs are
+ * then unspecified); FMM_ERR_CUDA with the failing step in fmm_last_error().
  * The first call on each device looks up the scratch array's address there; make that
  * first call before any stream capture.  All calls share the one array, so calls whose
  * GPU work overlaps (different streams or threads) race: serialise them. */

@@ -554,6 +554,15 @@ int fmm_walk_retries(fmm_ctx* c, int64_t* retries) {
     return FMM_OK;
 }
 
+int fmm_set_wait_limit(fmm_ctx* c, int64_t polls, int never_satisfied) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_wait_limit: NULL context");
+    if (polls < 0) return fail(FMM_ERR_INVALID, "fmm_set_wait_limit: polls must be >= 0");
+    c->walk_spin_limit = polls > 0 ? (long long)polls : gbfmm::WALK_SPIN_LIMIT;
+    c->walk_wait_never = never_satisfied != 0;
+    c->list_theta = -1.0;   // the next fmm_forces walks again under these limits
+    return FMM_OK;
+}
+
 int fmm_stage_times(fmm_ctx* c, double* ms, int n) {
     if (!c || !ms) return fail(FMM_ERR_INVALID, "fmm_stage_times: NULL argument");
     return guarded(c, [&]() -> int {

@@ -60,6 +60,9 @@ struct ItemSet {
 constexpr int M2L_CHUNK = 32;
 constexpr int M2L_CHUNK_MIXED = 64;  // default in FMM_MIXED
 constexpr int P2P_CHUNK = 64;
+// polls of one status word before a walk tile gives up waiting for the tiles before it
+// (~0.1-1 s; never reached in a correct run)
+constexpr long long WALK_SPIN_LIMIT = 1ll << 22;
 
 enum Stage {
     ST_BUILD = 0,   // bounding cube .. r_max
@@ -118,6 +121,8 @@ struct fmm_ctx {
     int m2l_chunk = gbfmm::M2L_CHUNK;          // directed M2L entries per work item (fmm_set_tiles)
     int p2p_chunk = gbfmm::P2P_CHUNK;          // directed P2P entries per reduction item
     int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
+    long long walk_spin_limit = gbfmm::WALK_SPIN_LIMIT;  // polls per look-back wait (fmm_set_wait_limit)
+    bool walk_wait_never = false;              // test of the timeout path: no wait is ever satisfied
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
     gbfmm::DevBuf m2l_dir;                     // uint32 source ids, per-target segments in list order
     gbfmm::DevBuf m2l_dirp;                    // uint32 (pair << 1 | side) of the same entries

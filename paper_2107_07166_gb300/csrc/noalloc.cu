@@ -8,6 +8,7 @@
 // that pointer.  Every call shares the array: calls whose work overlaps on the GPU
 // race, and each call clears what must start at zero.
 #include <mutex>
+#include <string>
 
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
@@ -43,6 +44,10 @@ constexpr size_t OFF_PART = OFF_SUMS + al256(sizeof(int) * 64);
 constexpr size_t OFF_GEOM = OFF_PART + al256(sizeof(double) * 6 * NA_MAX_BB);
 constexpr size_t OFF_FLAG = OFF_GEOM + al256(sizeof(double) * 8);
 constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_FLAG + al256(sizeof(int) * 4);   // ~2.2 MiB
+// the cube kernel reads N zero masses from vals_a..vals_b (see below): the two payload
+// regions must be adjacent, exactly 4 NA_MAX_N bytes apart, and end before the histograms
+static_assert(OFF_VALS_B - OFF_VALS_A == sizeof(uint32_t) * NA_MAX_N, "payload regions must be adjacent");
+static_assert(OFF_HIST - OFF_VALS_A >= sizeof(double) * NA_MAX_N, "zero masses must fit before the histograms");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -55,13 +60,16 @@ __global__ void widen_perm_k(const uint32_t* __restrict__ v, int64_t n, int64_t*
     if (i < n) perm[i] = v[i];
 }
 
-bool is_device_memory(const void* p) {
+// true when p is memory the kernels on device dev may access directly: device memory of
+// dev itself, or managed memory
+bool is_device_memory(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -71,6 +79,14 @@ using namespace gbfmm;
 
 namespace gbfmm {
 void set_last_error(const char* msg);
+}
+
+// a failed CUDA step: clear the sticky error, record which step failed and why
+static int na_cuda_fail(const char* step, cudaError_t e) {
+    cudaGetLastError();
+    std::string msg = std::string("fmm_morton_sort_noalloc: ") + step + ": " + cudaGetErrorString(e);
+    set_last_error(msg.c_str());
+    return FMM_ERR_CUDA;
 }
 
 extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* keys_sorted, int64_t* perm,
@@ -88,13 +104,15 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
         return FMM_ERR_CAPACITY;
     }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) {
-        cudaGetLastError();
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_cuda_fail("cudaGetDevice", e);
+    if (dev < 0 || dev >= NA_MAX_DEV) {
+        set_last_error("fmm_morton_sort_noalloc: device ordinal above the supported 64");
         return FMM_ERR_CUDA;
     }
-    if (!is_device_memory(x) || !is_device_memory(keys_sorted) || !is_device_memory(perm) ||
-        (lo && !is_device_memory(lo)) || (side && !is_device_memory(side))) {
-        set_last_error("fmm_morton_sort_noalloc: every array must be device memory");
+    if (!is_device_memory(x, dev) || !is_device_memory(keys_sorted, dev) || !is_device_memory(perm, dev) ||
+        (lo && !is_device_memory(lo, dev)) || (side && !is_device_memory(side, dev))) {
+        set_last_error("fmm_morton_sort_noalloc: every array must be device memory of the current device");
         return FMM_ERR_INVALID;
     }
     // one-time set-up on this device: the device address of the scratch array
@@ -103,10 +121,10 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
         std::lock_guard<std::mutex> g(g_na_mutex);
         if (!g_na_addr[dev]) {
             void* ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                set_last_error("fmm_morton_sort_noalloc: cudaGetSymbolAddress of the scratch array failed");
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return na_cuda_fail("cudaGetSymbolAddress of the scratch array", e);
+            if (!ptr) {
+                set_last_error("fmm_morton_sort_noalloc: the scratch array has no device address");
                 return FMM_ERR_CUDA;
             }
             g_na_addr[dev] = static_cast<unsigned char*>(ptr);
@@ -125,13 +143,13 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
     double* geom = reinterpret_cast<double*>(base + OFF_GEOM);
     int* flag = reinterpret_cast<int*>(base + OFF_FLAG);
     int nb = (int)((N + NA_TB - 1) / NA_TB);
-    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int) * 4, s);
-    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    e = cudaMemsetAsync(flag, 0, sizeof(int) * 4, s);
+    if (e != cudaSuccess) return na_cuda_fail("clearing the status flag", e);
     // a1: cube, with the finiteness check of the coordinates.  The cube kernel also checks
     // masses; none are given here, so it reads N zero doubles (+0.0, a valid mass) from the
     // payload regions vals_a..vals_b (8 N bytes, cleared here, overwritten by the keys step).
     e = cudaMemsetAsync(vals_a, 0, sizeof(double) * (size_t)N, s);
-    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    if (e != cudaSuccess) return na_cuda_fail("clearing the zero masses", e);
     bbox_partial_k<<<nb, NA_TB, 0, s>>>(x, reinterpret_cast<const double*>(vals_a), N, part, flag);
     bbox_final_k<<<1, 512, 0, s>>>(part, nb, geom);
     // a2: keys and identity payload
@@ -148,21 +166,21 @@ extern "C" int fmm_morton_sort_noalloc(const double* x, int64_t N, uint64_t* key
         vals_b = tv;
     }
     if (keys_a != keys_sorted &&
-        cudaMemcpyAsync(keys_sorted, keys_a, sizeof(uint64_t) * (size_t)N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return FMM_ERR_CUDA;
+        (e = cudaMemcpyAsync(keys_sorted, keys_a, sizeof(uint64_t) * (size_t)N, cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+        return na_cuda_fail("copying the sorted keys", e);
     widen_perm_k<<<(unsigned)((N + NA_TB - 1) / NA_TB), NA_TB, 0, s>>>(vals_a, N, perm);
     if (lo && (e = cudaMemcpyAsync(lo, geom, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return FMM_ERR_CUDA;
+        return na_cuda_fail("copying lo", e);
     if (side && (e = cudaMemcpyAsync(side, geom + 3, sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return FMM_ERR_CUDA;
+        return na_cuda_fail("copying side", e);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    if (e != cudaSuccess) return na_cuda_fail("a kernel launch", e);
+    // the finiteness flag is read back on the host: the call waits for its stream here
     int bad = 0;
-    if (cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return FMM_ERR_CUDA;
-    }
+    if ((e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return na_cuda_fail("reading the status flag", e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return na_cuda_fail("synchronising the stream", e);
     if (bad) set_last_error("fmm_morton_sort_noalloc: non-finite coordinate");
     return bad ? FMM_ERR_INVALID : FMM_OK;
 }

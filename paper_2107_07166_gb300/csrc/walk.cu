@@ -104,7 +104,6 @@ struct WalkCounters {
 // order: every list the walk emits is a fixed function of the tree.  The tags carry the
 // step index, so the status words are cleared once per walk.
 constexpr int WIPT = 4, WTILE = WB * WIPT;
-constexpr long long WALK_SPIN_LIMIT = 1ll << 22;  // polls of one status word (~0.1-1 s)
 
 __device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
     unsigned long long v;
@@ -120,13 +119,20 @@ __global__ void __launch_bounds__(WB, 6) walk_step_k(const int2* __restrict__ fr
                                                   WalkCounters* __restrict__ cnt, int par, int step,
                                                   unsigned long long* __restrict__ status, NodeView nv,
                                                   double theta, float th2, int2* __restrict__ m2l, int cap_m2l,
-                                                  int2* __restrict__ p2p, int cap_p2p, int cap_fr) {
+                                                  int2* __restrict__ p2p, int cap_p2p, int cap_fr,
+                                                  long long spin_limit, unsigned tag_bias) {
     __shared__ int s_tile;
     __shared__ int sbase[3];
+    // after a wait ran out in an earlier step the frontier may hold slots that no tile
+    // wrote: the remaining steps read nothing (the host reports FMM_ERR_TIMEOUT)
+    if (cnt->err) return;
     int nf = min(cnt->nf[par], cap_fr);  // a frontier beyond the buffer was not stored (retried)
     int bm = cnt->n_m2l, bp = cnt->n_p2p;
     int ntiles = (nf + WTILE - 1) / WTILE;
     const unsigned tag_agg = 2u * (unsigned)step + 1u, tag_pre = 2u * (unsigned)step + 2u;
+    // the tags a waiting tile looks for: the published ones, unless a test of the timeout
+    // path sets tag_bias != 0, which no tile publishes (every wait then runs out)
+    const unsigned want_agg = tag_agg + tag_bias, want_pre = tag_pre + tag_bias;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&cnt->ticket, 1);
         __syncthreads();
@@ -175,14 +181,14 @@ __global__ void __launch_bounds__(WB, 6) walk_step_k(const int2* __restrict__ fr
                 for (;;) {
                     int u = t - lane;
                     // before tile 0 every counter starts at 0: a published prefix of 0
-                    unsigned long long w = u >= 0 ? ld_status(word + 3 * (int64_t)u) : (unsigned long long)tag_pre << 32;
+                    unsigned long long w = u >= 0 ? ld_status(word + 3 * (int64_t)u) : (unsigned long long)want_pre << 32;
                     unsigned tag = (unsigned)(w >> 32);
-                    unsigned pre = __ballot_sync(FULL, tag == tag_pre);
-                    unsigned wait = __ballot_sync(FULL, tag != tag_pre && tag != tag_agg);
+                    unsigned pre = __ballot_sync(FULL, tag == want_pre);
+                    unsigned wait = __ballot_sync(FULL, tag != want_pre && tag != want_agg);
                     int first = pre ? __ffs(pre) - 1 : 32;  // nearest tile with a prefix
                     unsigned need = first >= 31 ? FULL : ((2u << first) - 1u);
                     if (wait & need) {  // a tile in the window has not published yet
-                        if (++spins > WALK_SPIN_LIMIT) {
+                        if (++spins > spin_limit) {
                             if (lane == 0) atomicExch(&cnt->err, 1);
                             break;
                         }
@@ -394,6 +400,8 @@ static int bits_for(int64_t nn) {
 
 void run_walk(fmm_ctx* c, double theta) {
     cudaStream_t s = c->stream;
+    // the pair buffers are rewritten below: until this walk has finished, no list is valid
+    c->list_theta = -1.0;
     NodeView nv = node_view(c);
     int64_t nn = c->n_nodes;
     // fixed number of steps, no host round trip between them; one retry if a buffer overflowed
@@ -423,7 +431,8 @@ void run_walk(fmm_ctx* c, double theta) {
             int2* fin = par ? c->fr1.as<int2>() : c->fr0.as<int2>();
             int2* fout = par ? c->fr0.as<int2>() : c->fr1.as<int2>();
             walk_step_k<<<grid, WB, 0, s>>>(fin, fout, cnt, par, k, status, nv, theta, th2, c->m2l_pairs.as<int2>(),
-                                            (int)cap_m2l, c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr);
+                                            (int)cap_m2l, c->p2p_pairs.as<int2>(), (int)cap_p2p, (int)cap_fr,
+                                            c->walk_spin_limit, c->walk_wait_never ? 0x40000000u : 0u);
             GB_LAUNCH("walk_step_k");
             walk_advance_k<<<1, 1, 0, s>>>(cnt, par, max_fr);
             GB_LAUNCH("walk_advance_k");

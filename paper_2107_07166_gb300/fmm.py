@@ -32,7 +32,7 @@ EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_buil
            "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
-           "fmm_walk_retries", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
             "fmm_autotune": (i32, [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, P, i32, i32, P, P, P]),
             "fmm_leapfrog": (i32, [P, P, P, P, i64, i32, i32, dbl, i32, dbl, i32, P]),
             "fmm_walk_retries": (i32, [P, P]),
+            "fmm_set_wait_limit": (i32, [P, i64, i32]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
             "fmm_strerror": (C.c_char_p, [i32]),
@@ -273,6 +274,11 @@ class FMM:
         r = np.zeros(1, np.int64)
         _check(self.lib.fmm_walk_retries(self.h, _ptr(r)), "fmm_walk_retries")
         return int(r[0])
+
+    def set_wait_limit(self, polls: int = 0, never_satisfied: bool = False):
+        """Limit of the walk's look-back wait (0: default); never_satisfied for tests of the
+        FMM_ERR_TIMEOUT path."""
+        _check(self.lib.fmm_set_wait_limit(self.h, int(polls), int(bool(never_satisfied))), "fmm_set_wait_limit")
 
     def stage_times(self):
         ms = np.zeros(len(STAGES))

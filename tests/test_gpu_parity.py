@@ -200,6 +200,49 @@ def test_diagnostics_and_conservation(fmm, torch_cuda):
         g["f"].close()
 
 
+def _walk_cases():
+    import os
+    cases, cur = [], None
+    with open(os.path.join(os.path.dirname(__file__), "golden", "walk_hand.txt")) as fh:
+        for line in fh:
+            w = line.split()
+            if not w or w[0].startswith("#"):
+                continue
+            if w[0] == "case":
+                cur = {"name": w[1], "tree": [], "m2l": [], "p2p": []}
+            elif w[0] == "x":
+                cur["x"] = [float(v) for v in w[1:]]
+            elif w[0] in ("tree", "m2l", "p2p"):
+                cur[w[0]].append([int(v) for v in w[1:]])
+            elif w[0] == "end":
+                cases.append(cur)
+    return cases
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+def test_walk_hand_worked_lists(fmm, torch_cuda, precision):
+    """The trees and lists worked out by hand from eq. mac_criterion and the mutual walk
+    (tests/golden/walk_hand.txt), on the GPU in every arithmetic mode: the larger r_max is
+    split, ties go to the larger count and then the lower id, and a pair exactly on
+    r_A + r_B = theta R is accepted."""
+    names = ("first", "count", "level", "parent", "child_first", "nchild")
+    for case in _walk_cases():
+        n = len(case["x"])
+        x = np.zeros((n, 3))
+        x[:, 0] = case["x"]
+        f = new_ctx(fmm, torch_cuda, precision)
+        f.build(x, np.ones(n), 2)
+        f.forces(2, 0.5, 1, np.empty((n, 3)), None)
+        t = f.get_tree()
+        want = np.array(case["tree"], dtype=np.int32)
+        for j, k in enumerate(names):
+            assert np.array_equal(t[k], want[:, j]), (case["name"], k)
+        m2l, p2p = f.get_lists()
+        assert m2l.tolist() == case["m2l"], case["name"]
+        assert p2p.tolist() == case["p2p"], case["name"]
+        f.close()
+
+
 def test_walk_retries_after_buffer_overflow(fmm, torch_cuda, orc):
     """Tiny walk buffers force the overflow path: the walk is re-run with larger buffers
     and the lists and forces are those of an ordinary run."""
@@ -211,6 +254,34 @@ def test_walk_retries_after_buffer_overflow(fmm, torch_cuda, orc):
     acc = np.empty((6000, 3))
     f.forces(3, 0.5, 1, acc, None)
     assert f.walk_retries() >= 3
+    m2l, p2p = f.get_lists()
+    assert np.array_equal(m2l, r.m2l) and np.array_equal(p2p, r.p2p)
+    assert rel(acc, r.acc) < TOL
+    f.close()
+
+
+def test_walk_wait_timeout_returns_status(fmm, torch_cuda, orc):
+    """The walk's only device-side wait (a tile polling the status words of the tiles before
+    it) is bounded.  Here every wait looks for a status that no tile publishes and gives up
+    after 64 polls: fmm_forces must return FMM_ERR_TIMEOUT (-6) with the outputs untouched,
+    and the context must stay usable -- the next walk, with the default limit, gives the
+    oracle's lists and forces."""
+    x, m = synth.plummer(1 << 15, 18)
+    r = orc.run(x, m, 16, 3, 0.5, 1, want_pot=False)
+    f = new_ctx(fmm, torch_cuda)
+    f.build(x, m, 16)
+    acc = np.full((1 << 15, 3), 7.0)
+    pot = np.full(1 << 15, 7.0)
+    f.set_wait_limit(64, never_satisfied=True)
+    with pytest.raises(fmm.FMMError) as e:
+        f.forces(3, 0.5, 1, acc, pot)
+    assert e.value.status == -6
+    assert np.all(acc == 7.0) and np.all(pot == 7.0)
+    with pytest.raises(fmm.FMMError) as e:   # the failed walk left no list to export
+        f.get_lists()
+    assert e.value.status == -2
+    f.set_wait_limit(0)
+    f.forces(3, 0.5, 1, acc, None)
     m2l, p2p = f.get_lists()
     assert np.array_equal(m2l, r.m2l) and np.array_equal(p2p, r.p2p)
     assert rel(acc, r.acc) < TOL
