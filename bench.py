@@ -139,22 +139,40 @@ def algorithmic_flops(counts, tree_counts, p, variant):
             "per_m2l_pair": per_m2l}
 
 
-# DRAM bytes (read + write) per unit of the dominant binary64 kernels, from an ncu capture
-# of their DRAM counters at N = 2^19 (profiles/p2p_k-m2l_con_k_plummer-512k.md), scaled
-# here by the units of the timed launch: per mutual M2L pair, per particle pair.
-# DRAM bytes per unit from ncu at N = 2^19 (profiles/): the binary64 M2L stage is the pair-tensor
-# kernel plus m2l_con_t_k (per mutual pair), the binary64 P2P is p2p_k (per particle pair)
+# DRAM bytes (read + write) per unit of the dominant binary64 kernels, from ncu captures of
+# their DRAM counters at N = 2^19 (p = 4), scaled by the units of the timed launch: per mutual
+# M2L pair for the M2L stage (the pair-tensor kernel plus m2l_con_t_k), per particle pair for
+# p2p_k.  Traffic grows in proportion to these units (per-pair tensors and partials).
 NCU_TRAFFIC_PER_UNIT = {("m2l_con_t_k", "fp64"): 659.0, ("p2p_k", "fp64"): 5.13}
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
-    """binary64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops."""
+    """binary64 FMA rate of a GB300 from unit counts: 152 SMs x 2 FP64 FMA per SM per clock
+    x 2 flops (context for the measured rate)."""
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
-    """binary32 FMA peak of a GB300: 152 SMs x 128 FP32 FMA per SM per clock x 2 flops."""
+    """binary32 FMA rate of a GB300 from unit counts: 152 SMs x 128 FP32 FMA per SM per clock
+    x 2 flops (context for the measured rate)."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# bytes per particle of the tree build (bounding cube .. sorted SoA): read x, y, z, m (32 B),
+# write key and index (12 B), one read and write of (key, index) per radix pass (24 B x 8
+# passes), write the sorted SoA (32 B); and the one-pass minimum (read 32 B, write key and
+# index 12 B, write the sorted SoA 32 B)
+BUILD_BYTES_PER_PARTICLE = 268
+BUILD_BYTES_MIN_PER_PARTICLE = 76
+
+
+def workload_config(W, world, n_total, n_systems, tune=None):
+    """The "config" object of the JSON line (the same for the GPU arm and the reference arm)."""
+    return {"workload": W["workload"], "N": n_total, "n_systems": n_systems,
+            "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
+            "variant": W["variant"], "precision": W["precision"],
+            "parallelism": (f"lpt-shard{world}" if W.get("n_sys_total") else f"replicas{world}"),
+            "autotune": tune, "l2": "flushed between timed steps (512 MiB write)"}
 
 
 def run_gbfmm(args):
@@ -202,6 +220,8 @@ def run_gbfmm(args):
     acc = torch.empty((N, 3), dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": fmm.FP64, "df64": fmm.DF64, "mixed": fmm.MIXED}[args.precision]
+    # measured FMA rate of the units the pair kernels run on (roofline denominator), untimed
+    alu_peak = fmm.probe_fma_rate(local, fmm.MIXED if prec == fmm.MIXED else fmm.FP64)
     f = fmm.FMM(local, prec, stream)
     variant = fmm.CONSERVING if args.variant == "conserving" else fmm.STANDARD
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -316,6 +336,8 @@ def run_gbfmm(args):
         stream.synchronize()
         r = ref.cpu().numpy()
         err["vs_fp64_gpu"] = float(np.linalg.norm(a - r) / np.linalg.norm(r))
+        pe = np.linalg.norm(a - r, axis=1) / np.maximum(np.linalg.norm(r, axis=1), 1e-300)
+        err["vs_fp64_gpu_per_particle"] = {"median": float(np.median(pe)), "max": float(pe.max())}
         g.close()
     ts = float((m * np.linalg.norm(x, axis=1) * np.linalg.norm(a, axis=1)).sum())
     fsum = float((m * np.linalg.norm(a, axis=1)).sum())
@@ -378,6 +400,51 @@ def run_gbfmm(args):
             "force_err_rel_l2": {"vs_direct_sampled": sampled_direct_error(torch, dev, x, m, o, offsets=offsets)},
             "stage_ms": {k: round(v, 4) for k, v in f.stage_times().items()}}
 
+    # accuracy-matched comparison: the realigned form costs accuracy at equal order, so it
+    # is also timed one order higher (conserving at p + 1) against the standard form at p,
+    # on the same input and tree, with the error of each against the direct sum
+    matched = None
+    if args.modes and world == 1 and W["p"] + 1 <= (fmm.MIXED_P_MAX if prec == fmm.MIXED else
+                                                   (fmm.DF64_P_MAX if prec == fmm.DF64 else fmm.P_MAX)):
+        out = torch.empty_like(acc)
+        rows = {}
+        for name, pp, vv in (("standard_p", W["p"], fmm.STANDARD), ("conserving_p", W["p"], fmm.CONSERVING),
+                             ("conserving_p_plus_1", W["p"] + 1, fmm.CONSERVING)):
+            def sv():
+                if offsets is not None:
+                    f.build_batch(xd, md, offsets, W["leaf"])
+                else:
+                    f.build(xd, md, W["leaf"])
+                f.forces(pp, W["theta"], vv, out, None)
+
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    sv()
+            stream.synchronize()
+            ts_ = []
+            for _ in range(max(3, min(args.steps, 5))):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sv()
+                e1.record(stream)
+                e1.synchronize()
+                ts_.append(e0.elapsed_time(e1))
+            o = out.cpu().numpy()
+            Fm, Tm = f.diagnostics()
+            rows[name] = {"p": pp, "variant": "standard" if vv == fmm.STANDARD else "conserving",
+                          "ms_per_step": statistics.mean(ts_),
+                          "force_err_vs_direct_sampled": sampled_direct_error(torch, dev, x, m, o, offsets=offsets),
+                          "net_torque_rel": float(np.linalg.norm(Tm) / float(
+                              (m * np.linalg.norm(x, axis=1) * np.linalg.norm(o, axis=1)).sum()))}
+        s0, s1 = rows["standard_p"], rows["conserving_p_plus_1"]
+        matched = dict(rows, time_ratio_conserving_p_plus_1_over_standard_p=s1["ms_per_step"] / s0["ms_per_step"],
+                       err_ratio_conserving_p_plus_1_over_standard_p=(s1["force_err_vs_direct_sampled"]
+                                                                      / s0["force_err_vs_direct_sampled"]))
+
     # the other arithmetic modes of the pair kernels on the same input (same timing method)
     modes = {}
     if args.modes and world == 1 and args.workload == "plummer1m" and not args.n:
@@ -420,9 +487,12 @@ def run_gbfmm(args):
                 ref = rr.cpu().numpy()
                 g.close()
             tm = statistics.mean(ts_)
+            pe = np.linalg.norm(o - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
             modes[name] = {"value": N / (tm / 1e3), "ms_per_step": tm,
                            "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[name],
                            "force_err_vs_fp64_gpu": float(np.linalg.norm(o - ref) / np.linalg.norm(ref)),
+                           "force_err_per_particle_vs_fp64_gpu": {"median": float(np.median(pe)),
+                                                                  "max": float(pe.max())},
                            "stage_ms": {k: round(v, 4) for k, v in h.stage_times().items()}}
             h.close()
 
@@ -435,14 +505,15 @@ def run_gbfmm(args):
     stage_avg = {s: (statistics.mean(v) if v and v[0] >= 0 else None) for s, v in stage_ms.items()}
     dom = "m2l" if (stage_avg["m2l"] or 0) >= (stage_avg["p2p"] or 0) else "p2p"
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    if args.precision == "mixed":
-        peak = fp32_peak_tflops(2070.0)
-        basis = "binary32 FMA rate derived from unit counts: 152 SMs x 128 FFMA/clk x 2 flops x 2070 MHz"
-    else:
-        peak = fp64_peak_tflops(2070.0)
-        basis = ("binary64 FMA rate derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz"
-                 + ("; the double-float kernels run on the binary32 units and are rated against the binary64 "
-                    "peak they replace" if args.precision == "df64" else ""))
+    nominal = fp32_peak_tflops(2070.0) if args.precision == "mixed" else fp64_peak_tflops(2070.0)
+    peak = alu_peak or nominal
+    unit_name = "binary32" if args.precision == "mixed" else "binary64"
+    basis = (f"measured live: {unit_name} FMA-chain probe (fmm_probe_fma_rate, best of 3) = {alu_peak:.4g} TFLOP/s; "
+             f"unit-count figure {nominal:.4g} TFLOP/s (152 SMs x "
+             f"{'128 FFMA' if args.precision == 'mixed' else '2 DFMA'}/clk x 2 flops x 2070 MHz)"
+             if alu_peak else f"{unit_name} unit-count figure (probe unavailable)")
+    if args.precision == "df64":
+        basis += "; the double-float kernels run on the binary32 units and are rated against the binary64 peak they replace"
     def stage_roofline(st):
         """roofline of one pair stage: algorithmic flops over its event time, ncu traffic"""
         achieved = work[st] / (stage_avg[st] / 1e3) / 1e12
@@ -467,6 +538,18 @@ def run_gbfmm(args):
     # (26 flops, the reciprocal square root counted as one) is far below the binary64
     # instructions it takes, so the P2P line reads low while its binary64 pipe is busy
     roofline_stages = {st: stage_roofline(st) for st in ("m2l", "p2p") if stage_avg[st]}
+    # the tree build (bounding cube .. r_max) against the measured HBM copy bandwidth, on the
+    # survey's byte model of the build (and its one-pass minimum)
+    hbm = measured_peaks().get("hbm_gbs")
+    roofline_build = None
+    if stage_avg["build"] and hbm:
+        gbs = BUILD_BYTES_PER_PARTICLE * N / (stage_avg["build"] / 1e3) / 1e9
+        roofline_build = {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
+                          "frac": round(gbs / hbm, 4), "bytes_per_particle": BUILD_BYTES_PER_PARTICLE,
+                          "achieved_min_model": round(BUILD_BYTES_MIN_PER_PARTICLE * N / (stage_avg["build"] / 1e3) / 1e9, 2),
+                          "bytes_per_particle_min_model": BUILD_BYTES_MIN_PER_PARTICLE,
+                          "stage_ms": stage_avg["build"], "peak_basis": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                          "note": "whole build stage (cube, keys, sort, gather, octree, COM, r_max) by CUDA events"}
     cpu = cpu_baseline() if (args.cpu_baseline and world == 1 and not args.n and args.workload == "plummer1m") else None
     rng = np.random.default_rng(0)
     line = {
@@ -477,12 +560,8 @@ def run_gbfmm(args):
                  "binary": "synthetic (seeded binary of two Plummer spheres, 10 apart)",
                  "disk": "synthetic (seeded exponential disk + Hernquist bulge)",
                  "batch": "synthetic (seeded batch of Plummer/Hernquist systems, log-uniform sizes)"}[gen],
-        "config": {"workload": W["workload"], "N": n_total if W.get("n_sys_total") else N,
-                   "n_systems": W.get("n_sys_total") or (len(offsets) - 1 if offsets is not None else 1),
-                   "p": W["p"], "theta": W["theta"], "leaf_size": W["leaf"],
-                   "variant": W["variant"], "precision": W["precision"], "parallelism": (f"lpt-shard{world}" if W.get("n_sys_total") else f"replicas{world}"),
-                   "autotune": tune,
-                   "l2": "flushed between timed steps (512 MiB write)"},
+        "config": workload_config(W, world, n_total if W.get("n_sys_total") else N,
+                                  W.get("n_sys_total") or (len(offsets) - 1 if offsets is not None else 1), tune),
         "stage_ms": {k: (round(v, 4) if v is not None else None) for k, v in stage_avg.items()},
         "work": {"n_m2l_pairs": work["n_m2l"], "n_p2p_particle_pairs": work["n_pp"],
                  "m2l_flops": work["m2l"], "p2p_flops": work["p2p"]},
@@ -490,6 +569,8 @@ def run_gbfmm(args):
         "net_force_rel": float(np.linalg.norm(Fsum) / fsum), "net_torque_rel": float(np.linalg.norm(Tsum) / ts),
         "roofline": roofline,
         "roofline_stages": roofline_stages,
+        "roofline_build": roofline_build,
+        "accuracy_matched": matched,
         "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,
@@ -536,18 +617,18 @@ def sampled_direct_error(torch, dev, x, m, a, n_targets=400, offsets=None):
     return float(np.linalg.norm(a[tg] - ref) / np.linalg.norm(ref))
 
 
-def oracle_sample_rate():
-    """The CPU oracle on a bounded sample of the workload (same generator, p, theta,
-    leaf, variant; N = 2^17): particles/s."""
+def oracle_sample_rate(n=CPU_SAMPLE_N):
+    """The CPU oracle on a bounded sample of the workload (same generator, p, theta, leaf,
+    variant; n particles): particles/s and seconds."""
     import oracle
     from paper_2107_07166_gb300 import synth
     W = WORKLOAD
-    x, m = synth.plummer(CPU_SAMPLE_N, W["seed"])
+    x, m = synth.plummer(n, W["seed"])
     oracle.build()
     t0 = time.perf_counter()
     oracle.run(x, m, W["leaf"], W["p"], W["theta"], 1, want_pot=False, want_internals=False)
     dt = time.perf_counter() - t0
-    return CPU_SAMPLE_N / dt, dt
+    return n / dt, dt
 
 
 def cpu_baseline():
@@ -557,28 +638,37 @@ def cpu_baseline():
                       f"one build+forces, {dt:.1f} s single-threaded"}
 
 
+# per-step sample of the reference arm: a quarter of the workload, so that the driver's
+# 20 timed + 5 warm-up steps end within a few minutes on one host core
+REF_SAMPLE_N = 1 << 18
+
+
 def run_reference(args):
+    """The oracle as it stands, single-threaded on the host, on this workload's config:
+    every step is one build + forces of a bounded sample (REF_SAMPLE_N particles of the
+    same generator, p, theta, leaf size and variant); value = sample particles / step time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        oracle_sample_rate()
+    for _ in range(max(0, args.warmup)):
+        oracle_sample_rate(REF_SAMPLE_N)
     times = []
     for _ in range(max(1, args.steps)):
-        rate, dt = oracle_sample_rate()
+        _, dt = oracle_sample_rate(REF_SAMPLE_N)
         times.append(dt)
     t = statistics.mean(times)
-    rate = CPU_SAMPLE_N / t
+    rate = REF_SAMPLE_N / t
+    W = dict(WORKLOAD)
     line = {
         "metric": METRIC, "value": rate, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer sphere)", "impl": "reference",
-        "config": {"workload": WORKLOAD["workload"], "N": WORKLOAD["N"], "p": WORKLOAD["p"],
-                   "theta": WORKLOAD["theta"], "leaf_size": WORKLOAD["leaf"], "variant": WORKLOAD["variant"],
-                   "precision": WORKLOAD["precision"], "parallelism": "cpu-oracle"},
+        "config": workload_config(W, world, W["N"], 1),
+        "sample": {"N": REF_SAMPLE_N, "of_N": W["N"],
+                   "note": "each step times the oracle on this bounded sample of the configured workload"},
         "cpu_baseline": {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
-                         "sample": f"Plummer N={CPU_SAMPLE_N} per step (bounded sample of the N=2^20 workload), "
-                                   "single-threaded FP64 C oracle"},
+                         "sample": f"Plummer N={REF_SAMPLE_N} per step (bounded sample of the N=2^20 workload, "
+                                   "same seed, p, theta, leaf size, variant), single-threaded FP64 C oracle"},
         "e2e": {"value": rate, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

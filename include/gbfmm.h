@@ -234,6 +234,14 @@ GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
 GBFMM_API int fmm_morton_sort_noalloc(const double *x, int64_t N, uint64_t *keys_sorted, int64_t *perm,
                                       double *lo, double *side, void *cuda_stream);
 
+/* Measured fused multiply-add rate of device `device` in TFLOP/s (an FMA counted as two
+ * flops): binary64 for precision FMM_FP64, binary32 for FMM_MIXED.  A kernel of eight
+ * independent FMA chains per thread, four blocks of 256 threads per SM, timed with CUDA
+ * events (best of three after a warm-up run, about 20 ms each).  The paper has no
+ * counterpart: this is the measured peak against which the ALU-bound pair kernels (M2L,
+ * P2P) are rated.  Synchronises the device's work on a private stream; allocates 16 bytes. */
+GBFMM_API int fmm_probe_fma_rate(int device, int precision, double *tflops);
+
 /* Number of CUDA kernels this library has launched in this process so far (all contexts). */
 GBFMM_API int64_t fmm_kernel_launches(void);
 

@@ -86,12 +86,33 @@ __device__ __forceinline__ float dsep(float ah, float al, float bh, float bl) {
     return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
 }
 
+// The double-float centre words hold a centre to about 2^-48 |Z| (the rounding of the low
+// word), so (hi - hi) + (lo - lo) carries an absolute error of up to ~2^-47 |Z|.  Below
+// |R|_inf = 2^-20 max(|Z_a|, |Z_b|) that is more than 2^-27 of R, and R is formed again
+// from the binary64 centres (rounded once to binary32).  Only cells that nearly coincide
+// take this branch.
+__device__ __forceinline__ void close_sep_fix(float4 ah, float4 bh, const double* __restrict__ Zx,
+                                              const double* __restrict__ Zy, const double* __restrict__ Zz, int t,
+                                              int s, float& rx, float& ry, float& rz) {
+    float r = fmaxf(fabsf(rx), fmaxf(fabsf(ry), fabsf(rz)));
+    float z = fmaxf(fmaxf(fmaxf(fabsf(ah.x), fabsf(ah.y)), fabsf(ah.z)),
+                    fmaxf(fmaxf(fabsf(bh.x), fabsf(bh.y)), fabsf(bh.z)));
+    if (r < 0x1p-20f * z) {
+        rx = (float)(Zx[t] - Zx[s]);
+        ry = (float)(Zy[t] - Zy[s]);
+        rz = (float)(Zz[t] - Zz[s]);
+    }
+}
+
 // 2^e as binary64 for |e| <= 1022
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
-// the item unit exponent: min over the item's sources of floor(log2 |R|_inf)
+// the item unit exponent: min over the item's sources of floor(log2 |R|_inf), with R formed
+// as the M2L kernels form it (close_sep_fix included)
 __device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint32_t* __restrict__ dir,
-                                        const float4* __restrict__ zh, const float4* __restrict__ zl) {
+                                        const float4* __restrict__ zh, const float4* __restrict__ zl,
+                                        const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                        const double* __restrict__ Zz) {
     float4 ah = zh[tgt], al = zl[tgt];
     int k = 100;
     // four entries per round with all loads first: the id -> centre chains overlap (an index
@@ -107,9 +128,12 @@ __device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint32_t*
             bl[j] = zl[s[j]];
         }
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            k = min(k, sep_exp(dsep(ah.x, al.x, bh[j].x, bl[j].x), dsep(ah.y, al.y, bh[j].y, bl[j].y),
-                               dsep(ah.z, al.z, bh[j].z, bl[j].z)));
+        for (int j = 0; j < 4; j++) {
+            float rx = dsep(ah.x, al.x, bh[j].x, bl[j].x), ry = dsep(ah.y, al.y, bh[j].y, bl[j].y);
+            float rz = dsep(ah.z, al.z, bh[j].z, bl[j].z);
+            close_sep_fix(ah, bh[j], Zx, Zy, Zz, tgt, s[j], rx, ry, rz);
+            k = min(k, sep_exp(rx, ry, rz));
+        }
     }
     return k;
 }
@@ -164,12 +188,13 @@ struct SepOf<df64> {
 };
 template <>
 struct SepOf<float> {
-    __device__ static void get(const double*, const double*, const double*, const float4* zh, const float4* zl,
-                               int tgt, int src, float& rx, float& ry, float& rz) {
+    __device__ static void get(const double* Zx, const double* Zy, const double* Zz, const float4* zh,
+                               const float4* zl, int tgt, int src, float& rx, float& ry, float& rz) {
         float4 ah = zh[tgt], al = zl[tgt], bh = zh[src], bl = zl[src];
         rx = dsep(ah.x, al.x, bh.x, bl.x);
         ry = dsep(ah.y, al.y, bh.y, bl.y);
         rz = dsep(ah.z, al.z, bh.z, bl.z);
+        close_sep_fix(ah, bh, Zx, Zy, Zz, tgt, src, rx, ry, rz);
     }
     __device__ static float approx(float v) { return v; }
 };
@@ -279,7 +304,7 @@ struct TgtGeo {
         z = g.Zz[t];
     }
     // R = Z_tgt - Z_src, formed in binary64 and rounded to T
-    __device__ void sep(const SrcGeo<T>& s, T& rx, T& ry, T& rz) const {
+    __device__ void sep(const SrcGeo<T>& s, T& rx, T& ry, T& rz, const M2LGeom&, int, int) const {
         rx = to_kernel(x - s.x, T());
         ry = to_kernel(y - s.y, T());
         rz = to_kernel(z - s.z, T());
@@ -292,11 +317,14 @@ struct TgtGeo<float> {
         h = g.zh[t];
         l = g.zl[t];
     }
-    // R from the double-float centre words: (hi - hi) + (lo - lo)
-    __device__ void sep(const SrcGeo<float>& s, float& rx, float& ry, float& rz) const {
+    // R from the double-float centre words: (hi - hi) + (lo - lo), or from the binary64
+    // centres for nearly coincident cells (close_sep_fix)
+    __device__ void sep(const SrcGeo<float>& s, float& rx, float& ry, float& rz, const M2LGeom& g, int t,
+                        int src) const {
         rx = dsep(h.x, l.x, s.h.x, s.l.x);
         ry = dsep(h.y, l.y, s.h.y, s.l.y);
         rz = dsep(h.z, l.z, s.h.z, s.l.z);
+        close_sep_fix(h, s.h, g.Zx, g.Zy, g.Zz, t, src, rx, ry, rz);
     }
 };
 
@@ -319,7 +347,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
     for (int k = 0; k < E::NM; k++) L[k] = T(0);
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl, g.Zx, g.Zy, g.Zz);
         kpart[it] = kI;
     }
     TgtGeo<T> tg;
@@ -330,7 +358,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
     for (int e = w.y; e < w.z; e++) {
         int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
         T rx, ry, rz;
-        tg.sep(sg, rx, ry, rz);
+        tg.sep(sg, rx, ry, rz, g, w.x, src);
         T D[E::NM];
         if constexpr (SC) {
             T ux, uy, uz;
@@ -379,7 +407,7 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     for (int k = 0; k < E::NSU; k++) SU[k] = T(0);
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl, g.Zx, g.Zy, g.Zz);
         kpart[it] = kI;
     }
     TgtGeo<T> tg;
@@ -390,7 +418,7 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     for (int e = w.y; e < w.z; e++) {
         int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
         T rx, ry, rz;
-        tg.sep(sg, rx, ry, rz);
+        tg.sep(sg, rx, ry, rz, g, w.x, src);
         T H[E::NQ];
         if constexpr (SC) {
             T ux, uy, uz;
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(EB) m2l_con_t_k(int64_t nitems, const int4* __
     for (int e = w.y; e < w.z; e++) {
         int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
         double rx, ry, rz;
-        tg.sep(sg, rx, ry, rz);
+        tg.sep(sg, rx, ry, rz, g, w.x, src);
         double H[E::NQ];
         load_pair_tensor<E::NQ>(T, dirp[e], H);
         E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
@@ -543,7 +571,7 @@ __global__ void __launch_bounds__(EB) m2l_p0_k(int64_t nitems, const int4* __res
     for (int k = 0; k < NSU; k++) SU[k] = T(0);
     int kI = 0;
     if constexpr (SC) {
-        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl);
+        kI = item_exp(w.x, w.y, w.z, dir, g.zh, g.zl, g.Zx, g.Zy, g.Zz);
         kpart[it] = kI;
     }
     for (int e = w.y; e < w.z; e++) {

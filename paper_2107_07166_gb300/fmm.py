@@ -32,7 +32,7 @@ EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_buil
            "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
-           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
             "fmm_leapfrog": (i32, [P, P, P, P, i64, i32, i32, dbl, i32, dbl, i32, P]),
             "fmm_walk_retries": (i32, [P, P]),
             "fmm_set_wait_limit": (i32, [P, i64, i32]),
+            "fmm_probe_fma_rate": (i32, [i32, i32, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
             "fmm_strerror": (C.c_char_p, [i32]),
@@ -88,6 +89,13 @@ def load(path: str = LIB_PATH):
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def probe_fma_rate(device: int = 0, precision: int = FP64) -> float:
+    """Measured FMA rate (TFLOP/s) of the binary64 (FP64) or binary32 (MIXED) units."""
+    out = np.zeros(1)
+    _check(load().fmm_probe_fma_rate(int(device), int(precision), _ptr(out)), "fmm_probe_fma_rate")
+    return float(out[0])
 
 
 def kernel_launches() -> int:
