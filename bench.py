@@ -643,6 +643,73 @@ def cpu_baseline():
 REF_SAMPLE_N = 1 << 18
 
 
+def workload_inputs(W, n=None, n_sys=None):
+    """Seeded inputs of a workload (optionally a smaller sample of the same generator):
+    x, m and the batch offsets (None for one system)."""
+    from paper_2107_07166_gb300 import synth
+    gen = W.get("gen", "plummer")
+    N = n or W["N"]
+    if gen == "binary":
+        x, m = synth.binary(N // 2, W["seed"], W["seed"] + 1)
+    elif gen == "disk":
+        x, m = synth.disk_bulge(N, W["seed"])
+    elif gen == "batch":
+        x, m, off = synth.batch(n_sys or W["n_sys"], W["seed"])
+        return x, m, off
+    else:
+        x, m = synth.plummer(N, W["seed"])
+    return x, m, None
+
+
+def oracle_extrapolated(W):
+    """Oracle time of a workload too large to run in full on one host core.  The oracle
+    (conserving, the workload's p, theta, leaf size) runs once on a sample of the same
+    generator (N = 2^17, or 32 systems of a batch) with its own stage timers; each stage's
+    time per unit (P2P per unordered particle pair, M2L per mutual pair, the walk per
+    visited pair, the rest per particle with an N log N factor for the tree) is applied to
+    the full workload's exact walk counts (oracle.counts: tree and walk only).  Returns a
+    dict; the figure is an extrapolation, not a run of the full workload."""
+    import oracle
+    oracle.build()
+    smp = dict(n_sys=32) if W.get("gen") == "batch" else dict(n=1 << 17)
+    x, m, off = workload_inputs(W, **smp)
+    bounds = [(0, x.shape[0])] if off is None else list(zip(off[:-1], off[1:]))
+    st = dict(tree=0.0, moments=0.0, walk=0.0, m2l=0.0, l2l_l2p=0.0, p2p=0.0)
+    cnt = np.zeros(4, dtype=np.int64)
+    nlogn = 0.0
+    for a, b in bounds:
+        r = oracle.run(x[a:b], m[a:b], W["leaf"], W["p"], W["theta"], 1, want_pot=False, want_internals=False)
+        for k, v in r.stage_seconds.items():
+            st[k] += v
+        cnt += np.array(oracle.counts(x[a:b], m[a:b], W["leaf"], W["theta"]))
+        nlogn += (b - a) * math.log2(b - a)
+    ns = x.shape[0]
+    per = {"p2p_per_particle_pair": st["p2p"] / cnt[3], "m2l_per_pair": st["m2l"] / cnt[1],
+           "walk_per_pair": st["walk"] / (cnt[1] + cnt[2]), "tree_per_nlogn": st["tree"] / nlogn,
+           "moments_l2p_per_particle": (st["moments"] + st["l2l_l2p"]) / ns}
+    x, m, off = workload_inputs(W)
+    bounds = [(0, x.shape[0])] if off is None else list(zip(off[:-1], off[1:]))
+    full = np.zeros(4, dtype=np.int64)
+    nlogn_f = 0.0
+    t0 = time.perf_counter()
+    for a, b in bounds:
+        full += np.array(oracle.counts(x[a:b], m[a:b], W["leaf"], W["theta"]))
+        nlogn_f += (b - a) * math.log2(b - a)
+    tc = time.perf_counter() - t0
+    N = x.shape[0]
+    parts = {"p2p": per["p2p_per_particle_pair"] * full[3], "m2l": per["m2l_per_pair"] * full[1],
+             "walk": per["walk_per_pair"] * (full[1] + full[2]), "tree": per["tree_per_nlogn"] * nlogn_f,
+             "moments_l2l_l2p": per["moments_l2p_per_particle"] * N}
+    est = float(sum(parts.values()))
+    return {"N": N, "extrapolated_seconds": est, "particles_per_s": N / est,
+            "seconds_by_stage": {k: float(v) for k, v in parts.items()},
+            "seconds_per_unit": {k: float(v) for k, v in per.items()},
+            "full_counts": {"n_nodes": int(full[0]), "n_m2l_pairs": int(full[1]), "n_p2p_pairs": int(full[2]),
+                            "n_particle_pairs": int(full[3])},
+            "sample": {"N": ns, "seconds_by_stage": st, "n_particle_pairs": int(cnt[3]), "n_m2l_pairs": int(cnt[1])},
+            "count_walk_seconds": tc}
+
+
 def run_reference(args):
     """The oracle as it stands, single-threaded on the host, on this workload's config:
     every step is one build + forces of a bounded sample (REF_SAMPLE_N particles of the
@@ -650,6 +717,19 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return None
+    if args.workload != "plummer1m" and (WORKLOADS[args.workload].get("gen") == "batch"
+                                         or (WORKLOADS[args.workload]["N"] or 0) > (1 << 19)):
+        # the large workloads: extrapolated from timed samples and exact walk counts
+        W = dict(WORKLOADS[args.workload])
+        ex = oracle_extrapolated(W)
+        line = {"metric": METRIC, "value": ex["particles_per_s"], "unit": "particles/s", "n_gpus": world,
+                "impl": "reference", "kind": "oracle, extrapolated", "dtype": "f64",
+                "config": workload_config(W, world, ex["N"], W.get("n_sys", 1)), "extrapolation": ex,
+                "cpu_baseline": {"value": ex["particles_per_s"], "unit": "particles/s", "cores": 1, "kind": "oracle",
+                                 "sample": "one timed sample of the same generator (stage timers per unit) "
+                                           "applied to the full workload's walk counts (extrapolated)"}}
+        print(json.dumps(line))
+        return line
     for _ in range(max(0, args.warmup)):
         oracle_sample_rate(REF_SAMPLE_N)
     times = []

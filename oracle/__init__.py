@@ -63,6 +63,8 @@ def _load():
         lib.orc_get_locals.restype = i32
         lib.orc_get_lists.argtypes = [P, P, P]
         lib.orc_set_trace.argtypes = [i32]
+        lib.orc_counts.argtypes = [P, P, i64, i32, dbl, P]
+        lib.orc_stage_seconds.argtypes = [P, P]
         lib.orc_get_trace.argtypes = [P, P]
         lib.orc_get_result.argtypes = [P, P, P]
         lib.orc_nmi.argtypes = [i32]
@@ -215,6 +217,15 @@ def l2l(p, s, Lp):
     return out
 
 
+def counts(x, m, leaf_size, theta):
+    """Walk counts without expansions: (nodes, mutual M2L pairs, P2P pairs, particle pairs)."""
+    x = _f64(x, (-1, 3))
+    m = _f64(m)
+    out = np.zeros(4, dtype=np.int64)
+    _load().orc_counts(_p(x), _p(m), x.shape[0], int(leaf_size), float(theta), _p(out))
+    return tuple(int(v) for v in out)
+
+
 class Result:
     """Everything one oracle evaluation produced (numpy copies)."""
 
@@ -247,7 +258,10 @@ def run(x, m, leaf_size, p, theta, variant=STANDARD, want_pot=True, want_interna
         acc = np.zeros((N, 3))
         pot = np.zeros(N) if want_pot else None
         lib.orc_get_result(h, _p(acc), _p(pot))
-        r = Result(acc=acc, pot=pot, n_nodes=nn, n_m2l=nm2l, n_p2p=np2p)
+        st = np.zeros(6)
+        lib.orc_stage_seconds(h, _p(st))
+        r = Result(acc=acc, pot=pot, n_nodes=nn, n_m2l=nm2l, n_p2p=np2p,
+                   stage_seconds=dict(zip(("tree", "moments", "walk", "m2l", "l2l_l2p", "p2p"), st.tolist())))
         if want_trace:
             tr = np.zeros((lib.orc_n_trace(h), 3), dtype=np.int32)
             lib.orc_get_trace(h, _p(tr))

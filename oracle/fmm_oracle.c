@@ -44,8 +44,10 @@
  * order 2, so the run carries order-2 moments (and, for the potential, the
  * standard order-2 locals) and degree-1 conserving locals.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
+#include <time.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -266,6 +268,8 @@ typedef struct {
     /* optional record of the walk: every visited pair (A, B) with its decision */
     int64_t n_trace, cap_trace;
     int32_t *trace; /* triples (A, B, decision), see WALK_* */
+    /* seconds spent in [tree and geometry, P2M/M2M, walk, M2L, L2L + L2P, P2P] */
+    double stage_s[6];
     /* results (input order) */
     double *acc, *pot;
     double *acc_s, *pot_s; /* sorted order */
@@ -631,6 +635,12 @@ static void p2p_pair(orc_t *o, int64_t a, int64_t b, double *acc, double *pot) {
 
 /* ---------------- driver ---------------- */
 
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 void orc_free(orc_t *o);
 
 /* Full evaluation.  x: N x 3 input order, m: N.  variant 0 standard, 1 conserving,
@@ -651,6 +661,7 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
     o->theta = theta;
     o->variant = variant;
     o->want_pot = want_pot;
+    double t0 = now_s();
     /* a1 bounding cube, a2 keys, a3 sort */
     uint64_t *k0 = (uint64_t *)malloc(8 * (size_t)N);
     orc_bbox(x, N, o->lo, &o->side);
@@ -669,6 +680,8 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
     build_tree(o);
     node_geometry(o);
     int64_t nn = o->n_nodes;
+    double t1 = now_s();
+    o->stage_s[0] = t1 - t0;
     /* a5 P2M, a6 M2M (children before parents: reverse breadth-first order) */
     o->nmom = orc_nmi(p);
     o->nloc = 4 * orc_nmi(p - 1);
@@ -679,10 +692,14 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
         else
             for (int64_t c = o->child_first[n]; c < o->child_first[n] + o->nchild[n]; c++) m2m(o, c, n);
     }
+    double t2 = now_s();
+    o->stage_s[1] = t2 - t1;
     /* a7 walk, canonical order */
     walk_self(o, 0);
     if (o->n_m2l) qsort(o->m2l, (size_t)o->n_m2l, 8, pair_cmp);
     if (o->n_p2p) qsort(o->p2p, (size_t)o->n_p2p, 8, pair_cmp);
+    double t3 = now_s();
+    o->stage_s[2] = t3 - t2;
     /* a8 M2L (both partners of each mutual pair), a9 accumulation in list order */
     int need_L = (variant == 0) || want_pot;
     if (need_L) o->L = (double *)calloc((size_t)nn * o->nmom, 8);
@@ -702,6 +719,8 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
             m2l_paper0(o, B, A);
         }
     }
+    double t4 = now_s();
+    o->stage_s[3] = t4 - t3;
     /* a10 L2L, parents before children (breadth-first order) */
     double w[ORC_NMI_MAX];
     for (int64_t n = 1; n < nn; n++) {
@@ -733,6 +752,8 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
         for (int d = 0; d < 3; d++) xv[d] = o->X[3 * i + d] - o->Z[3 * n + d];
         l2p_one(o, n, xv, o->acc_s + 3 * i, want_pot ? o->pot_s + i : NULL);
     }
+    double t5 = now_s();
+    o->stage_s[4] = t5 - t4;
     /* a12 P2P (mutual, list order) */
     double *acc_pp = (double *)calloc(3 * (size_t)N, 8);
     double *pot_pp = want_pot ? (double *)calloc((size_t)N, 8) : NULL;
@@ -746,6 +767,7 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
                 for (int64_t b = o->first[B]; b < o->first[B] + o->count[B]; b++) p2p_pair(o, a, b, acc_pp, pot_pp);
         }
     }
+    o->stage_s[5] = now_s() - t5;
     /* a13 sum and return to input order */
     o->acc = (double *)malloc(24 * (size_t)N);
     o->pot = want_pot ? (double *)malloc(8 * (size_t)N) : NULL;
@@ -765,6 +787,43 @@ orc_t *orc_run(const double *x, const double *m, int64_t N, int leaf_size, int p
     return o;
 }
 
+/* Interaction counts of the walk alone (steps a1..a4 and a7, no expansions), for the
+ * timing model of the oracle at sizes it is not run at: nodes, mutual M2L pairs, P2P
+ * pairs, and unordered particle pairs evaluated directly. */
+void orc_counts(const double *x, const double *m, int64_t N, int leaf_size, double theta, int64_t *out4) {
+    orc_tables();
+    orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
+    o->N = N;
+    o->leaf_size = leaf_size;
+    o->theta = theta;
+    uint64_t *k0 = (uint64_t *)malloc(8 * (size_t)N);
+    orc_bbox(x, N, o->lo, &o->side);
+    orc_keys(x, N, o->lo, o->side, k0);
+    o->keys = (uint64_t *)malloc(8 * (size_t)N);
+    o->perm = (int64_t *)malloc(8 * (size_t)N);
+    orc_sort(k0, N, o->keys, o->perm);
+    free(k0);
+    o->X = (double *)malloc(24 * (size_t)N);
+    o->m = (double *)malloc(8 * (size_t)N);
+    for (int64_t i = 0; i < N; i++) {
+        for (int d = 0; d < 3; d++) o->X[3 * i + d] = x[3 * o->perm[i] + d];
+        o->m[i] = m[o->perm[i]];
+    }
+    build_tree(o);
+    node_geometry(o);
+    walk_self(o, 0);
+    int64_t npp = 0;
+    for (int64_t k = 0; k < o->n_p2p; k++) {
+        int64_t a = o->count[o->p2p[2 * k]], b = o->count[o->p2p[2 * k + 1]];
+        npp += o->p2p[2 * k] == o->p2p[2 * k + 1] ? a * (a - 1) / 2 : a * b;
+    }
+    out4[0] = o->n_nodes;
+    out4[1] = o->n_m2l;
+    out4[2] = o->n_p2p;
+    out4[3] = npp;
+    orc_free(o);
+}
+
 void orc_free(orc_t *o) {
     if (!o) return;
     void *ptrs[] = {o->keys, o->perm, o->X, o->m, o->first, o->count, o->level, o->parent, o->child_first,
@@ -778,6 +837,8 @@ void orc_free(orc_t *o) {
 
 int64_t orc_n_nodes(const orc_t *o) { return o->n_nodes; }
 int64_t orc_n_trace(const orc_t *o) { return o->n_trace; }
+/* seconds of [tree and geometry, P2M/M2M, walk, M2L, L2L + L2P, P2P] of the run */
+void orc_stage_seconds(const orc_t *o, double *out6) { memcpy(out6, o->stage_s, sizeof(o->stage_s)); }
 /* the walk trace (orc_set_trace): n_trace x 3 int32, in visiting order */
 void orc_get_trace(const orc_t *o, int32_t *out) {
     if (o->n_trace) memcpy(out, o->trace, sizeof(int32_t) * 3 * (size_t)o->n_trace);

@@ -91,13 +91,12 @@ __device__ __forceinline__ float dsep(float ah, float al, float bh, float bl) {
 // |R|_inf = 2^-20 max(|Z_a|, |Z_b|) that is more than 2^-27 of R, and R is formed again
 // from the binary64 centres (rounded once to binary32).  Only cells that nearly coincide
 // take this branch.
-__device__ __forceinline__ void close_sep_fix(float4 ah, float4 bh, const double* __restrict__ Zx,
+// (al.w and bl.w hold max_i |hi(Z_i)| of the two centres.)
+__device__ __forceinline__ void close_sep_fix(float4 al, float4 bl, const double* __restrict__ Zx,
                                               const double* __restrict__ Zy, const double* __restrict__ Zz, int t,
                                               int s, float& rx, float& ry, float& rz) {
     float r = fmaxf(fabsf(rx), fmaxf(fabsf(ry), fabsf(rz)));
-    float z = fmaxf(fmaxf(fmaxf(fabsf(ah.x), fabsf(ah.y)), fabsf(ah.z)),
-                    fmaxf(fmaxf(fabsf(bh.x), fabsf(bh.y)), fabsf(bh.z)));
-    if (r < 0x1p-20f * z) {
+    if (r < 0x1p-20f * fmaxf(al.w, bl.w)) {
         rx = (float)(Zx[t] - Zx[s]);
         ry = (float)(Zy[t] - Zy[s]);
         rz = (float)(Zz[t] - Zz[s]);
@@ -131,7 +130,7 @@ __device__ __forceinline__ int item_exp(int tgt, int e0, int e1, const uint32_t*
         for (int j = 0; j < 4; j++) {
             float rx = dsep(ah.x, al.x, bh[j].x, bl[j].x), ry = dsep(ah.y, al.y, bh[j].y, bl[j].y);
             float rz = dsep(ah.z, al.z, bh[j].z, bl[j].z);
-            close_sep_fix(ah, bh[j], Zx, Zy, Zz, tgt, s[j], rx, ry, rz);
+            close_sep_fix(al, bl[j], Zx, Zy, Zz, tgt, s[j], rx, ry, rz);
             k = min(k, sep_exp(rx, ry, rz));
         }
     }
@@ -194,7 +193,7 @@ struct SepOf<float> {
         rx = dsep(ah.x, al.x, bh.x, bl.x);
         ry = dsep(ah.y, al.y, bh.y, bl.y);
         rz = dsep(ah.z, al.z, bh.z, bl.z);
-        close_sep_fix(ah, bh, Zx, Zy, Zz, tgt, src, rx, ry, rz);
+        close_sep_fix(al, bl, Zx, Zy, Zz, tgt, src, rx, ry, rz);
     }
     __device__ static float approx(float v) { return v; }
 };
@@ -324,7 +323,7 @@ struct TgtGeo<float> {
         rx = dsep(h.x, l.x, s.h.x, s.l.x);
         ry = dsep(h.y, l.y, s.h.y, s.l.y);
         rz = dsep(h.z, l.z, s.h.z, s.l.z);
-        close_sep_fix(h, s.h, g.Zx, g.Zy, g.Zz, t, src, rx, ry, rz);
+        close_sep_fix(l, s.l, g.Zx, g.Zy, g.Zz, t, src, rx, ry, rz);
     }
 };
 
@@ -518,11 +517,13 @@ __global__ void __launch_bounds__(EB) m2l_std_t_k(int64_t nitems, const int4* __
     for (int k = 0; k < E::NM; k++) part[it * E::NM + k] = L[k];
 }
 
+// conserving, on the root-relative source moments of con_moments_k: 4 nmi(p-1)-term
+// contractions per entry and no per-pair geometry (con_origin_k adds the target term)
 template <int P>
 __global__ void __launch_bounds__(EB) m2l_con_t_k(int64_t nitems, const int4* __restrict__ items,
                                                   const uint32_t* __restrict__ dir, const uint32_t* __restrict__ dirp,
-                                                  M2LGeom g, const double* __restrict__ T,
-                                                  const double* __restrict__ cmom, double* __restrict__ part) {
+                                                  const double* __restrict__ T, const double* __restrict__ cmom,
+                                                  double* __restrict__ part) {
     using E = Exp<P>;
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
@@ -530,20 +531,11 @@ __global__ void __launch_bounds__(EB) m2l_con_t_k(int64_t nitems, const int4* __
     double SU[E::NSU];
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) SU[k] = 0.0;
-    TgtGeo<double> tg;
-    tg.load(g, w.x);
-    int src = (int)dir[w.y];  // an item holds at least one entry
-    SrcGeo<double> sg;
-    sg.load(g, src);
     for (int e = w.y; e < w.z; e++) {
-        int nsrc = e + 1 < w.z ? (int)dir[e + 1] : src;
-        double rx, ry, rz;
-        tg.sep(sg, rx, ry, rz, g, w.x, src);
+        int src = (int)dir[e];
         double H[E::NQ];
         load_pair_tensor<E::NQ>(T, dirp[e], H);
-        E::m2l_con(cmom + (int64_t)src * E::NSU, H, rx, ry, rz, SU);
-        src = nsrc;
-        sg.load(g, src);
+        E::m2l_con_o(cmom + (int64_t)src * E::NSU, H, SU);
     }
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = SU[k];
@@ -673,16 +665,56 @@ __global__ void scale_moments_k(int nn, const double* __restrict__ mom, const do
     if (k == 0) nk[n] = kn;
 }
 
-// conserving source moments of every cell (formed once per moment build)
+// the root of node nd's system (roots are nodes 0 .. nsys-1; systems are contiguous in
+// particle order, so the node's first particle decides)
+__device__ __forceinline__ int root_of(const long long* __restrict__ off, int nsys, int first) {
+    int lo = 0, hi = nsys;  // off[lo] <= first < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= first)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// conserving source moments of every cell (formed once per moment build), about the
+// centre of the cell's system root: Q = [M_b | (b_i+1) M_{b+e_i} - z_i M_b], z = Z - Z_root.
+// The binary64 M2L then needs no per-pair work on them: with R = z_tgt - z_src,
+// sum_b (C_{i,b} + R_i M_b) h_{b+g} = sum_b Q_{i,b} h_{b+g} + z_tgt,i S_g, and the last term
+// is added once per target (con_origin_k).  The rounding it adds is about 2^-53 |z| / R
+// of the U locals, R the pair separation: 1e-15 for the cells of a Plummer sphere.
 template <int P>
-__global__ void __launch_bounds__(EB) con_moments_k(int nn, const double* __restrict__ mom, double* __restrict__ cmom) {
+__global__ void __launch_bounds__(EB) con_moments_k(int nn, const double* __restrict__ mom,
+                                                    const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                                    const double* __restrict__ Zz, const int* __restrict__ nfirst,
+                                                    const long long* __restrict__ off, int nsys,
+                                                    double* __restrict__ cmom) {
     using E = Exp<P>;
     int nd = blockIdx.x * EB + threadIdx.x;
     if (nd >= nn) return;
+    int r = root_of(off, nsys, nfirst[nd]);
     double C[E::NSU];
-    E::con_moments(mom + (int64_t)nd * E::NM, C);
+    E::con_moments_o(mom + (int64_t)nd * E::NM, Zx[nd] - Zx[r], Zy[nd] - Zy[r], Zz[nd] - Zz[r], C);
 #pragma unroll
     for (int k = 0; k < E::NSU; k++) cmom[(int64_t)nd * E::NSU + k] = C[k];
+}
+
+// the target-side term of the root-relative conserving M2L: U_{i,g} += z_i S_g, z = Z - Z_root,
+// on the M2L sums of every node (before L2L); one thread per (node, U coefficient)
+template <int NQ>
+__global__ void con_origin_k(int nn, const double* __restrict__ Zx, const double* __restrict__ Zy,
+                             const double* __restrict__ Zz, const int* __restrict__ nfirst,
+                             const long long* __restrict__ off, int nsys, double* __restrict__ loc) {
+    int64_t t = (int64_t)blockIdx.x * EB + threadIdx.x;
+    if (t >= (int64_t)nn * 3 * NQ) return;
+    int nd = (int)(t / (3 * NQ)), k = (int)(t - (int64_t)nd * 3 * NQ);
+    int i = k / NQ, g = k - i * NQ;
+    int r = root_of(off, nsys, nfirst[nd]);
+    double z = i == 0 ? Zx[nd] - Zx[r] : (i == 1 ? Zy[nd] - Zy[r] : Zz[nd] - Zz[r]);
+    double* L = loc + (int64_t)nd * 4 * NQ;
+    L[NQ + k] = fma(z, L[g], L[NQ + k]);
 }
 
 // a6 M2M in two steps per level: one thread per (parent, child) shifts the child's
@@ -943,9 +975,14 @@ void run_moments_p(fmm_ctx* c) {
         GB_LAUNCH("m2m_sum_k");
     }
     if (c->precision == FMM_FP64) {
-        ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
-        con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->cmom.as<double>());
-        GB_LAUNCH("con_moments_k");
+        if constexpr (P <= 6) {  // the shared-tensor M2L (p = 7, 8 read the raw moments)
+            ensure(c->cmom, sizeof(double) * (size_t)nn * E::NSU);
+            con_moments_k<P><<<grid_for(nn, EB), EB, 0, s>>>(nn, c->mom.as<double>(), c->nZx.as<double>(),
+                                                             c->nZy.as<double>(), c->nZz.as<double>(),
+                                                             c->nfirst.as<int>(), c->sys_off.as<long long>(),
+                                                             c->n_sys, c->cmom.as<double>());
+            GB_LAUNCH("con_moments_k");
+        }
         return;
     }
     // the scaled modes: raw moments in the pair-kernel type, range-scaled and padded
@@ -1033,7 +1070,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
             } else if constexpr (std::is_same<T, double>::value) {
                 const double* pt = pair_tensors<P, 1>(c, c->m2l_pth, c->pth_gen, c->pth_p);
                 m2l_con_t_k<P><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir,
-                                                               c->m2l_dirp.as<uint32_t>(), g, pt, cmom, part);
+                                                               c->m2l_dirp.as<uint32_t>(), pt, cmom, part);
                 GB_LAUNCH("m2l_con_t_k");
             } else {
                 m2l_con_k<P, T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, cmom, part,
@@ -1042,6 +1079,12 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
             }
         }
         reduce(m2l_reduce_k<E::NSU, E::NQ, 1, T>, E::NSU, c->loc.as<double>());
+        if constexpr (P <= 6 && std::is_same<T, double>::value) {
+            con_origin_k<E::NQ><<<grid_for((int64_t)nn * 3 * E::NQ, EB), EB, 0, s>>>(
+                nn, c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->nfirst.as<int>(),
+                c->sys_off.as<long long>(), c->n_sys, c->loc.as<double>());
+            GB_LAUNCH("con_origin_k");
+        }
     }
     if (std_locals) {
         DevBuf& L = variant == 0 ? c->loc : c->locp;

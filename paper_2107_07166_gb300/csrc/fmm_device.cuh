@@ -115,6 +115,57 @@ __global__ void scan_apply_k(const In* __restrict__ in, int64_t n, const T* __re
     if (blockIdx.x == ntiles - 1 && threadIdx.x == SCAN_BLOCK - 1) out[n] = tile_sums[ntiles];
 }
 
+// ------------------------------------------------------------------ ordered tile claims
+// Status words of a decoupled look-back: (tag << 32) | value, read and written with relaxed
+// gpu-scope accesses (the walk's frontier steps and the octree's levels).
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned tag, int value) {
+    unsigned long long v = ((unsigned long long)tag << 32) | (unsigned)value;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive prefix of tile `tile` over the values published before it: tiles t - 1,
+// t - 2, ... are read 32 per round by one warp (lane l reads tile t - 1 - l) until one has
+// published its inclusive prefix (tag_pre); published counts (tag_agg) are added on the
+// way.  Every tile waited on has been claimed by a running block that publishes its count
+// without waiting, so the waits end; they are still bounded by spin_limit polls, after
+// which *err is set and the partial sum is returned.  Called by one whole warp; the
+// result is valid in every lane.
+__device__ __forceinline__ int lookback_prefix(const unsigned long long* __restrict__ status, int tile,
+                                               unsigned tag_agg, unsigned tag_pre, long long spin_limit,
+                                               int* __restrict__ err) {
+    int lane = threadIdx.x & 31, ex = 0, t = tile - 1;
+    long long spins = 0;
+    while (t >= 0) {
+        int u = t - lane;
+        unsigned long long w = u >= 0 ? ld_status(status + u) : (unsigned long long)tag_pre << 32;
+        unsigned tag = (unsigned)(w >> 32);
+        unsigned pre = __ballot_sync(FULL, tag == tag_pre);
+        unsigned wait = __ballot_sync(FULL, tag != tag_pre && tag != tag_agg);
+        int first = pre ? __ffs(pre) - 1 : 32;  // nearest tile with a prefix
+        unsigned need = first >= 31 ? FULL : ((2u << first) - 1u);
+        if (wait & need) {  // a tile in the window has not published yet
+            if (++spins > spin_limit) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        int val = lane <= first ? (int)(unsigned)w : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(FULL, val, o);
+        ex += val;
+        if (first < 32) break;
+        t -= 32;
+    }
+    return ex;
+}
+
 // ------------------------------------------------------------------ radix sort
 // Stable least-significant-digit sort of 64-bit keys with optional 32-bit payloads,
 // RS_BITS-bit digits (9: seven passes for 63-bit Morton keys, four for 36-bit list keys).

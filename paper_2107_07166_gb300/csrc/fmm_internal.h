@@ -102,6 +102,7 @@ struct fmm_ctx {
     int64_t n_nodes = 0, cap_nodes = 0;
     int n_levels = 0;                          // levels 0 .. n_levels-1
     std::vector<int> level_start;              // size n_levels + 1
+    gbfmm::DevBuf lvl_ctl, lvl_status;         // octree level table and look-back words (build)
     gbfmm::DevBuf nfirst, ncount, nlevel, nparent, nchildf, nnchild;
     gbfmm::DevBuf nM, nSx, nSy, nSz, nZx, nZy, nZz, nr2, nrmax;
     gbfmm::DevBuf nr2f;                        // binary32 estimate of r_max^2 (prefilter)

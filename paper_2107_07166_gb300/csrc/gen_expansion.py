@@ -16,6 +16,11 @@ T (double, or float in mixed precision), for:
            s_gamma = sum M_beta h_{beta+gamma},  w_{i,gamma} = sum (beta_i+1) M_{beta+e_i} h_{beta+gamma};
            the (beta_i+1) M_{beta+e_i} factors are formed once per cell (con_moments) and R is
            folded into them per pair, so U_{i,gamma} += sum_beta (C_{i,beta} + R_i M_beta) h_{beta+gamma}
+  m2l_con_o  the same without the per-pair fold: the source factors are formed once per
+           cell about its system's root centre, Q_{i,beta} = C_{i,beta} - z_i M_beta with
+           z = Z_cell - Z_root (con_moments_o), so U_{i,gamma} += sum_beta Q_{i,beta} h_{beta+gamma},
+           and z_tgt,i S_gamma is added once per target cell after the sum over its sources
+           (R = z_tgt - z_src makes the two forms equal in exact arithmetic)
   p2m      M_alpha += m (-y)^alpha / alpha!
   m2m      M^P_alpha += sum_{beta<=alpha} M^c_{alpha-beta} (-c)^beta / beta!
   l2l      L'_gamma += sum_beta L_{gamma+beta} s^beta / beta!
@@ -213,6 +218,42 @@ def m2l_con(p):
     return L
 
 
+def con_moments_o(p):
+    q = p - 1
+    nq = nmi(q)
+    L = ["  /* conserving source moments about the system's root centre: [M_b | (b_i+1) M_{b+e_i} - z_i M_b],",
+         "     |b| <= p-1, z = Z_cell - Z_root */",
+         "  template <class T> __device__ __forceinline__ static void con_moments_o(const T* __restrict__ M, T zx, T zy, T zz, T* __restrict__ C) {"]
+    for b in mis(q):
+        bi = idx(b)
+        L.append(f"    C[{bi}] = M[{bi}];")
+        L.append(f"    C[{nq + bi}] = fma_t(-zx, M[{bi}], T({b[0] + 1}.0) * M[{idx((b[0] + 1, b[1], b[2]))}]);")
+        L.append(f"    C[{2 * nq + bi}] = fma_t(-zy, M[{bi}], T({b[1] + 1}.0) * M[{idx((b[0], b[1] + 1, b[2]))}]);")
+        L.append(f"    C[{3 * nq + bi}] = fma_t(-zz, M[{bi}], T({b[2] + 1}.0) * M[{idx((b[0], b[1], b[2] + 1))}]);")
+    L.append("  }")
+    return L
+
+
+def m2l_con_o(p):
+    q = p - 1
+    nq = nmi(q)
+    L = ["  /* conserving M2L from the root-relative source moments of con_moments_o: S_g += sum_b Q_b h_{b+g},",
+         "     U_{i,g} += sum_b Q_{i,b} h_{b+g}; the target's z_i S_g is added once after all its sources */",
+         "  template <class T, class A> __device__ __forceinline__ static void m2l_con_o(const T* __restrict__ C, const T* __restrict__ H, A* __restrict__ SU) {"]
+    for b in mis(q):
+        bi = idx(b)
+        rem = q - sum(b)
+        L.append(f"    {{ const T m = C[{bi}], mx = C[{nq + bi}], my = C[{2 * nq + bi}], mz = C[{3 * nq + bi}];")
+        for g in mis(rem):
+            gi = idx(g)
+            hb = f"H[{idx((b[0] + g[0], b[1] + g[1], b[2] + g[2]))}]"
+            L.append(f"      SU[{gi}] = fma_t(m, {hb}, SU[{gi}]); SU[{nq + gi}] = fma_t(mx, {hb}, SU[{nq + gi}]);"
+                     f" SU[{2 * nq + gi}] = fma_t(my, {hb}, SU[{2 * nq + gi}]); SU[{3 * nq + gi}] = fma_t(mz, {hb}, SU[{3 * nq + gi}]);")
+        L.append("    }")
+    L.append("  }")
+    return L
+
+
 def m2l_con_s(p):
     """m2l_con with the conserving moments rescaled on load: the M_b block by f[|b|], the
     (b_i + 1) M_{b+e_i} blocks by f[|b| + 1]."""
@@ -376,7 +417,9 @@ def header(p):
     out += m2l_std(p)
     out += m2l_std_s(p)
     out += con_moments(p)
+    out += con_moments_o(p)
     out += m2l_con(p)
+    out += m2l_con_o(p)
     out += m2l_con_s(p)
     out += m2l_con_m(p)
     out += p2m(p)

@@ -30,6 +30,35 @@ struct Panel {
     static constexpr int SIZE = 32 * ROW;     // elements per warp panel
 };
 
+// Columns per panel for an nA x nB leaf pair.  A panel of k columns costs
+// ceil(nA k / 32) lane rounds of pair terms (about 17 arithmetic steps each), then rows
+// (ceil(NC nA / 32) rounds of k steps) and columns (ceil(NC k / 32) rounds of nA steps);
+// the width with the fewest lane rounds over all panels wins, ties to the wider panel.
+// Leaves hold ~9 particles on average, so a fixed width of 8 leaves the last pair round
+// of most panels partly idle.
+template <int NC>
+__device__ __forceinline__ int panel_cols(int nA, int nB, int cmax) {
+    constexpr int KC = 17;
+    int best = 1, bcost = 0x7fffffff;
+    for (int k = min(cmax, nB); k >= 1; k--) {
+        int full = nB / k, rem = nB - full * k;
+        int ck = ((nA * k + 31) >> 5) * KC + ((NC * nA + 31) >> 5) * k + ((NC * k + 31) >> 5) * nA;
+        int cr = rem ? ((nA * rem + 31) >> 5) * KC + ((NC * nA + 31) >> 5) * rem + ((NC * rem + 31) >> 5) * nA : 0;
+        int cost = full * ck + cr;
+        if (cost < bcost) {
+            bcost = cost;
+            best = k;
+        }
+    }
+    return best;
+}
+
+// r^2 == 0 (coincident particles) without a floating-point compare: r^2 is a sum of squares,
+// so it is +0 exactly when its bit pattern is 0 (binary64: keeps the test off the FP64 unit)
+__device__ __forceinline__ bool r2_zero(double v) { return __double_as_longlong(v) == 0ll; }
+__device__ __forceinline__ bool r2_zero(float v) { return __float_as_uint(v) == 0u; }
+__device__ __forceinline__ bool r2_zero(df64 v) { return is_zero(v); }
+
 
 template <class S>
 struct PState {
@@ -107,10 +136,15 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
             }
             if (lane < nB) sB[w][lane] = pos[fB + lane];
             cacc[w][lane] = Quad<T>{T(0), T(0), T(0), T(0)};
-            T racc[4] = {T(0), T(0), T(0), T(0)};  // row task tau = lane + 32 q: (a, comp) = (tau >> 2, tau & 3)
+            // row task tau = lane + 32 q: (a, comp) = (tau / NC, tau % NC), NC = 4 with potentials, else 3
+            constexpr int NC = POT ? 4 : 3;
+            T racc[NC] = {};
             __syncwarp();
-            for (int cb = 0; cb < nB; cb += PCOL) {
-                int ncol = min(PCOL, nB - cb);
+            // binary64: the width from the lane-round model; double-float keeps the full width
+            // (its pair terms cost several times the binary64 ones, which the model does not weigh)
+            const int pcol = std::is_same<T, double>::value ? panel_cols<NC>(nA, nB, PCOL) : PCOL;
+            for (int cb = 0; cb < nB; cb += pcol) {
+                int ncol = min(pcol, nB - cb);
                 int nint = nA * ncol;
                 float rcol = 1.0f / (float)ncol;
                 // pair terms of the panel: d = X_a - X_b (formed in the storage type), r^-1, d r^-3
@@ -124,7 +158,7 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                         T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y);
                         T dz = Prec<T>::sep(pa.z, pb.z);
                         T r2 = dx * dx + dy * dy + dz * dz;
-                        if (!is_zero(r2)) {
+                        if (!r2_zero(r2)) {
                             T ir = rsqrt_t(r2);
                             T ir3 = ir * ir * ir;
                             fx = dx * ir3;
@@ -137,25 +171,25 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     e[0] = fx;
                     e[1] = fy;
                     e[2] = fz;
-                    e[3] = fr;
+                    if (POT) e[3] = fr;
                 }
                 __syncwarp();
-                // rows: sum_b m_b F[a][b]
+                // rows: sum_b m_b F[a][b], one lane per (a, component), NC nA tasks
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
-                    if (a < nA && (POT || c < 3)) {
+                for (int q = 0; q < NC; q++) {
+                    if (32 * q >= NC * nA) break;
+                    int tau = lane + 32 * q, a = tau / NC, c = tau - a * NC;
+                    if (a < nA) {
                         const T* row = F + a * PROW + c;
                         T sum = racc[q];
                         for (int bl = 0; bl < ncol; bl++) sum = fma_t(Prec<T>::mass(sB[w][cb + bl].m), row[bl * 4], sum);
                         racc[q] = sum;
                     }
                 }
-                // columns: sum_a m_a F[a][b]
-#pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    int tau = lane + 32 * q, bl = tau >> 2, c = tau & 3;
-                    if (bl < ncol && (POT || c < 3)) {
+                // columns: sum_a m_a F[a][b], one lane per (b, component), NC ncol tasks
+                for (int tau = lane; tau < NC * ncol; tau += 32) {
+                    int bl = tau / NC, c = tau - bl * NC;
+                    {
                         const T* col = F + bl * 4 + c;
                         T sum = cac[(cb + bl) * 4 + c];
                         for (int a = 0; a < nA; a++) sum = fma_t(Prec<T>::mass(sA[w][a].m), col[a * PROW], sum);
@@ -167,12 +201,13 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
             // write: rows are a_a = -sum (and phi_a = -sum); columns a_b = +sum, phi_b = -sum
             T* pd = reinterpret_cast<T*>(part);
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                int tau = lane + 32 * q, a = tau >> 2, c = tau & 3;
+            for (int q = 0; q < NC; q++) {
+                int tau = lane + 32 * q, a = tau / NC, c = tau - a * NC;
                 if (a < nA) {
                     T v = -racc[q];
                     if (self) v = v + ((c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c]);
-                    pd[(o + a) * 4 + c] = (POT || c < 3) ? Prec<T>::fin(v) : T(0);
+                    pd[(o + a) * 4 + c] = Prec<T>::fin(v);
+                    if (!POT && c == 2) pd[(o + a) * 4 + 3] = T(0);
                 }
             }
             if (!self) {

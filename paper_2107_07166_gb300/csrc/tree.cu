@@ -11,6 +11,9 @@
 //          children's sums in child order; Z = (sum m X) / M
 //   r_max: sqrt of the maximum over the node's particles of (dx*dx + dy*dy) + dz*dz
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
@@ -216,6 +219,91 @@ __global__ void split_emit_k(const uint64_t* __restrict__ keys, int lo, int m, i
     }
 }
 
+// The octree level by level without host round trips.  One launch per level fuses the
+// child count, its prefix over the level and the emission of the children: blocks take
+// tiles of LV_NODES consecutive nodes in ticket order, the node's 8 lanes find its octant
+// bounds (octant_of), a block scan places the children inside the tile, and the tile's
+// place among the level's children comes from a decoupled look-back over the tiles
+// before it.  The level's bounds live in device memory (LevelCtl::start); the last tile
+// of level L writes start[L + 2], so the host launches all MAX_LEVEL levels back to back
+// and reads the table once.  Children beyond the node capacity are counted but not
+// stored (the host grows the arrays and builds the levels again).
+constexpr int LV_NODES = TB / 8;
+constexpr long long LEVEL_SPIN_LIMIT = 1ll << 22;  // polls of one status word (~0.1-1 s)
+
+struct LevelCtl {
+    int start[MAX_LEVEL + 2];  // first node id of level L; start[L + 1] - start[L] nodes at level L
+    int ticket[MAX_LEVEL];     // tile tickets of level L's launch
+    int overflow;              // a level did not fit the node arrays
+    int err;                   // a look-back wait ran out
+};
+
+__global__ void __launch_bounds__(TB) split_level_k(const uint64_t* __restrict__ keys, int level, int leaf,
+                                                    int cap_nodes, LevelCtl* __restrict__ ctl,
+                                                    unsigned long long* __restrict__ status,
+                                                    int* __restrict__ nfirst, int* __restrict__ ncount,
+                                                    int* __restrict__ nlevel, int* __restrict__ nparent,
+                                                    int* __restrict__ nchildf, int* __restrict__ nnchild) {
+    __shared__ int s_tile, s_base;
+    if (ctl->err || ctl->overflow) return;
+    int lo = ctl->start[level], hi = ctl->start[level + 1];
+    int m = hi - lo;
+    if (m <= 0) {  // below the deepest level: pass the (empty) bound on
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->start[level + 2] = hi;
+        return;
+    }
+    if (hi > cap_nodes) {  // the level's nodes were not stored
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctl->overflow, 1);
+        return;
+    }
+    int ntiles = (m + LV_NODES - 1) / LV_NODES;
+    const unsigned tag_agg = 2u * (unsigned)level + 1u, tag_pre = 2u * (unsigned)level + 2u;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->ticket[level], 1);
+        __syncthreads();
+        int tile = s_tile;
+        if (tile >= ntiles) break;
+        int t = tile * LV_NODES + (threadIdx.x >> 3), o = threadIdx.x & 7;
+        bool in = t < m;  // groups of 8 lanes are whole: all in or all out
+        int nd = lo + t;
+        int f = in ? nfirst[nd] : 0, cn = in ? ncount[nd] : 0;
+        Octant q = octant_of(keys, in, f, cn, level, leaf, o);
+        int cnt = __popc(q.grp);
+        int tot;
+        int ex = block_exclusive_scan((in && o == 0) ? cnt : 0, &tot);
+        int pos = __shfl_sync(FULL, ex, (threadIdx.x & 31) & ~7);  // the node's offset in the tile
+        if (threadIdx.x < 32) {
+            // publish the tile's count before looking back (tiles behind it need not wait
+            // for its prefix), then its inclusive prefix; one thread writes both, in order
+            if (threadIdx.x == 0 && tile > 0) st_status(status + tile, tag_agg, tot);
+            int pre = lookback_prefix(status, tile, tag_agg, tag_pre, LEVEL_SPIN_LIMIT, &ctl->err);
+            if (threadIdx.x == 0) {
+                st_status(status + tile, tag_pre, pre + tot);
+                if (tile == ntiles - 1) ctl->start[level + 2] = hi + pre + tot;
+                s_base = hi + pre;
+            }
+        }
+        __syncthreads();
+        if (in && q.grp != 0u) {
+            int base = s_base + pos;
+            if (o == 0) {
+                nchildf[nd] = base;
+                nnchild[nd] = cnt;
+            }
+            int id = base + __popc(q.grp & ((1u << o) - 1u));
+            if (((q.grp >> o) & 1u) && id < cap_nodes) {
+                nfirst[id] = q.b;
+                ncount[id] = q.next - q.b;
+                nlevel[id] = level + 1;
+                nparent[id] = nd;
+                nchildf[id] = -1;
+                nnchild[id] = 0;
+            }
+        }
+        __syncthreads();  // s_tile and s_base are reused by the next tile
+    }
+}
+
 // leaf of every particle
 __global__ void leaf_of_k(int nn, const int* __restrict__ nfirst, const int* __restrict__ ncount,
                           const int* __restrict__ nnchild, int* __restrict__ leaf_of) {
@@ -282,8 +370,8 @@ __global__ void com_inner_k(int lo, int hi, const int* __restrict__ nfirst, cons
 
 // ------------------------------------------------------------------ r_max
 
-// Every node's centre as double-float words: zh = (hi(Z), 0), zl = (lo(Z), 0); rmax_k fills
-// zh.w with r_max rounded up.  The walk's binary32 acceptance prefilter, the binary32 M2L
+// Every node's centre as double-float words: zh = (hi(Z), 0), zl = (lo(Z), max_i |hi(Z_i)|);
+// rmax_k fills zh.w with r_max rounded up.  The walk's binary32 acceptance prefilter, the binary32 M2L
 // separations and the r_max prefilter below read these.
 __global__ void centre_words_k(int nn, const double* __restrict__ Zx, const double* __restrict__ Zy,
                                const double* __restrict__ Zz, float4* __restrict__ zh, float4* __restrict__ zl) {
@@ -297,7 +385,7 @@ __global__ void centre_words_k(int nn, const double* __restrict__ Zx, const doub
         l[i] = (float)(z[i] - (double)h[i]);
     }
     zh[nd] = make_float4(h[0], h[1], h[2], 0.f);
-    zl[nd] = make_float4(l[0], l[1], l[2], 0.f);
+    zl[nd] = make_float4(l[0], l[1], l[2], fmaxf(fmaxf(fabsf(h[0]), fabsf(h[1])), fabsf(h[2])));
 }
 
 // r_max^2 = max over the node's particles of |X - Z|^2 for every node, exact in binary64
@@ -567,10 +655,8 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
         bbox_sys_k<<<nsys, TB, 0, s>>>(x, m, off, geom, c->errflag.as<int>());
         GB_LAUNCH("bbox_sys_k");
     }
-    int bad = 0;
-    GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    if (bad) return FMM_ERR_INVALID;
+    // (the input check is read with the level table below: every step of the build is
+    // index-safe on any values, so invalid input costs one build and returns FMM_ERR_INVALID)
     // a2: keys; a3: sort
     ensure(c->keys0, sizeof(uint64_t) * (size_t)n);
     ensure(c->vals0, sizeof(uint32_t) * (size_t)n);
@@ -610,39 +696,55 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     // a4: octree, level by level (breadth-first ids)
     const uint64_t* keys = c->keys0.as<uint64_t>();
     ensure_nodes(c, (int64_t)n / 4 + 64);
-    size_t lev_max = (size_t)(n > nsys ? n : nsys);  // nodes of one level: the roots, or at most n
-    ensure(c->flags, sizeof(int) * lev_max);
-    ensure(c->scan_out, sizeof(int) * (lev_max + 1));
     ensure(c->leaf_of, sizeof(int) * (size_t)n);
     ensure_nodes(c, (int64_t)nsys + 64);
     roots_k<<<grid_for(nsys, TB), TB, 0, s>>>(off, nsys, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
                                               c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
     GB_LAUNCH("roots_k");
+    // levels 1 .. MAX_LEVEL: one launch each, bounds and counts on the device, one read of
+    // the level table (and of the input check) at the end; a tree that outgrows the node
+    // arrays is built again with arrays of the size it reported
+    int dev_sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
+    ensure(c->lvl_ctl, sizeof(LevelCtl));
+    LevelCtl* ctl = c->lvl_ctl.as<LevelCtl>();
+    LevelCtl h;
+    int bad = 0;
+    int64_t n_nodes = nsys;
+    for (int attempt = 0;; attempt++) {
+        int cap = (int)std::min<int64_t>(c->cap_nodes, INT32_MAX);
+        size_t nstat = (size_t)cap / LV_NODES + 2;
+        ensure(c->lvl_status, sizeof(unsigned long long) * nstat);
+        memset(&h, 0, sizeof(h));
+        h.start[1] = nsys;
+        GB_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(LevelCtl), cudaMemcpyHostToDevice, s));
+        GB_CUDA(cudaMemsetAsync(c->lvl_status.p, 0, sizeof(unsigned long long) * nstat, s));
+        for (int level = 0; level < MAX_LEVEL; level++) {
+            split_level_k<<<dev_sms * 4, TB, 0, s>>>(keys, level, c->leaf, cap, ctl, c->lvl_status.as<unsigned long long>(),
+                                                    c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
+                                                    c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
+            GB_LAUNCH("split_level_k");
+        }
+        GB_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        if (bad) return FMM_ERR_INVALID;
+        if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "octree: a level tile waited too long for the tiles before it"};
+        if (!h.overflow) break;
+        // the levels that were built report their sizes: grow past the last one and retry
+        int64_t known = nsys;
+        for (int L = 1; L <= MAX_LEVEL + 1 && h.start[L] >= h.start[L - 1]; L++) known = std::max<int64_t>(known, h.start[L]);
+        if (attempt >= 8) throw FmmError{FMM_ERR_CAPACITY, "octree: node arrays still too small after 8 retries"};
+        ensure_nodes(c, std::max<int64_t>(2 * c->cap_nodes, known + known / 2));
+        roots_k<<<grid_for(nsys, TB), TB, 0, s>>>(off, nsys, c->nfirst.as<int>(), c->ncount.as<int>(),
+                                                  c->nlevel.as<int>(), c->nparent.as<int>(), c->nchildf.as<int>(),
+                                                  c->nnchild.as<int>());
+        GB_LAUNCH("roots_k");
+    }
     c->level_start.assign(1, 0);
     c->level_start.push_back(nsys);
-    int64_t n_nodes = nsys;
-    // below the roots the nodes of a level are disjoint and non-empty: at most n of them
-    for (int level = 0; level < MAX_LEVEL; level++) {
-        int lo = c->level_start[level];
-        int m = c->level_start[level + 1] - lo;
-        split_count_k<<<grid_for(8 * (int64_t)m, TB), TB, 0, s>>>(keys, lo, m, level, c->leaf, c->nfirst.as<int>(),
-                                                     c->ncount.as<int>(), c->flags.as<int>());
-        GB_LAUNCH("split_count_k");
-        scan_int(c, c->flags.as<int>(), m, c->scan_out.as<int>());
-        int total = 0;
-        GB_CUDA(cudaMemcpyAsync(&total, c->scan_out.as<int>() + m, sizeof(int), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaStreamSynchronize(s));
-        if (total == 0) break;
-        ensure_nodes(c, n_nodes + total);
-        split_emit_k<<<grid_for(8 * (int64_t)m, TB), TB, 0, s>>>(keys, lo, m, level, c->leaf, (int)n_nodes,
-                                                                 c->scan_out.as<int>(),
-                                                    c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
-                                                    c->nparent.as<int>(), c->nchildf.as<int>(),
-                                                    c->nnchild.as<int>());
-        GB_LAUNCH("split_emit_k");
-        n_nodes += total;
-        c->level_start.push_back((int)n_nodes);
-    }
+    for (int L = 2; L <= MAX_LEVEL + 1 && h.start[L] > h.start[L - 1]; L++) c->level_start.push_back(h.start[L]);
+    n_nodes = c->level_start.back();
     leaf_of_k<<<grid_for(n_nodes, TB), TB, 0, s>>>((int)n_nodes, c->nfirst.as<int>(), c->ncount.as<int>(),
                                                    c->nnchild.as<int>(), c->leaf_of.as<int>());
     GB_LAUNCH("leaf_of_k");

@@ -105,15 +105,6 @@ struct WalkCounters {
 // step index, so the status words are cleared once per walk.
 constexpr int WIPT = 4, WTILE = WB * WIPT;
 
-__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_status(unsigned long long* p, unsigned tag, int value) {
-    unsigned long long v = ((unsigned long long)tag << 32) | (unsigned)value;
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 __global__ void __launch_bounds__(WB, 6) walk_step_k(const int2* __restrict__ fr_in, int2* __restrict__ fr_out,
                                                   WalkCounters* __restrict__ cnt, int par, int step,

@@ -588,6 +588,17 @@ def test_walk_decisions_follow_the_rule(orc, case):
     _check_trace(r, theta)
 
 
+def test_walk_counts_match_the_full_run(orc):
+    """oracle.counts (tree and walk only, used to extrapolate the oracle's time to sizes it
+    is not run at) gives the node, pair and particle-pair counts of the full evaluation."""
+    x, m = synth.hernquist(5000, 21)
+    r = orc.run(x, m, 12, 2, 0.55, 1, want_pot=False)
+    c = r.tree["count"].astype(np.int64)
+    P = r.p2p
+    npp = int(np.where(P[:, 0] == P[:, 1], c[P[:, 0]] * (c[P[:, 0]] - 1) // 2, c[P[:, 0]] * c[P[:, 1]]).sum())
+    assert orc.counts(x, m, 12, 0.55) == (r.n_nodes, r.n_m2l, r.n_p2p, npp)
+
+
 def test_geometry_matches_definition(orc):
     x, m = synth.hernquist(2000, 6)
     r = orc.run(x, m, 12, 2, 0.5, 0)
