@@ -445,6 +445,41 @@ def run_gbfmm(args):
                        err_ratio_conserving_p_plus_1_over_standard_p=(s1["force_err_vs_direct_sampled"]
                                                                       / s0["force_err_vs_direct_sampled"]))
 
+    # the fused schedule (no interaction lists; binary64) on the same input and variant
+    schedules = None
+    if args.modes and world == 1 and prec == fmm.FP64 and W["p"] <= 6:
+        out = torch.empty_like(acc)
+        f.set_schedule(fmm.SCHEDULE_FUSED)
+
+        def sf():
+            if offsets is not None:
+                f.build_batch(xd, md, offsets, W["leaf"])
+            else:
+                f.build(xd, md, W["leaf"])
+            f.forces(W["p"], W["theta"], variant, out, None)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                sf()
+        stream.synchronize()
+        ts_ = []
+        for _ in range(max(3, min(args.steps, 5))):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sf()
+            e1.record(stream)
+            e1.synchronize()
+            ts_.append(e0.elapsed_time(e1))
+        o = out.cpu().numpy()
+        schedules = {"fused": {"ms_per_step": statistics.mean(ts_), "value": N / (statistics.mean(ts_) / 1e3),
+                               "force_err_vs_list_schedule": float(np.linalg.norm(o - a) / np.linalg.norm(a)),
+                               "stage_ms": {k: round(v, 4) for k, v in f.stage_times().items()}}}
+        f.set_schedule(fmm.SCHEDULE_LISTS)
+
     # the other arithmetic modes of the pair kernels on the same input (same timing method)
     modes = {}
     if args.modes and world == 1 and args.workload == "plummer1m" and not args.n:
@@ -571,6 +606,7 @@ def run_gbfmm(args):
         "roofline_stages": roofline_stages,
         "roofline_build": roofline_build,
         "accuracy_matched": matched,
+        "schedules": schedules,
         "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,

@@ -69,6 +69,14 @@ enum {
                       words, ~48-bit significand): binary64-level results at the binary32 issue rate */
 };
 
+/* schedules of the interaction stage (fmm_set_schedule) */
+enum {
+    FMM_SCHEDULE_LISTS = 0, /* the mutual walk stores its M2L and P2P pairs once, sorted by target, and
+                               the pair kernels evaluate them (each P2P pair force formed once) */
+    FMM_SCHEDULE_FUSED = 1  /* no lists: every target node walks the same recursion restricted to its
+                               own pairs and evaluates them as it finds them (binary64 only) */
+};
+
 /* status codes */
 enum {
     FMM_OK = 0,
@@ -187,6 +195,18 @@ GBFMM_API int fmm_autotune(fmm_ctx *c, const double *x, const double *m, int64_t
 
 /* Number of walks this context has re-run after a buffer overflow. */
 GBFMM_API int fmm_walk_retries(fmm_ctx *c, int64_t *retries);
+
+/* Schedule of the interactions of later fmm_forces calls (FMM_SCHEDULE_LISTS, the default,
+ * or FMM_SCHEDULE_FUSED).  Both evaluate exactly the pairs of the mutual walk of Sec. 2
+ * (eq. mac_criterion); results differ only in summation order.  The fused schedule keeps no
+ * interaction list: every target node runs the walk's recursion restricted to the pairs
+ * that contain one of its ancestors, evaluates its M2L sources and P2P partners as it finds
+ * them and writes each result once (no list sort, no partial buffers, no gather).  It forms
+ * every particle-pair force from both sides, so it does about 1.5x the binary64 P2P work of
+ * the list schedule.  It runs in FMM_FP64 for p <= 6 and the FMM_STANDARD and FMM_CONSERVING
+ * variants; other combinations return FMM_ERR_INVALID from fmm_forces.  fmm_get_lists needs
+ * the list schedule.  Invalidates cached lists. */
+GBFMM_API int fmm_set_schedule(fmm_ctx *c, int schedule);
 
 /* Limit of the walk's only device-side wait, for tests of its failure path.  Each walk
  * step places its outputs after those of the tiles before it (eq. mac_criterion decides

@@ -135,7 +135,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
                           &c->momT, &c->nk, &c->zhl, &c->m2l_kpart, &c->p2p_sep, &c->p2p_cls, &c->p2p_cls2, &c->p2p_list, &c->p2p_list2, &c->p2p_tab, &c->m2m_tmp,
                           &c->lf_x, &c->lf_v,
-                          &c->lf_m, &c->lf_a, &c->lf_diag, &c->tune_acc, &c->lvl_ctl, &c->lvl_status, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
+                          &c->lf_m, &c->lf_a, &c->lf_diag, &c->tune_acc, &c->lvl_ctl, &c->lvl_status, &c->p2p_direct, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -251,6 +251,9 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
     if (variant == FMM_CONSERVING_PAPER0 && p != 1)
         return fail(FMM_ERR_INVALID, "fmm_forces: FMM_CONSERVING_PAPER0 needs p = 1");
     if (!acc) return fail(FMM_ERR_INVALID, "fmm_forces: acc is required");
+    if (c->schedule == FMM_SCHEDULE_FUSED &&
+        (c->precision != FMM_FP64 || p > 6 || variant == FMM_CONSERVING_PAPER0))
+        return fail(FMM_ERR_INVALID, "fmm_forces: the fused schedule runs FMM_FP64, p <= 6, standard or conserving");
     // the literal order-0 form reads the second moments (eq. aaB0): expansion order 2
     if (variant == FMM_CONSERVING_PAPER0) p = 2;
     return guarded(c, [&]() -> int {
@@ -263,13 +266,25 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
             stage_end(c, ST_MOMENTS);
             c->mom_p = p;
         }
-        if (c->list_theta != theta) {
+        bool fused = c->schedule == FMM_SCHEDULE_FUSED;
+        if (fused) {
+            // no walk and no lists: every target node traverses for its own pairs
+            c->list_theta = -1.0;
+            c->fused_theta = theta;
+            GB_CUDA(cudaMemsetAsync(c->errflag.as<int>() + 2, 0, sizeof(int), c->stream));
+        } else if (c->list_theta != theta) {
             stage_begin(c, ST_WALK);
             run_walk(c, theta);
             stage_end(c, ST_WALK);
         }
         run_far_field_dispatch(c, p, variant, want_pot);
-        run_p2p(c, want_pot);
+        if (fused) {
+            stage_begin(c, ST_P2P);
+            run_p2p_fused(c, want_pot, theta);
+            stage_end(c, ST_P2P);
+        } else {
+            run_p2p(c, want_pot);
+        }
         ensure(c->acc_s, sizeof(double) * 3 * n);
         ensure(c->pot_s, sizeof(double) * n);
         bool acc_dev = is_device_ptr(acc);
@@ -278,9 +293,15 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
         double* acc_d = acc_dev ? acc : c->out_stage.as<double>();
         double* pot_d = want_pot ? (pot_dev ? pot : c->out_stage.as<double>() + 3 * n) : nullptr;
         stage_begin(c, ST_L2P);
-        run_p2p_gather(c);
+        if (!fused) run_p2p_gather(c);
         run_finish_dispatch(c, p, variant, want_pot, acc_d, pot_d);
         stage_end(c, ST_L2P);
+        if (fused) {  // a traversal stack that would have overflowed (none is expected)
+            int over = 0;
+            GB_CUDA(cudaMemcpyAsync(&over, c->errflag.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            GB_CUDA(cudaStreamSynchronize(c->stream));
+            if (over) throw FmmError{FMM_ERR_CAPACITY, "fused schedule: traversal stack exceeded"};
+        }
         if (!acc_dev)
             GB_CUDA(cudaMemcpyAsync(acc, acc_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
         if (want_pot && !pot_dev)
@@ -551,6 +572,15 @@ int fmm_autotune(fmm_ctx* c, const double* x, const double* m, int64_t N, const 
 int fmm_walk_retries(fmm_ctx* c, int64_t* retries) {
     if (!c || !retries) return fail(FMM_ERR_INVALID, "fmm_walk_retries: NULL argument");
     *retries = c->walk_retries;
+    return FMM_OK;
+}
+
+int fmm_set_schedule(fmm_ctx* c, int schedule) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_schedule: NULL context");
+    if (schedule != FMM_SCHEDULE_LISTS && schedule != FMM_SCHEDULE_FUSED)
+        return fail(FMM_ERR_INVALID, "fmm_set_schedule: unknown schedule");
+    c->schedule = schedule;
+    c->list_theta = -1.0;
     return FMM_OK;
 }
 

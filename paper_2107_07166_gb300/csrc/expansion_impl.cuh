@@ -34,6 +34,7 @@
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
+#include "fused_traverse.cuh"
 #include "prec.cuh"
 
 namespace gbfmm {
@@ -91,15 +92,21 @@ __device__ __forceinline__ float dsep(float ah, float al, float bh, float bl) {
 // |R|_inf = 2^-20 max(|Z_a|, |Z_b|) that is more than 2^-27 of R, and R is formed again
 // from the binary64 centres (rounded once to binary32).  Only cells that nearly coincide
 // take this branch.
-// (al.w and bl.w hold max_i |hi(Z_i)| of the two centres.)
+// (al.w and bl.w hold max_i |hi(Z_i)| of the two centres.)  The binary64 path is a call
+// that is not inlined, so that its loads are not hoisted into every entry.
+static __device__ __noinline__ float3 close_sep_slow(const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                              const double* __restrict__ Zz, int t, int s) {
+    return make_float3((float)(Zx[t] - Zx[s]), (float)(Zy[t] - Zy[s]), (float)(Zz[t] - Zz[s]));
+}
 __device__ __forceinline__ void close_sep_fix(float4 al, float4 bl, const double* __restrict__ Zx,
                                               const double* __restrict__ Zy, const double* __restrict__ Zz, int t,
                                               int s, float& rx, float& ry, float& rz) {
     float r = fmaxf(fabsf(rx), fmaxf(fabsf(ry), fabsf(rz)));
     if (r < 0x1p-20f * fmaxf(al.w, bl.w)) {
-        rx = (float)(Zx[t] - Zx[s]);
-        ry = (float)(Zy[t] - Zy[s]);
-        rz = (float)(Zz[t] - Zz[s]);
+        float3 v = close_sep_slow(Zx, Zy, Zz, t, s);
+        rx = v.x;
+        ry = v.y;
+        rz = v.z;
     }
 }
 
@@ -847,6 +854,7 @@ __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ le
                                                const long long* __restrict__ fo,
                                                const long long* __restrict__ po, long long nfull,
                                                const long long* __restrict__ islot, const Quad<G>* __restrict__ ipart,
+                                               const Quad<double>* __restrict__ pdirect,
                                                const uint32_t* __restrict__ perm, double* __restrict__ acc_s,
                                                double* __restrict__ pot_s, double* __restrict__ acc_out,
                                                double* __restrict__ pot_out) {
@@ -902,14 +910,21 @@ __global__ void __launch_bounds__(EB) finish_k(int n, const int* __restrict__ le
         }
     }
     double px = 0.0, py = 0.0, pz = 0.0, pp = 0.0;
-    for (long long k = fo[lf]; k < fo[lf + 1]; k++) {
+    if (pdirect) {  // the fused schedule's per-particle sums
+        Quad<double> q = pdirect[i];
+        px = q.x;
+        py = q.y;
+        pz = q.z;
+        pp = q.w;
+    }
+    for (long long k = pdirect ? 0 : fo[lf]; k < (pdirect ? 0 : fo[lf + 1]); k++) {
         Quad<G> q = ipart[islot[k] + slot];
         px += as_double(q.x);
         py += as_double(q.y);
         pz += as_double(q.z);
         pp += as_double(q.w);
     }
-    if (po[lf + 1] > po[lf]) {
+    if (!pdirect && po[lf + 1] > po[lf]) {
         Quad<G> q = ipart[islot[nfull + po[lf]] + slot];
         px += as_double(q.x);
         py += as_double(q.y);
@@ -1062,6 +1077,24 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
             reduce(m2l_reduce_k<E::NSU, E::NQ, 1, T>, E::NSU, c->loc.as<double>());
         }
     }
+    if constexpr (std::is_same<T, double>::value && P <= 6) {
+        if (c->schedule == FMM_SCHEDULE_FUSED) {  // no lists: one traversal per target node
+            if (variant == 1) {
+                ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
+                fused_m2l_launch<P>(c, 1, c->fused_theta, c->loc.as<double>());
+                con_origin_k<E::NQ><<<grid_for((int64_t)nn * 3 * E::NQ, EB), EB, 0, s>>>(
+                    nn, c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->nfirst.as<int>(),
+                    c->sys_off.as<long long>(), c->n_sys, c->loc.as<double>());
+                GB_LAUNCH("con_origin_k");
+            }
+            if (std_locals) {
+                DevBuf& L = variant == 0 ? c->loc : c->locp;
+                ensure(L, sizeof(double) * (size_t)nn * E::NM);
+                fused_m2l_launch<P>(c, 0, c->fused_theta, L.as<double>());
+            }
+            return;
+        }
+    }
     if (variant == 1) {
         ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
         if (ni > 0) {
@@ -1182,7 +1215,9 @@ static void finish_launch(fmm_ctx* c, int variant, bool want_pot, double* acc_ou
             c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(), c->nrmax.as<double>(), c->nk.as<int>(),
             c->loc.as<double>(), pot_con ? c->locp.as<double>() : nullptr, locX, locpX,
             it.fo.as<long long>(), it.po.as<long long>(), it.n_full, c->p2p_islot.as<long long>(),
-            c->p2p_ipart.as<Quad<G>>(), c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
+            c->p2p_ipart.as<Quad<G>>(),
+            c->schedule == FMM_SCHEDULE_FUSED ? c->p2p_direct.as<Quad<double>>() : nullptr,
+            c->perm.as<uint32_t>(), c->acc_s.as<double>(), c->pot_s.as<double>(), acc_out,
             want_pot ? pot_out : nullptr);
     };
     if (variant == 0)

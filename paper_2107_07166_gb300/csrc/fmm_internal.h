@@ -124,6 +124,9 @@ struct fmm_ctx {
     int64_t walk_retries = 0;                  // walks re-run after a buffer overflow
     long long walk_spin_limit = gbfmm::WALK_SPIN_LIMIT;  // polls per look-back wait (fmm_set_wait_limit)
     bool walk_wait_never = false;              // test of the timeout path: no wait is ever satisfied
+    int schedule = FMM_SCHEDULE_LISTS;         // fmm_set_schedule
+    double fused_theta = 0.0;                  // theta of the running fused evaluation
+    gbfmm::DevBuf p2p_direct;                  // fused schedule: per-particle P2P sums (Quad<double>)
     gbfmm::DevBuf m2l_pairs, p2p_pairs;        // int2, walk order
     gbfmm::DevBuf m2l_dir;                     // uint32 source ids, per-target segments in list order
     gbfmm::DevBuf m2l_dirp;                    // uint32 (pair << 1 | side) of the same entries
@@ -202,6 +205,8 @@ void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
 
 // particle-particle + final reduction (p2p.cu)
 void run_p2p(fmm_ctx* c, bool want_pot);
+// the fused schedule's near field: per-particle P2P sums into c->p2p_direct (p2p.cu)
+void run_p2p_fused(fmm_ctx* c, bool want_pot, double theta);
 void run_p2p_gather(fmm_ctx* c);
 
 // high-order (p = 7, 8) binary64 M2L into the item partials and L2L of one level

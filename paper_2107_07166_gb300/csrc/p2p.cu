@@ -15,6 +15,7 @@
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 #include "fmm_math.cuh"
+#include "fused_traverse.cuh"
 #include "prec.cuh"
 
 namespace gbfmm {
@@ -112,7 +113,12 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                                             const typename Prec<T>::S* __restrict__ sep,
                                             Quad<T>* __restrict__ part) {
     using S = typename Prec<T>::S;
-    constexpr int PCOL = Panel<T>::COLS, PROW = Panel<T>::ROW, PANEL = Panel<T>::SIZE;
+    // panel row stride in elements: with 8-byte elements a warp's row reads (lane = (row a,
+    // component c)) need 2 wavefronts at best; a stride of 4 mod 16 does that for 4
+    // components per row task, 3 mod 16 for 3 (the stride 36 with 3-component tasks put
+    // rows a and a + 4 on the same banks: 3 wavefronts per read)
+    constexpr int PCOL = Panel<T>::COLS, PANEL = Panel<T>::SIZE;
+    constexpr int PROW = (sizeof(T) == 8 && !POT) ? PCOL * 4 + 3 : Panel<T>::ROW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PState<S> sA[PW][32], sB[PW][32];
     __shared__ Quad<T> cacc[PW][32];
@@ -588,6 +594,26 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     stage_end(c, ST_P2P);
 }
 
+void fused_p2p_launch(fmm_ctx* c, bool want_pot, double theta, Quad<double>* out);
+
+// the fused schedule's near field (binary64): pack the leaf-relative positions, then one
+// traversal per target leaf writes the leaf's per-particle P2P sums to p2p_direct
+void run_p2p_fused(fmm_ctx* c, bool want_pot, double theta) {
+    cudaStream_t s = c->stream;
+    int n = (int)c->N;
+    if (!c->pos_valid) {
+        ensure(c->pos4, sizeof(PState<double>) * (size_t)n);
+        pack_pos_k<double><<<grid_for(n, PB), PB, 0, s>>>(n, c->leaf_of.as<int>(), c->xs.as<double>(),
+                                                        c->ys.as<double>(), c->zs.as<double>(), c->ms.as<double>(),
+                                                        c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
+                                                        c->pos4.as<PState<double>>());
+        GB_LAUNCH("pack_pos_k");
+        c->pos_valid = true;
+    }
+    ensure(c->p2p_direct, sizeof(Quad<double>) * (size_t)n);
+    fused_p2p_launch(c, want_pot, theta, c->p2p_direct.as<Quad<double>>());
+}
+
 void run_p2p(fmm_ctx* c, bool want_pot) {
     if (c->precision == FMM_FP64)
         p2p_launch<double>(c, want_pot);
@@ -848,6 +874,163 @@ void run_diagnostics(fmm_ctx* c, double* out6) {
     GB_LAUNCH("diag_final_k");
     GB_CUDA(cudaMemcpyAsync(out6, part + 6 * nb, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+}
+
+// ================================================================ fused schedule
+// Near field of the fused schedule (fused_traverse.cuh): P2P evaluated from every target
+// leaf's own traversal, with no P2P list, partial buffer or gather (binary64).
+
+// ---------------------------------------------------------------- near field
+
+template <bool POT>
+struct NearVisitor {
+    const NodeView* nv;
+    const PState<double>* pos;
+    int T, fT, nT, a, grp, ngrp;
+    bool live;
+    double ax, ay, az, ph;
+
+    __device__ void m2l(int) {}
+    __device__ void p2p(int Y) {
+        if (!live) return;
+        bool self = Y == T;
+        int fY = nv->first[Y], nY = nv->count[Y];
+        // T's particle with its side of R = Z_T - Z_Y, as the list schedule's panel forms it
+        double rx = nv->Zx[T] - nv->Zx[Y], ry = nv->Zy[T] - nv->Zy[Y], rz = nv->Zz[T] - nv->Zz[Y];
+        PState<double> pa = pos[fT + a];
+        double xa = rx + pa.x, ya = ry + pa.y, za = rz + pa.z;
+        for (int b = grp; b < nY; b += ngrp) {
+            if (self && b == a) continue;
+            PState<double> pb = pos[fY + b];
+            double dx = xa - pb.x, dy = ya - pb.y, dz = za - pb.z;
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (__double_as_longlong(r2) != 0ll) {
+                double ir = rsqrt(r2);
+                double mir3 = pb.m * (ir * ir * ir);
+                ax = fma(-mir3, dx, ax);
+                ay = fma(-mir3, dy, ay);
+                az = fma(-mir3, dz, az);
+                if (POT) ph = fma(-pb.m, ir, ph);
+            }
+        }
+    }
+};
+
+// a12 without lists: one warp per target leaf of at most 32 particles.  Lane l takes
+// particle a = l mod nT and group g = l / nT of G = floor(32 / nT) groups; group g meets the
+// partner's particles g, g + G, ...; at the end lane a adds its groups' sums in group
+// order.  Leaves above 32 particles (only at the deepest level, from coincident keys) run
+// in fused_p2p_big_k.
+template <bool POT>
+__global__ void __launch_bounds__(FB) fused_p2p_k(int nn, NodeView nv, double theta, float th2,
+                                                  const PState<double>* __restrict__ pos,
+                                                  Quad<double>* __restrict__ out, int* __restrict__ err) {
+    __shared__ int2 stk[FW][FSTACK];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int T = blockIdx.x * FW + w; T < nn; T += gridDim.x * FW) {
+        if (nv.nchild[T] != 0) continue;  // warp-uniform
+        int nT = nv.count[T];
+        if (nT > 32) continue;
+        NearVisitor<POT> vis;
+        vis.nv = &nv;
+        vis.pos = pos;
+        vis.T = T;
+        vis.fT = nv.first[T];
+        vis.nT = nT;
+        vis.ngrp = 32 / nT;
+        vis.a = lane % nT;
+        vis.grp = lane / nT;
+        vis.live = vis.grp < vis.ngrp;
+        vis.ax = vis.ay = vis.az = vis.ph = 0.0;
+        traverse(nv, T, theta, th2, stk[w], err, vis);
+        double s[4] = {vis.ax, vis.ay, vis.az, vis.ph};
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int g = 0; g < vis.ngrp; g++) {
+#pragma unroll
+            for (int cc = 0; cc < 4; cc++) tot[cc] += __shfl_sync(FULL, s[cc], (g * nT + vis.a) & 31);
+        }
+        if (lane < nT) out[vis.fT + lane] = Quad<double>{tot[0], tot[1], tot[2], POT ? tot[3] : 0.0};
+        __syncwarp();
+    }
+}
+
+// leaves above 32 particles: one warp per leaf, 32 particles per pass, partners in the
+// traversal's order (these leaves are rare: coincident particles at the deepest level)
+template <bool POT>
+struct BigVisitor {
+    const NodeView* nv;
+    const PState<double>* pos;
+    int T, fT, a;
+    double ax, ay, az, ph;
+    __device__ void m2l(int) {}
+    __device__ void p2p(int Y) {
+        bool self = Y == T;
+        int fY = nv->first[Y], nY = nv->count[Y];
+        double rx = nv->Zx[T] - nv->Zx[Y], ry = nv->Zy[T] - nv->Zy[Y], rz = nv->Zz[T] - nv->Zz[Y];
+        PState<double> pa = pos[fT + a];
+        double xa = rx + pa.x, ya = ry + pa.y, za = rz + pa.z;
+        for (int b = 0; b < nY; b++) {
+            if (self && b == a) continue;
+            PState<double> pb = pos[fY + b];
+            double dx = xa - pb.x, dy = ya - pb.y, dz = za - pb.z;
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (__double_as_longlong(r2) != 0ll) {
+                double ir = rsqrt(r2);
+                double mir3 = pb.m * (ir * ir * ir);
+                ax = fma(-mir3, dx, ax);
+                ay = fma(-mir3, dy, ay);
+                az = fma(-mir3, dz, az);
+                if (POT) ph = fma(-pb.m, ir, ph);
+            }
+        }
+    }
+};
+
+template <bool POT>
+__global__ void __launch_bounds__(FB) fused_p2p_big_k(int nn, NodeView nv, double theta, float th2,
+                                                      const PState<double>* __restrict__ pos,
+                                                      Quad<double>* __restrict__ out, int* __restrict__ err) {
+    __shared__ int2 stk[FW][FSTACK];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int T = blockIdx.x * FW + w; T < nn; T += gridDim.x * FW) {
+        if (nv.nchild[T] != 0 || nv.count[T] <= 32) continue;  // warp-uniform
+        int nT = nv.count[T], fT = nv.first[T];
+        for (int a0 = 0; a0 < nT; a0 += 32) {
+            BigVisitor<POT> vis;
+            vis.nv = &nv;
+            vis.pos = pos;
+            vis.T = T;
+            vis.fT = fT;
+            vis.a = min(a0 + lane, nT - 1);  // lanes past the end repeat the last particle (not stored)
+            vis.ax = vis.ay = vis.az = vis.ph = 0.0;
+            traverse(nv, T, theta, th2, stk[w], err, vis);
+            if (a0 + lane < nT) out[fT + a0 + lane] = Quad<double>{vis.ax, vis.ay, vis.az, POT ? vis.ph : 0.0};
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+void fused_p2p_launch(fmm_ctx* c, bool want_pot, double theta, Quad<double>* out) {
+    NodeView nv = node_view(c);
+    float th2 = (float)theta * (float)theta;
+    int nn = (int)c->n_nodes;
+    int* err = c->errflag.as<int>() + 2;
+    const PState<double>* pos = c->pos4.as<PState<double>>();
+    int sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    int g = sms * 8;
+    if (want_pot) {
+        fused_p2p_k<true><<<g, FB, 0, c->stream>>>(nn, nv, theta, th2, pos, out, err);
+        GB_LAUNCH("fused_p2p_k");
+        fused_p2p_big_k<true><<<g, FB, 0, c->stream>>>(nn, nv, theta, th2, pos, out, err);
+    } else {
+        fused_p2p_k<false><<<g, FB, 0, c->stream>>>(nn, nv, theta, th2, pos, out, err);
+        GB_LAUNCH("fused_p2p_k");
+        fused_p2p_big_k<false><<<g, FB, 0, c->stream>>>(nn, nv, theta, th2, pos, out, err);
+    }
+    GB_LAUNCH("fused_p2p_big_k");
 }
 
 }  // namespace gbfmm

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(HERE, "libgbfmm.so")
 
 STANDARD, CONSERVING, CONSERVING_PAPER0 = 0, 1, 2
 FP64, MIXED, DF64 = 0, 1, 2
+SCHEDULE_LISTS, SCHEDULE_FUSED = 0, 1
 P_MAX = 8
 MIXED_P_MAX = 6
 DF64_P_MAX = 5
@@ -32,7 +33,7 @@ EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_buil
            "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
-           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_set_schedule", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
             "fmm_leapfrog": (i32, [P, P, P, P, i64, i32, i32, dbl, i32, dbl, i32, P]),
             "fmm_walk_retries": (i32, [P, P]),
             "fmm_set_wait_limit": (i32, [P, i64, i32]),
+            "fmm_set_schedule": (i32, [P, i32]),
             "fmm_probe_fma_rate": (i32, [i32, i32, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
@@ -282,6 +284,10 @@ class FMM:
         r = np.zeros(1, np.int64)
         _check(self.lib.fmm_walk_retries(self.h, _ptr(r)), "fmm_walk_retries")
         return int(r[0])
+
+    def set_schedule(self, schedule: int):
+        """SCHEDULE_LISTS (default) or SCHEDULE_FUSED (no interaction lists; binary64)."""
+        _check(self.lib.fmm_set_schedule(self.h, int(schedule)), "fmm_set_schedule")
 
     def set_wait_limit(self, polls: int = 0, never_satisfied: bool = False):
         """Limit of the walk's look-back wait (0: default); never_satisfied for tests of the

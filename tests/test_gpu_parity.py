@@ -825,3 +825,113 @@ def test_long_list_segments(fmm, torch_cuda, orc):
     assert np.array_equal(p2p, r.p2p) and np.array_equal(m2l, r.m2l)
     assert rel(g["acc"], r.acc) < 1e-13
     g["f"].close()
+
+
+# ------------------------------------------------------------- fused schedule (no lists)
+
+def run_fused(fmm, torch, x, m, leaf, p, theta, variant, want_pot=True, offsets=None):
+    f = new_ctx(fmm, torch)
+    f.set_schedule(fmm.SCHEDULE_FUSED)
+    N = x.shape[0]
+    acc = np.empty((N, 3))
+    pot = np.empty(N) if want_pot else None
+    if offsets is None:
+        f.build(x, m, leaf)
+        f.forces(p, theta, variant, acc, pot)
+    else:
+        f.build_batch(x, m, offsets, leaf)
+        f.forces_batch(p, theta, variant, acc, pot)
+    return f, acc, pot
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fused_schedule_against_oracle(fmm, torch_cuda, orc, case, variant):
+    """The fused schedule (every target traverses for its own pairs; no lists) against the
+    oracle: forces and potentials within 1e-12, and the same conservation."""
+    name, gen, N, leaf, p, theta = case
+    x, m = gen(N)
+    r = orc.run(x, m, leaf, p, theta, variant, want_pot=True, want_internals=False)
+    f, acc, pot = run_fused(fmm, torch_cuda, x, m, leaf, p, theta, variant)
+    assert rel(acc, r.acc) < TOL, (name, variant, rel(acc, r.acc))
+    assert rel(pot, r.pot) < TOL
+    F, T = f.diagnostics()
+    fs = (m * np.linalg.norm(acc, axis=1)).sum()
+    ts = (m * np.linalg.norm(x, axis=1) * np.linalg.norm(acc, axis=1)).sum()
+    assert np.linalg.norm(F) < 1e-14 * fs
+    if variant == 1:
+        assert np.linalg.norm(T) < 1e-14 * ts
+    st = f.stage_times()
+    assert st["walk"] < 0                    # no walk, no lists
+    with pytest.raises(fmm.FMMError) as e:
+        f.get_lists()
+    assert e.value.status == -2
+    f.close()
+
+
+def test_fused_matches_list_schedule_at_size(fmm, torch_cuda):
+    """N = 2^17 at the benchmark's p, theta and leaf size: the two schedules evaluate the same
+    pair set, so their forces differ only by summation order (a missing or extra pair would
+    show at 1e-6 or more)."""
+    x, m = synth.plummer(1 << 17, 2)
+    for variant in (0, 1):
+        g = run_gpu(fmm, torch_cuda, x, m, 32, 4, 0.6, variant, want_pot=True, device_arrays=False)
+        f, acc, pot = run_fused(fmm, torch_cuda, x, m, 32, 4, 0.6, variant)
+        assert rel(acc, g["acc"]) < 1e-13, rel(acc, g["acc"])
+        assert rel(pot, g["pot"]) < 1e-13
+        g["f"].close()
+        f.close()
+
+
+def test_fused_edge_cases(fmm, torch_cuda, orc):
+    """Leaves above 32 particles at the deepest level (coincident positions), massless
+    particles, theta = 0 (direct sum), tiny N, run-to-run identity, and the rejected
+    combinations."""
+    rng = np.random.default_rng(14)
+    base = rng.normal(size=(400, 3))
+    x = np.concatenate([base, np.repeat(base[:2], 70, axis=0), np.repeat(base[5:8], 35, axis=0)])
+    m = rng.random(x.shape[0])
+    m[::9] = 0.0
+    for variant in (0, 1):
+        r = orc.run(x, m, 8, 3, 0.5, variant, want_pot=True, want_internals=False)
+        f, acc, pot = run_fused(fmm, torch_cuda, x, m, 8, 3, 0.5, variant)
+        assert rel(acc, r.acc) < TOL and rel(pot, r.pot) < TOL
+        f.close()
+    x, m = synth.plummer(3000, 17)
+    a, ph = orc.direct(x, m)
+    f, acc, pot = run_fused(fmm, torch_cuda, x, m, 16, 2, 0.0, 1)
+    assert rel(acc, a) < TOL and rel(pot, ph) < TOL
+    f2, acc2, pot2 = run_fused(fmm, torch_cuda, x, m, 16, 2, 0.0, 1)
+    assert np.array_equal(acc, acc2) and np.array_equal(pot, pot2)
+    f.close()
+    f2.close()
+    for N in (1, 2, 33):
+        x, m = synth.plummer(N, 30 + N) if N > 1 else (np.zeros((1, 3)), np.ones(1))
+        r = orc.run(x, m, 4, 2, 0.5, 1, want_pot=True, want_internals=False)
+        f, acc, pot = run_fused(fmm, torch_cuda, x, m, 4, 2, 0.5, 1)
+        assert rel(acc, r.acc) < TOL or np.abs(acc - r.acc).max() == 0
+        f.close()
+    x, m = synth.plummer(1000, 14)
+    for prec, p, v in ((1, 2, 0), (0, 7, 0), (0, 1, 2)):
+        f = new_ctx(fmm, torch_cuda, prec)
+        f.set_schedule(fmm.SCHEDULE_FUSED)
+        f.build(x, m, 16)
+        acc = np.full((1000, 3), 7.0)
+        with pytest.raises(fmm.FMMError) as e:
+            f.forces(p, 0.5, v, acc, None)
+        assert e.value.status == -1 and np.all(acc == 7.0)
+        f.close()
+
+
+def test_fused_batch_bitwise_equals_each_system_alone(fmm, torch_cuda):
+    """A batch under the fused schedule: every target's traversal starts at its own system's
+    root, so a system inside the batch gets the bits it gets alone."""
+    x, m, off = synth.batch(5, 500, 300, 4000)
+    f, acc, pot = run_fused(fmm, torch_cuda, x, m, 16, 4, 0.6, 1, offsets=off)
+    f.close()
+    for s in range(len(off) - 1):
+        a, b = off[s], off[s + 1]
+        g, acc1, pot1 = run_fused(fmm, torch_cuda, x[a:b], m[a:b], 16, 4, 0.6, 1)
+        assert np.array_equal(acc[a:b], acc1), s
+        assert np.array_equal(pot[a:b], pot1), s
+        g.close()
