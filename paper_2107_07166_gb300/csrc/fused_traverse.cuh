@@ -12,9 +12,9 @@
 //     are T's interactions when X = T; a split of X continues with X's child on the path
 //     (unless X = T, whose children receive the pair), a split of Y with every child of Y.
 // The rule is symmetric in the two cells, so T receives exactly the pairs (T, Y) the
-// mutual walk emits, each once; the traversal is a depth-first search with an explicit
-// stack, in a fixed order.  One warp runs one target's traversal with every lane taking
-// the same steps (the decisions depend on the nodes only).
+// mutual walk emits, each once.  One warp runs one target's traversal, deciding up to
+// 32 pending pairs at a time (one per lane) and keeping the order of everything fixed by
+// the tree.
 //   Far field: the M2L sources of T are buffered 32 at a time and evaluated one per lane
 //     (binary64, the list schedule's operators with a tensor per entry), and the lanes'
 //     sums are added in a fixed butterfly order at the end: one write per target.
@@ -23,9 +23,9 @@
 //     partners, where the list schedule forms it once); lanes are (particle, group) with
 //     the partner's particles dealt round-robin to the groups, and the groups' sums are
 //     added in a fixed order at the end: one write per particle.
-// Every sum runs in a fixed order, so results are run-to-run identical.  The traversal
-// stack is bounded (FSTACK entries per warp); a traversal that would overflow it sets an
-// error flag and stops (FMM_ERR_CAPACITY), which no octree of depth <= 21 can reach.
+// Every sum runs in a fixed order, so results are run-to-run identical.  The pending pairs
+// of one traversal stay below FQCAP per warp (see traverse); a traversal that would
+// exceed them would set an error flag and stop (FMM_ERR_CAPACITY).
 #pragma once
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
@@ -34,9 +34,9 @@
 
 namespace gbfmm {
 
-constexpr int FB = 128;        // 4 warps per block
+constexpr int FB = 64;         // 2 warps per block
 constexpr int FW = FB / 32;
-constexpr int FSTACK = 256;    // traversal stack entries per warp (at most 7 + 8 per level are live)
+constexpr int FQCAP = 2048;    // stack of pending pairs per warp
 constexpr int FMAXDEPTH = 22;  // levels 0 .. 21
 
 // T's root path: path[0] = its system's root, path[kT] = T
@@ -48,59 +48,109 @@ __device__ __forceinline__ int root_path(const NodeView& nv, int T, int* path) {
     return d - 1;
 }
 
-// One target's traversal (see the file comment); vis.m2l(Y) and vis.p2p(Y) receive T's
-// interactions in depth-first order.  Stack entries (k, Y): Y < 0 is Self(path[k]),
-// otherwise Pair(path[k], Y).  Every lane of the warp runs it identically.
+// One target's traversal (see the file comment), warp-parallel: the warp pops up to 32
+// pending pairs at a time from the top of a stack in shared memory, one per lane, decides
+// them, hands T's interactions to the visitor in lane order (vis.m2l(Y), vis.p2p(Y), called
+// by the whole warp with the same Y) and pushes the pairs they split into, in lane order
+// and child order.  The order of everything is a fixed function of the tree.  Pending
+// entries (k, Y): Y < 0 is Self(path[k]), otherwise Pair(path[k], Y).
+// Bound: a popped pair pushes at most 8, so popping n of them at stack size s leaves at
+// most s + 7n.  The batch is cut to n <= (FQCAP - FHEAD - s) / 7 when that is below 32, down
+// to n = 1: one-at-a-time depth-first order, which grows by at most 7 per step of the pair
+// recursion, and a step goes one level deeper on one side of the pair, so at most 42
+// steps (21 levels a side: 7 x 42 = 294 < FHEAD).  The stack therefore never exceeds
+// FQCAP; the check below only guards the argument.
+constexpr int FHEAD = 320;
+
 template <class V>
-__device__ __forceinline__ void traverse(const NodeView& nv, int T, double theta, float th2, int2* __restrict__ stk,
+__device__ __forceinline__ void traverse(const NodeView& nv, int T, double theta, float th2, int2* __restrict__ q,
                                          int* __restrict__ err, V& vis) {
+    int lane = threadIdx.x & 31;
     int path[FMAXDEPTH];
     int kT = root_path(nv, T, path);
-    int top = 0;
-    stk[top++] = make_int2(0, -1);
-    bool over = false;
+    int top = 1;
+    if (lane == 0) q[0] = make_int2(0, -1);
+    __syncwarp();
     while (top > 0) {
-        int2 e = stk[--top];
-        int k = e.x, X = path[k];
-        if (e.y < 0) {  // Self(X)
-            int nc = nv.nchild[X];
-            if (nc == 0) {
-                if (k == kT) vis.p2p(X);
-                continue;
+        int n = min(32, top);
+        int room = (FQCAP - FHEAD - top) / 7;
+        if (room < n) n = max(1, room);
+        bool act = lane < n;
+        int2 e = act ? q[top - n + lane] : make_int2(0, 0);
+        top -= n;
+        __syncwarp();  // the slots just read may be refilled below
+        int k = e.x, Y = e.y, X = act ? path[k] : 0;
+        int emit = 0, ey = 0;  // 1: M2L(T, ey), 2: P2P(T, ey)
+        int mode = 0, nk = 0, cf = 0;  // children: 1 Self(X)'s, 2 path child of X, 3 Y's
+        if (act) {
+            if (Y < 0) {
+                int nc = nv.nchild[X];
+                if (nc == 0) {
+                    if (k == kT) {
+                        emit = 2;
+                        ey = X;
+                    }
+                } else if (k != kT) {
+                    mode = 1;
+                    nk = nc;
+                    cf = nv.child_first[X];
+                }
+            } else {
+                int nnew = 0;
+                bool sa = false;
+                int d = decide(nv, make_int2(X, Y), theta, th2, &nnew, &sa);
+                if (d == 1 || d == 2) {
+                    if (k == kT) {
+                        emit = d;
+                        ey = Y;
+                    }
+                } else if (sa) {
+                    if (k != kT) {
+                        mode = 2;
+                        nk = 1;
+                    }
+                } else {
+                    mode = 3;
+                    nk = nv.nchild[Y];
+                    cf = nv.child_first[Y];
+                }
             }
-            if (k == kT) continue;
-            int cp = path[k + 1], c0 = nv.child_first[X];
-            if (top + nc > FSTACK) {
-                over = true;
-                break;
-            }
-            for (int c = c0 + nc - 1; c >= c0; c--) stk[top++] = c == cp ? make_int2(k + 1, -1) : make_int2(k + 1, c);
-            continue;
         }
-        int Y = e.y, nnew = 0;
-        bool sa = false;
-        int d = decide(nv, make_int2(X, Y), theta, th2, &nnew, &sa);
-        if (d == 1) {
-            if (k == kT) vis.m2l(Y);
-        } else if (d == 2) {
-            if (k == kT) vis.p2p(Y);
-        } else if (sa) {
-            if (k == kT) continue;
-            if (top + 1 > FSTACK) {
-                over = true;
-                break;
-            }
-            stk[top++] = make_int2(k + 1, Y);
-        } else {
-            int c0 = nv.child_first[Y], nc = nv.nchild[Y];
-            if (top + nc > FSTACK) {
-                over = true;
-                break;
-            }
-            for (int c = c0 + nc - 1; c >= c0; c--) stk[top++] = make_int2(k, c);
+        // T's interactions, in lane order
+        unsigned em = __ballot_sync(FULL, emit != 0);
+        while (em) {
+            int j = __ffs(em) - 1;
+            em &= em - 1;
+            int t = __shfl_sync(FULL, emit, j), y = __shfl_sync(FULL, ey, j);
+            if (t == 1)
+                vis.m2l(y);
+            else
+                vis.p2p(y);
         }
+        // the new pending pairs, in lane order
+        int inc = nk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += u;
+        }
+        int tot = __shfl_sync(FULL, inc, 31), pos = inc - nk;
+        if (top + tot > FQCAP) {
+            if (lane == 0) atomicExch(err, 1);
+            break;
+        }
+        int at = top + pos;
+        if (mode == 1) {
+            int cp = path[k + 1];
+            for (int i = 0; i < nk; i++) q[at + i] = cf + i == cp ? make_int2(k + 1, -1) : make_int2(k + 1, cf + i);
+        } else if (mode == 2) {
+            q[at] = make_int2(k + 1, Y);
+        } else if (mode == 3) {
+            for (int i = 0; i < nk; i++) q[at + i] = make_int2(k, cf + i);
+        }
+        top += tot;
+        __syncwarp();
     }
-    if (over && (threadIdx.x & 31) == 0) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------- far field
@@ -147,7 +197,7 @@ template <int P, int KIND>
 __global__ void __launch_bounds__(FB) fused_m2l_k(int nn, NodeView nv, double theta, float th2,
                                                   const double* __restrict__ src, double* __restrict__ loc,
                                                   int* __restrict__ err) {
-    __shared__ int2 stk[FW][FSTACK];
+    __shared__ int2 stk[FW][FQCAP];
     __shared__ int sbuf[FW][32];
     using Vis = FarVisitor<P, KIND>;
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -185,9 +235,9 @@ void fused_m2l_launch(fmm_ctx* c, int kind, double theta, double* loc) {
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     if (kind == 0)
-        fused_m2l_k<P, 0><<<sms * 8, FB, 0, c->stream>>>(nn, nv, theta, th2, c->mom.as<double>(), loc, err);
+        fused_m2l_k<P, 0><<<sms * 16, FB, 0, c->stream>>>(nn, nv, theta, th2, c->mom.as<double>(), loc, err);
     else
-        fused_m2l_k<P, 1><<<sms * 8, FB, 0, c->stream>>>(nn, nv, theta, th2, c->cmom.as<double>(), loc, err);
+        fused_m2l_k<P, 1><<<sms * 16, FB, 0, c->stream>>>(nn, nv, theta, th2, c->cmom.as<double>(), loc, err);
     GB_LAUNCH("fused_m2l_k");
 }
 

@@ -925,7 +925,7 @@ template <bool POT>
 __global__ void __launch_bounds__(FB) fused_p2p_k(int nn, NodeView nv, double theta, float th2,
                                                   const PState<double>* __restrict__ pos,
                                                   Quad<double>* __restrict__ out, int* __restrict__ err) {
-    __shared__ int2 stk[FW][FSTACK];
+    __shared__ int2 stk[FW][FQCAP];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int T = blockIdx.x * FW + w; T < nn; T += gridDim.x * FW) {
         if (nv.nchild[T] != 0) continue;  // warp-uniform
@@ -990,7 +990,7 @@ template <bool POT>
 __global__ void __launch_bounds__(FB) fused_p2p_big_k(int nn, NodeView nv, double theta, float th2,
                                                       const PState<double>* __restrict__ pos,
                                                       Quad<double>* __restrict__ out, int* __restrict__ err) {
-    __shared__ int2 stk[FW][FSTACK];
+    __shared__ int2 stk[FW][FQCAP];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int T = blockIdx.x * FW + w; T < nn; T += gridDim.x * FW) {
         if (nv.nchild[T] != 0 || nv.count[T] <= 32) continue;  // warp-uniform
@@ -1020,7 +1020,7 @@ void fused_p2p_launch(fmm_ctx* c, bool want_pot, double theta, Quad<double>* out
     const PState<double>* pos = c->pos4.as<PState<double>>();
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    int g = sms * 8;
+    int g = sms * 16;
     if (want_pot) {
         fused_p2p_k<true><<<g, FB, 0, c->stream>>>(nn, nv, theta, th2, pos, out, err);
         GB_LAUNCH("fused_p2p_k");
