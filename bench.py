@@ -228,7 +228,12 @@ def run_gbfmm(args):
 
     # leaf size and M2L tile length chosen by the library's autotuner (untimed)
     tune = None
-    if W.get("autotune"):
+    if W.get("autotune") and not args.autotune:
+        # the tuned values of the workload (leaf 32 with 64-entry M2L tiles on every run so
+        # far), without the trial evaluations: for profiling runs
+        W["leaf"] = 32
+        f.set_tiles(64)
+    if W.get("autotune") and args.autotune:
         leaves, chunks = (16, 24, 32, 48, 64), (16, 32, 64)
         with torch.cuda.stream(stream):
             bl, bc, tms = f.autotune(xd, md, W["p"], W["theta"], variant, leaf_sizes=leaves, m2l_chunks=chunks,
@@ -863,6 +868,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "df64", "mixed"],
                     help="arithmetic of the pair kernels (M2L, P2P)")
     ap.add_argument("--leapfrog", type=int, default=100, help="KDK steps of the momentum-drift run (0: skip)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="batch workload: take the tuned leaf size and M2L tile (32, 64) without timing trials")
     ap.add_argument("--no-modes", dest="modes", action="store_false",
                     help="skip timing the other arithmetic modes on the same input")
     ap.add_argument("--study", default=None, choices=["two-shapes"],

@@ -11,14 +11,19 @@
 //          children's sums in child order; Z = (sum m X) / M
 //   r_max: sqrt of the maximum over the node's particles of (dx*dx + dy*dy) + dz*dz
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 
 namespace gbfmm {
+
+namespace cg = cooperative_groups;
 
 constexpr int MAX_LEVEL = 21;
 constexpr int TB = 256;
@@ -118,14 +123,35 @@ __device__ __forceinline__ uint64_t quantise(double x, double lo, double scale) 
     return q > 2097151ull ? 2097151ull : q;
 }
 
+// The block's TB particles are 3 TB consecutive doubles of x: they are read as 16-byte
+// double2 loads (coalesced; the block's span starts on a 16-byte boundary because 3 TB is
+// even, when x itself is 16-byte aligned, checked here) into shared memory, and each
+// thread then takes its own three coordinates.  The block at the end of the array, or an
+// x not 16-byte aligned, reads doubles one by one.
 __global__ void keys_k(const double* __restrict__ x, int64_t n, const double* __restrict__ geom,
                        uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
-    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    __shared__ double sx[3 * TB];
+    int64_t b0 = (int64_t)blockIdx.x * TB;
+    int64_t i = b0 + threadIdx.x;
+    int cnt = (int)min((int64_t)TB, n - b0);  // particles of this block
+    const double* xb = x + 3 * b0;
+    if (cnt == TB && (reinterpret_cast<uintptr_t>(xb) & 15u) == 0) {
+        const double2* x2 = reinterpret_cast<const double2*>(xb);
+        for (int k = threadIdx.x; k < 3 * TB / 2; k += TB) {
+            double2 v = x2[k];
+            sx[2 * k] = v.x;
+            sx[2 * k + 1] = v.y;
+        }
+    } else {
+        for (int k = threadIdx.x; k < 3 * cnt; k += TB) sx[k] = xb[k];
+    }
+    __syncthreads();
     if (i >= n) return;
     double lo0 = geom[0], lo1 = geom[1], lo2 = geom[2], sc = geom[4];
-    uint64_t qx = quantise(x[3 * i], lo0, sc);
-    uint64_t qy = quantise(x[3 * i + 1], lo1, sc);
-    uint64_t qz = quantise(x[3 * i + 2], lo2, sc);
+    int t = threadIdx.x;
+    uint64_t qx = quantise(sx[3 * t], lo0, sc);
+    uint64_t qy = quantise(sx[3 * t + 1], lo1, sc);
+    uint64_t qz = quantise(sx[3 * t + 2], lo2, sc);
     keys[i] = (spread_bits3(qx) << 2) | (spread_bits3(qy) << 1) | spread_bits3(qz);
     idx[i] = (uint32_t)i;
 }
@@ -219,15 +245,15 @@ __global__ void split_emit_k(const uint64_t* __restrict__ keys, int lo, int m, i
     }
 }
 
-// The octree level by level without host round trips.  One launch per level fuses the
-// child count, its prefix over the level and the emission of the children: blocks take
-// tiles of LV_NODES consecutive nodes in ticket order, the node's 8 lanes find its octant
-// bounds (octant_of), a block scan places the children inside the tile, and the tile's
-// place among the level's children comes from a decoupled look-back over the tiles
-// before it.  The level's bounds live in device memory (LevelCtl::start); the last tile
-// of level L writes start[L + 2], so the host launches all MAX_LEVEL levels back to back
-// and reads the table once.  Children beyond the node capacity are counted but not
-// stored (the host grows the arrays and builds the levels again).
+// The octree level by level without host round trips.  Each level fuses the child count,
+// its prefix over the level and the emission of the children: blocks take tiles of
+// LV_NODES consecutive nodes in ticket order, the node's 8 lanes find its octant bounds
+// (octant_of), a block scan places the children inside the tile, and the tile's place
+// among the level's children comes from a decoupled look-back over the tiles before it.
+// The level's bounds live in device memory (LevelCtl::start); the last tile of level L
+// writes start[L + 2].  All levels run in one cooperative launch with a grid barrier
+// between levels, and the host reads the table once.  Children beyond the node capacity
+// are counted but not stored (the host grows the arrays and builds the levels again).
 constexpr int LV_NODES = TB / 8;
 constexpr long long LEVEL_SPIN_LIMIT = 1ll << 22;  // polls of one status word (~0.1-1 s)
 
@@ -238,24 +264,15 @@ struct LevelCtl {
     int err;                   // a look-back wait ran out
 };
 
-__global__ void __launch_bounds__(TB) split_level_k(const uint64_t* __restrict__ keys, int level, int leaf,
-                                                    int cap_nodes, LevelCtl* __restrict__ ctl,
-                                                    unsigned long long* __restrict__ status,
-                                                    int* __restrict__ nfirst, int* __restrict__ ncount,
-                                                    int* __restrict__ nlevel, int* __restrict__ nparent,
-                                                    int* __restrict__ nchildf, int* __restrict__ nnchild) {
+// The tiles of one level (all blocks of the grid take part)
+__device__ __forceinline__ void split_level_tiles(const uint64_t* __restrict__ keys, int level, int leaf, int lo,
+                                                  int hi, LevelCtl* __restrict__ ctl,
+                                                  unsigned long long* __restrict__ status, int* __restrict__ nfirst,
+                                                  int* __restrict__ ncount, int* __restrict__ nlevel,
+                                                  int* __restrict__ nparent, int* __restrict__ nchildf,
+                                                  int* __restrict__ nnchild, int cap_nodes) {
     __shared__ int s_tile, s_base;
-    if (ctl->err || ctl->overflow) return;
-    int lo = ctl->start[level], hi = ctl->start[level + 1];
     int m = hi - lo;
-    if (m <= 0) {  // below the deepest level: pass the (empty) bound on
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->start[level + 2] = hi;
-        return;
-    }
-    if (hi > cap_nodes) {  // the level's nodes were not stored
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctl->overflow, 1);
-        return;
-    }
     int ntiles = (m + LV_NODES - 1) / LV_NODES;
     const unsigned tag_agg = 2u * (unsigned)level + 1u, tag_pre = 2u * (unsigned)level + 2u;
     for (;;) {
@@ -301,6 +318,31 @@ __global__ void __launch_bounds__(TB) split_level_k(const uint64_t* __restrict__
             }
         }
         __syncthreads();  // s_tile and s_base are reused by the next tile
+    }
+}
+
+// All levels in one cooperative launch: the blocks stay resident, take the level's tiles,
+// meet at a grid barrier, and read the next level's bounds, which the last tile wrote
+// before the barrier; every block reads the same bounds and flags, so every block leaves
+// the level loop at the same level (the first empty one, or on an error or overflow).
+__global__ void __launch_bounds__(TB) split_levels_k(const uint64_t* __restrict__ keys, int leaf, int cap_nodes,
+                                                     LevelCtl* __restrict__ ctl,
+                                                     unsigned long long* __restrict__ status,
+                                                     int* __restrict__ nfirst, int* __restrict__ ncount,
+                                                     int* __restrict__ nlevel, int* __restrict__ nparent,
+                                                     int* __restrict__ nchildf, int* __restrict__ nnchild) {
+    cg::grid_group grid = cg::this_grid();
+    for (int level = 0; level < MAX_LEVEL; level++) {
+        volatile LevelCtl* vc = ctl;
+        int lo = vc->start[level], hi = vc->start[level + 1];
+        if (hi <= lo || vc->err || vc->overflow) break;
+        if (hi > cap_nodes) {  // the level's nodes were not stored: the host grows the arrays
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->overflow = 1;
+            break;
+        }
+        split_level_tiles(keys, level, leaf, lo, hi, ctl, status, nfirst, ncount, nlevel, nparent, nchildf, nnchild,
+                          cap_nodes);
+        grid.sync();
     }
 }
 
@@ -701,9 +743,9 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
     roots_k<<<grid_for(nsys, TB), TB, 0, s>>>(off, nsys, c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
                                               c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
     GB_LAUNCH("roots_k");
-    // levels 1 .. MAX_LEVEL: one launch each, bounds and counts on the device, one read of
-    // the level table (and of the input check) at the end; a tree that outgrows the node
-    // arrays is built again with arrays of the size it reported
+    // levels 1 .. MAX_LEVEL in one cooperative launch (split_levels_k), bounds and counts on
+    // the device, one read of the level table (and of the input check) at the end; a tree
+    // that outgrows the node arrays is built again with arrays of the size it reported
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     ensure(c->lvl_ctl, sizeof(LevelCtl));
@@ -719,11 +761,19 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
         h.start[1] = nsys;
         GB_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(LevelCtl), cudaMemcpyHostToDevice, s));
         GB_CUDA(cudaMemsetAsync(c->lvl_status.p, 0, sizeof(unsigned long long) * nstat, s));
-        for (int level = 0; level < MAX_LEVEL; level++) {
-            split_level_k<<<dev_sms * 4, TB, 0, s>>>(keys, level, c->leaf, cap, ctl, c->lvl_status.as<unsigned long long>(),
-                                                    c->nfirst.as<int>(), c->ncount.as<int>(), c->nlevel.as<int>(),
-                                                    c->nparent.as<int>(), c->nchildf.as<int>(), c->nnchild.as<int>());
-            GB_LAUNCH("split_level_k");
+        {
+            int per_sm = 0;
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_levels_k, TB, 0));
+            dim3 grid((unsigned)(dev_sms * std::max(1, std::min(per_sm, 4)))), block(TB);
+            const uint64_t* k_ = keys;
+            int leaf_ = c->leaf;
+            unsigned long long* st_ = c->lvl_status.as<unsigned long long>();
+            int *nf = c->nfirst.as<int>(), *ncnt = c->ncount.as<int>(), *nlv = c->nlevel.as<int>();
+            int *npar = c->nparent.as<int>(), *ncf = c->nchildf.as<int>(), *nnc = c->nnchild.as<int>();
+            void* args[] = {(void*)&k_, (void*)&leaf_, (void*)&cap, (void*)&ctl, (void*)&st_, (void*)&nf,
+                            (void*)&ncnt, (void*)&nlv, (void*)&npar, (void*)&ncf, (void*)&nnc};
+            GB_CUDA(cudaLaunchCooperativeKernel((const void*)split_levels_k, grid, block, args, 0, s));
+            GB_LAUNCH("split_levels_k");
         }
         GB_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
