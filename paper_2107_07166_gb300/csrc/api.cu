@@ -125,7 +125,7 @@ int fmm_destroy(fmm_ctx* c) {
         if (c->stream) cudaStreamSynchronize(c->stream);
         DevBuf* bufs[] = {&c->x_stage, &c->m_stage, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->xs, &c->ys,
                           &c->zs, &c->ms, &c->perm, &c->flags, &c->scan_out, &c->scan_tmp, &c->geom, &c->errflag,
-                          &c->rs_hist, &c->rs_offs, &c->leaf_of, &c->nfirst, &c->ncount,
+                          &c->rs_hist, &c->rs_status, &c->rs_err, &c->leaf_of, &c->nfirst, &c->ncount,
                           &c->nlevel, &c->nparent, &c->nchildf, &c->nnchild, &c->nM, &c->nSx, &c->nSy, &c->nSz,
                           &c->nZx, &c->nZy, &c->nZz, &c->nr2, &c->nr2f, &c->nrmax, &c->leaf_key, &c->leaf_key2, &c->leaf_order, &c->leaf_order2, &c->mom, &c->loc, &c->locp, &c->locT, &c->locpT, &c->fr0,
                           &c->fr1, &c->cnt, &c->cnt_off, &c->m2l_pairs, &c->p2p_pairs, &c->m2l_dir, &c->m2l_dirp, &c->m2l_pth, &c->m2l_ptd, &c->m2l_seg,

@@ -96,7 +96,10 @@ struct fmm_ctx {
     gbfmm::DevBuf xs, ys, zs, ms;              // sorted SoA positions and masses
     gbfmm::DevBuf perm;                        // sorted position -> input index (uint32)
     gbfmm::DevBuf flags, scan_out, scan_tmp, geom, errflag;
-    gbfmm::DevBuf rs_hist, rs_offs;            // radix sort histograms and offsets
+    gbfmm::DevBuf rs_hist;                     // radix sort digit totals, tickets and offsets
+    gbfmm::DevBuf rs_status;                   // radix sort look-back words (tile x digit)
+    gbfmm::DevBuf rs_err;                      // set by a radix sort tile whose wait gave up
+    unsigned rs_epoch = 0;                     // last look-back tag handed out
     gbfmm::DevBuf leaf_of;                     // leaf of every sorted particle
     // nodes
     int64_t n_nodes = 0, cap_nodes = 0;
@@ -191,6 +194,10 @@ void scan_i64_from_i64(fmm_ctx* c, const long long* in, int64_t n, long long* ou
 void radix_sort(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
 // the same on 32-bit keys
 void radix_sort32(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n, int bits);
+// the sorts' wait-timeout flag (device int, zero until a look-back gives up), and the check
+// of its value read at a host read point (throws FMM_ERR_TIMEOUT and clears it)
+int* sort_err(fmm_ctx* c);
+void sort_err_throw(fmm_ctx* c, int flag);
 
 // tree (tree.cu)
 int build_tree(fmm_ctx* c, const double* x_dev, const double* m_dev);

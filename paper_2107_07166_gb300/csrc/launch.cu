@@ -4,7 +4,9 @@
 #include "fmm_device.cuh"
 #include "fmm_internal.h"
 
+#include <algorithm>
 #include <atomic>
+#include <utility>
 
 namespace gbfmm {
 
@@ -162,49 +164,244 @@ void rs_pass_raw(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint3
                                                              reinterpret_cast<const uint32_t*>(offs), ntiles);
 }
 
+
+// ------------------------------------------------------------------ one-sweep radix sort
+//
+// The sort of radix_sort(): every pass is one kernel.  The digit totals of all passes come
+// from one read of the keys (rs_ghist_k, integer atomics: order-independent) and one scan
+// (rs_gscan_k); inside a pass, tile t learns how many keys of digit d the tiles before it
+// hold from their status words (decoupled look-back per digit), so the per-pass tile
+// histograms and their scans of the multi-kernel form are gone.  Tiles take their data
+// range from an atomic ticket, in launch-independent order, and rank their keys as
+// rs_scatter_k does (warp match masks, warp-major order): the sort stays stable and its
+// result is the same permutation.
+
+constexpr int RS_MAXP = 8;  // passes per sort (64-bit keys: at most 8 digits of 9 bits)
+
+template <class K>
+__global__ void __launch_bounds__(RS_BLOCK) rs_ghist_k(const K* __restrict__ keys, int64_t n, int passes,
+                                                       uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t sh[RS_MAXP * RS_BINS];
+    for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK) sh[i] = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31;
+    int64_t stride = (int64_t)gridDim.x * RS_BLOCK;
+    for (int64_t i0 = (int64_t)blockIdx.x * RS_BLOCK; i0 < n; i0 += stride) {  // same trip count in a block
+        int64_t i = i0 + threadIdx.x;
+        bool ok = i < n;
+        K k = ok ? keys[i] : K(0);
+        for (int p = 0; p < passes; p++) {
+            unsigned d = ok ? (unsigned)((k >> (RS_BITS * p)) & (RS_BINS - 1)) : (unsigned)RS_BINS;
+            unsigned peers = __match_any_sync(FULL, d);
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&sh[p * RS_BINS + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK)
+        if (sh[i]) atomicAdd(&ghist[i], sh[i]);
+}
+
+// exclusive scan of each pass's digit totals (one block per pass; RS_BINS = 2 RS_BLOCK)
+static_assert(RS_BINS == 2 * RS_BLOCK && RS_BLOCK == SCAN_BLOCK, "rs_gscan_k: two digits per thread");
+__global__ void __launch_bounds__(RS_BLOCK) rs_gscan_k(const uint32_t* __restrict__ ghist, uint32_t* __restrict__ gofs) {
+    const uint32_t* h = ghist + (int64_t)blockIdx.x * RS_BINS;
+    uint32_t* o = gofs + (int64_t)blockIdx.x * RS_BINS;
+    int t = threadIdx.x;
+    uint32_t a = h[2 * t], b = h[2 * t + 1];
+    int tot;
+    int ex = block_exclusive_scan<int>((int)(a + b), &tot);
+    o[2 * t] = (uint32_t)ex;
+    o[2 * t + 1] = (uint32_t)ex + a;
+}
+
+// keys of digit d in the tiles before `tile`: status words of tiles tile - 1, tile - 2, ...
+// (four per round) are summed until one holds its inclusive count (tag_pre); a tile that
+// has not published yet is waited for.  Every tile waited on holds an earlier ticket and
+// publishes its counts before it waits itself, so the waits end; they are still bounded by
+// spin_limit polls, after which *err is set.
+__device__ __forceinline__ int digit_lookback(const unsigned long long* __restrict__ status, int tile, int d,
+                                              unsigned tag_agg, unsigned tag_pre, long long spin_limit,
+                                              int* __restrict__ err) {
+    int ex = 0, t = tile - 1;
+    long long spins = 0;
+    while (t >= 0) {
+        unsigned long long w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            w[j] = t - j >= 0 ? ld_status(status + (int64_t)(t - j) * RS_BINS + d) : (unsigned long long)tag_pre << 32;
+        int j = 0;
+        for (; j < 4; j++) {
+            unsigned tag = (unsigned)(w[j] >> 32);
+            if (tag == tag_pre) return ex + (int)(unsigned)w[j];
+            if (tag != tag_agg) break;  // not published yet
+            ex += (int)(unsigned)w[j];
+        }
+        t -= j;
+        if (j == 0) {
+            if (++spins > spin_limit) {
+                atomicExch(err, 1);
+                return ex;
+            }
+            __nanosleep(32);
+        }
+    }
+    return ex;
+}
+
+template <class K, bool V>
+__global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(const K* __restrict__ kin,
+                                                       const uint32_t* __restrict__ vin, K* __restrict__ kout,
+                                                       uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                       const uint32_t* __restrict__ gofs,
+                                                       unsigned long long* __restrict__ status,
+                                                       int* __restrict__ ticket, unsigned tag_agg, unsigned tag_pre,
+                                                       long long spin_limit, int* __restrict__ err) {
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+    __shared__ uint32_t dbase[RS_BINS];
+    __shared__ int tile_s;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) tile_s = atomicAdd(ticket, 1);
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_BLOCK) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    int tile = tile_s;
+    int64_t base = (int64_t)tile * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
+    K k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    uint32_t rank[RS_ITEMS];
+    unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        int64_t i = base + j * 32 + lane;
+        bool ok = i < n;
+        k[j] = ok ? kin[i] : K(0);
+        if (V) v[j] = ok ? vin[i] : 0u;
+        unsigned d = ok ? (unsigned)((k[j] >> shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
+        unsigned peers = __match_any_sync(FULL, d);
+        uint32_t r = 0;
+        if (ok) r = wcnt[warp][d] + (uint32_t)__popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+        rank[j] = r;
+    }
+    __syncthreads();
+    // the tile's count of every digit (warp offsets left in wcnt), published at once: a
+    // later tile may be waiting for it
+    uint32_t cnt[RS_BINS / RS_BLOCK];
+#pragma unroll
+    for (int q = 0; q < RS_BINS / RS_BLOCK; q++) {
+        int d = threadIdx.x + q * RS_BLOCK;
+        uint32_t s = 0;
+        for (int w = 0; w < RS_WARPS; w++) {
+            uint32_t t = wcnt[w][d];
+            wcnt[w][d] = s;
+            s += t;
+        }
+        cnt[q] = s;
+        st_status(status + (int64_t)tile * RS_BINS + d, tile == 0 ? tag_pre : tag_agg, (int)s);
+    }
+#pragma unroll
+    for (int q = 0; q < RS_BINS / RS_BLOCK; q++) {
+        int d = threadIdx.x + q * RS_BLOCK;
+        int ex = 0;
+        if (tile > 0) {
+            ex = digit_lookback(status, tile, d, tag_agg, tag_pre, spin_limit, err);
+            st_status(status + (int64_t)tile * RS_BINS + d, tag_pre, ex + (int)cnt[q]);
+        }
+        dbase[d] = gofs[d] + (uint32_t)ex;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        int64_t i = base + j * 32 + lane;
+        if (i < n) {
+            unsigned d = (unsigned)((k[j] >> shift) & (RS_BINS - 1));
+            uint32_t pos = dbase[d] + wcnt[warp][d] + rank[j];
+            if (pos < (uint64_t)n) {  // always, unless a look-back gave up (then the prefix is short)
+                kout[pos] = k[j];
+                if (V) vout[pos] = v[j];
+            }
+        }
+    }
+}
+
+// polls of one status word before a sort tile gives up (never reached in a correct run)
+constexpr long long RS_SPIN_LIMIT = 1ll << 22;
+
+static unsigned next_tag(fmm_ctx* c) {
+    if (++c->rs_epoch == 0u) ++c->rs_epoch;
+    return c->rs_epoch;
+}
+
+int* sort_err(fmm_ctx* c) {
+    if (!c->rs_err.p) {
+        ensure(c->rs_err, sizeof(int) * 4);
+        GB_CUDA(cudaMemsetAsync(c->rs_err.p, 0, c->rs_err.bytes, c->stream));
+    }
+    return c->rs_err.as<int>();
+}
+
+void sort_err_throw(fmm_ctx* c, int flag) {
+    if (!flag) return;
+    GB_CUDA(cudaMemsetAsync(c->rs_err.p, 0, sizeof(int), c->stream));
+    throw FmmError{FMM_ERR_TIMEOUT, "radix sort: a tile waited too long for the tiles before it"};
+}
+
 template <class K>
 static void radix_sort_t(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevBuf* vals_tmp, int64_t n,
                          int bits) {
     if (n <= 1 || bits <= 0) return;
     if (n >= (int64_t)1 << 31) throw FmmError{FMM_ERR_CAPACITY, "radix sort: more than 2^31 keys"};
+    cudaStream_t s = c->stream;
     int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    int passes = (bits + RS_BITS - 1) / RS_BITS;
+    if (passes > RS_MAXP) throw FmmError{FMM_ERR_INVALID, "radix sort: more than 8 digits"};
     ensure(keys_tmp, sizeof(K) * (size_t)n);
     if (vals) ensure(*vals_tmp, sizeof(uint32_t) * (size_t)n);
-    ensure(c->rs_hist, sizeof(uint32_t) * (size_t)(RS_BINS * ntiles + 1));
-    ensure(c->rs_offs, sizeof(int) * (size_t)(RS_BINS * ntiles + 1));
+    // [digit totals | tickets] (cleared per sort), then the digit offsets
+    ensure(c->rs_hist, sizeof(uint32_t) * (size_t)(2 * RS_MAXP * RS_BINS + RS_MAXP));
+    uint32_t* ghist = c->rs_hist.as<uint32_t>();
+    int* tick = reinterpret_cast<int*>(ghist + RS_MAXP * RS_BINS);
+    uint32_t* gofs = ghist + RS_MAXP * RS_BINS + RS_MAXP;
+    GB_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (size_t)(RS_MAXP * RS_BINS + RS_MAXP), s));
+    // status words (tag << 32 | count) per (tile, digit); tags are new for every pass, so
+    // the words of earlier passes read as "not published" and the buffer is cleared only
+    // when it is allocated (or the tags wrap)
+    void* old = c->rs_status.p;
+    ensure(c->rs_status, sizeof(unsigned long long) * (size_t)ntiles * RS_BINS);
+    if (c->rs_status.p != old || c->rs_epoch > 0xFFFFFF00u) {
+        GB_CUDA(cudaMemsetAsync(c->rs_status.p, 0, c->rs_status.bytes, s));
+        c->rs_epoch = 0;
+    }
+    unsigned long long* status = c->rs_status.as<unsigned long long>();
+    int* err = sort_err(c);
+    int dev_sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     K* ka = keys.as<K>();
     K* kb = keys_tmp.as<K>();
     uint32_t* va = vals ? vals->as<uint32_t>() : nullptr;
     uint32_t* vb = vals ? vals_tmp->as<uint32_t>() : nullptr;
-    int passes = (bits + RS_BITS - 1) / RS_BITS;
+    int gh = std::min(ntiles, dev_sms * 4);
+    rs_ghist_k<K><<<gh, RS_BLOCK, 0, s>>>(ka, n, passes, ghist);
+    GB_LAUNCH("rs_ghist_k");
+    rs_gscan_k<<<passes, RS_BLOCK, 0, s>>>(ghist, gofs);
+    GB_LAUNCH("rs_gscan_k");
     for (int ps = 0; ps < passes; ps++) {
         int shift = RS_BITS * ps;
-        uint32_t* hist = c->rs_hist.as<uint32_t>();
-        rs_hist_k<K><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, n, shift, hist, ntiles);
-        GB_LAUNCH("rs_hist_k");
-        scan_int(c, reinterpret_cast<const int*>(hist), (int64_t)RS_BINS * ntiles, c->rs_offs.as<int>());
-        const uint32_t* offs = reinterpret_cast<const uint32_t*>(c->rs_offs.as<int>());
+        unsigned ta = next_tag(c), tp = next_tag(c);
         if (vals)
-            rs_scatter_k<K, true><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+            rs_sweep_k<K, true><<<ntiles, RS_BLOCK, 0, s>>>(ka, va, kb, vb, n, shift, gofs + ps * RS_BINS, status,
+                                                            tick + ps, ta, tp, RS_SPIN_LIMIT, err);
         else
-            rs_scatter_k<K, false><<<ntiles, RS_BLOCK, 0, c->stream>>>(ka, nullptr, kb, nullptr, n, shift, offs, ntiles);
-        GB_LAUNCH("rs_scatter_k");
-        K* tk = ka;
-        ka = kb;
-        kb = tk;
-        uint32_t* tv = va;
-        va = vb;
-        vb = tv;
+            rs_sweep_k<K, false><<<ntiles, RS_BLOCK, 0, s>>>(ka, nullptr, kb, nullptr, n, shift, gofs + ps * RS_BINS,
+                                                             status, tick + ps, ta, tp, RS_SPIN_LIMIT, err);
+        GB_LAUNCH("rs_sweep_k");
+        std::swap(ka, kb);
+        std::swap(va, vb);
     }
     if (passes & 1) {  // result sits in the temporary: swap buffer ownership
-        DevBuf t = keys;
-        keys = keys_tmp;
-        keys_tmp = t;
-        if (vals) {
-            DevBuf u = *vals;
-            *vals = *vals_tmp;
-            *vals_tmp = u;
-        }
+        std::swap(keys, keys_tmp);
+        if (vals) std::swap(*vals, *vals_tmp);
     }
 }
 

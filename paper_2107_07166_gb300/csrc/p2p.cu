@@ -521,21 +521,6 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
         GB_LAUNCH("pack_pos_k");
         c->pos_valid = true;
     }
-    long long total = 0;
-    GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
-                            cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
-    int dev_sms = 0;
-    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
-    int64_t blocks = (c->n_p2p + PW - 1) / PW;
-    int64_t cap = (int64_t)dev_sms * 16;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
-    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
-                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
-    GB_LAUNCH("p2p_sep_k");
     if constexpr (P2PRing<T>::value) {
         int64_t np = c->n_p2p;
         if (c->p2p_cls_gen != c->walk_gen && np > 0) {
@@ -556,6 +541,24 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
             c->p2p_cls_gen = c->walk_gen;
         }
     }
+    long long total = 0;
+    GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
+                            cudaMemcpyDeviceToHost, s));
+    int serr = 0;  // the ring class sort above
+    GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    sort_err_throw(c, serr);
+    ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
+    int dev_sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int64_t blocks = (c->n_p2p + PW - 1) / PW;
+    int64_t cap = (int64_t)dev_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
+    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
+                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
+    GB_LAUNCH("p2p_sep_k");
     stage_begin(c, ST_P2P);
     if constexpr (P2PRing<T>::value) {
         int64_t np = c->n_p2p;

@@ -777,8 +777,11 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
         }
         GB_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int serr = 0;
+        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
         if (bad) return FMM_ERR_INVALID;
+        sort_err_throw(c, serr);
         if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "octree: a level tile waited too long for the tiles before it"};
         if (!h.overflow) break;
         // the levels that were built report their sizes: grow past the last one and retry

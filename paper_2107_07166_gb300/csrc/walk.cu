@@ -316,7 +316,10 @@ void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it) {
     long long tot[2];
     GB_CUDA(cudaMemcpyAsync(&tot[0], it.fo.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&tot[1], it.po.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    int serr = 0;  // the segment sorts before this read
+    GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    sort_err_throw(c, serr);
     it.n_full = tot[0];
     it.n_items = tot[0] + tot[1];
     it.chunk = CH;
@@ -375,7 +378,10 @@ void run_walk(fmm_ctx* c, double theta) {
         int hmax = 0;
         GB_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(WalkCounters), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaMemcpyAsync(&hmax, max_fr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int serr = 0;  // a sort of the build (node order by leaf size) that gave up
+        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
+        sort_err_throw(c, serr);
         if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "walk: a frontier tile waited too long for the tiles before it"};
         if (h.nf[0] != 0 || h.nf[1] != 0) throw FmmError{FMM_ERR_CAPACITY, "walk did not finish in 2 x levels + 2 steps"};
         bool over = h.n_m2l > cap_m2l || h.n_p2p > cap_p2p || hmax > cap_fr;
