@@ -184,17 +184,13 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_ghist_k(const K* __restrict__ key
     __shared__ uint32_t sh[RS_MAXP * RS_BINS];
     for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK) sh[i] = 0;
     __syncthreads();
-    int lane = threadIdx.x & 31;
     int64_t stride = (int64_t)gridDim.x * RS_BLOCK;
-    for (int64_t i0 = (int64_t)blockIdx.x * RS_BLOCK; i0 < n; i0 += stride) {  // same trip count in a block
+    for (int64_t i0 = (int64_t)blockIdx.x * RS_BLOCK; i0 < n; i0 += stride) {
         int64_t i = i0 + threadIdx.x;
         bool ok = i < n;
         K k = ok ? keys[i] : K(0);
-        for (int p = 0; p < passes; p++) {
-            unsigned d = ok ? (unsigned)((k >> (RS_BITS * p)) & (RS_BINS - 1)) : (unsigned)RS_BINS;
-            unsigned peers = __match_any_sync(FULL, d);
-            if (ok && lane == __ffs(peers) - 1) atomicAdd(&sh[p * RS_BINS + d], (uint32_t)__popc(peers));
-        }
+        if (ok)
+            for (int p = 0; p < passes; p++) atomicAdd(&sh[p * RS_BINS + (unsigned)((k >> (RS_BITS * p)) & (RS_BINS - 1))], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK)
@@ -214,38 +210,64 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_gscan_k(const uint32_t* __restric
     o[2 * t + 1] = (uint32_t)ex + a;
 }
 
-// keys of digit d in the tiles before `tile`: status words of tiles tile - 1, tile - 2, ...
-// (four per round) are summed until one holds its inclusive count (tag_pre); a tile that
-// has not published yet is waited for.  Every tile waited on holds an earlier ticket and
-// publishes its counts before it waits itself, so the waits end; they are still bounded by
+// keys of digits d_q = d0 + q RS_BLOCK (q < Q) in the tiles before `tile`: status words of
+// tiles tile - 1, tile - 2, ... (R per digit and round, all digits' reads in flight
+// together) are summed until one holds its inclusive count (tag_pre); a tile that has not
+// published yet is waited for.  Every tile waited on holds an earlier ticket and publishes
+// its counts before it waits itself, so the waits end; they are still bounded by
 // spin_limit polls, after which *err is set.
-__device__ __forceinline__ int digit_lookback(const unsigned long long* __restrict__ status, int tile, int d,
-                                              unsigned tag_agg, unsigned tag_pre, long long spin_limit,
-                                              int* __restrict__ err) {
-    int ex = 0, t = tile - 1;
-    long long spins = 0;
-    while (t >= 0) {
-        unsigned long long w[4];
+template <int Q, int R>
+__device__ __forceinline__ void digit_lookback(const unsigned long long* __restrict__ status, int tile, int d0,
+                                               unsigned tag_agg, unsigned tag_pre, long long spin_limit,
+                                               int* __restrict__ err, int* ex) {
+    int t[Q];
+    bool done[Q];
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            w[j] = t - j >= 0 ? ld_status(status + (int64_t)(t - j) * RS_BINS + d) : (unsigned long long)tag_pre << 32;
-        int j = 0;
-        for (; j < 4; j++) {
-            unsigned tag = (unsigned)(w[j] >> 32);
-            if (tag == tag_pre) return ex + (int)(unsigned)w[j];
-            if (tag != tag_agg) break;  // not published yet
-            ex += (int)(unsigned)w[j];
+    for (int q = 0; q < Q; q++) {
+        ex[q] = 0;
+        t[q] = tile - 1;
+        done[q] = t[q] < 0;
+    }
+    long long spins = 0;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < Q; q++) all = all && done[q];
+        if (all) return;
+        unsigned long long w[Q][R];
+#pragma unroll
+        for (int q = 0; q < Q; q++)
+#pragma unroll
+            for (int j = 0; j < R; j++)
+                w[q][j] = !done[q] && t[q] - j >= 0
+                              ? ld_status(status + (int64_t)(t[q] - j) * RS_BINS + d0 + q * RS_BLOCK)
+                              : (unsigned long long)tag_pre << 32;
+        bool moved = false;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            if (done[q]) continue;
+            int j = 0;
+            for (; j < R; j++) {
+                unsigned tag = (unsigned)(w[q][j] >> 32);
+                if (tag == tag_pre) {
+                    ex[q] += (int)(unsigned)w[q][j];
+                    done[q] = true;
+                    break;
+                }
+                if (tag != tag_agg) break;  // not published yet
+                ex[q] += (int)(unsigned)w[q][j];
+            }
+            if (!done[q]) t[q] -= j;
+            moved = moved || done[q] || j > 0;
         }
-        t -= j;
-        if (j == 0) {
+        if (!moved) {
             if (++spins > spin_limit) {
                 atomicExch(err, 1);
-                return ex;
+                return;
             }
             __nanosleep(32);
         }
     }
-    return ex;
 }
 
 template <class K, bool V>
@@ -300,15 +322,15 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
         cnt[q] = s;
         st_status(status + (int64_t)tile * RS_BINS + d, tile == 0 ? tag_pre : tag_agg, (int)s);
     }
+    constexpr int Q = RS_BINS / RS_BLOCK;
+    int ex[Q];
+    // reads per digit and round: what the registers left by the tile's keys allow
+    digit_lookback<Q, sizeof(K) == 8 ? 4 : 2>(status, tile, threadIdx.x, tag_agg, tag_pre, spin_limit, err, ex);
 #pragma unroll
-    for (int q = 0; q < RS_BINS / RS_BLOCK; q++) {
+    for (int q = 0; q < Q; q++) {
         int d = threadIdx.x + q * RS_BLOCK;
-        int ex = 0;
-        if (tile > 0) {
-            ex = digit_lookback(status, tile, d, tag_agg, tag_pre, spin_limit, err);
-            st_status(status + (int64_t)tile * RS_BINS + d, tag_pre, ex + (int)cnt[q]);
-        }
-        dbase[d] = gofs[d] + (uint32_t)ex;
+        if (tile > 0) st_status(status + (int64_t)tile * RS_BINS + d, tag_pre, ex[q] + (int)cnt[q]);
+        dbase[d] = gofs[d] + (uint32_t)ex[q];
     }
     __syncthreads();
 #pragma unroll
