@@ -289,6 +289,42 @@ def run_gbfmm(args):
     launches = (fmm.kernel_launches() - l0) // max(args.steps, 1) * args.steps
     barrier()
     clocks = sampler.stop()
+
+    # forces on the built tree (moments and lists kept): direct fmm_forces calls against
+    # the same evaluation recorded once as a CUDA graph (fmm_forces_graph); untimed by the line
+    graph = None
+    if world == 1:
+        out_d, out_g = torch.empty_like(acc), torch.empty_like(acc)
+
+        def timed(fn, reps=5):
+            ts_ = []
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts_.append(e0.elapsed_time(e1))
+            return statistics.mean(ts_)
+
+        with torch.cuda.stream(stream):
+            f.forces(W["p"], W["theta"], variant, out_d, None)
+            f.forces_graph(W["p"], W["theta"], variant, out_g, None)  # records the graph
+        stream.synchronize()
+        k0 = fmm.kernel_launches()
+        t_dir = timed(lambda: f.forces(W["p"], W["theta"], variant, out_d, None), reps=1)
+        k_dir = fmm.kernel_launches() - k0
+        t_dir, t_gr = [], []
+        for _ in range(5):  # alternated, so that a clock change shows in both
+            t_gr.append(timed(lambda: f.forces_graph(W["p"], W["theta"], variant, out_g, None), reps=1))
+            t_dir.append(timed(lambda: f.forces(W["p"], W["theta"], variant, out_d, None), reps=1))
+        t_dir, t_gr = statistics.mean(t_dir), statistics.mean(t_gr)
+        graph = {"forces_direct_ms": t_dir, "forces_graph_ms": t_gr, "kernels_per_forces": k_dir,
+                 "graph_launches_per_forces": 1, "bitwise_equal": bool(torch.equal(out_d, out_g))}
     t_step = sum(step_ms) / len(step_ms) / 1e3
     if world > 1:
         import torch.distributed as dist
@@ -612,6 +648,7 @@ def run_gbfmm(args):
         "roofline_build": roofline_build,
         "accuracy_matched": matched,
         "schedules": schedules,
+        "graph": graph,
         "variants": variants or None,
         "modes": modes or None,
         "leapfrog": leap,

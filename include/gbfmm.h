@@ -133,6 +133,21 @@ GBFMM_API int fmm_build_batch(fmm_ctx *c, const double *x, const double *m, cons
  * mutual P2P, deterministic reductions (no floating-point atomics). */
 GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
 
+/* fmm_forces recorded once as a CUDA graph and replayed: the same evaluation (every
+ * stage from M2L to the outputs, on the moments and lists of the last build and walk)
+ * as one graph launch on the context's stream, with no host read.
+ *   Arguments as fmm_forces; acc and pot (or NULL) must be device memory, and the context
+ *   must use the list schedule (FMM_SCHEDULE_LISTS), else FMM_ERR_INVALID.
+ *   The first call, and any call after a change of arguments, of the tree (fmm_build*),
+ *   of a setting (fmm_set_*), after a direct fmm_forces that formed moments or lists anew
+ *   (another p or theta), or after any device buffer of the library was allocated or
+ *   freed, runs fmm_forces once (moments, walk, buffer sizes), then records a second
+ *   evaluation and launches it; other calls only launch.
+ *   Results are bitwise those of fmm_forces.  The replay does not synchronise the stream
+ *   and times no stage (fmm_stage_times reports -1 after it).  FMM_ERR_CUDA if the
+ *   evaluation could not be recorded. */
+GBFMM_API int fmm_forces_graph(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
+
 /* fmm_forces for a batch, plus per-system diagnostics: diag (n_sys x 6, host or device, or
  * NULL) receives [sum m a, sum m X x a] of every system, summed in a fixed order. */
 GBFMM_API int fmm_forces_batch(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot,

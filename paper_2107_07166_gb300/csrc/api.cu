@@ -137,6 +137,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->lf_x, &c->lf_v,
                           &c->lf_m, &c->lf_a, &c->lf_diag, &c->tune_acc, &c->lvl_ctl, &c->lvl_status, &c->p2p_direct, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -147,6 +148,7 @@ int fmm_destroy(fmm_ctx* c) {
 
 int fmm_set_stream(fmm_ctx* c, void* cuda_stream) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_set_stream: NULL context");
+    c->op_gen++;
     return guarded(c, [&]() -> int {
         GB_CUDA(cudaStreamSynchronize(c->stream));
         if (c->own_stream) GB_CUDA(cudaStreamDestroy(c->stream));
@@ -207,6 +209,7 @@ static int build_common(fmm_ctx* c, const double* x, const double* m, int64_t N,
 
 int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_size) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_build: NULL context");
+    c->op_gen++;
     if (!x || !m) return fail(FMM_ERR_INVALID, "fmm_build: x and m are required");
     if (N < 1) return fail(FMM_ERR_INVALID, "fmm_build: N must be >= 1");
     if (N >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_CAPACITY, "fmm_build: N must be < 2^31 - 1");
@@ -217,6 +220,7 @@ int fmm_build(fmm_ctx* c, const double* x, const double* m, int64_t N, int leaf_
 int fmm_build_batch(fmm_ctx* c, const double* x, const double* m, const int64_t* offsets, int n_sys,
                     int leaf_size) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_build_batch: NULL context");
+    c->op_gen++;
     if (!x || !m || !offsets) return fail(FMM_ERR_INVALID, "fmm_build_batch: x, m and offsets are required");
     if (n_sys < 1) return fail(FMM_ERR_INVALID, "fmm_build_batch: n_sys must be >= 1");
     if (leaf_size < 1) return fail(FMM_ERR_INVALID, "fmm_build_batch: leaf_size must be >= 1");
@@ -307,6 +311,68 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
         if (want_pot && !pot_dev)
             GB_CUDA(cudaMemcpyAsync(pot, pot_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
         if (!acc_dev || (want_pot && !pot_dev)) GB_CUDA(cudaStreamSynchronize(c->stream));
+        c->have_forces = true;
+        return FMM_OK;
+    });
+}
+
+int fmm_forces_graph(fmm_ctx* c, int p, double theta, int variant, double* acc, double* pot) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_forces_graph: NULL context");
+    if (!c->built) return fail(FMM_ERR_STATE, "fmm_forces_graph: call fmm_build first");
+    if (!acc || !is_device_ptr(acc) || (pot && !is_device_ptr(pot)))
+        return fail(FMM_ERR_INVALID, "fmm_forces_graph: acc (and pot) must be device memory");
+    if (c->schedule != FMM_SCHEDULE_LISTS)
+        return fail(FMM_ERR_INVALID, "fmm_forces_graph: needs the list schedule");
+    // the recording assumes the moments, lists and buffers it was made on: a direct
+    // fmm_forces that formed none of them anew leaves it valid
+    bool same = c->graph_exec && c->graph_p == p && c->graph_theta == theta && c->graph_variant == variant &&
+                c->graph_acc == acc && c->graph_pot == pot && c->graph_op_gen == c->op_gen &&
+                c->graph_walk_gen == c->walk_gen && c->graph_mom_p == c->mom_p &&
+                c->graph_reallocs == realloc_count();
+    if (!same) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        // one direct evaluation forms the moments and lists and sizes every buffer; the
+        // next one then has no host read and no allocation, and is recorded
+        int rc = fmm_forces(c, p, theta, variant, acc, pot);
+        if (rc != FMM_OK) return rc;
+        long long before = realloc_count();
+        rc = guarded(c, [&]() -> int {
+            GB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            return FMM_OK;
+        });
+        if (rc != FMM_OK) return rc;
+        c->capturing = true;  // no stage timer events inside the recording
+        rc = fmm_forces(c, p, theta, variant, acc, pot);
+        c->capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc == FMM_OK && (e != cudaSuccess || realloc_count() != before)) {
+            cudaGetLastError();
+            rc = fail(FMM_ERR_CUDA, "fmm_forces_graph: the evaluation could not be recorded");
+        }
+        if (rc == FMM_OK && cudaGraphInstantiate(&c->graph_exec, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_exec = nullptr;
+            rc = fail(FMM_ERR_CUDA, "fmm_forces_graph: graph instantiation failed");
+        }
+        if (g) cudaGraphDestroy(g);
+        if (rc != FMM_OK) return rc;
+        c->graph_p = p;
+        c->graph_theta = theta;
+        c->graph_variant = variant;
+        c->graph_acc = acc;
+        c->graph_pot = pot;
+        c->graph_op_gen = c->op_gen;
+        c->graph_walk_gen = c->walk_gen;
+        c->graph_mom_p = c->mom_p;
+        c->graph_reallocs = realloc_count();
+    }
+    return guarded(c, [&]() -> int {
+        GB_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+        for (int s = 0; s < ST_COUNT; s++) c->stage_valid[s] = false;  // the replay times no stage
         c->have_forces = true;
         return FMM_OK;
     });
@@ -484,6 +550,7 @@ int fmm_get_lists(fmm_ctx* c, int32_t* m2l, int32_t* p2p) {
 
 int fmm_set_walk_capacity(fmm_ctx* c, int64_t frontier, int64_t m2l, int64_t p2p) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_set_walk_capacity: NULL context");
+    c->op_gen++;
     if (frontier < 1 || m2l < 1 || p2p < 1) return fail(FMM_ERR_INVALID, "fmm_set_walk_capacity: sizes must be >= 1");
     c->cap_fr = frontier;
     c->cap_m2l = m2l;
@@ -495,6 +562,7 @@ int fmm_set_walk_capacity(fmm_ctx* c, int64_t frontier, int64_t m2l, int64_t p2p
 
 int fmm_set_tiles(fmm_ctx* c, int m2l_chunk, int p2p_chunk) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_set_tiles: NULL context");
+    c->op_gen++;
     if (m2l_chunk < 1 || m2l_chunk > 4096 || p2p_chunk < 1 || p2p_chunk > 4096)
         return fail(FMM_ERR_INVALID, "fmm_set_tiles: chunk lengths must be in [1, 4096]");
     if (c->m2l_chunk != m2l_chunk || c->p2p_chunk != p2p_chunk) c->list_theta = -1.0;
@@ -577,6 +645,7 @@ int fmm_walk_retries(fmm_ctx* c, int64_t* retries) {
 
 int fmm_set_schedule(fmm_ctx* c, int schedule) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_set_schedule: NULL context");
+    c->op_gen++;
     if (schedule != FMM_SCHEDULE_LISTS && schedule != FMM_SCHEDULE_FUSED)
         return fail(FMM_ERR_INVALID, "fmm_set_schedule: unknown schedule");
     c->schedule = schedule;
@@ -586,6 +655,7 @@ int fmm_set_schedule(fmm_ctx* c, int schedule) {
 
 int fmm_set_wait_limit(fmm_ctx* c, int64_t polls, int never_satisfied) {
     if (!c) return fail(FMM_ERR_INVALID, "fmm_set_wait_limit: NULL context");
+    c->op_gen++;
     if (polls < 0) return fail(FMM_ERR_INVALID, "fmm_set_wait_limit: polls must be >= 0");
     c->walk_spin_limit = polls > 0 ? (long long)polls : gbfmm::WALK_SPIN_LIMIT;
     c->walk_wait_never = never_satisfied != 0;

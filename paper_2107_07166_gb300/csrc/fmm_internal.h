@@ -160,6 +160,18 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_tab;                     // ring class table: start, count, warp prefix per width
     int64_t walk_gen = 0, p2p_cls_gen = -1;    // walks run so far; walk the classes belong to
     int64_t gather_gen = -1;                   // walk the P2P item slots and entry bases belong to
+    int64_t p2p_total_gen = -1;                // walk p2p_total belongs to
+    long long p2p_total = 0;                   // P2P partial slots of that walk
+    // fmm_forces_graph: the recorded evaluation and what it was recorded for
+    int64_t op_gen = 0;                        // builds and settings (change what a recorded graph assumes)
+    cudaGraphExec_t graph_exec = nullptr;
+    bool capturing = false;                    // inside the recording (stage timers off)
+    int64_t graph_op_gen = -1, graph_walk_gen = -1;
+    int graph_mom_p = -1;
+    long long graph_reallocs = -1;
+    int graph_p = 0, graph_variant = 0;
+    double graph_theta = -1.0;
+    double *graph_acc = nullptr, *graph_pot = nullptr;
     long long p2p_nslots = 0;                  // particle slots over all P2P reduction items
     gbfmm::DevBuf p2p_pbase;                   // int64 first partial slot of every directed P2P entry
     bool pos_valid = false;
@@ -185,6 +197,7 @@ namespace gbfmm {
 void ensure(DevBuf& b, size_t bytes);                              // grow, contents lost
 void ensure_keep(DevBuf& b, size_t bytes, cudaStream_t s);         // grow, contents kept
 void release(DevBuf& b);
+long long realloc_count();  // allocations and frees of DevBufs so far (all contexts)
 
 // scans (launch.cu); out must hold n + 1 entries, out[n] = total
 void scan_int(fmm_ctx* c, const int* in, int64_t n, int* out);

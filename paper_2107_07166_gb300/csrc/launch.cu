@@ -14,6 +14,11 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
+// device buffers allocated or freed so far (any context): a recorded CUDA graph holds
+// buffer addresses and stays valid only while this count does not change
+static std::atomic<long long> g_reallocs{0};
+long long realloc_count() { return g_reallocs.load(std::memory_order_relaxed); }
+
 void cuda_check(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return;
     int code = (e == cudaErrorMemoryAllocation) ? FMM_ERR_OOM : FMM_ERR_CUDA;
@@ -23,6 +28,7 @@ void cuda_check(cudaError_t e, const char* what) {
 
 void ensure(DevBuf& b, size_t bytes) {
     if (bytes <= b.bytes && b.p) return;
+    g_reallocs.fetch_add(1, std::memory_order_relaxed);
     if (b.p) GB_CUDA(cudaFree(b.p));
     b.p = nullptr;
     b.bytes = 0;
@@ -34,6 +40,7 @@ void ensure(DevBuf& b, size_t bytes) {
 void ensure_keep(DevBuf& b, size_t bytes, cudaStream_t s) {
     if (bytes <= b.bytes && b.p) return;
     size_t want = bytes + bytes / 2 + 256;
+    g_reallocs.fetch_add(1, std::memory_order_relaxed);
     void* np = nullptr;
     GB_CUDA(cudaMalloc(&np, want));
     if (b.p) {
@@ -46,6 +53,7 @@ void ensure_keep(DevBuf& b, size_t bytes, cudaStream_t s) {
 }
 
 void release(DevBuf& b) {
+    if (b.p) g_reallocs.fetch_add(1, std::memory_order_relaxed);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -438,6 +446,7 @@ void radix_sort32(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevB
 // ------------------------------------------------------------------ stage timers
 
 void stage_begin(fmm_ctx* c, Stage s) {
+    if (c->capturing) return;
     if (!c->ev[2 * s]) {
         GB_CUDA(cudaEventCreate(&c->ev[2 * s]));
         GB_CUDA(cudaEventCreate(&c->ev[2 * s + 1]));
@@ -446,6 +455,7 @@ void stage_begin(fmm_ctx* c, Stage s) {
 }
 
 void stage_end(fmm_ctx* c, Stage s) {
+    if (c->capturing) return;
     GB_CUDA(cudaEventRecord(c->ev[2 * s + 1], c->stream));
     c->stage_valid[s] = true;
 }

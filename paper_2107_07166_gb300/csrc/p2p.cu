@@ -541,13 +541,20 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
             c->p2p_cls_gen = c->walk_gen;
         }
     }
-    long long total = 0;
-    GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
-                            cudaMemcpyDeviceToHost, s));
-    int serr = 0;  // the ring class sort above
-    GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    sort_err_throw(c, serr);
+    // partial slots of the walk's pairs: read once per walk (with the flag of the ring
+    // class sort above), so that later evaluations on the same lists never wait on the host
+    if (c->p2p_total_gen != c->walk_gen) {
+        long long total = 0;
+        GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
+                                cudaMemcpyDeviceToHost, s));
+        int serr = 0;
+        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        sort_err_throw(c, serr);
+        c->p2p_total = total;
+        c->p2p_total_gen = c->walk_gen;
+    }
+    long long total = c->p2p_total;
     ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));

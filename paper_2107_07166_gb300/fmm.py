@@ -30,7 +30,7 @@ MIXED_P_MAX = 6
 DF64_P_MAX = 5
 STAGES = ("build", "moments", "walk", "m2l", "l2l", "p2p", "l2p")
 EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_build_batch", "fmm_forces",
-           "fmm_forces_batch", "fmm_diagnostics",
+           "fmm_forces_graph", "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
            "fmm_walk_retries", "fmm_set_wait_limit", "fmm_set_schedule", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
@@ -63,6 +63,7 @@ def load(path: str = LIB_PATH):
             "fmm_set_stream": (i32, [P, P]),
             "fmm_build": (i32, [P, P, P, i64, i32]),
             "fmm_forces": (i32, [P, i32, dbl, i32, P, P]),
+            "fmm_forces_graph": (i32, [P, i32, dbl, i32, P, P]),
             "fmm_build_batch": (i32, [P, P, P, P, i32, i32]),
             "fmm_forces_batch": (i32, [P, i32, dbl, i32, P, P, P]),
             "fmm_diagnostics": (i32, [P, P, P]),
@@ -200,6 +201,13 @@ class FMM:
             raise ValueError("acc must be (N, 3) and pot (N,)")
         _check(self.lib.fmm_forces(self.h, int(p), float(theta), int(variant), _ptr(acc, np.float64),
                                    _ptr(pot, np.float64)), "fmm_forces")
+
+    def forces_graph(self, p: int, theta: float, variant: int, acc, pot=None):
+        """fmm_forces replayed as one recorded CUDA graph (device outputs only)."""
+        if self.N and (tuple(acc.shape) != (self.N, 3) or (pot is not None and tuple(pot.shape) != (self.N,))):
+            raise ValueError("acc must be (N, 3) and pot (N,)")
+        _check(self.lib.fmm_forces_graph(self.h, int(p), float(theta), int(variant), _ptr(acc, np.float64),
+                                         _ptr(pot, np.float64)), "fmm_forces_graph")
 
     def diagnostics(self):
         f = np.zeros(3)

@@ -935,3 +935,60 @@ def test_fused_batch_bitwise_equals_each_system_alone(fmm, torch_cuda):
         assert np.array_equal(acc[a:b], acc1), s
         assert np.array_equal(pot[a:b], pot1), s
         g.close()
+
+
+# ------------------------------------------------------------- recorded CUDA graph
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+def test_forces_graph_replays_bitwise(fmm, torch_cuda, precision):
+    """fmm_forces_graph replays bitwise what fmm_forces gives, for a single system and a
+    batch; a rebuild on other positions or a direct fmm_forces in between is recorded
+    again; host outputs and the fused schedule are refused."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()  # stream capture needs a stream other than the legacy one
+    f = fmm.FMM(0, precision=precision, stream=stream)
+    x, m = synth.plummer(20000, 5)
+    x2, m2 = synth.hernquist(20000, 6)
+    xb, mb, off = synth.batch(8, 70, 500, 4000)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def direct(N, variant):
+        a = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        ph = torch.empty(N, dtype=torch.float64, device="cuda")
+        f.forces(4, 0.6, variant, a, ph)
+        torch.cuda.synchronize()
+        return a.clone(), ph.clone()
+
+    def replay(N, variant, times=3):
+        a = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+        ph = torch.empty(N, dtype=torch.float64, device="cuda")
+        outs = []
+        for _ in range(times):
+            a.fill_(0.0)
+            ph.fill_(0.0)
+            torch.cuda.synchronize()
+            f.forces_graph(4, 0.6, variant, a, ph)
+            torch.cuda.synchronize()
+            outs.append((a.clone(), ph.clone()))
+        return outs
+
+    for xs, ms in ((x, m), (x2, m2)):
+        f.build(dev(xs), dev(ms), 32)
+        for variant in (0, 1):
+            ra, rp = direct(len(ms), variant)
+            for ga, gp in replay(len(ms), variant):
+                assert torch.equal(ga, ra) and torch.equal(gp, rp), (precision, variant)
+    f.build_batch(dev(xb), dev(mb), off, 32)
+    ra, rp = direct(len(mb), 1)
+    for ga, gp in replay(len(mb), 1, times=2):
+        assert torch.equal(ga, ra) and torch.equal(gp, rp)
+    with pytest.raises(fmm.FMMError):
+        f.forces_graph(4, 0.6, 1, np.empty((len(mb), 3)), None)
+    if precision == 0:
+        f.set_schedule(fmm.SCHEDULE_FUSED)
+        with pytest.raises(fmm.FMMError):
+            f.forces_graph(4, 0.6, 1, torch.empty((len(mb), 3), dtype=torch.float64, device="cuda"), None)
+    f.close()
