@@ -278,6 +278,15 @@ __device__ __forceinline__ void digit_lookback(const unsigned long long* __restr
     }
 }
 
+// Shared memory of rs_sweep_k: the warps' digit counts while the keys are ranked, then the
+// tile's keys (and payloads) in digit order.
+template <class K, bool V>
+constexpr size_t rs_sweep_smem() {
+    size_t cnt = sizeof(uint32_t) * RS_WARPS * RS_BINS;
+    size_t tile = (sizeof(K) + (V ? sizeof(uint32_t) : 0)) * (size_t)RS_TILE;
+    return cnt > tile ? cnt : tile;
+}
+
 template <class K, bool V>
 __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(const K* __restrict__ kin,
                                                        const uint32_t* __restrict__ vin, K* __restrict__ kout,
@@ -286,8 +295,12 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
                                                        unsigned long long* __restrict__ status,
                                                        int* __restrict__ ticket, unsigned tag_agg, unsigned tag_pre,
                                                        long long spin_limit, int* __restrict__ err) {
-    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint32_t(*wcnt)[RS_BINS] = reinterpret_cast<uint32_t(*)[RS_BINS]>(rs_smem);
+    K* ks = reinterpret_cast<K*>(rs_smem);  // after ranking: the tile in digit order
+    uint32_t* vs = reinterpret_cast<uint32_t*>(rs_smem + sizeof(K) * RS_TILE);
     __shared__ uint32_t dbase[RS_BINS];
+    __shared__ uint32_t lstart[RS_BINS];  // first slot of every digit in the tile's digit order
     __shared__ int tile_s;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) tile_s = atomicAdd(ticket, 1);
@@ -317,9 +330,11 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
     __syncthreads();
     // the tile's count of every digit (warp offsets left in wcnt), published at once: a
     // later tile may be waiting for it
-    uint32_t cnt[RS_BINS / RS_BLOCK];
+    constexpr int Q = RS_BINS / RS_BLOCK;
+    static_assert(Q == 2, "rs_sweep_k: two digits per thread");
+    uint32_t cnt[Q];
 #pragma unroll
-    for (int q = 0; q < RS_BINS / RS_BLOCK; q++) {
+    for (int q = 0; q < Q; q++) {
         int d = threadIdx.x + q * RS_BLOCK;
         uint32_t s = 0;
         for (int w = 0; w < RS_WARPS; w++) {
@@ -330,7 +345,30 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
         cnt[q] = s;
         st_status(status + (int64_t)tile * RS_BINS + d, tile == 0 ? tag_pre : tag_agg, (int)s);
     }
-    constexpr int Q = RS_BINS / RS_BLOCK;
+    // digit starts inside the tile (digits 0..255, then 256..511)
+    int tot0, tot1;
+    int ls0 = block_exclusive_scan<int>((int)cnt[0], &tot0);
+    int ls1 = block_exclusive_scan<int>((int)cnt[1], &tot1) + tot0;
+    lstart[threadIdx.x] = (uint32_t)ls0;
+    lstart[threadIdx.x + RS_BLOCK] = (uint32_t)ls1;
+    __syncthreads();
+    // every key's slot in the tile's digit order (warp-major, so the order inside a digit
+    // is the input order and the sort stays stable)
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        unsigned d = (unsigned)((k[j] >> shift) & (RS_BINS - 1));
+        rank[j] += lstart[d] + wcnt[warp][d];
+    }
+    __syncthreads();  // wcnt is read: its space now takes the staged tile
+    int tn = (int)min((int64_t)RS_TILE, n - (int64_t)tile * RS_TILE);
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        int64_t i = base + j * 32 + lane;
+        if (i < n) {
+            ks[rank[j]] = k[j];
+            if (V) vs[rank[j]] = v[j];
+        }
+    }
     int ex[Q];
     // reads per digit and round: what the registers left by the tile's keys allow
     digit_lookback<Q, sizeof(K) == 8 ? 4 : 2>(status, tile, threadIdx.x, tag_agg, tag_pre, spin_limit, err, ex);
@@ -341,16 +379,15 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
         dbase[d] = gofs[d] + (uint32_t)ex[q];
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; j++) {
-        int64_t i = base + j * 32 + lane;
-        if (i < n) {
-            unsigned d = (unsigned)((k[j] >> shift) & (RS_BINS - 1));
-            uint32_t pos = dbase[d] + wcnt[warp][d] + rank[j];
-            if (pos < (uint64_t)n) {  // always, unless a look-back gave up (then the prefix is short)
-                kout[pos] = k[j];
-                if (V) vout[pos] = v[j];
-            }
+    // the staged tile goes out in digit order: consecutive threads of a digit's run write
+    // consecutive outputs
+    for (int i = threadIdx.x; i < tn; i += RS_BLOCK) {
+        K key = ks[i];
+        unsigned d = (unsigned)((key >> shift) & (RS_BINS - 1));
+        uint32_t pos = dbase[d] + ((uint32_t)i - lstart[d]);
+        if (pos < (uint64_t)n) {  // always, unless a look-back gave up (then the prefix is short)
+            kout[pos] = key;
+            if (V) vout[pos] = vs[i];
         }
     }
 }
@@ -416,15 +453,19 @@ static void radix_sort_t(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* val
     GB_LAUNCH("rs_ghist_k");
     rs_gscan_k<<<passes, RS_BLOCK, 0, s>>>(ghist, gofs);
     GB_LAUNCH("rs_gscan_k");
+    constexpr size_t shm_v = rs_sweep_smem<K, true>(), shm_k = rs_sweep_smem<K, false>();
+    GB_CUDA(cudaFuncSetAttribute(rs_sweep_k<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_v));
+    GB_CUDA(cudaFuncSetAttribute(rs_sweep_k<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_k));
     for (int ps = 0; ps < passes; ps++) {
         int shift = RS_BITS * ps;
         unsigned ta = next_tag(c), tp = next_tag(c);
         if (vals)
-            rs_sweep_k<K, true><<<ntiles, RS_BLOCK, 0, s>>>(ka, va, kb, vb, n, shift, gofs + ps * RS_BINS, status,
-                                                            tick + ps, ta, tp, RS_SPIN_LIMIT, err);
+            rs_sweep_k<K, true><<<ntiles, RS_BLOCK, shm_v, s>>>(ka, va, kb, vb, n, shift, gofs + ps * RS_BINS, status,
+                                                                tick + ps, ta, tp, RS_SPIN_LIMIT, err);
         else
-            rs_sweep_k<K, false><<<ntiles, RS_BLOCK, 0, s>>>(ka, nullptr, kb, nullptr, n, shift, gofs + ps * RS_BINS,
-                                                             status, tick + ps, ta, tp, RS_SPIN_LIMIT, err);
+            rs_sweep_k<K, false><<<ntiles, RS_BLOCK, shm_k, s>>>(ka, nullptr, kb, nullptr, n, shift,
+                                                                 gofs + ps * RS_BINS, status, tick + ps, ta, tp,
+                                                                 RS_SPIN_LIMIT, err);
         GB_LAUNCH("rs_sweep_k");
         std::swap(ka, kb);
         std::swap(va, vb);

@@ -31,6 +31,20 @@ struct Panel {
     static constexpr int SIZE = 32 * ROW;     // elements per warp panel
 };
 
+// Row stride and per-warp shared elements of p2p_k.  With 8-byte elements a warp's row
+// reads (lane = (row a, component c)) need 2 wavefronts at best; a stride of 4 mod 16 does
+// that for 4 components per row task, 3 mod 16 for 3 (the stride 36 with 3-component tasks
+// put rows a and a + 4 on the same banks: 3 wavefronts per read).  Binary64 folds the
+// masses into the pair terms (FOLD): the panel holds [d_x, d_y, d_z, m_b r^-3] per pair,
+// then come [a][column] arrays of m_a r^-3 and, with potentials, of r^-1.
+template <class T, bool POT>
+struct PanelRow {
+    static constexpr bool FOLD = std::is_same<T, double>::value;
+    static constexpr int ROW = (sizeof(T) == 8 && !POT) ? Panel<T>::COLS * 4 + 3 : Panel<T>::ROW;
+    static constexpr int AUX = FOLD ? (POT ? 2 : 1) : 0;
+    static constexpr int WARP = FOLD ? 32 * ROW + 32 * Panel<T>::COLS * AUX : Panel<T>::SIZE;
+};
+
 // Columns per panel for an nA x nB leaf pair.  A panel of k columns costs
 // ceil(nA k / 32) lane rounds of pair terms (about 17 arithmetic steps each), then rows
 // (ceil(NC nA / 32) rounds of k steps) and columns (ceil(NC k / 32) rounds of nA steps);
@@ -59,6 +73,38 @@ __device__ __forceinline__ int panel_cols(int nA, int nB, int cmax) {
 __device__ __forceinline__ bool r2_zero(double v) { return __double_as_longlong(v) == 0ll; }
 __device__ __forceinline__ bool r2_zero(float v) { return __float_as_uint(v) == 0u; }
 __device__ __forceinline__ bool r2_zero(df64 v) { return is_zero(v); }
+
+// s^(-3/2) (and, if IR, s^(-1/2)) for a binary64 s > 0: six binary64 operations for
+// s^(-3/2), where the library reciprocal square root and the cube take seven.  The seed
+// y0 ~ s^(-1/2) is the binary32 reciprocal square root of the mantissa of s rescaled into
+// [1, 4), taken back to s's scale by integer exponent arithmetic, so the seed costs no
+// binary64 instruction (relative error below 2^-21).  With t = y0^2 (exact: y0 has 24
+// significant bits) and e = 1 - s t (one rounding, |e| < 2^-20),
+//   s^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3/2 e + 15/8 e^2 + ...),
+//   s^(-1/2) = y0 (1 - e)^(-1/2)   = y0 (1 + 1/2 e + 3/8 e^2 + ...):
+// the binomial series cut after e^2 leave remainders below 2^-58, under binary64's own
+// rounding.  Exponents far from 0 (subnormal, huge or non-finite s) take the library path.
+template <bool IR>
+__device__ __forceinline__ void rinv_f64(double s, double& w3, double& ir) {
+    long long b = __double_as_longlong(s);
+    int e = (int)(b >> 52) - 1023;  // s > 0: no sign bit
+    if (e < -1000 || e > 1000) {
+        double r = rsqrt(s);
+        w3 = r * r * r;
+        if (IR) ir = r;
+        return;
+    }
+    int k = e >> 1;  // s = 2^(2k) s', s' in [1, 4)
+    unsigned sb = ((unsigned)(e - 2 * k + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+    unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(sb)));  // ~ s'^(-1/2), in (0.5, 1]
+    long long y0b = ((long long)((int)(yb >> 23) - 127 - k + 1023) << 52) | ((long long)(yb & 0x7fffff) << 29);
+    double y0 = __longlong_as_double(y0b);  // 2^-k s'^(-1/2) ~ s^(-1/2), exactly the binary32 value
+    double t = y0 * y0;
+    double er = fma(-s, t, 1.0);
+    double w0 = t * y0;
+    w3 = fma(w0, er * fma(er, 1.875, 1.5), w0);
+    if (IR) ir = fma(y0, er * fma(er, 0.375, 0.5), y0);
+}
 
 
 template <class S>
@@ -113,17 +159,18 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                                             const typename Prec<T>::S* __restrict__ sep,
                                             Quad<T>* __restrict__ part) {
     using S = typename Prec<T>::S;
-    // panel row stride in elements: with 8-byte elements a warp's row reads (lane = (row a,
-    // component c)) need 2 wavefronts at best; a stride of 4 mod 16 does that for 4
-    // components per row task, 3 mod 16 for 3 (the stride 36 with 3-component tasks put
-    // rows a and a + 4 on the same banks: 3 wavefronts per read)
-    constexpr int PCOL = Panel<T>::COLS, PANEL = Panel<T>::SIZE;
-    constexpr int PROW = (sizeof(T) == 8 && !POT) ? PCOL * 4 + 3 : Panel<T>::ROW;
+    // panel layout and row stride: PanelRow
+    constexpr int PCOL = Panel<T>::COLS;
+    constexpr int PROW = PanelRow<T, POT>::ROW;
+    // binary64: the masses are folded into the pair terms (FOLD)
+    constexpr bool FOLD = PanelRow<T, POT>::FOLD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PState<S> sA[PW][32], sB[PW][32];
     __shared__ Quad<T> cacc[PW][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* F = reinterpret_cast<T*>(smem_raw) + (size_t)w * PANEL;
+    T* F = reinterpret_cast<T*>(smem_raw) + (size_t)w * PanelRow<T, POT>::WARP;
+    T* WA = F + 32 * PROW;    // FOLD: m_a r^-3 of the panel's pairs, [a][column]
+    T* IRR = WA + 32 * PCOL;  // FOLD with potentials: r^-1, [a][column]
     T* cac = reinterpret_cast<T*>(&cacc[w][0]);
     int64_t gw = (int64_t)blockIdx.x * PW + w, nw = (int64_t)gridDim.x * PW;
     for (int64_t k = gw; k < npairs; k += nw) {
@@ -157,14 +204,29 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 for (int t = lane; t < nint; t += 32) {
                     int a = __float2int_rz(((float)t + 0.5f) * rcol);  // t / ncol, exact for t < 2^12
                     int bl = t - a * ncol, b = cb + bl;
-                    T fx = T(0), fy = T(0), fz = T(0), fr = T(0);
+                    T fx = T(0), fy = T(0), fz = T(0), fr = T(0), fa = T(0);
                     if (!self || a < b) {
                         const PState<S>& pa = sA[w][a];
                         const PState<S>& pb = sB[w][b];
                         T dx = Prec<T>::sep(pa.x, pb.x), dy = Prec<T>::sep(pa.y, pb.y);
                         T dz = Prec<T>::sep(pa.z, pb.z);
                         T r2 = dx * dx + dy * dy + dz * dz;
-                        if (!r2_zero(r2)) {
+                        if constexpr (FOLD) {
+                            // the panel keeps d and m_b r^-3 (rows), WA m_a r^-3 (columns): two
+                            // products per pair instead of the three of d r^-3
+                            fx = dx;
+                            fy = dy;
+                            fz = dz;
+                            if (!r2_zero(r2)) {
+                                double w3, ir = 0.0;
+                                rinv_f64<POT>(r2, w3, ir);
+                                fr = pb.m * w3;
+                                fa = pa.m * w3;
+                                if (POT) IRR[a * PCOL + bl] = ir;
+                            } else if (POT) {
+                                IRR[a * PCOL + bl] = 0.0;
+                            }
+                        } else if (!r2_zero(r2)) {
                             T ir = rsqrt_t(r2);
                             T ir3 = ir * ir * ir;
                             fx = dx * ir3;
@@ -172,12 +234,15 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                             fz = dz * ir3;
                             fr = ir;
                         }
+                    } else if constexpr (FOLD && POT) {
+                        IRR[a * PCOL + bl] = 0.0;
                     }
                     T* e = F + a * PROW + bl * 4;
                     e[0] = fx;
                     e[1] = fy;
                     e[2] = fz;
-                    if (POT) e[3] = fr;
+                    if (POT || FOLD) e[3] = fr;
+                    if constexpr (FOLD) WA[a * PCOL + bl] = fa;
                 }
                 __syncwarp();
                 // rows: sum_b m_b F[a][b], one lane per (a, component), NC nA tasks
@@ -188,7 +253,16 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     if (a < nA) {
                         const T* row = F + a * PROW + c;
                         T sum = racc[q];
-                        for (int bl = 0; bl < ncol; bl++) sum = fma_t(Prec<T>::mass(sB[w][cb + bl].m), row[bl * 4], sum);
+                        if constexpr (FOLD) {
+                            // m_b r^-3 d_c, or m_b r^-1 for the potential (c = 3)
+                            const T* wv = c < 3 ? F + a * PROW + 3 : &sB[w][cb].m;
+                            const T* vv = c < 3 ? row : IRR + a * PCOL;
+                            int vs = c < 3 ? 4 : 1;
+                            for (int bl = 0; bl < ncol; bl++) sum = fma_t(wv[bl * 4], vv[bl * vs], sum);
+                        } else {
+                            for (int bl = 0; bl < ncol; bl++)
+                                sum = fma_t(Prec<T>::mass(sB[w][cb + bl].m), row[bl * 4], sum);
+                        }
                         racc[q] = sum;
                     }
                 }
@@ -198,7 +272,15 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     {
                         const T* col = F + bl * 4 + c;
                         T sum = cac[(cb + bl) * 4 + c];
-                        for (int a = 0; a < nA; a++) sum = fma_t(Prec<T>::mass(sA[w][a].m), col[a * PROW], sum);
+                        if constexpr (FOLD) {
+                            // m_a r^-3 d_c, or m_a r^-1 for the potential (c = 3)
+                            const T* wv = c < 3 ? WA + bl : &sA[w][0].m;
+                            const T* vv = c < 3 ? col : IRR + bl;
+                            int ws = c < 3 ? PCOL : 4, vs = c < 3 ? PROW : PCOL;
+                            for (int a = 0; a < nA; a++) sum = fma_t(wv[a * ws], vv[a * vs], sum);
+                        } else {
+                            for (int a = 0; a < nA; a++) sum = fma_t(Prec<T>::mass(sA[w][a].m), col[a * PROW], sum);
+                        }
                         cac[(cb + bl) * 4 + c] = sum;
                     }
                 }
@@ -593,7 +675,7 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
             }
         }
     } else {
-        size_t shm = sizeof(T) * (size_t)Panel<T>::SIZE * PW;
+        size_t shm = sizeof(T) * (size_t)(want_pot ? PanelRow<T, true>::WARP : PanelRow<T, false>::WARP) * PW;
         auto kern = want_pot ? p2p_k<T, true> : p2p_k<T, false>;
         GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         kern<<<(unsigned)blocks, PB, shm, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
