@@ -192,13 +192,21 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_ghist_k(const K* __restrict__ key
     __shared__ uint32_t sh[RS_MAXP * RS_BINS];
     for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK) sh[i] = 0;
     __syncthreads();
-    int64_t stride = (int64_t)gridDim.x * RS_BLOCK;
-    for (int64_t i0 = (int64_t)blockIdx.x * RS_BLOCK; i0 < n; i0 += stride) {
-        int64_t i = i0 + threadIdx.x;
-        bool ok = i < n;
-        K k = ok ? keys[i] : K(0);
-        if (ok)
-            for (int p = 0; p < passes; p++) atomicAdd(&sh[p * RS_BINS + (unsigned)((k >> (RS_BITS * p)) & (RS_BINS - 1))], 1u);
+    // four keys per thread and round, loaded before their counts are added
+    constexpr int U = 4;
+    int64_t stride = (int64_t)gridDim.x * RS_BLOCK * U;
+    for (int64_t i0 = (int64_t)blockIdx.x * RS_BLOCK * U; i0 < n; i0 += stride) {
+        K k[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            int64_t i = i0 + u * RS_BLOCK + threadIdx.x;
+            k[u] = i < n ? keys[i] : K(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (i0 + u * RS_BLOCK + threadIdx.x < n)
+                for (int p = 0; p < passes; p++)
+                    atomicAdd(&sh[p * RS_BINS + (unsigned)((k[u] >> (RS_BITS * p)) & (RS_BINS - 1))], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_BLOCK)
@@ -312,12 +320,19 @@ __global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(c
     uint32_t v[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
     unsigned lt = (1u << lane) - 1u;
+    // all of the tile's loads are issued before the ranking: its warp barriers would
+    // otherwise keep each load's latency on the critical path
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; j++) {
         int64_t i = base + j * 32 + lane;
         bool ok = i < n;
         k[j] = ok ? kin[i] : K(0);
         if (V) v[j] = ok ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        int64_t i = base + j * 32 + lane;
+        bool ok = i < n;
         unsigned d = ok ? (unsigned)((k[j] >> shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
         unsigned peers = __match_any_sync(FULL, d);
         uint32_t r = 0;
