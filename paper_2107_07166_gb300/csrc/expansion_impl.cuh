@@ -223,18 +223,19 @@ __device__ __forceinline__ int entry_units(T& rx, T& ry, T& rz, int kI, T& ux, T
     return ke;
 }
 
-// N (a multiple of 4) binary32 values in 16-byte loads
+// N (a multiple of 8) binary32 values of a 32-byte aligned row in 32-byte loads: one
+// load per thread then fills whole 32-byte sectors (a 16-byte load per thread, to rows of
+// different threads, moves twice the sectors it uses); the rows are read-only in the
+// kernels that read them
 template <int N>
-__device__ __forceinline__ void load_f4(const float* __restrict__ src, float* dst) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
+__device__ __forceinline__ void load_f8(const float* __restrict__ src, float* dst) {
+    static_assert(N % 8 == 0, "load_f8: rows of whole 32-byte sectors");
 #pragma unroll
-    for (int k = 0; k < N / 4; k++) {
-        float4 v = s4[k];
-        dst[4 * k] = v.x;
-        dst[4 * k + 1] = v.y;
-        dst[4 * k + 2] = v.z;
-        dst[4 * k + 3] = v.w;
-    }
+    for (int k = 0; k < N / 8; k++)
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(dst[8 * k]), "=f"(dst[8 * k + 1]), "=f"(dst[8 * k + 2]), "=f"(dst[8 * k + 3]),
+                       "=f"(dst[8 * k + 4]), "=f"(dst[8 * k + 5]), "=f"(dst[8 * k + 6]), "=f"(dst[8 * k + 7])
+                     : "l"(src + 8 * k));
 }
 
 // geometry of the M2L kernels
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(EB) m2l_std_k(int64_t nitems, const int4* __re
             moment_factors<P + 1>(sg.nk - kI, f);
             if constexpr (sizeof(T) == 4) {
                 T Ms[E::NMP];
-                load_f4<E::NMP>(mom + (int64_t)src * E::NMP, Ms);
+                load_f8<E::NMP>(mom + (int64_t)src * E::NMP, Ms);
                 E::m2l_std_s(Ms, f, D, L);
             } else {
                 E::m2l_std_s(mom + (int64_t)src * E::NMP, f, D, L);
@@ -442,10 +443,10 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
             E::htensor(rx, ry, rz, H);
         }
         if constexpr (sizeof(T) == 4) {
-            // binary32: the raw moments (padded to a multiple of 4 floats) in 16-byte loads;
+            // binary32: the raw moments (padded to a multiple of 8 floats) in 32-byte loads;
             // the conserving moments are formed from them on load
             T Ms[E::NMP];
-            load_f4<E::NMP>(cmom + (int64_t)src * E::NMP, Ms);
+            load_f8<E::NMP>(cmom + (int64_t)src * E::NMP, Ms);
             float f[P + 1];
             moment_factors<P + 1>(sg.nk - kI, f);
             E::m2l_con_m(Ms, f, H, rx, ry, rz, SU);
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(EB) m2l_p0_k(int64_t nitems, const int4* __res
                                                const T* __restrict__ mom, T* __restrict__ part,
                                                int* __restrict__ kpart) {
     constexpr bool SC = !std::is_same<T, double>::value;
-    constexpr int NM = SC ? 12 : 10, NQ = 4, NSU = 16;  // moment stride: padded in the scaled modes
+    constexpr int NM = SC ? 16 : 10, NQ = 4, NSU = 16;  // moment stride (Exp<2>::NMP, ::NM): padded in the scaled modes
     int64_t it = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
@@ -1068,6 +1069,7 @@ void m2l_launch(fmm_ctx* c, int variant, bool std_locals) {
     if (variant == 2) {
         // the literal order-0 realigned form runs at expansion order 2 only
         if constexpr (P == 2) {
+            static_assert(E::NMP == 16 && E::NM == 10, "m2l_p0_k: moment strides of order 2");
             ensure(c->loc, sizeof(double) * (size_t)nn * E::NSU);
             if (ni > 0) {
                 m2l_p0_k<T><<<grid_for(ni, EB), EB, 0, s>>>(ni, it.items.as<int4>(), dir, g, mom, part,

@@ -428,7 +428,7 @@ def header(p):
            f"template <> struct Exp<{p}> {{",
            f"  static constexpr int P = {p};",
            f"  static constexpr int NM = {nmi(p)};   // moments / standard locals",
-           f"  static constexpr int NMP = {(nmi(p) + 3) // 4 * 4};   // moments padded to 16 bytes (binary32 storage)",
+           f"  static constexpr int NMP = {(nmi(p) + 7) // 8 * 8};   // moments padded to 32 bytes (binary32 storage)",
            f"  static constexpr int NQ = {nmi(q)};   // conserving scalar local S (|gamma| <= p-1)",
            f"  static constexpr int NSU = {4 * nmi(q)};  // conserving locals S, Ux, Uy, Uz"]
     out += radial_tensor(p, "d")
