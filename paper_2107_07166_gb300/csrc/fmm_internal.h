@@ -139,11 +139,11 @@ struct fmm_ctx {
     gbfmm::DevBuf m2l_seg;                     // int64 [n_nodes + 1] segment starts per target
     gbfmm::DevBuf p2p_dval;                    // uint32 (pair << 1 | side), per-target segments in list order
     gbfmm::DevBuf p2p_seg;                     // int64 [n_nodes + 1]
-    gbfmm::DevBuf p2p_psize;                   // int64 partial slots per P2P pair
+    gbfmm::DevBuf p2p_psize;                   // int64 partial slots per target node
     gbfmm::DevBuf seg_k, seg_k2, seg_v2;       // directed-entry keys of the list sort (+ scratch)
     gbfmm::DevBuf walk_status;                 // per-tile look-back words of the walk steps
     gbfmm::DevBuf seg_cnt;                     // per-segment chunk counts of the work items
-    gbfmm::DevBuf p2p_off;                     // int64 [n_p2p + 1] partial offsets
+    gbfmm::DevBuf p2p_off;                     // int64 [2 n_p2p] first partial slot of pair << 1 | side
     gbfmm::DevBuf p2p_part;                    // double4 partials
     gbfmm::ItemSet m2l_items, p2p_items;
     gbfmm::DevBuf m2l_part;                    // M2L partial locals per item
@@ -173,7 +173,7 @@ struct fmm_ctx {
     double graph_theta = -1.0;
     double *graph_acc = nullptr, *graph_pot = nullptr;
     long long p2p_nslots = 0;                  // particle slots over all P2P reduction items
-    gbfmm::DevBuf p2p_pbase;                   // int64 first partial slot of every directed P2P entry
+    gbfmm::DevBuf p2p_pbase;                   // int64 [n_nodes + 1] first partial slot of every target node
     bool pos_valid = false;
     gbfmm::DevBuf momT;                        // raw moments in the pair-kernel type (range-scaled, padded)
     gbfmm::DevBuf nk;                          // per-node moment unit exponent (scaled modes)

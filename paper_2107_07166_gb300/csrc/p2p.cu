@@ -115,7 +115,8 @@ struct PState {
 // Leaves above 32 particles (only at the deepest level): one side at a time, lane = target
 // particle, sources in increasing order.
 template <class T, bool POT>
-__device__ __forceinline__ void p2p_generic(int lane, bool self, int fA, int nA, int fB, int nB, long long o,
+__device__ __forceinline__ void p2p_generic(int lane, bool self, int fA, int nA, int fB, int nB, long long oA,
+                                            long long oB,
                                             typename Prec<T>::S rx, typename Prec<T>::S ry,
                                             typename Prec<T>::S rz,
                                             const PState<typename Prec<T>::S>* __restrict__ pos,
@@ -123,7 +124,7 @@ __device__ __forceinline__ void p2p_generic(int lane, bool self, int fA, int nA,
     using S = typename Prec<T>::S;
     for (int side = 0; side < (self ? 1 : 2); side++) {
         int fT = side ? fB : fA, nT = side ? nB : nA, fS = side ? fA : fB, nS = side ? nA : nB;
-        long long oT = side ? o + nA : o;
+        long long oT = side ? oB : oA;
         S sx = side ? -rx : rx, sy = side ? -ry : ry, sz = side ? -rz : rz;
         for (int t = lane; t < nT; t += 32) {
             PState<S> pt = pos[fT + t];
@@ -153,7 +154,7 @@ __device__ __forceinline__ void p2p_generic(int lane, bool self, int fA, int nA,
 // The pair kernel in arithmetic T over positions stored as S = Prec<T>::S.
 template <class T, bool POT>
 __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restrict__ pairs,
-                                            const long long* __restrict__ off, const int* __restrict__ nfirst,
+                                            const long long* __restrict__ pslot, const int* __restrict__ nfirst,
                                             const int* __restrict__ ncount,
                                             const PState<typename Prec<T>::S>* __restrict__ pos,
                                             const typename Prec<T>::S* __restrict__ sep,
@@ -177,8 +178,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
         int2 pr = pairs[k];
         int A = pr.x, B = pr.y;
         int nA = ncount[A], nB = ncount[B], fA = nfirst[A], fB = nfirst[B];
-        long long o = off[k];
         bool self = A == B;
+        long long oA = pslot[2 * k], oB = self ? 0 : pslot[2 * k + 1];  // first slots of A's and B's partials
         // positions are stored relative to their leaf's centre; the pair's centre
         // separation R = Z_A - Z_B (formed in binary64 by p2p_sep_k) is folded into the A side
         S rx = sep[3 * k], ry = sep[3 * k + 1], rz = sep[3 * k + 2];
@@ -294,8 +295,8 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                 if (a < nA) {
                     T v = -racc[q];
                     if (self) v = v + ((c < 3) ? cac[a * 4 + c] : -cac[a * 4 + c]);
-                    pd[(o + a) * 4 + c] = Prec<T>::fin(v);
-                    if (!POT && c == 2) pd[(o + a) * 4 + 3] = T(0);
+                    pd[(oA + a) * 4 + c] = Prec<T>::fin(v);
+                    if (!POT && c == 2) pd[(oA + a) * 4 + 3] = T(0);
                 }
             }
             if (!self) {
@@ -304,13 +305,13 @@ __global__ void __launch_bounds__(PB) p2p_k(int64_t npairs, const int2* __restri
                     int tau = lane + 32 * q, b = tau >> 2, c = tau & 3;
                     if (b < nB) {
                         T v = cac[b * 4 + c];
-                        pd[(o + nA + b) * 4 + c] = (c < 3) ? Prec<T>::fin(v) : (POT ? Prec<T>::fin(-v) : T(0));
+                        pd[(oB + b) * 4 + c] = (c < 3) ? Prec<T>::fin(v) : (POT ? Prec<T>::fin(-v) : T(0));
                     }
                 }
             }
             __syncwarp();
         } else {
-            p2p_generic<T, POT>(lane, self, fA, nA, fB, nB, o, rx, ry, rz, pos, part);
+            p2p_generic<T, POT>(lane, self, fA, nA, fB, nB, oA, oB, rx, ry, rz, pos, part);
         }
     }
 }
@@ -424,7 +425,7 @@ constexpr int RING_CHUNKS = 2;
 // P2P; 48 registers spilled into the ring loop and lost it again.
 template <bool POT>
 __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
-                                                 const int2* __restrict__ pairs, const long long* __restrict__ off,
+                                                 const int2* __restrict__ pairs, const long long* __restrict__ pslot,
                                                  const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                  const PState<df64>* __restrict__ pos, const df64* __restrict__ sep,
                                                  Quad<float>* __restrict__ part) {
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
         int64_t li = (q - tw[W]) * per + sg;
         bool ok = live && li < tc[W];
         int nA = 0, nB = 0, fA = 0, fB = 0;
-        long long o = 0;
+        long long oA = 0, oB = 0;
         bool self = false;
         df64 rx = df64(0.f), ry = df64(0.f), rz = df64(0.f);
         if (ok) {
@@ -466,7 +467,8 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
             nB = ncount[pr.y];
             fA = nfirst[pr.x];
             fB = nfirst[pr.y];
-            o = off[k];
+            oA = pslot[2 * k];
+            oB = self ? 0 : pslot[2 * k + 1];
             rx = sep[3 * k];
             ry = sep[3 * k + 1];
             rz = sep[3 * k + 2];
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
         // lane leaf: A unless B is the larger; its particles are shifted by its side of R
         bool laneA = nA >= nB;
         int fL = laneA ? fA : fB, nL = laneA ? nA : nB, fR = laneA ? fB : fA;
-        long long oL = laneA ? o : o + nA, oR = laneA ? o + nA : o;
+        long long oL = laneA ? oA : oB, oR = laneA ? oB : oA;
         if (!laneA) {
             rx = -rx;
             ry = -ry;
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
 // sorted list
 template <class T, bool POT>
 __global__ void __launch_bounds__(PB) p2p_big_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
-                                                const int2* __restrict__ pairs, const long long* __restrict__ off,
+                                                const int2* __restrict__ pairs, const long long* __restrict__ pslot,
                                                 const int* __restrict__ nfirst, const int* __restrict__ ncount,
                                                 const PState<typename Prec<T>::S>* __restrict__ pos,
                                                 const typename Prec<T>::S* __restrict__ sep,
@@ -549,7 +551,9 @@ __global__ void __launch_bounds__(PB) p2p_big_k(const RingTab* __restrict__ tab,
     for (int64_t li = gw; li < nlist; li += nw) {
         int k = (int)list[first + li];
         int2 pr = pairs[k];
-        p2p_generic<T, POT>(lane, pr.x == pr.y, nfirst[pr.x], ncount[pr.x], nfirst[pr.y], ncount[pr.y], off[k],
+        bool self = pr.x == pr.y;
+        p2p_generic<T, POT>(lane, self, nfirst[pr.x], ncount[pr.x], nfirst[pr.y], ncount[pr.y], pslot[2 * k],
+                            self ? 0 : pslot[2 * k + 1],
                             sep[3 * k], sep[3 * k + 1], sep[3 * k + 2], pos, part);
     }
 }
@@ -627,7 +631,7 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     // class sort above), so that later evaluations on the same lists never wait on the host
     if (c->p2p_total_gen != c->walk_gen) {
         long long total = 0;
-        GB_CUDA(cudaMemcpyAsync(&total, c->p2p_off.as<long long>() + c->n_p2p, sizeof(long long),
+        GB_CUDA(cudaMemcpyAsync(&total, c->p2p_pbase.as<long long>() + c->n_nodes, sizeof(long long),
                                 cudaMemcpyDeviceToHost, s));
         int serr = 0;
         GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -723,8 +727,10 @@ void run_p2p(fmm_ctx* c, bool want_pot) {
 // most lanes work (leaves hold ~9 particles; one lane per slot left two thirds of the
 // warp idle, and idle lanes cost full binary64 issue).  Larger leaves take one entry
 // stream per slot.
-//   part[] holds (ax, ay, az, phi) per (pair, side, slot); pair k's block starts at
-//   off[k]: first the slots of pairs[k].x, then (if distinct) those of pairs[k].y.
+//   part[] holds (ax, ay, az, phi) per (directed entry, slot), in target-segment order:
+//   target t's entries own consecutive runs of count[t] slots from tbase[t] on, so an
+//   item's partials are one contiguous run; the pair kernels write pair k's two sides at
+//   pslot[2k], pslot[2k + 1].
 // acc + v for the item sums: binary64 and double-float partials add as usual; a binary32
 // partial is added to the double-float sum by TwoSum on the high word with the rounding
 // error gathered in the low word (left unnormalised until the end: a few dozen terms keep
@@ -743,17 +749,19 @@ __device__ __forceinline__ df64 shfl_g(df64 v, int src) {
     return df64(__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src));
 }
 
-// sum of the partials of entries e0, e0 + step, ... < e1 for one slot, four in flight
+// sum of the partials of entries e0, e0 + step, ... < e1 for one slot, four in flight; the
+// entries' slot runs are consecutive (cnt slots each), entry e0's starting at b0
 template <class G, class PT>
-__device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, int slot,
-                                              const long long* __restrict__ pbase,
+__device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, long long b0, int cnt, int slot,
                                               const Quad<PT>* __restrict__ part) {
     Quad<G> acc{G(0), G(0), G(0), G(0)};
+    const Quad<PT>* p = part + b0 + slot;
+    const long long stride = (long long)step * cnt;
     int e = e0;
-    for (; e + 3 * step < e1; e += 4 * step) {
+    for (; e + 3 * step < e1; e += 4 * step, p += 4 * stride) {
         Quad<PT> q[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) q[u] = part[pbase[e + u * step] + slot];
+        for (int u = 0; u < 4; u++) q[u] = p[u * stride];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             acc.x = acc_add(acc.x, q[u].x);
@@ -762,8 +770,8 @@ __device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, int slot
             acc.w = acc_add(acc.w, q[u].w);
         }
     }
-    for (; e < e1; e += step) {
-        Quad<PT> q = part[pbase[e] + slot];
+    for (; e < e1; e += step, p += stride) {
+        Quad<PT> q = *p;
         acc.x = acc_add(acc.x, q.x);
         acc.y = acc_add(acc.y, q.y);
         acc.z = acc_add(acc.z, q.z);
@@ -774,7 +782,8 @@ __device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, int slot
 
 template <class G, class PT>
 __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* __restrict__ items,
-                                                   const int* __restrict__ ncount, const long long* __restrict__ pbase,
+                                                   const int* __restrict__ ncount, const long long* __restrict__ seg,
+                                                   const long long* __restrict__ tbase,
                                                    const Quad<PT>* __restrict__ part,
                                                    const long long* __restrict__ islot, Quad<G>* __restrict__ ipart) {
     int64_t it = ((int64_t)blockIdx.x * PB + threadIdx.x) >> 5;  // one item per warp
@@ -782,14 +791,15 @@ __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* _
     if (it >= nitems) return;
     int4 w = items[it];
     int cnt = ncount[w.x];
+    long long b = tbase[w.x] + (w.y - seg[w.x]) * (long long)cnt;  // first slot of entry w.y
     if (cnt > 32) {
         for (int slot = lane; slot < cnt; slot += 32)
-            ipart[islot[it] + slot] = gather_run<G, PT>(w.y, w.z, 1, slot, pbase, part);
+            ipart[islot[it] + slot] = gather_run<G, PT>(w.y, w.z, 1, b, cnt, slot, part);
         return;
     }
     int groups = 32 / cnt, grp = lane / cnt, slot = lane - grp * cnt;
     Quad<G> own{G(0), G(0), G(0), G(0)};
-    if (grp < groups) own = gather_run<G, PT>(w.y + grp, w.z, groups, slot, pbase, part);
+    if (grp < groups) own = gather_run<G, PT>(w.y + grp, w.z, groups, b + (long long)grp * cnt, cnt, slot, part);
     // group 0's lanes add the other groups' sums (read from the unchanged own values) in
     // group order
     Quad<G> acc = own;
@@ -801,18 +811,6 @@ __global__ void __launch_bounds__(PB) p2p_gather_k(int64_t nitems, const int4* _
     if (grp == 0) ipart[islot[it] + slot] = acc;
 }
 
-// first partial slot of every directed P2P entry: its pair's block, then (for side 1) past
-// the first leaf's slots
-__global__ void p2p_pbase_k(int64_t ne, const uint32_t* __restrict__ pdval, const int2* __restrict__ pairs,
-                            const long long* __restrict__ poff, const int* __restrict__ ncount,
-                            long long* __restrict__ pbase) {
-    int64_t e = (int64_t)blockIdx.x * PB + threadIdx.x;
-    if (e >= ne) return;
-    uint32_t v = pdval[e];
-    uint32_t k = v >> 1;
-    pbase[e] = poff[k] + ((v & 1u) ? (long long)ncount[pairs[k].x] : 0ll);
-}
-
 // slot offsets of the P2P items: islot[i] = sum of the leaf sizes of items before i
 __global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, const int* __restrict__ ncount,
                              long long* __restrict__ sizes) {
@@ -820,7 +818,8 @@ __global__ void item_slots_k(int64_t nitems, const int4* __restrict__ items, con
     if (i < nitems) sizes[i] = ncount[items[i].x];
 }
 
-// item slots and entry bases depend only on the lists: formed once per walk
+// item slots depend only on the lists: formed once per walk (the targets' partial bases,
+// p2p_pbase, come with the lists)
 static void gather_setup(fmm_ctx* c) {
     if (c->gather_gen == c->walk_gen) return;
     cudaStream_t s = c->stream;
@@ -831,19 +830,9 @@ static void gather_setup(fmm_ctx* c) {
     item_slots_k<<<grid_for(ni, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(), c->flags.as<long long>());
     GB_LAUNCH("item_slots_k");
     scan_i64_from_i64(c, c->flags.as<long long>(), ni, c->p2p_islot.as<long long>());
-    long long ne = 0;
     GB_CUDA(cudaMemcpyAsync(&c->p2p_nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long),
                             cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(&ne, c->p2p_seg.as<long long>() + c->n_nodes, sizeof(long long), cudaMemcpyDeviceToHost,
-                            s));
     GB_CUDA(cudaStreamSynchronize(s));
-    ensure(c->p2p_pbase, sizeof(long long) * (size_t)(ne > 0 ? ne : 1));
-    if (ne > 0) {
-        p2p_pbase_k<<<grid_for(ne, PB), PB, 0, s>>>(ne, c->p2p_dval.as<uint32_t>(), c->p2p_pairs.as<int2>(),
-                                                    c->p2p_off.as<long long>(), c->ncount.as<int>(),
-                                                    c->p2p_pbase.as<long long>());
-        GB_LAUNCH("p2p_pbase_k");
-    }
     c->gather_gen = c->walk_gen;
 }
 
@@ -857,6 +846,7 @@ static void gather_launch(fmm_ctx* c) {
     ensure(c->p2p_ipart, sizeof(Quad<G>) * (size_t)(nslots > 0 ? nslots : 1));
     if (ni > 0) {
         p2p_gather_k<G, PT><<<grid_for(ni * 32, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(),
+                                                                  c->p2p_seg.as<long long>(),
                                                                   c->p2p_pbase.as<long long>(),
                                                                   c->p2p_part.as<Quad<PT>>(),
                                                                   c->p2p_islot.as<long long>(),

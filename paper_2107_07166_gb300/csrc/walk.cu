@@ -250,13 +250,27 @@ __global__ void m2l_src_k(int64_t ne, const uint32_t* __restrict__ dirp, const i
     dir[e] = (uint32_t)((v & 1u) ? pr.x : pr.y);
 }
 
-// partial slots of every P2P pair: nA + nB (a self pair: nA)
-__global__ void p2p_psize_k(const int2* __restrict__ pairs, int64_t n, const int* __restrict__ count,
-                            long long* __restrict__ psize) {
-    int64_t k = (int64_t)blockIdx.x * WB + threadIdx.x;
-    if (k >= n) return;
-    int2 p = pairs[k];
-    psize[k] = p.x != p.y ? (long long)count[p.x] + count[p.y] : (long long)count[p.x];
+// Partial slots of the P2P pairs, laid out in target order: every sorted directed entry e
+// (target t = keys[e]) owns count[t] consecutive slots, so a target's partials form one
+// contiguous run in its segment order and the per-particle gather reads them as a stream.
+// Target t's run starts at tbase[t], the exclusive scan of tsz[t] = (seg[t+1] - seg[t]) count[t]
+// over the targets; entry e of t starts at tbase[t] + (e - seg[t]) count[t].
+__global__ void p2p_tslots_k(const long long* __restrict__ seg, int nn, const int* __restrict__ count,
+                             long long* __restrict__ tsz) {
+    int t = blockIdx.x * WB + threadIdx.x;
+    if (t >= nn) return;
+    tsz[t] = (seg[t + 1] - seg[t]) * (long long)count[t];
+}
+
+// pslot[pair << 1 | side] = first slot of that directed entry (the unused second entry of a
+// self pair sorts past the last target and gets none)
+__global__ void p2p_slot_of_k(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ dval, int64_t ne,
+                              int nn, const long long* __restrict__ seg, const long long* __restrict__ tbase,
+                              const int* __restrict__ count, long long* __restrict__ pslot) {
+    int64_t e = (int64_t)blockIdx.x * WB + threadIdx.x;
+    if (e >= ne) return;
+    uint32_t t = keys[e];
+    if (t < (uint32_t)nn) pslot[dval[e]] = tbase[t] + (e - seg[t]) * (long long)count[t];
 }
 
 // builds seg[0..nn] and the per-target lists out[] of the pairs[0..n)
@@ -417,17 +431,25 @@ void run_walk(fmm_ctx* c, double theta) {
     } else {
         build_segments(c, c->m2l_pairs.as<int2>(), n_m2l, (int)nn, false, c->m2l_seg, c->m2l_dir);
     }
-    // P2P: per-target segments of (pair << 1 | side) in list order, plus the
-    // partial offsets of every pair
-    ensure(c->p2p_off, sizeof(long long) * (size_t)(n_p2p + 1));
-    ensure(c->p2p_psize, sizeof(long long) * (size_t)(n_p2p + 1));
-    if (n_p2p > 0) {
-        p2p_psize_k<<<grid_for(n_p2p, WB), WB, 0, s>>>(c->p2p_pairs.as<int2>(), n_p2p, c->ncount.as<int>(),
-                                                      c->p2p_psize.as<long long>());
-        GB_LAUNCH("p2p_psize_k");
-    }
-    scan_i64_from_i64(c, c->p2p_psize.as<long long>(), n_p2p, c->p2p_off.as<long long>());
+    // P2P: per-target segments of (pair << 1 | side) in list order, then the partial
+    // slots in that order (p2p_pbase: first slot of every target, [nn] the total;
+    // p2p_off: first slot of every pair << 1 | side)
     build_segments(c, c->p2p_pairs.as<int2>(), n_p2p, (int)nn, true, c->p2p_seg, c->p2p_dval);
+    int64_t ne_p = 2 * n_p2p;
+    ensure(c->p2p_psize, sizeof(long long) * (size_t)(nn + 1));
+    ensure(c->p2p_pbase, sizeof(long long) * (size_t)(nn + 1));
+    ensure(c->p2p_off, sizeof(long long) * (size_t)(ne_p > 0 ? ne_p : 1));
+    p2p_tslots_k<<<grid_for(nn, WB), WB, 0, s>>>(c->p2p_seg.as<long long>(), (int)nn, c->ncount.as<int>(),
+                                                c->p2p_psize.as<long long>());
+    GB_LAUNCH("p2p_tslots_k");
+    scan_i64_from_i64(c, c->p2p_psize.as<long long>(), nn, c->p2p_pbase.as<long long>());
+    if (ne_p > 0) {
+        p2p_slot_of_k<<<grid_for(ne_p, WB), WB, 0, s>>>(c->seg_k.as<uint32_t>(), c->p2p_dval.as<uint32_t>(), ne_p,
+                                                       (int)nn, c->p2p_seg.as<long long>(),
+                                                       c->p2p_pbase.as<long long>(), c->ncount.as<int>(),
+                                                       c->p2p_off.as<long long>());
+        GB_LAUNCH("p2p_slot_of_k");
+    }
     // work items: m2l_chunk M2L sources (default 32) and p2p_chunk P2P entries (64) per chunk
     build_items(c, c->m2l_seg.as<long long>(), (int)nn, c->m2l_chunk, c->m2l_items);
     build_items(c, c->p2p_seg.as<long long>(), (int)nn, c->p2p_chunk, c->p2p_items);
