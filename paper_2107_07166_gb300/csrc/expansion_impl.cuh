@@ -464,6 +464,9 @@ __global__ void __launch_bounds__(EB) m2l_con_k(int64_t nitems, const int4* __re
     for (int k = 0; k < E::NSU; k++) part[it * E::NSU + k] = Prec<T>::fin(SU[k]);
 }
 
+// row stride of the stored pair tensors: NT doubles padded to whole 32-byte sectors
+__host__ __device__ constexpr int pair_tensor_stride(int nt) { return (nt + 3) / 4 * 4; }
+
 // Binary64 M2L with shared pair tensors.  The tensor of R = Z_A - Z_B (D for the standard
 // form, h for the conserving one) is formed once per mutual pair; the entry of cell A
 // (side 0) uses it as it is, the entry of cell B (side 1) sees R' = -R, whose tensor is the
@@ -476,28 +479,43 @@ __global__ void __launch_bounds__(EB) m2l_ptensor_k(int64_t npairs, const int2* 
                                                     const double* __restrict__ Zx, const double* __restrict__ Zy,
                                                     const double* __restrict__ Zz, double* __restrict__ T) {
     using E = Exp<P>;
-    constexpr int NT = V == 0 ? E::NM : E::NQ;
+    constexpr int NT = V == 0 ? E::NM : E::NQ, NTP = pair_tensor_stride(NT);
     int64_t k = (int64_t)blockIdx.x * EB + threadIdx.x;
     if (k >= npairs) return;
     int2 pr = pairs[k];
     double rx = Zx[pr.x] - Zx[pr.y], ry = Zy[pr.x] - Zy[pr.y], rz = Zz[pr.x] - Zz[pr.y];
-    double H[NT];
+    double H[NTP];
     if constexpr (V == 0)
         E::dtensor(rx, ry, rz, H);
     else
         E::htensor(rx, ry, rz, H);
 #pragma unroll
-    for (int j = 0; j < NT; j++) T[k * NT + j] = H[j];
+    for (int j = NT; j < NTP; j++) H[j] = 0.0;
+    // whole 32-byte sectors per store: one row per thread, rows 32-byte aligned
+    double* Tk = T + k * NTP;
+#pragma unroll
+    for (int j = 0; j < NTP; j += 4)
+        asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(Tk + j), "d"(H[j]), "d"(H[j + 1]),
+                     "d"(H[j + 2]), "d"(H[j + 3])
+                     : "memory");
 }
 
-// the pair tensor of entry v = pair << 1 | side, as seen from the entry's target
+// the pair tensor of entry v = pair << 1 | side, as seen from the entry's target, read in
+// 32-byte loads from its padded row (the tensors are read-only in the M2L kernels)
 template <int NT>
 __device__ __forceinline__ void load_pair_tensor(const double* __restrict__ T, uint32_t v, double* __restrict__ H) {
-    const double* Tp = T + (int64_t)(v >> 1) * NT;
+    constexpr int NTP = pair_tensor_stride(NT);
+    const double* Tp = T + (int64_t)(v >> 1) * NTP;
+    double R[NTP];
+#pragma unroll
+    for (int j = 0; j < NTP; j += 4)
+        asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+            : "=d"(R[j]), "=d"(R[j + 1]), "=d"(R[j + 2]), "=d"(R[j + 3])
+            : "l"(Tp + j));
     unsigned long long flip = (v & 1u) ? 0x8000000000000000ull : 0ull;
 #pragma unroll
     for (int j = 0; j < NT; j++) {
-        unsigned long long b = (unsigned long long)__double_as_longlong(Tp[j]);
+        unsigned long long b = (unsigned long long)__double_as_longlong(R[j]);
         if (mi_deg(j) & 1) b ^= flip;
         H[j] = __longlong_as_double((long long)b);
     }
@@ -1023,10 +1041,10 @@ void run_moments_p(fmm_ctx* c) {
 template <int P, int V>
 static const double* pair_tensors(fmm_ctx* c, DevBuf& buf, int64_t& gen, int& order) {
     using E = Exp<P>;
-    constexpr int NT = V == 0 ? E::NM : E::NQ;
+    constexpr int NT = V == 0 ? E::NM : E::NQ, NTP = pair_tensor_stride(NT);
     int64_t np = c->n_m2l;
     if (gen != c->walk_gen || order != P) {
-        ensure(buf, sizeof(double) * (size_t)NT * (size_t)(np > 0 ? np : 1));
+        ensure(buf, sizeof(double) * (size_t)NTP * (size_t)(np > 0 ? np : 1));
         if (np > 0) {
             m2l_ptensor_k<P, V><<<grid_for(np, EB), EB, 0, c->stream>>>(
                 np, c->m2l_pairs.as<int2>(), c->nZx.as<double>(), c->nZy.as<double>(), c->nZz.as<double>(),
