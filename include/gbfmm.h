@@ -77,6 +77,12 @@ enum {
                                own pairs and evaluates them as it finds them (binary64 only) */
 };
 
+/* stages of fmm_forces that may run concurrently (fmm_set_overlap, a bit mask) */
+enum {
+    FMM_OVERLAP_MOMENTS_WALK = 1, /* P2M/M2M beside the dual-tree walk (the default) */
+    FMM_OVERLAP_NEAR_FAR = 2      /* the P2P pair kernels beside M2L and L2L */
+};
+
 /* status codes */
 enum {
     FMM_OK = 0,
@@ -130,7 +136,10 @@ GBFMM_API int fmm_build_batch(fmm_ctx *c, const double *x, const double *m, cons
  *   is the standard order-p potential (a realigned force field has no potential); for
  *   FMM_CONSERVING_PAPER0 it is the standard order-2 potential of the moments it carries.
  * Steps: P2M/M2M (cached per p), dual-tree walk (cached per theta), M2L, L2L, L2P,
- * mutual P2P, deterministic reductions (no floating-point atomics). */
+ * mutual P2P, deterministic reductions (no floating-point atomics).  Stages that do not
+ * depend on each other may run concurrently on a second stream of the context
+ * (fmm_set_overlap), forked from and joined back into the context's stream, so all work
+ * of the call is ordered on that stream; the results do not depend on it (bitwise). */
 GBFMM_API int fmm_forces(fmm_ctx *c, int p, double theta, int variant, double *acc, double *pot);
 
 /* fmm_forces recorded once as a CUDA graph and replayed: the same evaluation (every
@@ -223,6 +232,17 @@ GBFMM_API int fmm_walk_retries(fmm_ctx *c, int64_t *retries);
  * the list schedule.  Invalidates cached lists. */
 GBFMM_API int fmm_set_schedule(fmm_ctx *c, int schedule);
 
+/* Which independent stages of later fmm_forces calls run concurrently: a mask of
+ * FMM_OVERLAP_MOMENTS_WALK (the moments on a second stream while the walk runs on the
+ * context's stream) and FMM_OVERLAP_NEAR_FAR (the P2P pair kernels on the second stream
+ * while M2L and L2L run; the list schedule only).  The default is FMM_OVERLAP_MOMENTS_WALK.
+ * Measured on one GB300: the moments beside the walk take 0.8-3% off an evaluation; the
+ * near field beside the far field takes another 3% off in FMM_MIXED, whose pair kernels
+ * are latency-bound, and adds 3% in FMM_FP64, whose pair kernels both keep the binary64
+ * units busy.  Results are bitwise the same for every mask.  FMM_ERR_INVALID for other
+ * bits.  The paper has no counterpart: this is a scheduling setting. */
+GBFMM_API int fmm_set_overlap(fmm_ctx *c, int mask);
+
 /* Limit of the walk's only device-side wait, for tests of its failure path.  Each walk
  * step places its outputs after those of the tiles before it (eq. mac_criterion decides
  * the pairs; the order of the lists is fixed by the tree), so a tile polls a status word
@@ -235,8 +255,10 @@ GBFMM_API int fmm_set_schedule(fmm_ctx *c, int schedule);
 GBFMM_API int fmm_set_wait_limit(fmm_ctx *c, int64_t polls, int never_satisfied);
 
 /* Device time in milliseconds of each stage of the last build/forces call, measured
- * with CUDA events on the context's stream: [build, moments, walk, m2l, l2l, p2p, l2p].
- * A stage that did not run in that call reports -1. */
+ * with CUDA events on the stream each stage ran on: [build, moments, walk, m2l, l2l, p2p,
+ * l2p].  Stages that ran concurrently (fmm_set_overlap) overlap in time, so the stage
+ * times of one call can add up to more than its duration.  A stage that did not run in
+ * that call reports -1. */
 GBFMM_API int fmm_stage_times(fmm_ctx *c, double *ms, int n);
 
 /* Largest N accepted by fmm_morton_sort_noalloc. */

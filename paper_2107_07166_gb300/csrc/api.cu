@@ -108,9 +108,17 @@ int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
             GB_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
             c->own_stream = true;
         }
+        // the side stream and its fork/join events (independent stages of fmm_forces)
+        GB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        GB_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        GB_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
         return FMM_OK;
     });
     if (rc != FMM_OK) {
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        if (c->join_ev) cudaEventDestroy(c->join_ev);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return rc;
     }
@@ -140,6 +148,12 @@ int fmm_destroy(fmm_ctx* c) {
         if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
+        if (c->side) {
+            cudaStreamSynchronize(c->side);
+            cudaStreamDestroy(c->side);
+        }
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        if (c->join_ev) cudaEventDestroy(c->join_ev);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -264,29 +278,61 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
         for (int s = ST_MOMENTS; s < ST_COUNT; s++) c->stage_valid[s] = false;
         bool want_pot = pot != nullptr;
         size_t n = (size_t)c->N;
-        if (c->mom_p != p) {
+        bool fused = c->schedule == FMM_SCHEDULE_FUSED;
+        bool need_mom = c->mom_p != p, need_walk = !fused && c->list_theta != theta;
+        auto moments = [&]() {
             stage_begin(c, ST_MOMENTS);
             run_moments_dispatch(c, p);
             stage_end(c, ST_MOMENTS);
+        };
+        auto walk = [&]() {
+            stage_begin(c, ST_WALK);
+            run_walk(c, theta);
+            stage_end(c, ST_WALK);
+        };
+        if (need_mom && need_walk && (c->overlap & FMM_OVERLAP_MOMENTS_WALK)) {
+            // the moments (build -> P2M -> M2M) do not depend on the walk, and neither on
+            // the other: the moments run on the side stream while the walk (with its host
+            // reads of list sizes) runs on the context's stream
+            c->mom_p = -1;
+            fork_side(c);
+            {
+                SideLaunches side(c);
+                moments();
+            }
+            walk();
+            join_side(c);
             c->mom_p = p;
+        } else {
+            if (need_mom) {
+                moments();
+                c->mom_p = p;
+            }
+            if (need_walk) walk();
         }
-        bool fused = c->schedule == FMM_SCHEDULE_FUSED;
         if (fused) {
             // no walk and no lists: every target node traverses for its own pairs
             c->list_theta = -1.0;
             c->fused_theta = theta;
             GB_CUDA(cudaMemsetAsync(c->errflag.as<int>() + 2, 0, sizeof(int), c->stream));
-        } else if (c->list_theta != theta) {
-            stage_begin(c, ST_WALK);
-            run_walk(c, theta);
-            stage_end(c, ST_WALK);
-        }
-        run_far_field_dispatch(c, p, variant, want_pot);
-        if (fused) {
+            run_far_field_dispatch(c, p, variant, want_pot);
             stage_begin(c, ST_P2P);
             run_p2p_fused(c, want_pot, theta);
             stage_end(c, ST_P2P);
+        } else if (c->overlap & FMM_OVERLAP_NEAR_FAR) {
+            // near field (pair kernels) beside the far field (M2L, L2L): independent until
+            // the per-particle sums; the set-up (with its host read of the partial count,
+            // once per walk) runs first on the context's stream
+            run_p2p_prepare(c);
+            fork_side(c);
+            {
+                SideLaunches side(c);
+                run_p2p_kernels(c, want_pot);
+            }
+            run_far_field_dispatch(c, p, variant, want_pot);
+            join_side(c);
         } else {
+            run_far_field_dispatch(c, p, variant, want_pot);
             run_p2p(c, want_pot);
         }
         ensure(c->acc_s, sizeof(double) * 3 * n);
@@ -650,6 +696,15 @@ int fmm_set_schedule(fmm_ctx* c, int schedule) {
         return fail(FMM_ERR_INVALID, "fmm_set_schedule: unknown schedule");
     c->schedule = schedule;
     c->list_theta = -1.0;
+    return FMM_OK;
+}
+
+int fmm_set_overlap(fmm_ctx* c, int mask) {
+    if (!c) return fail(FMM_ERR_INVALID, "fmm_set_overlap: NULL context");
+    if (mask & ~(FMM_OVERLAP_MOMENTS_WALK | FMM_OVERLAP_NEAR_FAR))
+        return fail(FMM_ERR_INVALID, "fmm_set_overlap: unknown bits in the mask");
+    c->op_gen++;
+    c->overlap = mask;
     return FMM_OK;
 }
 

@@ -185,6 +185,12 @@ struct fmm_ctx {
     gbfmm::DevBuf out_stage;
     gbfmm::DevBuf diag_tmp;
     bool have_forces = false;
+    // second stream for stages that do not depend on each other (the moments beside the
+    // walk; the pair kernels beside the far field), forked from and joined back into
+    // `stream` by events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    int overlap = FMM_OVERLAP_MOMENTS_WALK;    // fmm_set_overlap
     // timing
     cudaEvent_t ev[2 * gbfmm::ST_COUNT] = {};
     float stage_ms[gbfmm::ST_COUNT] = {};
@@ -223,8 +229,23 @@ void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it);
 void run_moments(fmm_ctx* c, int p);
 void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
 
-// particle-particle + final reduction (p2p.cu)
+// particle-particle + final reduction (p2p.cu): set-up (positions, ring classes, partial
+// buffer, separations; may read sizes on the host once per walk), then the pair kernels
 void run_p2p(fmm_ctx* c, bool want_pot);
+void run_p2p_prepare(fmm_ctx* c);
+void run_p2p_kernels(fmm_ctx* c, bool want_pot);
+
+// The side stream: fork_side makes c->side wait for the work queued on c->stream so far;
+// while a SideLaunches is alive, the launchers (which all queue on c->stream) queue on the
+// side stream; join_side makes c->stream wait for the side stream's work.
+void fork_side(fmm_ctx* c);
+void join_side(fmm_ctx* c);
+struct SideLaunches {
+    fmm_ctx* c;
+    cudaStream_t main;
+    explicit SideLaunches(fmm_ctx* ctx);
+    ~SideLaunches();
+};
 // the fused schedule's near field: per-particle P2P sums into c->p2p_direct (p2p.cu)
 void run_p2p_fused(fmm_ctx* c, bool want_pot, double theta);
 void run_p2p_gather(fmm_ctx* c);

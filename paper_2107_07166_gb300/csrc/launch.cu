@@ -499,6 +499,26 @@ void radix_sort32(fmm_ctx* c, DevBuf& keys, DevBuf& keys_tmp, DevBuf* vals, DevB
     radix_sort_t<uint32_t>(c, keys, keys_tmp, vals, vals_tmp, n, bits);
 }
 
+// ------------------------------------------------------------------ side stream
+
+void fork_side(fmm_ctx* c) {
+    if (!c->side) {
+        GB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        GB_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        GB_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    GB_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    GB_CUDA(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+}
+
+void join_side(fmm_ctx* c) {
+    GB_CUDA(cudaEventRecord(c->join_ev, c->side));
+    GB_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
+}
+
+SideLaunches::SideLaunches(fmm_ctx* ctx) : c(ctx), main(ctx->stream) { c->stream = c->side; }
+SideLaunches::~SideLaunches() { c->stream = main; }
+
 // ------------------------------------------------------------------ stage timers
 
 void stage_begin(fmm_ctx* c, Stage s) {

@@ -594,8 +594,10 @@ struct P2PRing {
     static constexpr bool value = std::is_same<T, float>::value;
 };
 
+// P2P set-up: packed positions, ring classes (binary32), the partial buffer (its size read
+// once per walk) and the pairs' centre separations
 template <class T>
-static void p2p_launch(fmm_ctx* c, bool want_pot) {
+static void p2p_prepare(fmm_ctx* c) {
     using S = typename Prec<T>::S;
     cudaStream_t s = c->stream;
     int n = (int)c->N;
@@ -642,16 +644,23 @@ static void p2p_launch(fmm_ctx* c, bool want_pot) {
     }
     long long total = c->p2p_total;
     ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
+    ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
+    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
+                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
+    GB_LAUNCH("p2p_sep_k");
+}
+
+// the pair kernels on the prepared lists (no host read, no allocation)
+template <class T>
+static void p2p_kernels(fmm_ctx* c, bool want_pot) {
+    using S = typename Prec<T>::S;
+    cudaStream_t s = c->stream;
     int dev_sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int64_t blocks = (c->n_p2p + PW - 1) / PW;
     int64_t cap = (int64_t)dev_sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
-    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
-                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
-    GB_LAUNCH("p2p_sep_k");
     stage_begin(c, ST_P2P);
     if constexpr (P2PRing<T>::value) {
         int64_t np = c->n_p2p;
@@ -710,13 +719,27 @@ void run_p2p_fused(fmm_ctx* c, bool want_pot, double theta) {
     fused_p2p_launch(c, want_pot, theta, c->p2p_direct.as<Quad<double>>());
 }
 
-void run_p2p(fmm_ctx* c, bool want_pot) {
+void run_p2p_prepare(fmm_ctx* c) {
     if (c->precision == FMM_FP64)
-        p2p_launch<double>(c, want_pot);
+        p2p_prepare<double>(c);
     else if (c->precision == FMM_DF64)
-        p2p_launch<df64>(c, want_pot);
+        p2p_prepare<df64>(c);
     else
-        p2p_launch<float>(c, want_pot);
+        p2p_prepare<float>(c);
+}
+
+void run_p2p_kernels(fmm_ctx* c, bool want_pot) {
+    if (c->precision == FMM_FP64)
+        p2p_kernels<double>(c, want_pot);
+    else if (c->precision == FMM_DF64)
+        p2p_kernels<df64>(c, want_pot);
+    else
+        p2p_kernels<float>(c, want_pot);
+}
+
+void run_p2p(fmm_ctx* c, bool want_pot) {
+    run_p2p_prepare(c);
+    run_p2p_kernels(c, want_pot);
 }
 
 // a12/a13 first level: one warp per P2P work item (up to P2P_CHUNK directed entries of

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "libgbfmm.so")
 STANDARD, CONSERVING, CONSERVING_PAPER0 = 0, 1, 2
 FP64, MIXED, DF64 = 0, 1, 2
 SCHEDULE_LISTS, SCHEDULE_FUSED = 0, 1
+OVERLAP_MOMENTS_WALK, OVERLAP_NEAR_FAR = 1, 2
 P_MAX = 8
 MIXED_P_MAX = 6
 DF64_P_MAX = 5
@@ -33,7 +34,7 @@ EXPORTS = ("fmm_create", "fmm_destroy", "fmm_set_stream", "fmm_build", "fmm_buil
            "fmm_forces_graph", "fmm_forces_batch", "fmm_diagnostics",
            "fmm_counts", "fmm_get_keys", "fmm_get_tree", "fmm_get_geometry", "fmm_get_lists",
            "fmm_stage_times", "fmm_leapfrog", "fmm_set_walk_capacity", "fmm_set_tiles", "fmm_autotune",
-           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_set_schedule", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
+           "fmm_walk_retries", "fmm_set_wait_limit", "fmm_set_schedule", "fmm_set_overlap", "fmm_probe_fma_rate", "fmm_morton_sort_noalloc", "fmm_kernel_launches", "fmm_strerror",
            "fmm_last_error")
 NOALLOC_MAX_N = 131072
 
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH):
             "fmm_walk_retries": (i32, [P, P]),
             "fmm_set_wait_limit": (i32, [P, i64, i32]),
             "fmm_set_schedule": (i32, [P, i32]),
+            "fmm_set_overlap": (i32, [P, i32]),
             "fmm_probe_fma_rate": (i32, [i32, i32, P]),
             "fmm_morton_sort_noalloc": (i32, [P, i64, P, P, P, P, P]),
             "fmm_kernel_launches": (i64, []),
@@ -296,6 +298,11 @@ class FMM:
     def set_schedule(self, schedule: int):
         """SCHEDULE_LISTS (default) or SCHEDULE_FUSED (no interaction lists; binary64)."""
         _check(self.lib.fmm_set_schedule(self.h, int(schedule)), "fmm_set_schedule")
+
+    def set_overlap(self, mask: int):
+        """Mask of OVERLAP_MOMENTS_WALK (default) and OVERLAP_NEAR_FAR: independent stages of
+        fmm_forces run on a second stream."""
+        _check(self.lib.fmm_set_overlap(self.h, int(mask)), "fmm_set_overlap")
 
     def set_wait_limit(self, polls: int = 0, never_satisfied: bool = False):
         """Limit of the walk's look-back wait (0: default); never_satisfied for tests of the

@@ -992,3 +992,50 @@ def test_forces_graph_replays_bitwise(fmm, torch_cuda, precision):
         with pytest.raises(fmm.FMMError):
             f.forces_graph(4, 0.6, 1, torch.empty((len(mb), 3), dtype=torch.float64, device="cuda"), None)
     f.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+def test_overlap_masks_bitwise_identical(fmm, torch_cuda, precision):
+    """fmm_set_overlap only changes which stages run concurrently: every mask gives the same
+    bits, for a single system and a batch, direct and recorded as a CUDA graph (whose
+    recording then holds the fork to the second stream and the join back); unknown bits
+    are refused."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    x, m = synth.plummer(30000, 41)
+    xb, mb, off = synth.batch(6, 72, 500, 5000)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    results = {}
+    for mask in (0, fmm.OVERLAP_MOMENTS_WALK, fmm.OVERLAP_NEAR_FAR,
+                 fmm.OVERLAP_MOMENTS_WALK | fmm.OVERLAP_NEAR_FAR):
+        f = fmm.FMM(0, precision=precision, stream=stream)
+        f.set_overlap(mask)
+        outs = []
+        for xs, ms, offs in ((x, m, None), (xb, mb, off)):
+            N = len(ms)
+            a = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+            ph = torch.empty(N, dtype=torch.float64, device="cuda")
+            g = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+            with torch.cuda.stream(stream):
+                if offs is None:
+                    f.build(dev(xs), dev(ms), 32)
+                else:
+                    f.build_batch(dev(xs), dev(ms), offs, 32)
+                f.forces(4, 0.6, 1, a, ph)
+                f.forces_graph(4, 0.6, 1, g, None)
+            stream.synchronize()
+            assert torch.equal(g, a), (precision, mask)
+            outs.append((a.cpu().numpy(), ph.cpu().numpy()))
+        results[mask] = outs
+        if mask == 0:
+            with pytest.raises(fmm.FMMError):
+                f.set_overlap(4)
+        f.close()
+    ref = results[0]
+    for mask, outs in results.items():
+        for (a, ph), (ra, rph) in zip(outs, ref):
+            assert np.array_equal(a, ra) and np.array_equal(ph, rph), (precision, mask)
