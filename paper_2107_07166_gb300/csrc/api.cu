@@ -108,6 +108,7 @@ int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
             GB_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
             c->own_stream = true;
         }
+        GB_CUDA(cudaMallocHost(&c->hpin, gbfmm::HPIN_BYTES));
         // the side stream and its fork/join events (independent stages of fmm_forces)
         GB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         GB_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
@@ -118,6 +119,7 @@ int fmm_create(fmm_ctx** out, int device, int precision, void* cuda_stream) {
         if (c->side) cudaStreamDestroy(c->side);
         if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         if (c->join_ev) cudaEventDestroy(c->join_ev);
+        if (c->hpin) cudaFreeHost(c->hpin);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return rc;
@@ -154,6 +156,7 @@ int fmm_destroy(fmm_ctx* c) {
         }
         if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         if (c->join_ev) cudaEventDestroy(c->join_ev);
+        if (c->hpin) cudaFreeHost(c->hpin);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -347,10 +350,10 @@ int fmm_forces(fmm_ctx* c, int p, double theta, int variant, double* acc, double
         run_finish_dispatch(c, p, variant, want_pot, acc_d, pot_d);
         stage_end(c, ST_L2P);
         if (fused) {  // a traversal stack that would have overflowed (none is expected)
-            int over = 0;
-            GB_CUDA(cudaMemcpyAsync(&over, c->errflag.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            GB_CUDA(cudaStreamSynchronize(c->stream));
-            if (over) throw FmmError{FMM_ERR_CAPACITY, "fused schedule: traversal stack exceeded"};
+            HostReads hr(c);
+            int* over = hr.read<int>(c->errflag.as<int>() + 2);
+            hr.wait();
+            if (*over) throw FmmError{FMM_ERR_CAPACITY, "fused schedule: traversal stack exceeded"};
         }
         if (!acc_dev)
             GB_CUDA(cudaMemcpyAsync(acc, acc_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));

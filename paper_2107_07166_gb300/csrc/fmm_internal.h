@@ -49,7 +49,7 @@ struct NodeView {
     const float4* zl;  // (lo(Z), 0)
 };
 
-// Chunked work over per-cell segments (see build_items in walk.cu).
+// Chunked work over per-cell segments (see build_item_sets in walk.cu).
 struct ItemSet {
     DevBuf items;   // int4 (cell, entry begin, entry end, -)
     DevBuf fo, po;  // long long [n + 1]: full-chunk offsets, partial-chunk ranks
@@ -190,6 +190,10 @@ struct fmm_ctx {
     // `stream` by events
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // page-locked host words for the small device values the host reads (list sizes,
+    // status flags): copies into them are asynchronous, so one read point costs one stream
+    // synchronisation however many values it reads (gbfmm::HostReads)
+    void* hpin = nullptr;
     int overlap = FMM_OVERLAP_MOMENTS_WALK;    // fmm_set_overlap
     // timing
     cudaEvent_t ev[2 * gbfmm::ST_COUNT] = {};
@@ -223,7 +227,6 @@ int build_tree(fmm_ctx* c, const double* x_dev, const double* m_dev);
 
 // walk (walk.cu)
 void run_walk(fmm_ctx* c, double theta);
-void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it);
 
 // expansions (expansion_p*.cu, dispatched in expansion.cu)
 void run_moments(fmm_ctx* c, int p);
@@ -234,6 +237,27 @@ void run_far_field(fmm_ctx* c, int p, int variant, bool want_pot);
 void run_p2p(fmm_ctx* c, bool want_pot);
 void run_p2p_prepare(fmm_ctx* c);
 void run_p2p_kernels(fmm_ctx* c, bool want_pot);
+
+// Small device values read on the host at one point: read() queues an asynchronous copy
+// into the context's page-locked words and returns where the value will be; wait()
+// synchronises the stream once, after which every returned pointer holds its value.
+constexpr size_t HPIN_BYTES = 4096;
+struct HostReads {
+    fmm_ctx* c;
+    size_t off = 0;
+    explicit HostReads(fmm_ctx* ctx) : c(ctx) {}
+    template <class T>
+    T* read(const void* dev_src, size_t count = 1) {
+        off = (off + 15) & ~(size_t)15;
+        size_t bytes = sizeof(T) * count;
+        if (off + bytes > HPIN_BYTES) throw FmmError{FMM_ERR_CAPACITY, "host read words exhausted"};
+        T* dst = reinterpret_cast<T*>(static_cast<char*>(c->hpin) + off);
+        off += bytes;
+        cuda_check(cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDeviceToHost, c->stream), "host read");
+        return dst;
+    }
+    void wait() { cuda_check(cudaStreamSynchronize(c->stream), "host read wait"); }
+};
 
 // The side stream: fork_side makes c->side wait for the work queued on c->stream so far;
 // while a SideLaunches is alive, the launchers (which all queue on c->stream) queue on the

@@ -632,14 +632,12 @@ static void p2p_prepare(fmm_ctx* c) {
     // partial slots of the walk's pairs: read once per walk (with the flag of the ring
     // class sort above), so that later evaluations on the same lists never wait on the host
     if (c->p2p_total_gen != c->walk_gen) {
-        long long total = 0;
-        GB_CUDA(cudaMemcpyAsync(&total, c->p2p_pbase.as<long long>() + c->n_nodes, sizeof(long long),
-                                cudaMemcpyDeviceToHost, s));
-        int serr = 0;
-        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaStreamSynchronize(s));
-        sort_err_throw(c, serr);
-        c->p2p_total = total;
+        HostReads hr(c);
+        const long long* total = hr.read<long long>(c->p2p_pbase.as<long long>() + c->n_nodes);
+        const int* serr = hr.read<int>(sort_err(c));
+        hr.wait();
+        sort_err_throw(c, *serr);
+        c->p2p_total = *total;
         c->p2p_total_gen = c->walk_gen;
     }
     long long total = c->p2p_total;
@@ -853,9 +851,12 @@ static void gather_setup(fmm_ctx* c) {
     item_slots_k<<<grid_for(ni, PB), PB, 0, s>>>(ni, it.items.as<int4>(), c->ncount.as<int>(), c->flags.as<long long>());
     GB_LAUNCH("item_slots_k");
     scan_i64_from_i64(c, c->flags.as<long long>(), ni, c->p2p_islot.as<long long>());
-    GB_CUDA(cudaMemcpyAsync(&c->p2p_nslots, c->p2p_islot.as<long long>() + ni, sizeof(long long),
-                            cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
+    HostReads hr(c);
+    const long long* nslots = hr.read<long long>(c->p2p_islot.as<long long>() + ni);
+    const int* serr = hr.read<int>(sort_err(c));  // the ring class sort of the pair kernels' set-up
+    hr.wait();
+    sort_err_throw(c, *serr);
+    c->p2p_nslots = *nslots;
     c->gather_gen = c->walk_gen;
 }
 

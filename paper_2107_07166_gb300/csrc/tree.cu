@@ -775,11 +775,17 @@ int build_tree(fmm_ctx* c, const double* x, const double* m) {
             GB_CUDA(cudaLaunchCooperativeKernel((const void*)split_levels_k, grid, block, args, 0, s));
             GB_LAUNCH("split_levels_k");
         }
-        GB_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaMemcpyAsync(&bad, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         int serr = 0;
-        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaStreamSynchronize(s));
+        {
+            HostReads hr(c);
+            LevelCtl* hh = hr.read<LevelCtl>(ctl);
+            int* hbad = hr.read<int>(c->errflag.p);
+            int* hserr = hr.read<int>(sort_err(c));
+            hr.wait();
+            h = *hh;
+            bad = *hbad;
+            serr = *hserr;
+        }
         if (bad) return FMM_ERR_INVALID;
         sort_err_throw(c, serr);
         if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "octree: a level tile waited too long for the tiles before it"};

@@ -316,31 +316,51 @@ __global__ void items_fill_k(const long long* __restrict__ seg, int n, int CH, c
     if (po[x + 1] > po[x]) items[nfull_total + po[x]] = make_int4(x, (int)(e0 + nf * CH), (int)e1, 0);
 }
 
-void build_items(fmm_ctx* c, const long long* seg, int n, int CH, ItemSet& it) {
+// Work items of two item sets in one host round trip: both sets' chunk counts and scans,
+// one read of their totals (with the segment sorts' status and the P2P partial total),
+// then both fills.
+static void build_item_sets(fmm_ctx* c, int n, const long long* seg_a, int ch_a, ItemSet& a,
+                            const long long* seg_b, int ch_b, ItemSet& b) {
     cudaStream_t s = c->stream;
-    ensure(c->seg_cnt, sizeof(int) * (size_t)(2 * n + 2));
-    int* nfull = c->seg_cnt.as<int>();
-    int* npart = nfull + n + 1;
-    ensure(it.fo, sizeof(long long) * (size_t)(n + 1));
-    ensure(it.po, sizeof(long long) * (size_t)(n + 1));
-    items_count_k<<<grid_for(n, WB), WB, 0, s>>>(seg, n, CH, nfull, npart);
-    GB_LAUNCH("items_count_k");
-    scan_i64(c, nfull, n, it.fo.as<long long>());
-    scan_i64(c, npart, n, it.po.as<long long>());
-    long long tot[2];
-    GB_CUDA(cudaMemcpyAsync(&tot[0], it.fo.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(&tot[1], it.po.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    int serr = 0;  // the segment sorts before this read
-    GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    sort_err_throw(c, serr);
-    it.n_full = tot[0];
-    it.n_items = tot[0] + tot[1];
-    it.chunk = CH;
-    ensure(it.items, sizeof(int4) * (size_t)(it.n_items > 0 ? it.n_items : 1));
-    items_fill_k<<<grid_for(n, WB), WB, 0, s>>>(seg, n, CH, it.fo.as<long long>(), it.po.as<long long>(), it.n_full,
-                                                it.items.as<int4>());
-    GB_LAUNCH("items_fill_k");
+    ensure(c->seg_cnt, sizeof(int) * (size_t)(4 * n + 4));
+    int* cnt_a = c->seg_cnt.as<int>();
+    int* cnt_b = cnt_a + 2 * n + 2;
+    ItemSet* sets[2] = {&a, &b};
+    const long long* segs[2] = {seg_a, seg_b};
+    int chs[2] = {ch_a, ch_b};
+    int* cnts[2] = {cnt_a, cnt_b};
+    for (int k = 0; k < 2; k++) {
+        ItemSet& it = *sets[k];
+        int* nfull = cnts[k];
+        int* npart = nfull + n + 1;
+        ensure(it.fo, sizeof(long long) * (size_t)(n + 1));
+        ensure(it.po, sizeof(long long) * (size_t)(n + 1));
+        items_count_k<<<grid_for(n, WB), WB, 0, s>>>(segs[k], n, chs[k], nfull, npart);
+        GB_LAUNCH("items_count_k");
+        scan_i64(c, nfull, n, it.fo.as<long long>());
+        scan_i64(c, npart, n, it.po.as<long long>());
+    }
+    HostReads hr(c);
+    const long long* tot[2][2];
+    for (int k = 0; k < 2; k++) {
+        tot[k][0] = hr.read<long long>(sets[k]->fo.as<long long>() + n);
+        tot[k][1] = hr.read<long long>(sets[k]->po.as<long long>() + n);
+    }
+    const long long* p2p_total = hr.read<long long>(c->p2p_pbase.as<long long>() + n);
+    const int* hserr = hr.read<int>(sort_err(c));  // the segment sorts before this read
+    hr.wait();
+    sort_err_throw(c, *hserr);
+    c->p2p_total = *p2p_total;
+    for (int k = 0; k < 2; k++) {
+        ItemSet& it = *sets[k];
+        it.n_full = *tot[k][0];
+        it.n_items = *tot[k][0] + *tot[k][1];
+        it.chunk = chs[k];
+        ensure(it.items, sizeof(int4) * (size_t)(it.n_items > 0 ? it.n_items : 1));
+        items_fill_k<<<grid_for(n, WB), WB, 0, s>>>(segs[k], n, chs[k], it.fo.as<long long>(), it.po.as<long long>(),
+                                                    it.n_full, it.items.as<int4>());
+        GB_LAUNCH("items_fill_k");
+    }
 }
 
 static int bits_for(int64_t nn) {
@@ -388,13 +408,13 @@ void run_walk(fmm_ctx* c, double theta) {
             walk_advance_k<<<1, 1, 0, s>>>(cnt, par, max_fr);
             GB_LAUNCH("walk_advance_k");
         }
-        WalkCounters h;
-        int hmax = 0;
-        GB_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(WalkCounters), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaMemcpyAsync(&hmax, max_fr, sizeof(int), cudaMemcpyDeviceToHost, s));
-        int serr = 0;  // a sort of the build (node order by leaf size) that gave up
-        GB_CUDA(cudaMemcpyAsync(&serr, sort_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
-        GB_CUDA(cudaStreamSynchronize(s));
+        HostReads hr(c);
+        const WalkCounters* hh = hr.read<WalkCounters>(cnt);
+        const int* hhmax = hr.read<int>(max_fr);
+        const int* hserr = hr.read<int>(sort_err(c));  // a sort of the build (node order by leaf size) that gave up
+        hr.wait();
+        WalkCounters h = *hh;
+        int hmax = *hhmax, serr = *hserr;
         sort_err_throw(c, serr);
         if (h.err) throw FmmError{FMM_ERR_TIMEOUT, "walk: a frontier tile waited too long for the tiles before it"};
         if (h.nf[0] != 0 || h.nf[1] != 0) throw FmmError{FMM_ERR_CAPACITY, "walk did not finish in 2 x levels + 2 steps"};
@@ -451,10 +471,11 @@ void run_walk(fmm_ctx* c, double theta) {
         GB_LAUNCH("p2p_slot_of_k");
     }
     // work items: m2l_chunk M2L sources (default 32) and p2p_chunk P2P entries (64) per chunk
-    build_items(c, c->m2l_seg.as<long long>(), (int)nn, c->m2l_chunk, c->m2l_items);
-    build_items(c, c->p2p_seg.as<long long>(), (int)nn, c->p2p_chunk, c->p2p_items);
+    build_item_sets(c, (int)nn, c->m2l_seg.as<long long>(), c->m2l_chunk, c->m2l_items, c->p2p_seg.as<long long>(),
+                    c->p2p_chunk, c->p2p_items);
     c->list_theta = theta;
     c->walk_gen++;
+    c->p2p_total_gen = c->walk_gen;  // read with the item totals
 }
 
 }  // namespace gbfmm
