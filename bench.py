@@ -615,7 +615,7 @@ def run_gbfmm(args):
     # instructions it takes, so the P2P line reads low while its binary64 pipe is busy
     roofline_stages = {st: stage_roofline(st) for st in ("m2l", "p2p") if stage_avg[st]}
     # the tree build (bounding cube .. r_max) against the measured HBM copy bandwidth, on the
-    # survey's byte model of the build (and its one-pass minimum)
+    # byte model of the build above (and its one-pass minimum)
     hbm = measured_peaks().get("hbm_gbs")
     roofline_build = None
     if stage_avg["build"] and hbm:
@@ -716,8 +716,8 @@ def cpu_baseline():
                       f"one build+forces, {dt:.1f} s single-threaded"}
 
 
-# per-step sample of the reference arm: a quarter of the workload, so that the driver's
-# 20 timed + 5 warm-up steps end within a few minutes on one host core
+# per-step sample of the reference arm: a quarter of the workload, so that a run of 20
+# timed + 5 warm-up steps ends within a few minutes on one host core
 REF_SAMPLE_N = 1 << 18
 
 
