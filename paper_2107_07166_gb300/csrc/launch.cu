@@ -296,7 +296,7 @@ constexpr size_t rs_sweep_smem() {
 }
 
 template <class K, bool V>
-__global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 3 : 2) rs_sweep_k(const K* __restrict__ kin,
+__global__ void __launch_bounds__(RS_BLOCK, sizeof(K) == 4 ? 4 : 2) rs_sweep_k(const K* __restrict__ kin,
                                                        const uint32_t* __restrict__ vin, K* __restrict__ kout,
                                                        uint32_t* __restrict__ vout, int64_t n, int shift,
                                                        const uint32_t* __restrict__ gofs,
