@@ -143,7 +143,7 @@ int fmm_destroy(fmm_ctx* c) {
                           &c->acc_s, &c->pot_s, &c->out_stage, &c->diag_tmp, &c->m2l_items.items,
                           &c->m2l_items.fo, &c->m2l_items.po, &c->p2p_items.items, &c->p2p_items.fo,
                           &c->p2p_items.po, &c->m2l_part, &c->p2p_islot, &c->p2p_ipart, &c->cmom, &c->pos4,
-                          &c->momT, &c->nk, &c->zhl, &c->m2l_kpart, &c->p2p_sep, &c->p2p_cls, &c->p2p_cls2, &c->p2p_list, &c->p2p_list2, &c->p2p_tab, &c->m2m_tmp,
+                          &c->momT, &c->nk, &c->zhl, &c->m2l_kpart, &c->p2p_sep, &c->p2p_cls, &c->p2p_cls2, &c->p2p_list, &c->p2p_list2, &c->p2p_tab, &c->p2p_desc, &c->m2m_tmp,
                           &c->lf_x, &c->lf_v,
                           &c->lf_m, &c->lf_a, &c->lf_diag, &c->tune_acc, &c->lvl_ctl, &c->lvl_status, &c->p2p_direct, &c->sys_off, &c->sys_k, &c->sys_v, &c->sys_diag};
         for (DevBuf* b : bufs) release(*b);

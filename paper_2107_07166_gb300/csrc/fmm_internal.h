@@ -158,6 +158,7 @@ struct fmm_ctx {
     gbfmm::DevBuf p2p_cls, p2p_cls2;           // ring-kernel class keys of the P2P pairs (+ sort scratch)
     gbfmm::DevBuf p2p_list, p2p_list2;         // P2P pair ids in class order (+ sort scratch)
     gbfmm::DevBuf p2p_tab;                     // ring class table: start, count, warp prefix per width
+    gbfmm::DevBuf p2p_desc;                    // ring descriptors of the P2P pairs in class order (binary32)
     int64_t walk_gen = 0, p2p_cls_gen = -1;    // walks run so far; walk the classes belong to
     int64_t gather_gen = -1;                   // walk the P2P item slots and entry bases belong to
     int64_t p2p_total_gen = -1;                // walk p2p_total belongs to

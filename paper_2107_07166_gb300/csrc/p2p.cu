@@ -377,6 +377,81 @@ __global__ void p2p_ring_tab_k(RingTab* __restrict__ tab) {
     tab->start[0] = tab->count[0] = tab->wpre[0] = 0;
 }
 
+// Everything the ring kernel needs of one leaf pair, in class order, as 64 aligned bytes:
+// the lane leaf L (the larger one, A on a tie and for a self pair) and the ring leaf R,
+// their first particles, L's count, both partial slots, and the centre separation
+// Z_L - Z_R as double-float words.  A segment lane then waits for one load before it
+// fetches particles, instead of the chain list -> pair -> leaf tables.
+struct __align__(32) RingDesc {
+    int fL, fR, nL, self;
+    long long oL, oR;
+    float rxh, rxl, ryh, ryl;
+    float rzh, rzl, pad0, pad1;
+};
+static_assert(sizeof(RingDesc) == 64, "RingDesc: two 32-byte sectors");
+
+// One thread per pair in class order: the ring descriptors, and the centre separation of
+// the pairs with a leaf above 32 particles (class 33, read by p2p_big_k at 3k).  The
+// separation is formed in binary64 and rounded to double-float words, as p2p_sep_k does;
+// a lane leaf B takes Z_B - Z_A, the exact negation of Z_A - Z_B.
+__global__ void p2p_ring_desc_k(int64_t n, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                                const int2* __restrict__ pairs, const long long* __restrict__ pslot,
+                                const int* __restrict__ nfirst, const int* __restrict__ ncount,
+                                const double* __restrict__ Zx, const double* __restrict__ Zy,
+                                const double* __restrict__ Zz, RingDesc* __restrict__ desc, df64* __restrict__ sep) {
+    int64_t li = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (li >= n) return;
+    int k = (int)list[li];
+    int2 p = pairs[k];
+    double dx = Zx[p.x] - Zx[p.y], dy = Zy[p.x] - Zy[p.y], dz = Zz[p.x] - Zz[p.y];
+    if (ring_cls(keys[li]) > 32) {
+        sep[3 * k] = to_df(dx);
+        sep[3 * k + 1] = to_df(dy);
+        sep[3 * k + 2] = to_df(dz);
+        return;
+    }
+    bool self = p.x == p.y;
+    int nA = ncount[p.x], nB = ncount[p.y];
+    bool laneA = nA >= nB;
+    int L = laneA ? p.x : p.y, R = laneA ? p.y : p.x;
+    long long oA = pslot[2 * k], oB = self ? 0 : pslot[2 * k + 1];
+    if (!laneA) {
+        dx = -dx;
+        dy = -dy;
+        dz = -dz;
+    }
+    df64 rx = to_df(dx), ry = to_df(dy), rz = to_df(dz);
+    RingDesc d;
+    d.fL = nfirst[L];
+    d.fR = nfirst[R];
+    d.nL = laneA ? nA : nB;
+    d.self = self ? 1 : 0;
+    d.oL = laneA ? oA : oB;
+    d.oR = laneA ? oB : oA;
+    d.rxh = rx.hi;
+    d.rxl = rx.lo;
+    d.ryh = ry.hi;
+    d.ryl = ry.lo;
+    d.rzh = rz.hi;
+    d.rzl = rz.lo;
+    d.pad0 = d.pad1 = 0.f;
+    desc[li] = d;
+}
+
+// a ring descriptor in two 32-byte loads through the non-coherent path
+__device__ __forceinline__ RingDesc load_desc(const RingDesc* __restrict__ p) {
+    RingDesc d;
+    int* w = reinterpret_cast<int*>(&d);
+    const int* s = reinterpret_cast<const int*>(p);
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+        asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(w[8 * h]), "=r"(w[8 * h + 1]), "=r"(w[8 * h + 2]), "=r"(w[8 * h + 3]), "=r"(w[8 * h + 4]),
+              "=r"(w[8 * h + 5]), "=r"(w[8 * h + 6]), "=r"(w[8 * h + 7])
+            : "l"(s + 8 * h));
+    return d;
+}
+
 // one ring step of a lane particle a with ring particle b, positions as double-float words
 // (hi, lo) in binary32 arithmetic: the pair force is formed once, -m_b d r^-3 goes to a's
 // sum and +m_a d r^-3 to b's travelling sum (potentials -m r^-1); r = 0 adds nothing.
@@ -405,6 +480,18 @@ __device__ __forceinline__ void ring_pair(const float4& ah, const float4& al, fl
     }
 }
 
+// a double-float particle (32 bytes at a 16-byte aligned address in the packed array) in
+// two 16-byte loads; the struct alone promises 4 bytes
+__device__ __forceinline__ PState<df64> ld_pstate_g(const PState<df64>* __restrict__ p) {
+    const float4* v = reinterpret_cast<const float4*>(p);
+    float4 u = __ldg(v), t = __ldg(v + 1);
+    return PState<df64>{df64(u.x, u.y), df64(u.z, u.w), df64(t.x, t.y), df64(t.z, t.w)};
+}
+// one binary32 partial (16 bytes, 16-byte aligned in the partial buffer) in one store
+__device__ __forceinline__ void st_quad(Quad<float>* p, float x, float y, float z, float w) {
+    *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+}
+
 // lane particles held at once by a ring lane (chunks of the lane leaf per pass)
 constexpr int RING_CHUNKS = 2;
 
@@ -424,11 +511,8 @@ constexpr int RING_CHUNKS = 2;
 // Eight blocks per SM (64 registers): 28 -> 32 warps per SM took 10% off the binary32
 // P2P; 48 registers spilled into the ring loop and lost it again.
 template <bool POT>
-__global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ tab, const uint32_t* __restrict__ list,
-                                                 const int2* __restrict__ pairs, const long long* __restrict__ pslot,
-                                                 const int* __restrict__ nfirst, const int* __restrict__ ncount,
-                                                 const PState<df64>* __restrict__ pos, const df64* __restrict__ sep,
-                                                 Quad<float>* __restrict__ part) {
+__global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ tab, const RingDesc* __restrict__ desc,
+                                                 const PState<df64>* __restrict__ pos, Quad<float>* __restrict__ part) {
     // the ring leaf twice in a row per segment (slots 0..w-1, 0..w-1): lane i reads slot
     // i + k without wrapping, at a fixed stride from one pointer
     __shared__ float4 sH[PW][64], sL[PW][64];
@@ -455,37 +539,19 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
         int i = live ? lane - sg * W : 0, base = live ? sg * W : 0;
         int64_t li = (q - tw[W]) * per + sg;
         bool ok = live && li < tc[W];
-        int nA = 0, nB = 0, fA = 0, fB = 0;
-        long long oA = 0, oB = 0;
-        bool self = false;
-        df64 rx = df64(0.f), ry = df64(0.f), rz = df64(0.f);
-        if (ok) {
-            int k = (int)list[ts[W] + li];
-            int2 pr = pairs[k];
-            self = pr.x == pr.y;
-            nA = ncount[pr.x];
-            nB = ncount[pr.y];
-            fA = nfirst[pr.x];
-            fB = nfirst[pr.y];
-            oA = pslot[2 * k];
-            oB = self ? 0 : pslot[2 * k + 1];
-            rx = sep[3 * k];
-            ry = sep[3 * k + 1];
-            rz = sep[3 * k + 2];
-        }
-        // lane leaf: A unless B is the larger; its particles are shifted by its side of R
-        bool laneA = nA >= nB;
-        int fL = laneA ? fA : fB, nL = laneA ? nA : nB, fR = laneA ? fB : fA;
-        long long oL = laneA ? oA : oB, oR = laneA ? oB : oA;
-        if (!laneA) {
-            rx = -rx;
-            ry = -ry;
-            rz = -rz;
-        }
+        // one descriptor load, then the ring particle and the first two lane particles
+        // together: two memory latencies before the ring starts
+        RingDesc d{};
+        if (ok) d = load_desc(desc + ts[W] + li);
+        bool self = d.self != 0;
+        int fL = d.fL, nL = d.nL;
+        long long oL = d.oL, oR = d.oR;
+        df64 rx(d.rxh, d.rxl), ry(d.ryh, d.ryl), rz(d.rzh, d.rzl);
+        PState<df64> rb{};
+        if (ok) rb = ld_pstate_g(pos + d.fR + i);  // i < W = the ring leaf's count
         __syncwarp();
-        if (ok) {  // i < W = the ring leaf's count; the segment's rows are [2 base, 2 base + 2 W)
-            PState<df64> b = pos[fR + i];
-            float4 h = make_float4(b.x.hi, b.y.hi, b.z.hi, b.m.hi), lo = make_float4(b.x.lo, b.y.lo, b.z.lo, 0.f);
+        if (ok) {  // the segment's rows are [2 base, 2 base + 2 W)
+            float4 h = make_float4(rb.x.hi, rb.y.hi, rb.z.hi, rb.m.hi), lo = make_float4(rb.x.lo, rb.y.lo, rb.z.lo, 0.f);
             sH[w][2 * base + i] = h;
             sH[w][2 * base + W + i] = h;
             sL[w][2 * base + i] = lo;
@@ -507,7 +573,7 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
                 ah[r] = al[r] = acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
                 ma[r] = 0.f;
                 if (mine[r]) {
-                    PState<df64> qa = pos[fL + g];
+                    PState<df64> qa = ld_pstate_g(pos + fL + g);
                     df64 x = rx + qa.x, y = ry + qa.y, z = rz + qa.z;
                     ah[r] = make_float4(x.hi, y.hi, z.hi, 0.f);
                     al[r] = make_float4(x.lo, y.lo, z.lo, 0.f);
@@ -529,9 +595,9 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
             }
 #pragma unroll
             for (int r = 0; r < RING_CHUNKS; r++)
-                if (mine[r]) part[oL + (ch + r) * W + i] = Quad<float>{acc[r].x, acc[r].y, acc[r].z, POT ? acc[r].w : 0.f};
+                if (mine[r]) st_quad(part + oL + (ch + r) * W + i, acc[r].x, acc[r].y, acc[r].z, POT ? acc[r].w : 0.f);
         }
-        if (ok && !self) part[oR + i] = Quad<float>{bx, by, bz, POT ? bp : 0.f};
+        if (ok && !self) st_quad(part + oR + i, bx, by, bz, POT ? bp : 0.f);
         __syncwarp();
     }
 }
@@ -643,9 +709,22 @@ static void p2p_prepare(fmm_ctx* c) {
     long long total = c->p2p_total;
     ensure(c->p2p_part, sizeof(Quad<T>) * (size_t)(total > 0 ? total : 1));
     ensure(c->p2p_sep, sizeof(S) * 3 * (size_t)(c->n_p2p > 0 ? c->n_p2p : 1));
-    p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
-                                                     c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
-    GB_LAUNCH("p2p_sep_k");
+    if constexpr (P2PRing<T>::value) {
+        // ring descriptors in class order (and the separations of the few large-leaf pairs)
+        int64_t np = c->n_p2p;
+        ensure(c->p2p_desc, sizeof(RingDesc) * (size_t)(np > 0 ? np : 1));
+        if (np > 0) {
+            p2p_ring_desc_k<<<grid_for(np, PB), PB, 0, s>>>(
+                np, c->p2p_cls.as<uint64_t>(), c->p2p_list.as<uint32_t>(), c->p2p_pairs.as<int2>(),
+                c->p2p_off.as<long long>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->nZx.as<double>(),
+                c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_desc.as<RingDesc>(), c->p2p_sep.as<df64>());
+            GB_LAUNCH("p2p_ring_desc_k");
+        }
+    } else {
+        p2p_sep_k<S><<<grid_for(c->n_p2p, PB), PB, 0, s>>>(c->n_p2p, c->p2p_pairs.as<int2>(), c->nZx.as<double>(),
+                                                         c->nZy.as<double>(), c->nZz.as<double>(), c->p2p_sep.as<S>());
+        GB_LAUNCH("p2p_sep_k");
+    }
 }
 
 // the pair kernels on the prepared lists (no host read, no allocation)
@@ -665,7 +744,11 @@ static void p2p_kernels(fmm_ctx* c, bool want_pot) {
         if (np > 0) {
             const RingTab* tab = c->p2p_tab.as<RingTab>();
             const uint32_t* lst = c->p2p_list.as<uint32_t>();
-            auto run = [&](auto kern, int64_t bl) {
+            const RingDesc* dsc = c->p2p_desc.as<RingDesc>();
+            auto ring = [&](auto kern, int64_t bl) {
+                kern<<<(unsigned)bl, PB, 0, s>>>(tab, dsc, c->pos4.as<PState<S>>(), c->p2p_part.as<Quad<T>>());
+            };
+            auto big = [&](auto kern, int64_t bl) {
                 kern<<<(unsigned)bl, PB, 0, s>>>(tab, lst, c->p2p_pairs.as<int2>(), c->p2p_off.as<long long>(),
                                                  c->nfirst.as<int>(), c->ncount.as<int>(), c->pos4.as<PState<S>>(),
                                                  c->p2p_sep.as<S>(), c->p2p_part.as<Quad<T>>());
@@ -674,14 +757,14 @@ static void p2p_kernels(fmm_ctx* c, bool want_pot) {
             int64_t ring_bl = (np + PW - 1) / PW;
             if (ring_bl > cap) ring_bl = cap;
             if (want_pot) {
-                run(p2p_ring_k<true>, ring_bl);
+                ring(p2p_ring_k<true>, ring_bl);
                 GB_LAUNCH("p2p_ring_k");
-                run(p2p_big_k<T, true>, dev_sms);
+                big(p2p_big_k<T, true>, dev_sms);
                 GB_LAUNCH("p2p_big_k");
             } else {
-                run(p2p_ring_k<false>, ring_bl);
+                ring(p2p_ring_k<false>, ring_bl);
                 GB_LAUNCH("p2p_ring_k");
-                run(p2p_big_k<T, false>, dev_sms);
+                big(p2p_big_k<T, false>, dev_sms);
                 GB_LAUNCH("p2p_big_k");
             }
         }
@@ -772,6 +855,27 @@ __device__ __forceinline__ df64 shfl_g(df64 v, int src) {
 
 // sum of the partials of entries e0, e0 + step, ... < e1 for one slot, four in flight; the
 // entries' slot runs are consecutive (cnt slots each), entry e0's starting at b0
+// One partial in one load: the partial buffer holds 16-byte (binary32) or 32-byte
+// (binary64, double-float) records from an aligned base, written by an earlier kernel.
+// The records' own types promise only the alignment of their words, and four word
+// loads per record cross each 32-byte sector four times.
+__device__ __forceinline__ Quad<float> ld_part(const Quad<float>* __restrict__ p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return Quad<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld_part(const Quad<double>* __restrict__ p) {
+    Quad<double> q;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(q.x), "=d"(q.y), "=d"(q.z), "=d"(q.w) : "l"(p));
+    return q;
+}
+__device__ __forceinline__ Quad<df64> ld_part(const Quad<df64>* __restrict__ p) {
+    float v[8];
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+    return Quad<df64>{df64(v[0], v[1]), df64(v[2], v[3]), df64(v[4], v[5]), df64(v[6], v[7])};
+}
+
 template <class G, class PT>
 __device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, long long b0, int cnt, int slot,
                                               const Quad<PT>* __restrict__ part) {
@@ -782,7 +886,7 @@ __device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, long lon
     for (; e + 3 * step < e1; e += 4 * step, p += 4 * stride) {
         Quad<PT> q[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) q[u] = p[u * stride];
+        for (int u = 0; u < 4; u++) q[u] = ld_part(p + u * stride);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             acc.x = acc_add(acc.x, q[u].x);
@@ -792,7 +896,7 @@ __device__ __forceinline__ Quad<G> gather_run(int e0, int e1, int step, long lon
         }
     }
     for (; e < e1; e += step, p += stride) {
-        Quad<PT> q = *p;
+        Quad<PT> q = ld_part(p);
         acc.x = acc_add(acc.x, q.x);
         acc.y = acc_add(acc.y, q.y);
         acc.z = acc_add(acc.z, q.z);
