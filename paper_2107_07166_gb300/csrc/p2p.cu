@@ -83,7 +83,7 @@ __device__ __forceinline__ double sq_to_f64(float v) {
                  : 0.0;
 }
 
-// s^(-3/2) (and, if IR, s^(-1/2)) for a binary64 s > 0: five binary64 operations for
+// s^(-3/2) (and, if IR, s^(-1/2)) for a binary64 s > 0: three binary64 operations for
 // s^(-3/2), where the library reciprocal square root and the cube take seven.  The seed
 // y0 ~ s^(-1/2) is the binary32 reciprocal square root of the mantissa of s rescaled into
 // [1, 4), taken back to s's scale by integer exponent arithmetic, so the seed costs no
@@ -94,13 +94,16 @@ __device__ __forceinline__ double sq_to_f64(float v) {
 // the binomial series cut after e^2 leave remainders below 2^-58, under binary64's own
 // rounding.  The e^2 terms are below 2^-40 of the result and need only ~12 correct bits,
 // so they are formed in binary32 (CPU emulation on 500 000 s with a seed perturbed by up
-// to 4 ulp: the same 1.96-ulp maximum error as the all-binary64 form).  Exponents far from
-// 0 (subnormal, huge or non-finite s) take the library path.
+// to 4 ulp: the same 1.96-ulp maximum error as the all-binary64 form).  t and y0^3 come
+// from y0's 24-bit integer significand by integer products, exactly the values of the
+// binary64 products y0 y0 and t y0 (checked on 300 000 significands and exponents), which
+// leaves e = 1 - s t and the two fused multiply-adds of the series to the binary64 unit.
+// Exponents far from 0 (|e| > 600: subnormal, huge or non-finite s) take the library path.
 template <bool IR>
 __device__ __forceinline__ void rinv_f64(double s, double& w3, double& ir) {
     long long b = __double_as_longlong(s);
     int e = (int)(b >> 52) - 1023;  // s > 0: no sign bit
-    if (e < -1000 || e > 1000) {
+    if (e < -600 || e > 600) {  // |e| <= 600 keeps y0^2 and y0^3 below normal binary64 numbers
         double r = rsqrt(s);
         w3 = r * r * r;
         if (IR) ir = r;
@@ -109,11 +112,28 @@ __device__ __forceinline__ void rinv_f64(double s, double& w3, double& ir) {
     int k = e >> 1;  // s = 2^(2k) s', s' in [1, 4)
     unsigned sb = ((unsigned)(e - 2 * k + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
     unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(sb)));  // ~ s'^(-1/2), in (0.5, 1]
-    long long y0b = ((long long)((int)(yb >> 23) - 127 - k + 1023) << 52) | ((long long)(yb & 0x7fffff) << 29);
+    int ey = (int)(yb >> 23) - 127 - k;  // y0 = m 2^(ey - 23), m the 24-bit significand
+    long long y0b = ((long long)(ey + 1023) << 52) | ((long long)(yb & 0x7fffff) << 29);
     double y0 = __longlong_as_double(y0b);  // 2^-k s'^(-1/2) ~ s^(-1/2), exactly the binary32 value
-    double t = y0 * y0;
+    // t = y0^2 and w0 = y0^3 rounded to nearest (what two binary64 products give) from the
+    // integer significand: m^2 < 2^48 is exact, m^3 < 2^72 is rounded to 53 bits, ties to even
+    unsigned long long m = (unsigned long long)((yb & 0x7fffffu) | 0x800000u);
+    unsigned long long m2 = m * m;
+    int h2 = (int)(m2 >> 47);  // m^2 has 47 + h2 bits after its leading one's place 0
+    double t = __longlong_as_double(((long long)(2 * ey + h2 + 1023) << 52) |
+                                    (long long)((m2 << (6 - h2)) & 0xfffffffffffffull));
+    unsigned long long lo = m2 * m, hi = __umul64hi(m2, m);  // m^3 = hi 2^64 + lo, hi in [2^5, 2^8)
+    int L = 127 - __clzll((long long)hi);                      // leading bit of m^3: 69..71
+    int sh = L - 52;
+    unsigned long long sig = (hi << (64 - sh)) | (lo >> sh), rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    sig += (rem > half || (rem == half && (sig & 1ull))) ? 1ull : 0ull;
+    int ew = 3 * ey - 69 + L;
+    if (sig >> 53) {  // rounded up to the next power of two
+        sig >>= 1;
+        ew++;
+    }
+    double w0 = __longlong_as_double(((long long)(ew + 1023) << 52) | (long long)(sig & 0xfffffffffffffull));
     double er = fma(-s, t, 1.0);
-    double w0 = t * y0;
     // the e^2 terms (below 2^-40 of the result) in binary32 from e's high word: e rebiased
     // to binary32 by integer arithmetic, two binary32 products, and the product rebiased
     // back (exact); |e| < 2^-126 leaves e^2 far below binary64 rounding and drops it
