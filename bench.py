@@ -144,9 +144,6 @@ def algorithmic_flops(counts, tree_counts, p, variant):
 # M2L pair for the M2L stage (the pair-tensor kernel plus m2l_con_t_k), per particle pair for
 # p2p_k.  Traffic grows in proportion to these units (per-pair tensors and partials).
 NCU_TRAFFIC_PER_UNIT = {("m2l_con_t_k", "fp64"): 555.0, ("p2p_k", "fp64"): 5.23}
-# share of m2l_con_t_k<4> in the binary64 M2L stage (ncu launch list of the headline,
-# N = 2^20: 14.89 of 16.75 ms; the pair tensors take 1.52 ms)
-M2L_MAIN_SHARE_FP64 = 0.89
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
@@ -582,12 +579,10 @@ def run_gbfmm(args):
         return None
 
     stage_avg = {s: (statistics.mean(v) if v and v[0] >= 0 else None) for s, v in stage_ms.items()}
-    # the dominant kernel: the binary64 M2L stage on shared pair tensors is several kernels
-    # (pair tensors, the contraction, the reduction, source ids, the root-relative term), of
-    # which the contraction is M2L_MAIN_SHARE_FP64 of the stage time in the headline's ncu
-    # launch list; the other stages are one pair kernel each (plus a small reduction)
-    m2l_main = (stage_avg["m2l"] or 0) * (M2L_MAIN_SHARE_FP64 if args.precision == "fp64" and W["p"] <= 6 else 1.0)
-    dom = "m2l" if m2l_main >= (stage_avg["p2p"] or 0) else "p2p"
+    # the dominant pair stage by its event time (the binary64 M2L stage is the pair-tensor
+    # kernel, the contraction, the reduction, the source ids and the root-relative term; its
+    # algorithmic flops are rated against the whole stage's time)
+    dom = "m2l" if (stage_avg["m2l"] or 0) >= (stage_avg["p2p"] or 0) else "p2p"
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     nominal = fp32_peak_tflops(2070.0) if args.precision == "mixed" else fp64_peak_tflops(2070.0)
     peak = alu_peak or nominal
