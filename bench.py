@@ -143,7 +143,7 @@ def algorithmic_flops(counts, tree_counts, p, variant):
 # their DRAM counters at N = 2^19 (p = 4), scaled by the units of the timed launch: per mutual
 # M2L pair for the M2L stage (the pair-tensor kernel plus m2l_con_t_k), per particle pair for
 # p2p_k.  Traffic grows in proportion to these units (per-pair tensors and partials).
-NCU_TRAFFIC_PER_UNIT = {("m2l_con_t_k", "fp64"): 555.0, ("p2p_k", "fp64"): 5.23}
+NCU_TRAFFIC_PER_UNIT = {("m2l_con_t_k", "fp64"): 555.0, ("p2p_k", "fp64"): 5.24}
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
