@@ -1153,8 +1153,9 @@ struct NearVisitor {
             double dx = xa - pb.x, dy = ya - pb.y, dz = za - pb.z;
             double r2 = dx * dx + dy * dy + dz * dz;
             if (__double_as_longlong(r2) != 0ll) {
-                double ir = rsqrt(r2);
-                double mir3 = pb.m * (ir * ir * ir);
+                double w3, ir = 0.0;
+                rinv_f64<POT>(r2, w3, ir);  // r^-3 (and r^-1) as the list schedule's panel forms them
+                double mir3 = pb.m * w3;
                 ax = fma(-mir3, dx, ax);
                 ay = fma(-mir3, dy, ay);
                 az = fma(-mir3, dz, az);
@@ -1223,8 +1224,9 @@ struct BigVisitor {
             double dx = xa - pb.x, dy = ya - pb.y, dz = za - pb.z;
             double r2 = dx * dx + dy * dy + dz * dz;
             if (__double_as_longlong(r2) != 0ll) {
-                double ir = rsqrt(r2);
-                double mir3 = pb.m * (ir * ir * ir);
+                double w3, ir = 0.0;
+                rinv_f64<POT>(r2, w3, ir);  // r^-3 (and r^-1) as the list schedule's panel forms them
+                double mir3 = pb.m * w3;
                 ax = fma(-mir3, dx, ax);
                 ay = fma(-mir3, dy, ay);
                 az = fma(-mir3, dz, az);
