@@ -620,17 +620,26 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
             }
             const float4* rh = &sH[w][2 * base + i];  // slot i + kk for kk < W: row < 2 base + 2 W <= 64
             const float4* rl = &sL[w][2 * base + i];
+            // one turn of the ring; a warp whose lanes hold no second chunk (equal leaves,
+            // self pairs, the last pass of an odd chunk count) runs the one-chunk form
+            auto turn = [&](auto both) {
 #pragma unroll 4
-            for (int kk = 0; kk < W; kk++) {
-                float4 bh = rh[kk], bl = rl[kk];
-#pragma unroll
-                for (int r = 0; r < RING_CHUNKS; r++)
-                    if (mine[r]) ring_pair<POT>(ah[r], al[r], ma[r], bh, bl, acc[r], bx, by, bz, bp);
-                bx = __shfl_sync(FULL, bx, nxt);
-                by = __shfl_sync(FULL, by, nxt);
-                bz = __shfl_sync(FULL, bz, nxt);
-                if (POT) bp = __shfl_sync(FULL, bp, nxt);
-            }
+                for (int kk = 0; kk < W; kk++) {
+                    float4 bh = rh[kk], bl = rl[kk];
+                    if (mine[0]) ring_pair<POT>(ah[0], al[0], ma[0], bh, bl, acc[0], bx, by, bz, bp);
+                    if constexpr (decltype(both)::value)
+                        if (mine[1]) ring_pair<POT>(ah[1], al[1], ma[1], bh, bl, acc[1], bx, by, bz, bp);
+                    bx = __shfl_sync(FULL, bx, nxt);
+                    by = __shfl_sync(FULL, by, nxt);
+                    bz = __shfl_sync(FULL, bz, nxt);
+                    if (POT) bp = __shfl_sync(FULL, bp, nxt);
+                }
+            };
+            static_assert(RING_CHUNKS == 2, "the ring turn is written for two chunks");
+            if (__any_sync(FULL, mine[1]))
+                turn(std::true_type{});
+            else
+                turn(std::false_type{});
 #pragma unroll
             for (int r = 0; r < RING_CHUNKS; r++)
                 if (mine[r]) st_quad(part + oL + (ch + r) * W + i, acc[r].x, acc[r].y, acc[r].z, POT ? acc[r].w : 0.f);
