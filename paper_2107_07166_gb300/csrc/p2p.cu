@@ -93,10 +93,11 @@ __device__ __forceinline__ double sq_to_f64(float v) {
 //   s^(-1/2) = y0 (1 - e)^(-1/2)   = y0 (1 + 1/2 e + 3/8 e^2 + ...):
 // the binomial series cut after e^2 leave remainders below 2^-58, under binary64's own
 // rounding.  The e^2 terms are below 2^-40 of the result and need only ~12 correct bits,
-// so they are formed in binary32 (CPU emulation on 500 000 s with a seed perturbed by up
-// to 4 ulp: the same 1.96-ulp maximum error as the all-binary64 form).  t and y0^3 come
+// so they are formed in binary32 (host emulation with a seed perturbed by a few ulp: the
+// same 1.96-ulp maximum error as the all-binary64 form).  t and y0^3 come
 // from y0's 24-bit integer significand by integer products, exactly the values of the
-// binary64 products y0 y0 and t y0 (checked on 300 000 significands and exponents), which
+// binary64 products y0 y0 and t y0 (host check on random significands and on every kind
+// of exact tie: tests/test_rinv_arith.py), which
 // leaves e = 1 - s t and the two fused multiply-adds of the series to the binary64 unit.
 // Exponents far from 0 (|e| > 600: subnormal, huge or non-finite s) take the library path.
 template <bool IR>
