@@ -62,7 +62,8 @@ enum {
 /* arithmetic of the pair kernels (M2L and P2P); tree, moments, translations (M2M, L2L),
  * L2P, accumulators and diagnostics are binary64 in every mode */
 enum {
-    FMM_FP64 = 0,  /* M2L and P2P in IEEE binary64 */
+    FMM_FP64 = 0,  /* M2L and P2P in IEEE binary64; the P2P's r^-3 is refined in binary64 from a
+                      binary32 seed (within 2 ulp, as a library reciprocal square root and cube) */
     FMM_MIXED = 1, /* M2L and P2P in binary32 (separations formed in double-float first),
                       per-pair and per-chunk partials summed in binary64 */
     FMM_DF64 = 2   /* M2L and P2P in double-float arithmetic on the binary32 units (two binary32
