@@ -94,12 +94,12 @@ __device__ __forceinline__ double sq_to_f64(float v) {
 // the binomial series cut after e^2 leave remainders below 2^-58, under binary64's own
 // rounding.  The e^2 terms are below 2^-40 of the result and need only ~12 correct bits,
 // so they are formed in binary32 (host emulation with a seed perturbed by a few ulp: the
-// same 1.96-ulp maximum error as the all-binary64 form).  t and y0^3 come
-// from y0's 24-bit integer significand by integer products, exactly the values of the
-// binary64 products y0 y0 and t y0 (host check on random significands and on every kind
-// of exact tie: tests/test_rinv_arith.py), which
-// leaves e = 1 - s t and the two fused multiply-adds of the series to the binary64 unit.
-// Exponents far from 0 (|e| > 600: subnormal, huge or non-finite s) take the library path.
+// same 1.96-ulp maximum error as the all-binary64 form).  t and y0^3 come from y0's 24-bit
+// integer significand by integer products, exactly the values of the binary64 products
+// y0 y0 and t y0 (host check on random significands and on exact ties:
+// tests/test_rinv_arith.py).  That leaves e = 1 - s t and the two fused multiply-adds of
+// the series to the binary64 unit.  Exponents far from 0 (|e| > 600: subnormal, huge or
+// non-finite s) take the library path.
 template <bool IR>
 __device__ __forceinline__ void rinv_f64(double s, double& w3, double& ir) {
     long long b = __double_as_longlong(s);
@@ -120,7 +120,7 @@ __device__ __forceinline__ void rinv_f64(double s, double& w3, double& ir) {
     // integer significand: m^2 < 2^48 is exact, m^3 < 2^72 is rounded to 53 bits, ties to even
     unsigned long long m = (unsigned long long)((yb & 0x7fffffu) | 0x800000u);
     unsigned long long m2 = m * m;
-    int h2 = (int)(m2 >> 47);  // m^2 has 47 + h2 bits after its leading one's place 0
+    int h2 = (int)(m2 >> 47);  // m^2 in [2^46, 2^48): its leading bit is 46 + h2
     double t = __longlong_as_double(((long long)(2 * ey + h2 + 1023) << 52) |
                                     (long long)((m2 << (6 - h2)) & 0xfffffffffffffull));
     unsigned long long lo = m2 * m, hi = __umul64hi(m2, m);  // m^3 = hi 2^64 + lo, hi in [2^5, 2^8)
