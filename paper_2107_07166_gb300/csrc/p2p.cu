@@ -578,8 +578,8 @@ __global__ void __launch_bounds__(PB, 8) p2p_ring_k(const RingTab* __restrict__ 
         int i = live ? lane - sg * W : 0, base = live ? sg * W : 0;
         int64_t li = (q - tw[W]) * per + sg;
         bool ok = live && li < tc[W];
-        // one descriptor load, then the ring particle and the first two lane particles
-        // together: two memory latencies before the ring starts
+        // one descriptor load, then the particles (the chain list -> pair -> leaf tables
+        // is resolved once per evaluation by p2p_ring_desc_k)
         RingDesc d{};
         if (ok) d = load_desc(desc + ts[W] + li);
         bool self = d.self != 0;
